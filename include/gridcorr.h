@@ -1,0 +1,115 @@
+/*
+ * gridcorr -- C ABI of a GB300 (sm_103a) implementation of the self-contained
+ * O(N log N) correlator system for redundant arrays on a regular grid
+ * (Gorthi, Parsons & Dillon 2020, "Calibration schemes with O(N log N)
+ * scaling for large-N radio interferometers built on a regular grid").
+ *
+ * The system (paper Fig. 1b) has three data-parallel parts:
+ *   correlate : gains + antenna voltages -> V^unique  (FFT-correlator)
+ *   reduce    : voltages + selection      -> V^reduced (calibrator step (a))
+ *   calibrate : V^reduced + redundancy    -> gains      (calibrator step (b))
+ *
+ * Conventions used by every entry point:
+ *   - antennas sit on an L x L unit grid; antenna i is at r_i = (x, y) with
+ *     i = y*L + x (row major);
+ *   - complex numbers are interleaved (re, im) float32 ("c64");
+ *   - a 4+4-bit complex ("i4c") is one byte: high nibble = Re, low nibble =
+ *     Im, both two's complement in [-8, 7] (the quantiser emits [-7, 7]);
+ *   - voltages are [C][T][N] (channel, time sample, antenna), contiguous;
+ *   - the visibility of the ordered pair (i, j) is <v_i v_j^*> and belongs
+ *     to the baseline-type d = r_i - r_j (paper Eq. redcal, d = r_0 - r_1);
+ *   - every data buffer is caller-owned DEVICE memory unless a comment says
+ *     HOST; the library never frees caller memory;
+ *   - calls are asynchronous on the CUDA stream passed as `stream`
+ *     (a cudaStream_t; NULL = the legacy default stream).  The returned
+ *     status covers argument validation and launch errors; errors detected
+ *     by the device (a bounded wait that ran out) are reported by
+ *     gc_device_status().
+ *   - no call allocates device memory except where stated (the context's
+ *     scratch workspace grows on demand and is released by gc_destroy).
+ */
+#ifndef GRIDCORR_H
+#define GRIDCORR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GC_API __attribute__((visibility("default")))
+#else
+#define GC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gc_status {
+    GC_OK = 0,
+    GC_EINVAL = 1,        /* bad argument (null pointer, size, alignment) */
+    GC_ENOMEM = 2,        /* device workspace allocation failed */
+    GC_ECUDA = 3,         /* a CUDA runtime / driver call failed */
+    GC_ENOCONV = 4,       /* a solver hit its iteration cap */
+    GC_ETIMEOUT = 5,      /* a device-side bounded wait ran out */
+    GC_EDEGEN = 6,        /* selection does not meet the degeneracy criterion */
+    GC_EUNSUPPORTED = 7   /* size / format combination not built */
+} gc_status;
+
+typedef enum gc_vfmt {
+    GC_C64 = 0,           /* complex64: 8 bytes per antenna-sample */
+    GC_I4C = 1            /* 4+4-bit complex: 1 byte per antenna-sample */
+} gc_vfmt;
+
+typedef struct gc_ctx gc_ctx;
+
+/* Create a context bound to CUDA device `device`.  Allocates a 4-byte device
+ * status word (cudaMalloc).  *out is set to NULL on failure. */
+GC_API gc_status gc_create(gc_ctx **out, int device);
+
+/* Release the context and its workspace.  Safe on NULL. */
+GC_API void gc_destroy(gc_ctx *ctx);
+
+/* Human-readable description of the last error on this context ("" if none).
+ * The pointer stays valid until the next call on the context. */
+GC_API const char *gc_last_error(const gc_ctx *ctx);
+
+/* Synchronise `stream`, read and clear the device-side error word.  Returns
+ * GC_ETIMEOUT if a kernel gave up a bounded wait since the last check. */
+GC_API gc_status gc_device_status(gc_ctx *ctx, void *stream);
+
+/* Smallest FFT side M for an L x L grid: the smallest power of two >= 2L - 1,
+ * so that the circular correlation of the zero-padded grid equals the
+ * linear one (paper Sec. 1, convolution theorem).  gc_correlate uses
+ * max(16, gc_fft_size(L)).  0 if L is out of range. */
+GC_API int gc_fft_size(int L);
+
+/*
+ * FFT-correlator (paper Fig. 1b yellow box; Sec. 1; Eq. modelvis).
+ *
+ * For every channel c: calibrate the voltages with the gains (w_i = v_i /
+ * g_i), take the zero-padded M x M spatial FFT of w at every time sample,
+ * integrate |X(k)|^2 over the T samples, inverse-FFT, and normalise each lag
+ * by T * N_d, giving the redundant average of Eq. modelvis:
+ *
+ *   V^unique_c(d) = 1/(T N_d) sum_t sum_{r_i - r_j = d} w_i(t) w_j(t)^*,
+ *   N_d = (L - |dx|)(L - |dy|).
+ *
+ *   volt     [C][T][L*L] c64 (8-byte aligned) or i4c (device)
+ *   gains    [C][L*L]    c64 (device); a zero gain gives inf/NaN output
+ *   vunique  [C][2L-1][2L-1] c64 (device), index [dy + L - 1][dx + L - 1]
+ *   1 <= L <= 64, C >= 1, T >= 1.
+ * Voltages are staged by TMA when the buffer is 16-byte aligned and a grid
+ * row is a multiple of 16 bytes (c64: L even; i4c: L % 16 == 0), by plain
+ * loads otherwise.
+ *
+ * Uses the context's scratch workspace for per-time-chunk power spectra
+ * (C * chunks * M^2 * 4 bytes; grown with cudaMalloc on first need, which
+ * synchronises the device).  Two kernels are enqueued on `stream`.
+ */
+GC_API gc_status gc_correlate(gc_ctx *ctx, const void *volt, int vfmt, int L, int C, int T,
+                       const float *gains, float *vunique, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRIDCORR_H */

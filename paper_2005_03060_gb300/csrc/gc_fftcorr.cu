@@ -1,0 +1,569 @@
+// FFT-correlator: calibrate voltages, zero-padded 2-D spatial FFT per time
+// sample, |X(k)|^2 integrated over time, inverse FFT to the unique-baseline
+// visibilities (paper Fig. 1b yellow box, Sec. 1 convolution theorem,
+// Eq. modelvis).
+//
+// Kernel 1 (fftcorr_accumulate) streams voltages through shared memory with
+// TMA and keeps the power spectrum of one time chunk in registers.  One
+// work item = (channel c, k_x residue class q mod R, time chunk).  Per time
+// sample:
+//   row pass    : for every grid row y < L and residue s, fold the row with
+//                 the twiddles of k = q + R s and run an F1-point FFT in
+//                 registers -> X1[y][k_x] for k_x = k + R S1 m;
+//   column pass : for every owned k_x and residue s2 of k_y, fold the column
+//                 and run an F2-point FFT -> X(k_y, k_x); P += |X|^2.
+// The zero padding to M x M is never materialised: the first FFT stages of
+// both passes see only the L non-zero inputs (folds over L <= M/2 inputs).
+//
+// Kernel 2 (fftcorr_finalize) sums the chunk spectra (FP64), inverse-DFTs
+// the (2L-1)^2 lags that exist, and divides by T N_d.
+#include <algorithm>
+#include <cstdio>
+
+#include "gc_internal.h"
+
+namespace {
+
+// ----------------------------------------------------------------- twiddles
+// omega_256^e = exp(-2 pi i e / 256), built at compile time from a Taylor
+// series (double) and rounded to float; exact at multiples of pi/4.
+struct cf {
+    float x, y;
+};
+struct Tw256 {
+    cf v[256];
+};
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr double cx_sin(double x) {
+    double t = x, s = x;
+    for (int n = 1; n < 40; ++n) {
+        t *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+        s += t;
+    }
+    return s;
+}
+constexpr double cx_cos(double x) {
+    double t = 1.0, s = 1.0;
+    for (int n = 1; n < 40; ++n) {
+        t *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+        s += t;
+    }
+    return s;
+}
+constexpr Tw256 make_tw256() {
+    Tw256 t{};
+    const double h = 0.70710678118654752440084436210484903928;
+    for (int e = 0; e < 256; ++e) {
+        double c = 0.0, s = 0.0;
+        if (e % 64 == 0) {
+            const int q = e / 64;
+            c = q == 0 ? 1.0 : (q == 2 ? -1.0 : 0.0);
+            s = q == 1 ? 1.0 : (q == 3 ? -1.0 : 0.0);
+        } else if (e % 32 == 0) {
+            const int q = e / 32;  // 1, 3, 5, 7
+            c = (q == 1 || q == 7) ? h : -h;
+            s = (q == 1 || q == 3) ? h : -h;
+        } else {
+            double th = 2.0 * kPi * e / 256.0;
+            if (th > kPi) th -= 2.0 * kPi;
+            c = cx_cos(th);
+            s = cx_sin(th);
+        }
+        t.v[e].x = (float)c;
+        t.v[e].y = (float)(-s);
+    }
+    return t;
+}
+__constant__ Tw256 c_tw = make_tw256();
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+    return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+}
+__device__ __forceinline__ float2 cfma(float2 acc, float2 a, float2 w) {
+    acc.x = fmaf(a.x, w.x, fmaf(-a.y, w.y, acc.x));
+    acc.y = fmaf(a.x, w.y, fmaf(a.y, w.x, acc.y));
+    return acc;
+}
+
+// multiply by omega_256^e; e is a compile-time constant after unrolling
+__device__ __forceinline__ float2 tw_apply(float2 d, int e) {
+    const float h = 0.70710678118654752f;
+    if (e == 0) return d;
+    if (e == 64) return make_float2(d.y, -d.x);                     // * (-i)
+    if (e == 32) return make_float2((d.x + d.y) * h, (d.y - d.x) * h);   // * (1-i)/sqrt2
+    if (e == 96) return make_float2((d.y - d.x) * h, -(d.x + d.y) * h);  // * (-1-i)/sqrt2
+    const cf w = c_tw.v[e];
+    return cmul(d, make_float2(w.x, w.y));
+}
+
+// In-register radix-2 decimation-in-frequency FFT of F points (forward,
+// omega = exp(-2 pi i / F)); output in bit-reversed order: a[i] = X[rev(i)].
+template <int F>
+__device__ __forceinline__ void fft_reg(float2 (&a)[F]) {
+#pragma unroll
+    for (int len = F; len >= 2; len >>= 1) {
+#pragma unroll
+        for (int blk = 0; blk < F; blk += len) {
+#pragma unroll
+            for (int j = 0; j < len / 2; ++j) {
+                const float2 u = a[blk + j], v = a[blk + j + len / 2];
+                a[blk + j] = cadd(u, v);
+                a[blk + j + len / 2] = tw_apply(make_float2(u.x - v.x, u.y - v.y), j * (256 / len));
+            }
+        }
+    }
+}
+
+template <int F>
+__host__ __device__ constexpr int bitrev(int i) {
+    int r = 0;
+    for (int b = 1; b < F; b <<= 1) {
+        r = (r << 1) | (i & 1);
+        i >>= 1;
+    }
+    return r;
+}
+
+// ----------------------------------------------------------------- config
+template <int M_, int R_, int F1_, int F2_, int NT_, int G_, int VF_>
+struct Cfg {
+    static constexpr int M = M_, R = R_, F1 = F1_, F2 = F2_, NT = NT_, G = G_, VF = VF_;
+    static constexpr int LMAX = M / 2;
+    static constexpr int MX = M / R;                    // k_x values per work item
+    static constexpr int S1 = MX / F1;                  // row residues
+    static constexpr int J1 = (LMAX + F1 - 1) / F1;     // row folds
+    static constexpr int S2 = M / F2;                   // column residues
+    static constexpr int J2 = (LMAX + F2 - 1) / F2;     // column folds
+    static constexpr int NCOL = MX * S2;                // column items per group
+    static constexpr int NTHREADS = G * NCOL;
+    static constexpr int GNT = G * NT;                  // samples per iteration
+    static constexpr int ESZ = VF == GC_C64 ? 8 : 1;    // bytes per antenna-sample
+    // padded stage row (bytes): the smallest odd number of 16-byte units
+    // holding LMAX elements, so rows read by consecutive lanes hit distinct banks
+    static constexpr int ROWU = (LMAX * ESZ + 15) / 16;
+    static constexpr int ROWB = 16 * (ROWU % 2 == 1 ? ROWU : ROWU + 1);
+    static constexpr int ROWE = ROWB / ESZ;             // elements per stage row
+    static constexpr int CROW = LMAX + 2;               // coefficient row (float2)
+    static constexpr int IROW = MX + 1;                 // intermediate row (float2)
+    static constexpr int STAGE_BYTES = GNT * LMAX * ROWB;
+    static constexpr int NSTAGE = 2;
+    // shared memory layout (bytes)
+    static constexpr int OFF_BAR = 0;
+    static constexpr int OFF_TW = 128;
+    static constexpr int OFF_COEF = OFF_TW + ((M * 8 + 127) / 128) * 128;
+    static constexpr int OFF_STAGE = OFF_COEF + ((LMAX * CROW * 8 + 127) / 128) * 128;
+    static constexpr int OFF_INTER = OFF_STAGE + NSTAGE * ((STAGE_BYTES + 127) / 128) * 128;
+    static constexpr int SMEM = OFF_INTER + GNT * LMAX * IROW * 8;
+    static_assert(MX % F1 == 0 && M % F2 == 0, "bad FFT split");
+    static_assert(ROWB % 16 == 0 && (ROWB / 16) % 2 == 1, "stage row must be an odd number of 16B");
+    static_assert(F1 % 2 == 0 && (VF == GC_C64 || F1 % 16 == 0 || LMAX <= 16), "row reads");
+};
+
+struct Params {
+    const void *volt;        // [C][T][L*L]
+    const float2 *gains;     // [C][L*L]
+    float *ppart;            // [C][n_chunks*G][M][M]
+    unsigned int *status;
+    int L, C, T;
+    int chunk_len;           // multiple of G*NT
+    int n_chunks;
+    int n_items;             // C * R * n_chunks
+};
+
+// Copy the G*NT samples starting at t into stage (plain-load fallback for
+// strides that TMA cannot describe).  Rows/columns beyond L and samples
+// beyond T are zero.
+template <class K>
+__device__ void stage_plain(const Params &p, unsigned char *stage, int c, int t) {
+    const int L = p.L, N = L * L;
+    const int total = K::GNT * K::LMAX * K::ROWE;
+    for (int idx = threadIdx.x; idx < total; idx += K::NTHREADS) {
+        const int x = idx % K::ROWE;
+        const int rest = idx / K::ROWE;
+        const int y = rest % K::LMAX;
+        const int u = rest / K::LMAX;
+        const int tt = t + u;
+        const bool ok = x < L && y < L && tt < p.T;
+        const size_t src = ((size_t)c * p.T + (ok ? tt : 0)) * N + (ok ? y * L + x : 0);
+        if (K::VF == GC_C64) {
+            float2 v = make_float2(0.f, 0.f);
+            if (ok) v = reinterpret_cast<const float2 *>(p.volt)[src];
+            reinterpret_cast<float2 *>(stage)[(u * K::LMAX + y) * K::ROWE + x] = v;
+        } else {
+            unsigned char v = 0;
+            if (ok) v = reinterpret_cast<const unsigned char *>(p.volt)[src];
+            stage[(u * K::LMAX + y) * K::ROWB + x] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ float2 i4c_to_f2(unsigned int byte) {
+    const int b = (int)(signed char)(byte & 0xFFu);
+    return make_float2((float)(b >> 4), (float)((int)(signed char)(byte << 4) >> 4));
+}
+
+template <class K, bool kTMA>
+__global__ void __launch_bounds__(K::NTHREADS)
+fftcorr_accumulate(const __grid_constant__ CUtensorMap tmap, const Params p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + K::OFF_BAR);
+    float2 *tws = reinterpret_cast<float2 *>(smem + K::OFF_TW);
+    float2 *coef = reinterpret_cast<float2 *>(smem + K::OFF_COEF);
+    unsigned char *stage0 = smem + K::OFF_STAGE;
+    float2 *inter = reinterpret_cast<float2 *>(smem + K::OFF_INTER);
+    __shared__ int s_err;
+
+    const int tid = threadIdx.x;
+    const int L = p.L;
+    constexpr int kStageStride = ((K::STAGE_BYTES + 127) / 128) * 128;
+
+    // one-time set-up: twiddles omega_M^e, zero pads and unused rows
+    for (int e = tid; e < K::M; e += K::NTHREADS) {
+        const cf w = c_tw.v[e * (256 / K::M)];
+        tws[e] = make_float2(w.x, w.y);
+    }
+    for (int i = tid; i < K::GNT * K::LMAX * K::IROW; i += K::NTHREADS) inter[i] = make_float2(0.f, 0.f);
+    if (tid == 0) {
+        s_err = 0;
+        if (kTMA) {
+            gc_mbar_init(&bars[0], 1);
+            gc_mbar_init(&bars[1], 1);
+            gc_fence_mbar_init();
+        }
+    }
+    __syncthreads();
+
+    // column item owned by this thread (fixed for the whole kernel)
+    const int g = tid / K::NCOL;
+    const int col = tid % K::NCOL;
+    const int kxl = col % K::MX;
+    const int s2 = col / K::MX;
+    const int n_it = p.chunk_len / K::GNT;
+    const int rows_per_it = K::GNT * L * K::S1;
+    uint32_t ld_count = 0, use_count = 0;   // TMA loads issued / consumed (phase tracking)
+
+    for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+        const int q = item % K::R;
+        const int chunk = (item / K::R) % p.n_chunks;
+        const int c = item / (K::R * p.n_chunks);
+        const int t0 = chunk * p.chunk_len;
+
+        // calibration coefficients 1/g_i = conj(g)/|g|^2 in the padded layout
+        for (int i = tid; i < K::LMAX * K::CROW; i += K::NTHREADS) {
+            const int x = i % K::CROW, y = i / K::CROW;
+            float2 cc = make_float2(0.f, 0.f);
+            if (x < L && y < L) {
+                const float2 gg = p.gains[(size_t)c * L * L + y * L + x];
+                const float d = gg.x * gg.x + gg.y * gg.y;
+                cc = make_float2(gg.x / d, -gg.y / d);
+            }
+            coef[i] = cc;
+        }
+        if (kTMA && tid == 0) {
+            for (int k = 0; k < 2 && k < n_it; ++k) {
+                unsigned char *dst = stage0 + (ld_count & 1u) * kStageStride;
+                gc_mbar_expect_tx(&bars[ld_count & 1u], K::STAGE_BYTES);
+                gc_tma_load_4d(dst, &tmap, &bars[ld_count & 1u], 0, 0, t0 + k * K::GNT, c);
+                ++ld_count;
+            }
+        }
+        __syncthreads();
+
+        float acc[K::F2];
+#pragma unroll
+        for (int i = 0; i < K::F2; ++i) acc[i] = 0.f;
+
+        for (int it = 0; it < n_it; ++it) {
+            const int t = t0 + it * K::GNT;
+            unsigned char *stage;
+            if (kTMA) {
+                const uint32_t buf = use_count & 1u;
+                stage = stage0 + buf * kStageStride;
+                if (!gc_mbar_wait(&bars[buf], (use_count >> 1) & 1u, GC_WAIT_LIMIT_NS)) {
+                    atomicOr(p.status, GC_DEV_TIMEOUT_FFT);
+                    s_err = 1;
+                } else {
+                    ++use_count;
+                }
+                __syncthreads();
+                if (s_err) break;
+            } else {
+                stage = stage0;
+                stage_plain<K>(p, stage, c, t);
+                __syncthreads();
+            }
+
+            // ---------------- row pass
+            for (int r = tid; r < rows_per_it; r += K::NTHREADS) {
+                const int y = r % L;
+                const int rest = r / L;
+                const int u = rest % K::GNT;
+                const int s = rest / K::GNT;
+                const int k = q + K::R * s;
+                float2 b[K::F1];
+#pragma unroll
+                for (int i = 0; i < K::F1; ++i) b[i] = make_float2(0.f, 0.f);
+                const float2 *crow = coef + y * K::CROW;
+                const unsigned char *srow = stage + (u * K::LMAX + y) * K::ROWB;
+#pragma unroll
+                for (int j = 0; j < K::J1; ++j) {
+                    if (K::VF == GC_C64) {
+#pragma unroll
+                        for (int xp = 0; xp < K::F1; xp += 2) {
+                            const int x = xp + K::F1 * j;
+                            if (x < K::LMAX) {
+                                const float4 vv = *reinterpret_cast<const float4 *>(srow + x * 8);
+                                const float4 cc = *reinterpret_cast<const float4 *>(crow + x);
+                                const float2 w0 = cmul(make_float2(vv.x, vv.y), make_float2(cc.x, cc.y));
+                                const float2 w1 = cmul(make_float2(vv.z, vv.w), make_float2(cc.z, cc.w));
+                                b[xp] = cfma(b[xp], w0, tws[(k * x) & (K::M - 1)]);
+                                b[xp + 1] = cfma(b[xp + 1], w1, tws[(k * (x + 1)) & (K::M - 1)]);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int xp = 0; xp < K::F1; xp += 16) {
+                            const int x0 = xp + K::F1 * j;
+                            if (x0 < K::LMAX) {
+                                const uint4 raw = *reinterpret_cast<const uint4 *>(srow + x0);
+                                const unsigned int words[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+                                for (int e = 0; e < 16 && xp + e < K::F1; ++e) {
+                                    const int x = x0 + e;
+                                    if (x < K::LMAX) {
+                                        const float2 v = i4c_to_f2(words[e >> 2] >> (8 * (e & 3)));
+                                        const float2 w = cmul(v, crow[x]);
+                                        b[xp + e] = cfma(b[xp + e], w, tws[(k * x) & (K::M - 1)]);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+                fft_reg<K::F1>(b);
+                float2 *irow = inter + (u * K::LMAX + y) * K::IROW;
+#pragma unroll
+                for (int i = 0; i < K::F1; ++i) irow[s + K::S1 * bitrev<K::F1>(i)] = b[i];
+            }
+            __syncthreads();
+
+            // refill the consumed stage with the samples two iterations ahead
+            if (kTMA && tid == 0 && it + 2 < n_it) {
+                gc_fence_proxy_async();
+                unsigned char *dst = stage0 + (ld_count & 1u) * kStageStride;
+                gc_mbar_expect_tx(&bars[ld_count & 1u], K::STAGE_BYTES);
+                gc_tma_load_4d(dst, &tmap, &bars[ld_count & 1u], 0, 0, t + 2 * K::GNT, c);
+                ++ld_count;
+            }
+
+            // ---------------- column pass + power
+#pragma unroll 1
+            for (int u = 0; u < K::NT; ++u) {
+                const float2 *icol = inter + ((g * K::NT + u) * K::LMAX) * K::IROW + kxl;
+                float2 b[K::F2];
+#pragma unroll
+                for (int i = 0; i < K::F2; ++i) b[i] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < K::J2; ++j) {
+#pragma unroll
+                    for (int yp = 0; yp < K::F2; ++yp) {
+                        const int y = yp + K::F2 * j;
+                        if (y < K::LMAX) b[yp] = cfma(b[yp], icol[y * K::IROW], tws[(s2 * y) & (K::M - 1)]);
+                    }
+                }
+                fft_reg<K::F2>(b);
+#pragma unroll
+                for (int i = 0; i < K::F2; ++i) acc[i] = fmaf(b[i].x, b[i].x, fmaf(b[i].y, b[i].y, acc[i]));
+            }
+            __syncthreads();
+        }
+        if (s_err) break;
+
+        // chunk spectrum of this group: P[k_y][k_x]
+        float *out = p.ppart + ((size_t)c * p.n_chunks * K::G + (size_t)chunk * K::G + g) * K::M * K::M;
+        const int kx = q + K::R * kxl;
+#pragma unroll
+        for (int i = 0; i < K::F2; ++i) out[(s2 + K::S2 * bitrev<K::F2>(i)) * K::M + kx] = acc[i];
+    }
+
+    if (kTMA && s_err && tid == 0) {
+        // let copies still in flight land before the CTA exits (bounded)
+        while (use_count < ld_count) {
+            gc_mbar_wait(&bars[use_count & 1u], (use_count >> 1) & 1u, GC_WAIT_LIMIT_NS / 10);
+            ++use_count;
+        }
+    }
+}
+
+// ----------------------------------------------------------------- finalize
+template <int M>
+__global__ void __launch_bounds__(256)
+fftcorr_finalize(const float *__restrict__ ppart, int n_parts, float2 *__restrict__ vunique, int L, int T) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *P = reinterpret_cast<float *>(smem);                 // [M][M]
+    float2 *Q = reinterpret_cast<float2 *>(smem + M * M * 4);   // [M][W]
+    float2 *tws = Q + M * (2 * L - 1);                          // [M]
+    const int c = blockIdx.x, W = 2 * L - 1;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) {
+        const cf w = c_tw.v[e * (256 / M)];
+        tws[e] = make_float2(w.x, w.y);
+    }
+    const float *src = ppart + (size_t)c * n_parts * M * M;
+    for (int k = threadIdx.x; k < M * M; k += blockDim.x) {
+        double s = 0.0;
+        for (int pp = 0; pp < n_parts; ++pp) s += (double)src[(size_t)pp * M * M + k];
+        P[k] = (float)s;
+    }
+    __syncthreads();
+    // Q[ky][dx] = sum_kx P[ky][kx] exp(+2 pi i kx dx / M)
+    for (int idx = threadIdx.x; idx < M * W; idx += blockDim.x) {
+        const int ky = idx / W, dx = idx % W - (L - 1);
+        float re = 0.f, im = 0.f;
+        for (int kx = 0; kx < M; ++kx) {
+            const float2 w = tws[(kx * dx) & (M - 1)];   // conj gives the + sign
+            const float pv = P[ky * M + kx];
+            re = fmaf(pv, w.x, re);
+            im = fmaf(-pv, w.y, im);
+        }
+        Q[ky * W + (dx + L - 1)] = make_float2(re, im);
+    }
+    __syncthreads();
+    // R[dy][dx] = (1/M^2) sum_ky Q[ky][dx] exp(+2 pi i ky dy / M); V = R / (T N_d)
+    for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+        const int dyi = idx / W, dxi = idx % W;
+        const int dy = dyi - (L - 1), dx = dxi - (L - 1);
+        float re = 0.f, im = 0.f;
+        for (int ky = 0; ky < M; ++ky) {
+            const float2 w = tws[(ky * dy) & (M - 1)];
+            const float2 qv = Q[ky * W + dxi];
+            // qv * conj(w)
+            re = fmaf(qv.x, w.x, fmaf(qv.y, w.y, re));
+            im = fmaf(qv.y, w.x, fmaf(-qv.x, w.y, im));
+        }
+        const int nd = (L - (dx < 0 ? -dx : dx)) * (L - (dy < 0 ? -dy : dy));
+        const float s = (float)(1.0 / ((double)M * M * (double)T * nd));
+        vunique[(size_t)c * W * W + idx] = make_float2(re * s, im * s);
+    }
+}
+
+// ----------------------------------------------------------------- host side
+template <class K>
+struct Launcher {
+    static gc_status run(gc_ctx *ctx, const void *volt, int L, int C, int T, const float *gains,
+                         float *vunique, cudaStream_t stream) {
+        const int N = L * L;
+        const bool tma = gc_aligned(volt, 16) && ((size_t)L * K::ESZ) % 16 == 0;
+        auto kern = tma ? fftcorr_accumulate<K, true> : fftcorr_accumulate<K, false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+        if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(fftcorr_accumulate)");
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, K::NTHREADS, K::SMEM);
+        if (e != cudaSuccess || occ < 1) return gc_cuda_fail(ctx, e, "occupancy(fftcorr_accumulate)");
+        const int slots = occ * ctx->sm_count;
+
+        // time chunking: chunks of <= 512 samples, chosen so the work items
+        // fill whole waves of the resident CTAs
+        const int step = K::GNT;
+        int best_n = 1, best_len = ((T + step - 1) / step) * step;
+        double best_eff = -1.0;
+        const int n_min = std::max(1, (T + 511) / 512);
+        for (int n = n_min; n <= n_min + 64; ++n) {
+            const int len = ((T + n - 1) / n + step - 1) / step * step;
+            const int nn = (T + len - 1) / len;
+            const long items = (long)C * K::R * nn;
+            const long waves = (items + slots - 1) / slots;
+            const double eff = (double)C * K::R * T / ((double)waves * slots * len);
+            if (eff > best_eff + 1e-9) {
+                best_eff = eff;
+                best_n = nn;
+                best_len = len;
+            }
+        }
+        Params p;
+        p.volt = volt;
+        p.gains = reinterpret_cast<const float2 *>(gains);
+        p.status = ctx->status_dev;
+        p.L = L;
+        p.C = C;
+        p.T = T;
+        p.chunk_len = best_len;
+        p.n_chunks = best_n;
+        p.n_items = C * K::R * best_n;
+        const size_t need = (size_t)C * best_n * K::G * K::M * K::M * sizeof(float);
+        gc_status st = gc_scratch_reserve(ctx, need);
+        if (st != GC_OK) return st;
+        p.ppart = reinterpret_cast<float *>(ctx->scratch);
+
+        CUtensorMap tmap;
+        memset(&tmap, 0, sizeof tmap);
+        if (tma) {
+            const uint64_t dims[4] = {(uint64_t)L, (uint64_t)L, (uint64_t)T, (uint64_t)C};
+            const uint64_t strides[3] = {(uint64_t)L * K::ESZ, (uint64_t)N * K::ESZ,
+                                         (uint64_t)T * N * K::ESZ};
+            const uint32_t box[4] = {(uint32_t)K::ROWE, (uint32_t)K::LMAX, (uint32_t)K::GNT, 1u};
+            st = gc_encode_tiled(ctx, &tmap,
+                                 K::VF == GC_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                                 4, const_cast<void *>(volt), dims, strides, box);
+            if (st != GC_OK) return st;
+        }
+        const int grid = (int)std::min<long>(p.n_items, slots);
+        kern<<<grid, K::NTHREADS, K::SMEM, stream>>>(tmap, p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch fftcorr_accumulate");
+
+        const int W = 2 * L - 1;
+        const size_t fsmem = (size_t)K::M * K::M * 4 + (size_t)K::M * W * 8 + K::M * 8;
+        auto fin = fftcorr_finalize<K::M>;
+        e = cudaFuncSetAttribute(fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+        if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(fftcorr_finalize)");
+        fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n * K::G, reinterpret_cast<float2 *>(vunique), L, T);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch fftcorr_finalize");
+        return GC_OK;
+    }
+};
+
+// configurations per FFT side (see the design notes for the smem budget)
+using CfgC16 = Cfg<16, 1, 16, 16, 2, 8, GC_C64>;
+using CfgC32 = Cfg<32, 1, 32, 32, 2, 4, GC_C64>;
+using CfgC64 = Cfg<64, 1, 32, 32, 2, 1, GC_C64>;
+using CfgC128 = Cfg<128, 4, 32, 32, 1, 1, GC_C64>;
+using CfgI16 = Cfg<16, 1, 16, 16, 2, 8, GC_I4C>;
+using CfgI32 = Cfg<32, 1, 32, 32, 2, 4, GC_I4C>;
+using CfgI64 = Cfg<64, 1, 32, 32, 2, 1, GC_I4C>;
+using CfgI128 = Cfg<128, 4, 32, 32, 2, 1, GC_I4C>;
+
+}  // namespace
+
+extern "C" gc_status gc_correlate(gc_ctx *ctx, const void *volt, int vfmt, int L, int C, int T,
+                                  const float *gains, float *vunique, void *stream) {
+    if (!ctx) return GC_EINVAL;
+    ctx->last_error.clear();
+    if (!volt || !gains || !vunique) return gc_fail(ctx, GC_EINVAL, "gc_correlate: null buffer");
+    if (L < 1 || L > 64 || C < 1 || T < 1)
+        return gc_fail(ctx, GC_EINVAL, "gc_correlate: need 1 <= L <= 64, C >= 1, T >= 1");
+    if (vfmt != GC_C64 && vfmt != GC_I4C) return gc_fail(ctx, GC_EINVAL, "gc_correlate: unknown voltage format");
+    if (!gc_aligned(gains, 8) || !gc_aligned(vunique, 8) || (vfmt == GC_C64 && !gc_aligned(volt, 8)))
+        return gc_fail(ctx, GC_EINVAL, "gc_correlate: misaligned buffer");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaSetDevice");
+    const int M = std::max(16, gc_fft_size(L));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (vfmt == GC_C64) {
+        switch (M) {
+            case 16: return Launcher<CfgC16>::run(ctx, volt, L, C, T, gains, vunique, s);
+            case 32: return Launcher<CfgC32>::run(ctx, volt, L, C, T, gains, vunique, s);
+            case 64: return Launcher<CfgC64>::run(ctx, volt, L, C, T, gains, vunique, s);
+            case 128: return Launcher<CfgC128>::run(ctx, volt, L, C, T, gains, vunique, s);
+        }
+    } else {
+        switch (M) {
+            case 16: return Launcher<CfgI16>::run(ctx, volt, L, C, T, gains, vunique, s);
+            case 32: return Launcher<CfgI32>::run(ctx, volt, L, C, T, gains, vunique, s);
+            case 64: return Launcher<CfgI64>::run(ctx, volt, L, C, T, gains, vunique, s);
+            case 128: return Launcher<CfgI128>::run(ctx, volt, L, C, T, gains, vunique, s);
+        }
+    }
+    return gc_fail(ctx, GC_EUNSUPPORTED, "gc_correlate: no kernel for this grid size");
+}
