@@ -77,6 +77,17 @@ GC_API const char *gc_last_error(const gc_ctx *ctx);
  * GC_ETIMEOUT if a kernel gave up a bounded wait since the last check. */
 GC_API gc_status gc_device_status(gc_ctx *ctx, void *stream);
 
+/* Launch timing (not part of the paper's method; used by benchmarks).
+ * When enabled, the library records a CUDA event pair on the launching
+ * stream around every kernel it enqueues.  gc_profile_read synchronises on
+ * those events, writes per-kernel-kind totals (names: 64-byte slots,
+ * NUL-terminated; total milliseconds; launch counts) for up to max_kinds
+ * kinds, clears the records and returns the number of kinds (-1 on a bad
+ * argument).  Any of names / total_ms / launches may be NULL. */
+GC_API gc_status gc_profile_enable(gc_ctx *ctx, int enable);
+GC_API int gc_profile_read(gc_ctx *ctx, char *names, double *total_ms, int *launches,
+                           int max_kinds);
+
 /* Smallest FFT side M for an L x L grid: the smallest power of two >= 2L - 1,
  * so that the circular correlation of the zero-padded grid equals the
  * linear one (paper Sec. 1, convolution theorem).  gc_correlate uses

@@ -508,7 +508,9 @@ struct Launcher {
             if (st != GC_OK) return st;
         }
         const int grid = (int)std::min<long>(p.n_items, slots);
+        int rec = gc_prof_begin(ctx, stream, "fftcorr_accumulate");
         kern<<<grid, K::NTHREADS, K::SMEM, stream>>>(tmap, p);
+        gc_prof_end(ctx, stream, rec);
         e = cudaGetLastError();
         if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch fftcorr_accumulate");
 
@@ -517,7 +519,9 @@ struct Launcher {
         auto fin = fftcorr_finalize<K::M>;
         e = cudaFuncSetAttribute(fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
         if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(fftcorr_finalize)");
+        rec = gc_prof_begin(ctx, stream, "fftcorr_finalize");
         fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n * K::G, reinterpret_cast<float2 *>(vunique), L, T);
+        gc_prof_end(ctx, stream, rec);
         e = cudaGetLastError();
         if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch fftcorr_finalize");
         return GC_OK;

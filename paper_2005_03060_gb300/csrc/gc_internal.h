@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/gridcorr.h"
 
@@ -18,6 +19,11 @@
 // bounded waits: give up after this many nanoseconds of %globaltimer
 #define GC_WAIT_LIMIT_NS     1000000000ull
 
+struct gc_prof_rec {
+    const char *name;
+    cudaEvent_t start, stop;
+};
+
 struct gc_ctx {
     int device = 0;
     int sm_count = 0;
@@ -26,7 +32,15 @@ struct gc_ctx {
     size_t scratch_bytes = 0;
     std::string last_error;
     void *encode_tiled = nullptr;         // cuTensorMapEncodeTiled entry point
+    // opt-in launch timing (gc_profile_enable): events around every launch
+    bool profile = false;
+    std::vector<gc_prof_rec> prof;        // records since the last read
+    std::vector<cudaEvent_t> event_pool;
 };
+
+// launch timing helpers: no-ops unless profiling is enabled
+int gc_prof_begin(gc_ctx *ctx, cudaStream_t s, const char *name);
+void gc_prof_end(gc_ctx *ctx, cudaStream_t s, int rec);
 
 // error helpers (gc_runtime.cu)
 gc_status gc_fail(gc_ctx *ctx, gc_status st, const std::string &msg);

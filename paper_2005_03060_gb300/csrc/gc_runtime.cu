@@ -71,6 +71,39 @@ gc_status gc_encode_tiled(gc_ctx *ctx, CUtensorMap *map, CUtensorMapDataType dt,
     return GC_OK;
 }
 
+static cudaEvent_t pool_get(gc_ctx *ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+int gc_prof_begin(gc_ctx *ctx, cudaStream_t s, const char *name) {
+    if (!ctx->profile) return -1;
+    gc_prof_rec r{name, pool_get(ctx), pool_get(ctx)};
+    if (!r.start || !r.stop) return -1;
+    cudaEventRecord(r.start, s);
+    ctx->prof.push_back(r);
+    return (int)ctx->prof.size() - 1;
+}
+
+void gc_prof_end(gc_ctx *ctx, cudaStream_t s, int rec) {
+    if (rec < 0 || rec >= (int)ctx->prof.size()) return;
+    cudaEventRecord(ctx->prof[rec].stop, s);
+}
+
+static void prof_clear(gc_ctx *ctx) {
+    for (auto &r : ctx->prof) {
+        ctx->event_pool.push_back(r.start);
+        ctx->event_pool.push_back(r.stop);
+    }
+    ctx->prof.clear();
+}
+
 extern "C" {
 
 gc_status gc_create(gc_ctx **out, int device) {
@@ -99,6 +132,8 @@ void gc_destroy(gc_ctx *ctx) {
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    prof_clear(ctx);
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->status_dev) cudaFree(ctx->status_dev);
     cudaSetDevice(prev);
@@ -123,6 +158,45 @@ gc_status gc_device_status(gc_ctx *ctx, void *stream) {
     }
     if (h & GC_DEV_BADINDEX) return gc_fail(ctx, GC_EINVAL, "device saw an out-of-range index");
     return GC_OK;
+}
+
+gc_status gc_profile_enable(gc_ctx *ctx, int enable) {
+    if (!ctx) return GC_EINVAL;
+    ctx->profile = enable != 0;
+    if (!ctx->profile) prof_clear(ctx);
+    return GC_OK;
+}
+
+int gc_profile_read(gc_ctx *ctx, char *names, double *total_ms, int *launches, int max_kinds) {
+    if (!ctx || max_kinds < 0) return -1;
+    std::vector<std::string> kinds;
+    std::vector<double> ms;
+    std::vector<int> cnt;
+    for (auto &r : ctx->prof) {
+        if (cudaEventSynchronize(r.stop) != cudaSuccess) continue;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.start, r.stop) != cudaSuccess) continue;
+        size_t k = 0;
+        while (k < kinds.size() && kinds[k] != r.name) ++k;
+        if (k == kinds.size()) {
+            kinds.push_back(r.name);
+            ms.push_back(0.0);
+            cnt.push_back(0);
+        }
+        ms[k] += t;
+        cnt[k] += 1;
+    }
+    prof_clear(ctx);
+    const int n = (int)kinds.size();
+    for (int k = 0; k < n && k < max_kinds; ++k) {
+        if (names) {
+            strncpy(names + 64 * k, kinds[k].c_str(), 63);
+            names[64 * k + 63] = 0;
+        }
+        if (total_ms) total_ms[k] = ms[k];
+        if (launches) launches[k] = cnt[k];
+    }
+    return n;
 }
 
 int gc_fft_size(int L) {

@@ -46,6 +46,11 @@ _lib.gc_device_status.argtypes = [_vp, _vp]
 _lib.gc_device_status.restype = _i
 _lib.gc_fft_size.argtypes = [_i]
 _lib.gc_fft_size.restype = _i
+_lib.gc_profile_enable.argtypes = [_vp, _i]
+_lib.gc_profile_enable.restype = _i
+_lib.gc_profile_read.argtypes = [_vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(_i), _i]
+_lib.gc_profile_read.restype = _i
 _lib.gc_correlate.argtypes = [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp]
 _lib.gc_correlate.restype = _i
 
@@ -93,6 +98,24 @@ class Context:
     def device_status(self):
         """Synchronise the current stream and raise if a kernel timed out."""
         self.check(_lib.gc_device_status(self._h, _vp(_stream_ptr(self.device))))
+
+    # ------------------------------------------------------------------ profiling
+    def profile(self, enable: bool = True):
+        """Record CUDA events around every kernel the library launches."""
+        self.check(_lib.gc_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since the last read (syncs)."""
+        kmax = 32
+        names = ctypes.create_string_buffer(64 * kmax)
+        ms = (ctypes.c_double * kmax)()
+        cnt = (_i * kmax)()
+        n = _lib.gc_profile_read(self._h, names, ms, cnt, kmax)
+        out = {}
+        for k in range(max(0, min(n, kmax))):
+            nm = names.raw[64 * k:64 * k + 64].split(b"\0", 1)[0].decode()
+            out[nm] = (ms[k], cnt[k])
+        return out
 
     # ------------------------------------------------------------------ correlate
     def correlate(self, volt: torch.Tensor, gains: torch.Tensor, L: int | None = None,
