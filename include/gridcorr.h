@@ -120,6 +120,43 @@ GC_API int gc_fft_size(int L);
 GC_API gc_status gc_correlate(gc_ctx *ctx, const void *volt, int vfmt, int L, int C, int T,
                        const float *gains, float *vunique, void *stream);
 
+/*
+ * FFT-correlator that allocates no device memory.  The paper has no
+ * counterpart: this is an interface for callers that cannot call cudaMalloc
+ * -- for example a real-time correlator process whose device memory is
+ * fixed when the observation starts (cudaMalloc and cudaFree can
+ * synchronise the whole device and stall the streams that keep up with the
+ * telescope), or a host framework that owns every device allocation and
+ * hands the library only the buffers it already holds.
+ *
+ * Same computation, arguments and layouts as gc_correlate, with no context:
+ * the per-chunk power spectra live in a fixed 64 MiB array in the library's
+ * device memory (every GPU that loads the library holds it until the
+ * process exits).  The call is rejected with GC_EINVAL when
+ *     C * ceil(T / 512) * G * M^2 * 4 bytes > 64 MiB
+ * (M = max(16, gc_fft_size(L)); G = 8 for M = 16, 4 for M = 32, else 1);
+ * e.g. L = 32, T = 4096 allows up to 512 channels per call.
+ *
+ * The first call on a device (the current device) looks up the device
+ * address of that array (cudaGetSymbolAddress) and the tensor-map encoder;
+ * make that first call before any stream capture.  Later calls only enqueue
+ * two kernels on `stream`.
+ *
+ * `status` (optional, device, caller-zeroed) receives the device-side error
+ * bits of the call (non-zero = a bounded wait ran out and the output is
+ * incomplete); NULL sends them to a word of the library that is not
+ * reported.  All calls on a device share the one scratch array, and each
+ * call overwrites every element it later reads, so nothing has to be
+ * cleared between calls; calls that overlap on the GPU (different streams
+ * without ordering between them) race on the array and give wrong results.
+ *
+ * Returns GC_EINVAL for bad arguments or sizes beyond the fixed scratch,
+ * GC_ECUDA when a CUDA call fails, GC_EUNSUPPORTED for an unbuilt size.
+ */
+GC_API gc_status gc_correlate_noalloc(const void *volt, int vfmt, int L, int C, int T,
+                                      const float *gains, float *vunique, unsigned int *status,
+                                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -571,3 +571,170 @@ extern "C" gc_status gc_correlate(gc_ctx *ctx, const void *volt, int vfmt, int L
     }
     return gc_fail(ctx, GC_EUNSUPPORTED, "gc_correlate: no kernel for this grid size");
 }
+
+// ============================================================================
+// gc_correlate_noalloc: the FFT-correlator for callers that may not allocate
+// device memory (see include/gridcorr.h).  The per-chunk power spectra live
+// in a fixed, file-scope device array instead of the context workspace.
+// ============================================================================
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = 64ull << 20;   // 64 MiB, held by every GPU that loads the library
+static __device__ __align__(256) float g_noalloc_scratch[kNoallocScratchBytes / sizeof(float)];
+static __device__ unsigned int g_noalloc_status;       // timeout flags when the caller passes none
+
+struct NoallocDev {
+    bool ready = false;
+    float *scratch = nullptr;
+    unsigned int *status = nullptr;
+};
+constexpr int kMaxDevices = 64;
+NoallocDev g_noalloc_dev[kMaxDevices];
+std::mutex g_noalloc_mu;
+void *g_noalloc_encode = nullptr;
+
+// Once per device, with that device current: resolve the device addresses of
+// the file-scope arrays (host code only sees a host-side stand-in symbol).
+gc_status noalloc_setup(int dev, NoallocDev **out) {
+    if (dev < 0 || dev >= kMaxDevices) return GC_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoallocDev &d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void *p = nullptr, *q = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return GC_ECUDA;
+        }
+        if (cudaGetSymbolAddress(&q, g_noalloc_status) != cudaSuccess) {
+            cudaGetLastError();
+            return GC_ECUDA;
+        }
+        d.scratch = static_cast<float *>(p);
+        d.status = static_cast<unsigned int *>(q);
+        d.ready = true;
+    }
+    if (!g_noalloc_encode) {
+        cudaDriverEntryPointQueryResult qr;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) ==
+                cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            g_noalloc_encode = fn;
+    }
+    *out = &d;
+    return GC_OK;
+}
+
+template <class K>
+gc_status noalloc_run(const NoallocDev &d, const void *volt, int L, int C, int T, const float *gains,
+                      float *vunique, unsigned int *status, cudaStream_t stream) {
+    const int N = L * L;
+    const size_t per_chunk = (size_t)C * K::G * K::M * K::M * sizeof(float);
+    const int n_min = std::max(1, (T + 511) / 512);      // chunks of <= 512 samples
+    if (per_chunk * n_min > kNoallocScratchBytes) return GC_EINVAL;
+    const int n_cap = (int)std::min<size_t>(kNoallocScratchBytes / per_chunk, (size_t)n_min + 64);
+    bool tma = gc_aligned(volt, 16) && ((size_t)L * K::ESZ) % 16 == 0 && g_noalloc_encode != nullptr;
+    auto kern = tma ? fftcorr_accumulate<K, true> : fftcorr_accumulate<K, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM) != cudaSuccess)
+        return GC_ECUDA;
+    int occ = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, K::NTHREADS, K::SMEM) != cudaSuccess ||
+        occ < 1 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GC_ECUDA;
+    const int slots = occ * sms;
+    const int step = K::GNT;
+    int best_n = n_min, best_len = ((T + n_min - 1) / n_min + step - 1) / step * step;
+    double best_eff = -1.0;
+    for (int n = n_min; n <= n_cap; ++n) {
+        const int len = ((T + n - 1) / n + step - 1) / step * step;
+        const int nn = (T + len - 1) / len;
+        if (nn > n_cap) continue;
+        const long items = (long)C * K::R * nn;
+        const long waves = (items + slots - 1) / slots;
+        const double eff = (double)C * K::R * T / ((double)waves * slots * len);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best_n = nn;
+            best_len = len;
+        }
+    }
+    Params p;
+    p.volt = volt;
+    p.gains = reinterpret_cast<const float2 *>(gains);
+    p.ppart = d.scratch;
+    p.status = status ? status : d.status;
+    p.L = L;
+    p.C = C;
+    p.T = T;
+    p.chunk_len = best_len;
+    p.n_chunks = best_n;
+    p.n_items = C * K::R * best_n;
+
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof tmap);
+    if (tma) {
+        using Fn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                CUtensorMapFloatOOBfill);
+        const cuuint64_t dims[4] = {(cuuint64_t)L, (cuuint64_t)L, (cuuint64_t)T, (cuuint64_t)C};
+        const cuuint64_t strides[3] = {(cuuint64_t)L * K::ESZ, (cuuint64_t)N * K::ESZ,
+                                       (cuuint64_t)T * N * K::ESZ};
+        const cuuint32_t box[4] = {(cuuint32_t)K::ROWE, (cuuint32_t)K::LMAX, (cuuint32_t)K::GNT, 1u};
+        const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+        CUresult r = reinterpret_cast<Fn>(g_noalloc_encode)(
+            &tmap, K::VF == GC_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 4,
+            const_cast<void *>(volt), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return GC_ECUDA;
+    }
+    const int grid = (int)std::min<long>(p.n_items, slots);
+    kern<<<grid, K::NTHREADS, K::SMEM, stream>>>(tmap, p);
+    if (cudaGetLastError() != cudaSuccess) return GC_ECUDA;
+    const int W = 2 * L - 1;
+    const size_t fsmem = (size_t)K::M * K::M * 4 + (size_t)K::M * W * 8 + K::M * 8;
+    auto fin = fftcorr_finalize<K::M>;
+    if (cudaFuncSetAttribute(fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem) != cudaSuccess)
+        return GC_ECUDA;
+    fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n * K::G, reinterpret_cast<float2 *>(vunique), L, T);
+    if (cudaGetLastError() != cudaSuccess) return GC_ECUDA;
+    return GC_OK;
+}
+
+}  // namespace
+
+extern "C" gc_status gc_correlate_noalloc(const void *volt, int vfmt, int L, int C, int T, const float *gains,
+                                          float *vunique, unsigned int *status, void *stream) {
+    if (!volt || !gains || !vunique) return GC_EINVAL;
+    if (L < 1 || L > 64 || C < 1 || T < 1) return GC_EINVAL;
+    if (vfmt != GC_C64 && vfmt != GC_I4C) return GC_EINVAL;
+    if (!gc_aligned(gains, 8) || !gc_aligned(vunique, 8) || (vfmt == GC_C64 && !gc_aligned(volt, 8)) ||
+        (status && !gc_aligned(status, 4)))
+        return GC_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GC_ECUDA;
+    NoallocDev *d = nullptr;
+    gc_status st = noalloc_setup(dev, &d);
+    if (st != GC_OK) return st;
+    const int M = std::max(16, gc_fft_size(L));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (vfmt == GC_C64) {
+        switch (M) {
+            case 16: return noalloc_run<CfgC16>(*d, volt, L, C, T, gains, vunique, status, s);
+            case 32: return noalloc_run<CfgC32>(*d, volt, L, C, T, gains, vunique, status, s);
+            case 64: return noalloc_run<CfgC64>(*d, volt, L, C, T, gains, vunique, status, s);
+            case 128: return noalloc_run<CfgC128>(*d, volt, L, C, T, gains, vunique, status, s);
+        }
+    } else {
+        switch (M) {
+            case 16: return noalloc_run<CfgI16>(*d, volt, L, C, T, gains, vunique, status, s);
+            case 32: return noalloc_run<CfgI32>(*d, volt, L, C, T, gains, vunique, status, s);
+            case 64: return noalloc_run<CfgI64>(*d, volt, L, C, T, gains, vunique, status, s);
+            case 128: return noalloc_run<CfgI128>(*d, volt, L, C, T, gains, vunique, status, s);
+        }
+    }
+    return GC_EUNSUPPORTED;
+}
