@@ -121,6 +121,68 @@ GC_API gc_status gc_correlate(gc_ctx *ctx, const void *volt, int vfmt, int L, in
                        const float *gains, float *vunique, void *stream);
 
 /*
+ * Reduced redundant-baseline calibration selections (paper Sec. 4 and 5).
+ *
+ * A selection lists the baseline-types (d = (dx, dy), canonical half-plane
+ * dy > 0 or dy == 0 and dx > 0, ordered by |d|^2 then by angle in [0, pi))
+ * and, per type, its redundant pairs (i = r_j + d, j = r_j, reference
+ * antenna r_j in row-major order) and the integration window [t0, t1) in
+ * which they are correlated.  It doubles as the redundancy map of the
+ * calibration.  Host objects; created without a GPU; device copies are made
+ * on first use by gc_reduce / gc_calibrate (cudaMalloc, freed by
+ * gc_sel_free).
+ *
+ * gc_selection_subset  (Sec. 5, Eq. subredcal_frac_bls, Sec. 6.1): whole
+ *   types, shortest first, stopping at the cumulative pair count closest to
+ *   p N log N (log to base `log_base`; 0 = natural); extended until the
+ *   degeneracy criterion of Sec. 5.2 holds (null space = 4).  Window [0, T).
+ *   GC_EDEGEN for L = 2 (never satisfiable), GC_EINVAL for L < 2, L > 256.
+ * gc_selection_lowcad  (Sec. 4, Eq. lowcadcal_inttime): every type; types
+ *   are packed first-fit, shortest first, into cycles of floor(p N log N)
+ *   pairs; N_cycle cycles of t_int = floor(T / N_cycle) samples; the types of
+ *   cycle c are integrated over [c t_int, (c + 1) t_int).
+ */
+typedef struct gc_sel gc_sel;
+GC_API gc_status gc_selection_subset(int L, int T, double p, double log_base, gc_sel **out);
+GC_API gc_status gc_selection_lowcad(int L, int T, double p, double log_base, gc_sel **out);
+GC_API void gc_sel_free(gc_sel *sel);
+/* info[8] = {L, T, P (pairs), n_ubl (types), n_cycle, t_int, null_dim, scheme (0 subset, 1 low-cadence)} */
+GC_API gc_status gc_sel_info(const gc_sel *sel, int32_t *info);
+/* Host arrays owned by the selection (valid until gc_sel_free): types [n_ubl][2],
+ * type_ptr [n_ubl + 1] (pairs of type k are [type_ptr[k], type_ptr[k+1])),
+ * pair_i, pair_j [P], win_t0, win_t1 [n_ubl].  Any output may be NULL. */
+GC_API gc_status gc_sel_arrays(const gc_sel *sel, const int32_t **types, const int32_t **type_ptr,
+                               const int32_t **pair_i, const int32_t **pair_j,
+                               const int32_t **win_t0, const int32_t **win_t1);
+
+/*
+ * Reduced X-engine (paper Fig. 1 calibrator step (a); Sec. 4 windows).
+ *
+ *   S_p = sum_{t in [t0_p, t1_p)} v_{i_p}(t) v_{j_p}(t)^*     (raw sums)
+ *   A_i = sum_{t in [0, N_cycle t_int)} |v_i(t)|^2            (autos)
+ *
+ *   volt      [C][T][L*L] c64 or i4c (device), T >= the selection's T
+ *   vreduced  c64: [C][P] c64 (FP32 sums); i4c: [C][P][2] int32, exact
+ *   autos     c64: [C][L*L] float; i4c: [C][L*L] int32; may be NULL
+ * Uses the context workspace (time-slice partial sums).  Two kernels.
+ */
+GC_API gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, int C, int T,
+                           const gc_sel *sel, void *vreduced, void *autos, void *stream);
+
+/*
+ * 4+4-bit quantiser (the precision variant of the voltage path; the paper
+ * does not quantise).  Per channel c: rms_c = sqrt(sum (re^2 + im^2) /
+ * (2 T N)) in FP64, scale_c = (float)(3 / rms_c) (RMS of 3 levels per
+ * component), q = clip(round_half_away(x * scale_c rounded to float), -7, 7),
+ * byte = (q_re << 4) | (q_im & 15).
+ *   volt   [C][T][N] c64 (device, 16-byte aligned), T * N even
+ *   out    [C][T][N] bytes (device)
+ *   scales [C] float (device) or NULL
+ */
+GC_API gc_status gc_quantize(gc_ctx *ctx, const float *volt, int C, int T, int N, uint8_t *out,
+                             float *scales, void *stream);
+
+/*
  * FFT-correlator that allocates no device memory.  The paper has no
  * counterpart: this is an interface for callers that cannot call cudaMalloc
  * -- for example a real-time correlator process whose device memory is

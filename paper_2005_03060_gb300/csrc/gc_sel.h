@@ -1,0 +1,34 @@
+// Internal layout of a selection (gc_sel) shared by the X-engine and the
+// calibration translation units.
+#pragma once
+
+#include <vector>
+
+#include "gc_internal.h"
+
+#define GC_XENG_NTY 16   // types per X-engine work group
+
+struct gc_sel {
+    int scheme = 0;        // 0 subset, 1 low-cadence
+    int L = 0, T = 0, P = 0, n_ubl = 0, n_cycle = 1, t_int = 0, null_dim = 0;
+    double target = 0.0;
+    std::vector<int32_t> types;      // [n_ubl][2] (dx, dy)
+    std::vector<int32_t> type_ptr;   // [n_ubl + 1]
+    std::vector<int32_t> pair_i, pair_j, pair_type;   // [P]
+    std::vector<int32_t> win_t0, win_t1;              // [n_ubl]
+    // X-engine work groups (types sharing a window, <= GC_XENG_NTY each)
+    int n_groups = 0, n_windows = 0;
+    std::vector<int32_t> grp_types;  // type indices, grouped
+    std::vector<int32_t> grp_off;    // [n_groups + 1]
+    std::vector<int32_t> grp_t0, grp_t1, grp_first, grp_win;   // [n_groups]
+    // device copies (one allocation, on `device`)
+    int device = -1;
+    void *d_base = nullptr;
+    int32_t *d_types = nullptr, *d_type_ptr = nullptr, *d_pair_i = nullptr, *d_pair_j = nullptr,
+            *d_pair_type = nullptr, *d_win_t0 = nullptr, *d_win_t1 = nullptr, *d_grp_types = nullptr,
+            *d_grp_off = nullptr, *d_grp_t0 = nullptr, *d_grp_t1 = nullptr, *d_grp_first = nullptr,
+            *d_grp_win = nullptr;
+};
+
+gc_status gc_sel_upload(gc_ctx *ctx, gc_sel *s);
+void gc_sel_release_device(gc_sel *s);

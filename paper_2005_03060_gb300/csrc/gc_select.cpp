@@ -1,0 +1,298 @@
+// Reduced redundant-calibration selections (host side).
+//
+// Subset redundant calibration (paper Sec. 5): whole redundant groups in
+// ascending order of baseline length until the pair count is the whole number
+// of groups closest to p N log N (Eq. subredcal_frac_bls, Sec. 6.1), subject
+// to the degeneracy criterion of Sec. 5.2.
+// Low-cadence calibration (Sec. 4): every pair, p N log N pairs per
+// integration cycle (Eq. lowcadcal_inttime), all pairs of a type in the same
+// cycle, t_int = floor(T / N_cycle).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gc_sel.h"
+
+namespace {
+
+struct TypeVec {
+    int dx, dy;
+};
+
+// Canonical half-plane (dy > 0, or dy == 0 and dx > 0), ordered by squared
+// length, ties by angle in [0, pi) -- compared exactly with a cross product.
+std::vector<TypeVec> ordered_types(int L) {
+    std::vector<TypeVec> t;
+    for (int dy = 0; dy < L; ++dy)
+        for (int dx = -(L - 1); dx < L; ++dx)
+            if (dy > 0 || dx > 0) t.push_back({dx, dy});
+    std::stable_sort(t.begin(), t.end(), [](const TypeVec &a, const TypeVec &b) {
+        const long la = (long)a.dx * a.dx + (long)a.dy * a.dy;
+        const long lb = (long)b.dx * b.dx + (long)b.dy * b.dy;
+        if (la != lb) return la < lb;
+        // both angles lie in [0, pi): a before b iff cross(a, b) > 0
+        return (long)a.dx * b.dy - (long)a.dy * b.dx > 0;
+    });
+    return t;
+}
+
+int group_size(int L, const TypeVec &d) { return (L - std::abs(d.dx)) * (L - std::abs(d.dy)); }
+
+double pair_budget(int N, double p, double log_base) {
+    const double lg = log_base > 0.0 ? std::log((double)N) / std::log(log_base) : std::log((double)N);
+    return p * N * lg;
+}
+
+// Null-space dimension of the linearised system for a prefix of the ordered
+// types on an L x L grid with L >= 3: the phase part keeps its three
+// directions (offset and two slopes) once (1,0) and (0,1) are present; the
+// amplitude part keeps only the overall scale once a type with dx + dy even
+// couples antennas of equal checkerboard parity (without one, the
+// checkerboard amplitude pattern is a fifth direction).  A set lacking an
+// axis type is reported as 6 (not a valid calibration set).
+int null_dim_of(int L, const std::vector<TypeVec> &types) {
+    if (L < 3) return 6;
+    bool x = false, y = false, even = false;
+    for (const auto &d : types) {
+        if (d.dx == 1 && d.dy == 0) x = true;
+        if (d.dx == 0 && d.dy == 1) y = true;
+        if (((d.dx + d.dy) & 1) == 0) even = true;
+    }
+    if (!x || !y) return 6;
+    return even ? 4 : 5;
+}
+
+void fill_pairs(gc_sel *s) {
+    const int L = s->L;
+    s->type_ptr.assign(1, 0);
+    s->pair_i.clear();
+    s->pair_j.clear();
+    s->pair_type.clear();
+    for (int k = 0; k < s->n_ubl; ++k) {
+        const int dx = s->types[2 * k], dy = s->types[2 * k + 1];
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                const int xi = x + dx, yi = y + dy;
+                if (xi < 0 || xi >= L || yi < 0 || yi >= L) continue;
+                s->pair_i.push_back(yi * L + xi);
+                s->pair_j.push_back(y * L + x);
+                s->pair_type.push_back(k);
+            }
+        s->type_ptr.push_back((int32_t)s->pair_i.size());
+    }
+    s->P = (int)s->pair_i.size();
+}
+
+// X-engine work groups: types that share a window, at most GC_XENG_NTY each.
+void fill_groups(gc_sel *s) {
+    s->grp_types.clear();
+    s->grp_off.assign(1, 0);
+    s->grp_t0.clear();
+    s->grp_t1.clear();
+    s->grp_first.clear();
+    s->grp_win.clear();
+    std::vector<int> order(s->n_ubl);
+    for (int k = 0; k < s->n_ubl; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return s->win_t0[a] < s->win_t0[b]; });
+    int k = 0;
+    s->n_windows = 0;
+    while (k < s->n_ubl) {
+        const int t0 = s->win_t0[order[k]], t1 = s->win_t1[order[k]];
+        bool first = true;
+        while (k < s->n_ubl && s->win_t0[order[k]] == t0) {
+            int n = 0;
+            while (k < s->n_ubl && s->win_t0[order[k]] == t0 && n < GC_XENG_NTY) {
+                s->grp_types.push_back(order[k]);
+                ++k;
+                ++n;
+            }
+            s->grp_off.push_back((int32_t)s->grp_types.size());
+            s->grp_t0.push_back(t0);
+            s->grp_t1.push_back(t1);
+            s->grp_first.push_back(first ? 1 : 0);
+            s->grp_win.push_back(s->n_windows);
+            first = false;
+        }
+        ++s->n_windows;
+    }
+    s->n_groups = (int)s->grp_t0.size();
+}
+
+}  // namespace
+
+void gc_sel_release_device(gc_sel *s) {
+    if (!s || !s->d_base) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->device);
+    cudaDeviceSynchronize();
+    cudaFree(s->d_base);
+    cudaSetDevice(prev);
+    s->d_base = nullptr;
+}
+
+gc_status gc_sel_upload(gc_ctx *ctx, gc_sel *s) {
+    if (s->d_base && s->device == ctx->device) return GC_OK;
+    gc_sel_release_device(s);
+    // one allocation: types, type_ptr, pair_i, pair_j, pair_type, win_t0, win_t1, grp_* arrays
+    const std::vector<int32_t> *parts[] = {&s->types,   &s->type_ptr, &s->pair_i,    &s->pair_j,
+                                           &s->pair_type, &s->win_t0, &s->win_t1,   &s->grp_types,
+                                           &s->grp_off, &s->grp_t0,   &s->grp_t1,   &s->grp_first,
+                                           &s->grp_win};
+    constexpr int kParts = 13;
+    size_t total = 0;
+    size_t offs[kParts];
+    for (int i = 0; i < kParts; ++i) {
+        offs[i] = total;
+        total += ((parts[i]->size() * sizeof(int32_t) + 255) / 256) * 256;
+    }
+    void *base = nullptr;
+    cudaError_t e = cudaMalloc(&base, std::max<size_t>(total, 256));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return gc_cuda_fail(ctx, e, "cudaMalloc(selection)");
+    }
+    for (int i = 0; i < kParts; ++i) {
+        if (parts[i]->empty()) continue;
+        e = cudaMemcpy(static_cast<char *>(base) + offs[i], parts[i]->data(), parts[i]->size() * sizeof(int32_t),
+                       cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(base);
+            return gc_cuda_fail(ctx, e, "upload selection");
+        }
+    }
+    int32_t **dst[] = {&s->d_types,   &s->d_type_ptr, &s->d_pair_i,   &s->d_pair_j,
+                       &s->d_pair_type, &s->d_win_t0, &s->d_win_t1,   &s->d_grp_types,
+                       &s->d_grp_off, &s->d_grp_t0,   &s->d_grp_t1,   &s->d_grp_first,
+                       &s->d_grp_win};
+    for (int i = 0; i < kParts; ++i) *dst[i] = reinterpret_cast<int32_t *>(static_cast<char *>(base) + offs[i]);
+    s->d_base = base;
+    s->device = ctx->device;
+    return GC_OK;
+}
+
+extern "C" {
+
+gc_status gc_selection_subset(int L, int T, double p, double log_base, gc_sel **out) {
+    if (!out) return GC_EINVAL;
+    *out = nullptr;
+    if (L == 2) return GC_EDEGEN;   // 6 visibilities for 8 unknowns: never four degeneracies
+    if (L < 3 || L > 256 || T < 1 || !(p > 0.0) || log_base < 0.0 || log_base == 1.0) return GC_EINVAL;
+    const std::vector<TypeVec> ord = ordered_types(L);
+    const double target = pair_budget(L * L, p, log_base);
+    long cum = 0;
+    int best_k = 1;
+    double best_err = -1.0;
+    for (size_t k = 0; k < ord.size(); ++k) {
+        cum += group_size(L, ord[k]);
+        const double err = std::fabs((double)cum - target);
+        if (best_err < 0.0 || err < best_err) {
+            best_err = err;
+            best_k = (int)k + 1;
+        }
+    }
+    // extend until the degeneracy criterion holds (Sec. 5.2)
+    int k = best_k;
+    while (k < (int)ord.size() && null_dim_of(L, std::vector<TypeVec>(ord.begin(), ord.begin() + k)) != 4) ++k;
+    std::vector<TypeVec> chosen(ord.begin(), ord.begin() + k);
+    const int nd = null_dim_of(L, chosen);
+    if (nd != 4) return GC_EDEGEN;
+    gc_sel *s = new (std::nothrow) gc_sel();
+    if (!s) return GC_ENOMEM;
+    s->scheme = 0;
+    s->L = L;
+    s->T = T;
+    s->n_ubl = k;
+    s->n_cycle = 1;
+    s->t_int = T;
+    s->null_dim = nd;
+    s->target = target;
+    for (const auto &d : chosen) {
+        s->types.push_back(d.dx);
+        s->types.push_back(d.dy);
+        s->win_t0.push_back(0);
+        s->win_t1.push_back(T);
+    }
+    fill_pairs(s);
+    fill_groups(s);
+    *out = s;
+    return GC_OK;
+}
+
+gc_status gc_selection_lowcad(int L, int T, double p, double log_base, gc_sel **out) {
+    if (!out) return GC_EINVAL;
+    *out = nullptr;
+    if (L < 3 || L > 256 || T < 1 || !(p > 0.0) || log_base < 0.0 || log_base == 1.0) return GC_EINVAL;
+    const std::vector<TypeVec> ord = ordered_types(L);
+    const double target = pair_budget(L * L, p, log_base);
+    const long cap = (long)std::floor(target);
+    std::vector<long> room;        // free capacity per cycle
+    std::vector<int> cycle(ord.size());
+    for (size_t k = 0; k < ord.size(); ++k) {
+        const long n = group_size(L, ord[k]);
+        if (n > cap) return GC_EINVAL;   // a redundant group must fit one cycle
+        size_t c = 0;
+        while (c < room.size() && room[c] < n) ++c;
+        if (c == room.size()) room.push_back(cap);
+        room[c] -= n;
+        cycle[k] = (int)c;
+    }
+    const int n_cycle = (int)room.size();
+    const int t_int = T / n_cycle;
+    if (t_int < 1) return GC_EINVAL;     // integration too short for the cycle count
+    gc_sel *s = new (std::nothrow) gc_sel();
+    if (!s) return GC_ENOMEM;
+    s->scheme = 1;
+    s->L = L;
+    s->T = T;
+    s->n_ubl = (int)ord.size();
+    s->n_cycle = n_cycle;
+    s->t_int = t_int;
+    s->null_dim = null_dim_of(L, ord);
+    s->target = target;
+    for (size_t k = 0; k < ord.size(); ++k) {
+        s->types.push_back(ord[k].dx);
+        s->types.push_back(ord[k].dy);
+        s->win_t0.push_back(cycle[k] * t_int);
+        s->win_t1.push_back((cycle[k] + 1) * t_int);
+    }
+    fill_pairs(s);
+    fill_groups(s);
+    *out = s;
+    return GC_OK;
+}
+
+void gc_sel_free(gc_sel *sel) {
+    if (!sel) return;
+    gc_sel_release_device(sel);
+    delete sel;
+}
+
+gc_status gc_sel_info(const gc_sel *s, int32_t *info) {
+    if (!s || !info) return GC_EINVAL;
+    info[0] = s->L;
+    info[1] = s->T;
+    info[2] = s->P;
+    info[3] = s->n_ubl;
+    info[4] = s->n_cycle;
+    info[5] = s->t_int;
+    info[6] = s->null_dim;
+    info[7] = s->scheme;
+    return GC_OK;
+}
+
+gc_status gc_sel_arrays(const gc_sel *s, const int32_t **types, const int32_t **type_ptr, const int32_t **pair_i,
+                        const int32_t **pair_j, const int32_t **win_t0, const int32_t **win_t1) {
+    if (!s) return GC_EINVAL;
+    if (types) *types = s->types.data();
+    if (type_ptr) *type_ptr = s->type_ptr.data();
+    if (pair_i) *pair_i = s->pair_i.data();
+    if (pair_j) *pair_j = s->pair_j.data();
+    if (win_t0) *win_t0 = s->win_t0.data();
+    if (win_t1) *win_t1 = s->win_t1.data();
+    return GC_OK;
+}
+
+}  // extern "C"

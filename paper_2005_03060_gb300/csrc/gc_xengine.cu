@@ -1,0 +1,297 @@
+// Reduced X-engine (paper Fig. 1, calibrator step (a)): cross-correlate only
+// the antenna pairs of the selection, each over its own integration window
+// (low-cadence cycles, Sec. 4; the whole integration for subset, Sec. 5).
+//
+// xeng_accumulate: one CTA per (channel, type group, block of reference
+// antennas, time slice).  Samples of the whole grid are staged in shared
+// memory by 1-D bulk TMA copies (double-buffered); each thread owns one
+// reference antenna j and accumulates v_{j+d} conj(v_j) for every type d of
+// its group in registers.  4+4-bit voltages are unpacked to float: products
+// and sums of those integers stay below 2^24, so FP32 sums are exact and the
+// int32 result is bit-exact.
+// xeng_reduce: sums the time slices (FP64) into V^reduced and the autos.
+#include <algorithm>
+#include <cstdio>
+
+#include "gc_sel.h"
+
+namespace {
+
+constexpr int kXThreads = 256;
+
+struct XParams {
+    const void *volt;         // [C][T][N]
+    int vfmt, L, N, C, T;
+    int n_groups, n_rowblk, n_tsplit;
+    int n_items;
+    int ns;                   // samples per stage
+    const int32_t *types, *type_ptr, *grp_types, *grp_off, *grp_t0, *grp_t1, *grp_first;
+    int P;
+    float2 *part;             // [n_tsplit][C][P]
+    float *apart;             // [n_windows * n_tsplit][C][N] (may be null)
+    const int32_t *grp_win;   // window index per group
+    unsigned int *status;
+    int use_tma;
+};
+
+__device__ __forceinline__ float2 ld_volt(const unsigned char *s, int idx, int vfmt) {
+    if (vfmt == GC_C64) return reinterpret_cast<const float2 *>(s)[idx];
+    const int b = (int)(signed char)s[idx];
+    return make_float2((float)(b >> 4), (float)((int)(signed char)(b << 4) >> 4));
+}
+
+__global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bars[2];
+    __shared__ int s_dx[GC_XENG_NTY], s_dy[GC_XENG_NTY], s_base[GC_XENG_NTY];
+    __shared__ int s_err;
+    const int tid = threadIdx.x;
+    const int esz = p.vfmt == GC_C64 ? 8 : 1;
+    const size_t sample_bytes = (size_t)p.N * esz;
+    const size_t stage_stride = ((sample_bytes * p.ns + 127) / 128) * 128;
+    const int L = p.L;
+    if (tid == 0) {
+        s_err = 0;
+        gc_mbar_init(&bars[0], 1);
+        gc_mbar_init(&bars[1], 1);
+        gc_fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t ld_count = 0, use_count = 0;
+
+    for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+        // item order: row block fastest, then group, time slice, channel
+        const int rb = item % p.n_rowblk;
+        const int g = (item / p.n_rowblk) % p.n_groups;
+        const int ts = (item / (p.n_rowblk * p.n_groups)) % p.n_tsplit;
+        const int c = item / (p.n_rowblk * p.n_groups * p.n_tsplit);
+        const int w0 = p.grp_t0[g], w1 = p.grp_t1[g];
+        const int len = (w1 - w0 + p.n_tsplit - 1) / p.n_tsplit;
+        const int ta = min(w1, w0 + ts * len), tb = min(w1, ta + len);
+        const int ntype = p.grp_off[g + 1] - p.grp_off[g];
+        if (tid < ntype) {
+            const int k = p.grp_types[p.grp_off[g] + tid];
+            s_dx[tid] = p.types[2 * k];
+            s_dy[tid] = p.types[2 * k + 1];
+            s_base[tid] = p.type_ptr[k];
+        }
+        const int j = rb * kXThreads + tid;
+        const int x = j % L, y = j / L;
+        const bool own = j < p.N;
+        const unsigned char *vc = static_cast<const unsigned char *>(p.volt) + (size_t)c * p.T * sample_bytes;
+        const int n_st = (tb - ta + p.ns - 1) / p.ns;
+        if (p.use_tma && tid == 0) {
+            for (int k = 0; k < 2 && k < n_st; ++k) {
+                const int t = ta + k * p.ns;
+                const int cnt = min(p.ns, tb - t);
+                const uint32_t b = ld_count & 1u;
+                gc_mbar_expect_tx(&bars[b], (uint32_t)(cnt * sample_bytes));
+                gc_bulk_load(smem + b * stage_stride, vc + (size_t)t * sample_bytes, (uint32_t)(cnt * sample_bytes),
+                             &bars[b]);
+                ++ld_count;
+            }
+        }
+        __syncthreads();
+
+        float2 acc[GC_XENG_NTY];
+#pragma unroll
+        for (int k = 0; k < GC_XENG_NTY; ++k) acc[k] = make_float2(0.f, 0.f);
+        float aut = 0.f;
+
+        for (int st = 0; st < n_st; ++st) {
+            const int t = ta + st * p.ns;
+            const int cnt = min(p.ns, tb - t);
+            const unsigned char *stage;
+            if (p.use_tma) {
+                const uint32_t b = use_count & 1u;
+                stage = smem + b * stage_stride;
+                if (!gc_mbar_wait(&bars[b], (use_count >> 1) & 1u, GC_WAIT_LIMIT_NS)) {
+                    atomicOr(p.status, GC_DEV_TIMEOUT_XENG);
+                    s_err = 1;
+                } else {
+                    ++use_count;
+                }
+                __syncthreads();
+                if (s_err) break;
+            } else {
+                // plain staging (sizes or alignment TMA cannot take)
+                for (size_t i = tid; i < cnt * sample_bytes; i += kXThreads)
+                    smem[i] = vc[(size_t)t * sample_bytes + i];
+                stage = smem;
+                __syncthreads();
+            }
+            if (own) {
+                for (int u = 0; u < cnt; ++u) {
+                    const unsigned char *sv = stage + u * sample_bytes;
+                    const float2 b = ld_volt(sv, j, p.vfmt);
+                    aut = fmaf(b.x, b.x, fmaf(b.y, b.y, aut));
+#pragma unroll
+                    for (int k = 0; k < GC_XENG_NTY; ++k) {
+                        if (k < ntype) {
+                            const int xi = x + s_dx[k], yi = y + s_dy[k];
+                            if (xi >= 0 && xi < L && yi >= 0 && yi < L) {
+                                const float2 a = ld_volt(sv, yi * L + xi, p.vfmt);
+                                // a * conj(b)
+                                acc[k].x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc[k].x));
+                                acc[k].y = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc[k].y));
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            if (p.use_tma && tid == 0 && st + 2 < n_st) {
+                gc_fence_proxy_async();
+                const int t2 = ta + (st + 2) * p.ns;
+                const int cnt2 = min(p.ns, tb - t2);
+                const uint32_t b = ld_count & 1u;
+                gc_mbar_expect_tx(&bars[b], (uint32_t)(cnt2 * sample_bytes));
+                gc_bulk_load(smem + b * stage_stride, vc + (size_t)t2 * sample_bytes,
+                             (uint32_t)(cnt2 * sample_bytes), &bars[b]);
+                ++ld_count;
+            }
+        }
+        if (s_err) break;
+        if (own) {
+            float2 *out = p.part + ((size_t)ts * p.C + c) * p.P;
+#pragma unroll
+            for (int k = 0; k < GC_XENG_NTY; ++k) {
+                if (k < ntype) {
+                    const int dx = s_dx[k], dy = s_dy[k];
+                    const int xlo = max(0, -dx), ylo = max(0, -dy);
+                    const int xi = x + dx, yi = y + dy;
+                    if (xi >= 0 && xi < L && yi >= 0 && yi < L)
+                        out[s_base[k] + (y - ylo) * (L - abs(dx)) + (x - xlo)] = acc[k];
+                }
+            }
+            if (p.apart && p.grp_first[g]) {
+                const int slot = p.grp_win[g] * p.n_tsplit + ts;
+                p.apart[((size_t)slot * p.C + c) * p.N + j] = aut;
+            }
+        }
+        __syncthreads();
+    }
+    if (p.use_tma && s_err && tid == 0) {
+        while (use_count < ld_count) {
+            gc_mbar_wait(&bars[use_count & 1u], (use_count >> 1) & 1u, GC_WAIT_LIMIT_NS / 10);
+            ++use_count;
+        }
+    }
+}
+
+// Sum the time slices: V^reduced (c64: float2, i4c: exact int32 pairs) and autos.
+__global__ void xeng_reduce(const float2 *__restrict__ part, int n_tsplit, int C, int P, int vfmt, void *vred,
+                            const float *__restrict__ apart, int n_aslots, int N, void *autos) {
+    const size_t total = (size_t)C * P;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total + (size_t)C * N;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        if (idx < total) {
+            double re = 0.0, im = 0.0;
+            for (int s = 0; s < n_tsplit; ++s) {
+                const float2 v = part[(size_t)s * total + idx];
+                re += v.x;
+                im += v.y;
+            }
+            if (vfmt == GC_C64) {
+                reinterpret_cast<float2 *>(vred)[idx] = make_float2((float)re, (float)im);
+            } else {
+                reinterpret_cast<int2 *>(vred)[idx] = make_int2((int)llrint(re), (int)llrint(im));
+            }
+        } else if (autos) {
+            const size_t a = idx - total;
+            double s = 0.0;
+            for (int k = 0; k < n_aslots; ++k) s += apart[(size_t)k * C * N + a];
+            if (vfmt == GC_C64) reinterpret_cast<float *>(autos)[a] = (float)s;
+            else reinterpret_cast<int *>(autos)[a] = (int)llrint(s);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, int C, int T, const gc_sel *csel,
+                               void *vreduced, void *autos, void *stream) {
+    if (!ctx) return GC_EINVAL;
+    ctx->last_error.clear();
+    gc_sel *sel = const_cast<gc_sel *>(csel);   // device copies are a cache of the immutable selection
+    if (!volt || !sel || !vreduced) return gc_fail(ctx, GC_EINVAL, "gc_reduce: null argument");
+    if (vfmt != GC_C64 && vfmt != GC_I4C) return gc_fail(ctx, GC_EINVAL, "gc_reduce: unknown voltage format");
+    if (L != sel->L || T < sel->T || C < 1)
+        return gc_fail(ctx, GC_EINVAL, "gc_reduce: grid or integration does not match the selection");
+    if (!gc_aligned(vreduced, 8) || (autos && !gc_aligned(autos, 4)) || (vfmt == GC_C64 && !gc_aligned(volt, 8)))
+        return gc_fail(ctx, GC_EINVAL, "gc_reduce: misaligned buffer");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaSetDevice");
+    gc_status st = gc_sel_upload(ctx, sel);
+    if (st != GC_OK) return st;
+    const int N = L * L;
+    const int esz = vfmt == GC_C64 ? 8 : 1;
+    const size_t sample_bytes = (size_t)N * esz;
+    const int ns = (int)std::max<size_t>(1, std::min<size_t>(8, (32u << 10) / sample_bytes));
+    const size_t stage_stride = ((sample_bytes * ns + 127) / 128) * 128;
+    const size_t smem = 2 * stage_stride;
+    if (smem > 200u * 1024u) return gc_fail(ctx, GC_EUNSUPPORTED, "gc_reduce: grid too large for the stage");
+    const bool tma = gc_aligned(volt, 16) && sample_bytes % 16 == 0;
+    e = cudaFuncSetAttribute(xeng_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(xeng_accumulate)");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, xeng_accumulate, kXThreads, smem);
+    if (e != cudaSuccess || occ < 1) return gc_cuda_fail(ctx, e, "occupancy(xeng_accumulate)");
+    const int slots = occ * ctx->sm_count;
+    const int n_rowblk = (N + kXThreads - 1) / kXThreads;
+    const long base_items = (long)C * sel->n_groups * n_rowblk;
+    // split long windows in time until the work fills two waves (bounded)
+    int n_tsplit = 1;
+    int max_win = 0;
+    for (int g = 0; g < sel->n_groups; ++g) max_win = std::max(max_win, sel->grp_t1[g] - sel->grp_t0[g]);
+    while (base_items * n_tsplit < 2L * slots && n_tsplit < 16 && max_win / (n_tsplit * 2) >= 64) n_tsplit *= 2;
+    const size_t part_bytes = (size_t)n_tsplit * C * sel->P * sizeof(float2);
+    const size_t apart_bytes = autos ? (size_t)sel->n_windows * n_tsplit * C * N * sizeof(float) : 0;
+    st = gc_scratch_reserve(ctx, part_bytes + apart_bytes + 512);
+    if (st != GC_OK) return st;
+    char *scr = static_cast<char *>(ctx->scratch);
+    float2 *part = reinterpret_cast<float2 *>(scr);
+    float *apart = autos ? reinterpret_cast<float *>(scr + ((part_bytes + 255) / 256) * 256) : nullptr;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+    XParams p;
+    p.volt = volt;
+    p.vfmt = vfmt;
+    p.L = L;
+    p.N = N;
+    p.C = C;
+    p.T = T;
+    p.n_groups = sel->n_groups;
+    p.n_rowblk = n_rowblk;
+    p.n_tsplit = n_tsplit;
+    p.n_items = (int)(base_items * n_tsplit);
+    p.ns = ns;
+    p.types = sel->d_types;
+    p.type_ptr = sel->d_type_ptr;
+    p.grp_types = sel->d_grp_types;
+    p.grp_off = sel->d_grp_off;
+    p.grp_t0 = sel->d_grp_t0;
+    p.grp_t1 = sel->d_grp_t1;
+    p.grp_first = sel->d_grp_first;
+    p.P = sel->P;
+    p.part = part;
+    p.apart = apart;
+    p.grp_win = sel->d_grp_win;
+    p.status = ctx->status_dev;
+    p.use_tma = tma ? 1 : 0;
+    const int grid = (int)std::min<long>(p.n_items, slots);
+    int rec = gc_prof_begin(ctx, s, "xeng_accumulate");
+    xeng_accumulate<<<grid, kXThreads, smem, s>>>(p);
+    gc_prof_end(ctx, s, rec);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch xeng_accumulate");
+    const size_t work = (size_t)C * sel->P + (autos ? (size_t)C * N : 0);
+    const int rgrid = (int)std::min<size_t>((work + 255) / 256, (size_t)ctx->sm_count * 8);
+    rec = gc_prof_begin(ctx, s, "xeng_reduce");
+    xeng_reduce<<<rgrid, 256, 0, s>>>(part, n_tsplit, C, sel->P, vfmt, vreduced, apart,
+                                      sel->n_windows * n_tsplit, N, autos);
+    gc_prof_end(ctx, s, rec);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch xeng_reduce");
+    return GC_OK;
+}

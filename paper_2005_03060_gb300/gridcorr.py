@@ -53,6 +53,21 @@ _lib.gc_profile_read.argtypes = [_vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_d
 _lib.gc_profile_read.restype = _i
 _lib.gc_correlate.argtypes = [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp]
 _lib.gc_correlate.restype = _i
+_lib.gc_selection_subset.argtypes = [_i, _i, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp)]
+_lib.gc_selection_subset.restype = _i
+_lib.gc_selection_lowcad.argtypes = [_i, _i, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp)]
+_lib.gc_selection_lowcad.restype = _i
+_lib.gc_sel_free.argtypes = [_vp]
+_lib.gc_sel_free.restype = None
+_lib.gc_sel_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
+_lib.gc_sel_info.restype = _i
+_i32pp = ctypes.POINTER(ctypes.POINTER(ctypes.c_int32))
+_lib.gc_sel_arrays.argtypes = [_vp] + [_i32pp] * 6
+_lib.gc_sel_arrays.restype = _i
+_lib.gc_reduce.argtypes = [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp]
+_lib.gc_reduce.restype = _i
+_lib.gc_quantize.argtypes = [_vp, _vp, _i, _i, _i, _vp, _vp, _vp]
+_lib.gc_quantize.restype = _i
 
 
 def lib() -> ctypes.CDLL:
@@ -141,6 +156,86 @@ class Context:
                                      _vp(gains.data_ptr()), _vp(out.data_ptr()),
                                      _vp(_stream_ptr(volt.device))))
         return out
+
+    # ------------------------------------------------------------------ reduce
+    def reduce(self, volt: torch.Tensor, sel: Selection, autos: bool = True, out=None, out_autos=None):
+        """V^reduced raw pair sums: complex64 [C, P] for complex64 voltages,
+        int32 [C, P, 2] (exact) for 4+4-bit voltages; plus autos [C, N]."""
+        vfmt = GC_C64 if volt.dtype == torch.complex64 else GC_I4C
+        C, T, N = volt.shape
+        if not volt.is_cuda or not volt.is_contiguous():
+            raise ValueError("voltages must be a contiguous CUDA tensor")
+        if out is None:
+            out = (torch.empty(C, sel.P, dtype=torch.complex64, device=volt.device) if vfmt == GC_C64
+                   else torch.empty(C, sel.P, 2, dtype=torch.int32, device=volt.device))
+        a = None
+        if autos:
+            a = out_autos if out_autos is not None else torch.empty(
+                C, N, dtype=torch.float32 if vfmt == GC_C64 else torch.int32, device=volt.device)
+        self.check(_lib.gc_reduce(self._h, _vp(volt.data_ptr()), vfmt, sel.L, C, T, sel.handle,
+                                  _vp(out.data_ptr()), _vp(a.data_ptr() if a is not None else None),
+                                  _vp(_stream_ptr(volt.device))))
+        return (out, a) if autos else out
+
+    # ------------------------------------------------------------------ quantise
+    def quantize(self, volt: torch.Tensor, out=None, scales=None):
+        """4+4-bit bytes [C, T, N] uint8 and per-channel float scales [C]."""
+        C, T, N = volt.shape
+        if volt.dtype != torch.complex64 or not volt.is_cuda or not volt.is_contiguous():
+            raise ValueError("voltages must be contiguous complex64 CUDA tensors")
+        out = out if out is not None else torch.empty(C, T, N, dtype=torch.uint8, device=volt.device)
+        scales = scales if scales is not None else torch.empty(C, dtype=torch.float32, device=volt.device)
+        self.check(_lib.gc_quantize(self._h, _vp(volt.data_ptr()), C, T, N, _vp(out.data_ptr()),
+                                    _vp(scales.data_ptr()), _vp(_stream_ptr(volt.device))))
+        return out, scales
+
+
+class Selection:
+    """A reduced-calibration selection (host object of the library).
+
+    Attributes (numpy int32 copies): types [n_ubl, 2], type_ptr [n_ubl+1],
+    pair_i, pair_j [P], win_t0, win_t1 [n_ubl]; scalars L, T, P, n_ubl,
+    n_cycle, t_int, null_dim, scheme ('subset' or 'lowcad')."""
+
+    def __init__(self, scheme: str, L: int, T: int, p: float = 1.0, log_base: float = 2.0):
+        import numpy as np
+        h = _vp()
+        fn = {"subset": _lib.gc_selection_subset, "lowcad": _lib.gc_selection_lowcad}[scheme]
+        st = fn(L, T, p, log_base, ctypes.byref(h))
+        if st != GC_OK:
+            raise GridcorrError(st, f"gc_selection_{scheme}(L={L}, T={T}, p={p})")
+        self._h = h
+        info = (ctypes.c_int32 * 8)()
+        _lib.gc_sel_info(h, info)
+        (self.L, self.T, self.P, self.n_ubl, self.n_cycle, self.t_int, self.null_dim,
+         sch) = list(info)
+        self.scheme = "subset" if sch == 0 else "lowcad"
+        ptrs = [ctypes.POINTER(ctypes.c_int32)() for _ in range(6)]
+        _lib.gc_sel_arrays(h, *[ctypes.byref(q) for q in ptrs])
+        sizes = [2 * self.n_ubl, self.n_ubl + 1, self.P, self.P, self.n_ubl, self.n_ubl]
+        arrs = [np.ctypeslib.as_array(q, shape=(n,)).copy() if n else np.zeros(0, np.int32)
+                for q, n in zip(ptrs, sizes)]
+        self.types = arrs[0].reshape(-1, 2)
+        self.type_ptr, self.pair_i, self.pair_j, self.win_t0, self.win_t1 = arrs[1:]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def pair_type(self):
+        import numpy as np
+        return np.repeat(np.arange(self.n_ubl, dtype=np.int32), np.diff(self.type_ptr))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.gc_sel_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fft_size(L: int) -> int:

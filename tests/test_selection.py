@@ -1,0 +1,57 @@
+"""Library selection builders (host C++) against the oracle's independent
+Python builders: identical types, pair lists and windows (bit-exact)."""
+import numpy as np
+import pytest
+
+from oracle import select as osel
+
+
+@pytest.fixture(scope="module")
+def gcmod():
+    from paper_2005_03060_gb300 import _build
+    _build.build()
+    from paper_2005_03060_gb300 import gridcorr
+    return gridcorr
+
+
+def _same(a, b):
+    assert [tuple(t) for t in a.types.tolist()] == [tuple(t) for t in b.types]
+    assert np.array_equal(a.type_ptr, b.type_ptr)
+    assert np.array_equal(a.pair_i, b.pair_i)
+    assert np.array_equal(a.pair_j, b.pair_j)
+    assert np.array_equal(a.win_t0, b.win_t0)
+    assert np.array_equal(a.win_t1, b.win_t1)
+    assert a.P == b.P and a.n_cycle == b.n_cycle and a.t_int == b.t_int
+
+
+@pytest.mark.parametrize("L,T,p", [(3, 10, 1.0), (4, 64, 1.0), (5, 100, 0.5), (6, 33, 0.05),
+                                   (8, 256, 1.0), (12, 2048, 1.0), (16, 100, 2.0), (32, 4096, 1.0)])
+def test_subset_matches_oracle(gcmod, L, T, p):
+    _same(gcmod.Selection("subset", L, T, p), osel.subset(L, T, p))
+
+
+def test_subset_paper_sizes(gcmod):
+    """Pair counts of the configured arrays (p = 1, log base 2)."""
+    for L, P, k in [(8, 390, 8), (32, 10446, 11), (64, 47250, 12), (128, 224786, 14)]:
+        s = gcmod.Selection("subset", L, 1024)
+        assert (s.P, s.n_ubl, s.null_dim) == (P, k, 4)
+    _same(gcmod.Selection("subset", 64, 8192), osel.subset(64, 8192))
+
+
+@pytest.mark.parametrize("L,T", [(3, 50), (4, 100), (8, 256), (12, 2048), (32, 4096)])
+def test_lowcad_matches_oracle(gcmod, L, T):
+    _same(gcmod.Selection("lowcad", L, T), osel.lowcad(L, T))
+
+
+def test_natural_log_budget(gcmod):
+    _same(gcmod.Selection("subset", 16, 100, 1.0, 0.0), osel.subset(16, 100, 1.0, 0.0))
+
+
+def test_selection_errors(gcmod):
+    with pytest.raises(gcmod.GridcorrError) as e:
+        gcmod.Selection("subset", 2, 10)
+    assert e.value.status == gcmod.GC_EDEGEN
+    with pytest.raises(gcmod.GridcorrError):
+        gcmod.Selection("subset", 1, 10)
+    with pytest.raises(gcmod.GridcorrError):
+        gcmod.Selection("lowcad", 8, 0)
