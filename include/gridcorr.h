@@ -183,6 +183,63 @@ GC_API gc_status gc_quantize(gc_ctx *ctx, const float *volt, int C, int T, int N
                              float *scales, void *stream);
 
 /*
+ * Per-channel redundant-baseline calibration (paper Sec. 2 Eq. redcal;
+ * lincal and omnical, Sec. 2 and Sec. 3; degeneracies Sec. 5.2; chi^2_r and
+ * DoF, Eq. redchi / Eq. dof).
+ *
+ * For every channel, V_p = S_p / t_p (the X-engine sums divided by the
+ * pair's window length) and the model V_p ~ g_i conj(g_j) V_alpha(p) is
+ * fitted by least squares with uniform weights (Eq. noisecov):
+ *   GC_LINCAL  Gauss-Newton on (Re, Im) of every gain and model visibility;
+ *              banded normal equations (antennas row-major), FP64 (GC_FP64)
+ *              or FP32 (GC_FP32); the four degeneracies are projected out
+ *              of each step; up to 64 baseline-types (subset selections).
+ *   GC_OMNICAL damped simultaneous least-squares fixed point (damping 0.3
+ *              by default, Sec. 3), FP32; any selection (low-cadence).
+ * Start point (unless warm_start): spanning-tree phases over the (1,0) and
+ * (0,1) types, unit amplitudes, group-mean model visibilities.  Warm start
+ * reads gains and vmodel as given.
+ * Output convention for the degeneracies: mean ln|g| = 0, arg g_0 = 0,
+ * arg V_(1,0) = arg V_(0,1) = 0.
+ *
+ *   vreduced  gc_reduce output (c64 [C][P] or i4c [C][P][2] int32)
+ *   autos     gc_reduce autos or NULL (then chi2r = -1)
+ *   gains     [C][L*L] c64 (device, out; in for warm start)
+ *   vmodel    [C][n_ubl] c64 (device, out; in for warm start)
+ *   stats     [C] gc_calstats (device): chi2 = sum |V_p - model|^2,
+ *             chi2r = sum |r|^2 / sigma_p^2 / DoF with the radiometer
+ *             sigma_p^2 = (A_i/T_a)(A_j/T_a)/t_p, DoF = P - N - n_ubl + 2,
+ *             iters, status (GC_OK, GC_ENOCONV at max_iter, GC_ETIMEOUT past
+ *             time_limit_ms, GC_EDEGEN on a non-positive pivot).
+ * Zero-valued option fields select the defaults: max_iter 50 (lincal) /
+ * 20000 (omnical), tol 1e-10 (lincal FP64) / 1e-6 (FP32, omnical), damping
+ * 0.3, time_limit_ms 10000 per channel.  Uses the context workspace.
+ */
+typedef enum gc_solver { GC_LINCAL = 0, GC_OMNICAL = 1 } gc_solver;
+typedef enum gc_precision { GC_FP64 = 0, GC_FP32 = 1 } gc_precision;
+typedef struct gc_calopts {
+    int solver;        /* gc_solver */
+    int precision;     /* gc_precision (lincal) */
+    int max_iter;
+    int warm_start;
+    double tol;        /* relative step / change */
+    double damping;    /* omnical */
+    int time_limit_ms; /* per channel, device-side */
+    int reserved;
+} gc_calopts;
+typedef struct gc_calstats {
+    double chi2;
+    double chi2r;
+    int dof;
+    int iters;
+    int status;
+    int reserved;
+} gc_calstats;
+GC_API gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, const gc_sel *sel, int C,
+                              const void *autos, const gc_calopts *opts, float *gains, float *vmodel,
+                              gc_calstats *stats, void *stream);
+
+/*
  * FFT-correlator that allocates no device memory.  The paper has no
  * counterpart: this is an interface for callers that cannot call cudaMalloc
  * -- for example a real-time correlator process whose device memory is

@@ -1,0 +1,1012 @@
+// Per-channel redundant-baseline calibration (paper Sec. 2, Eq. redcal;
+// lincal / omnical, Sec. 2 and Sec. 3; degeneracies, Sec. 5.2; chi^2_r and
+// DoF, Eq. redchi / Eq. dof).
+//
+// One CTA calibrates one channel at a time (grid-stride over channels) with
+// its state and linear-algebra workspace in global memory (L2 resident).
+//
+// lincal (Gauss-Newton): unknowns x = [Re g_0, Im g_0, Re g_1, ... ; Re V_0,
+// Im V_0, ...].  With antennas in row-major order every selected pair couples
+// antennas at most D = max |dy L + dx| apart, so the gain block of J^T J is a
+// band of half-width bw = 2D + 1; the model visibilities form a dense border.
+//   * assembly by gather: the thread owning antenna i walks its pairs (as
+//     i_p and as j_p) and writes its own band rows, border columns and
+//     right-hand side -- deterministic, no atomics;
+//   * banded Cholesky, one barrier per column (the scaling of column k is
+//     folded into the update pass of column k+1), with the forward solve of
+//     the right-hand side and of the border riding along;
+//   * Schur complement onto the model visibilities, a small dense Cholesky,
+//     then the banded back substitution;
+//   * the four exact degeneracy directions (amplitude, phase, two slopes)
+//     are projected out of the step, a vanishing Levenberg term keeps the
+//     factorisation definite, and a halving line search guards chi^2.
+// Template on the real type: double (FP64 normal equations) or float.
+//
+// omnical: damped simultaneous least-squares fixed point (FP32), gain update
+// by gather over each antenna's pairs, model-visibility update one warp per
+// baseline-type.
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "gc_sel.h"
+
+namespace {
+
+constexpr int kCThreads = 512;
+constexpr int kMaxUbl = 64;   // lincal border limit (2 * 64 reals)
+
+struct CalParams {
+    const void *vred;            // c64 [C][P] float2 | i4c [C][P] int2
+    int vfmt;
+    const void *autos;           // c64 float | i4c int [C][N], or null
+    int C, L, N, P, n_ubl;
+    const int32_t *types, *type_ptr, *pair_i, *pair_j, *pair_type, *win_t0, *win_t1;
+    int ax, ay;                  // indices of types (1,0) and (0,1)
+    int t_autos;                 // samples summed in autos
+    float2 *gains;               // [C][N] (in: warm start when warm != 0)
+    float2 *vmodel;              // [C][n_ubl]
+    gc_calstats *stats;          // [C]
+    int solver, max_iter, warm;
+    double tol, damping, mu_rel;
+    int bw;                      // band half-width (reals)
+    char *work;
+    size_t work_per_cta;
+    unsigned int *status;
+    unsigned long long deadline_ns;   // per-channel time budget
+};
+
+__device__ __forceinline__ float2 vobs(const CalParams &p, int c, int pidx) {
+    const int k = p.pair_type[pidx];
+    const float inv = 1.0f / (float)(p.win_t1[k] - p.win_t0[k]);
+    if (p.vfmt == GC_C64) {
+        const float2 v = reinterpret_cast<const float2 *>(p.vred)[(size_t)c * p.P + pidx];
+        return make_float2(v.x * inv, v.y * inv);
+    }
+    const int2 v = reinterpret_cast<const int2 *>(p.vred)[(size_t)c * p.P + pidx];
+    return make_float2((float)v.x * inv, (float)v.y * inv);
+}
+
+__device__ __forceinline__ float auto_of(const CalParams &p, int c, int i) {
+    if (!p.autos) return 1.0f;
+    if (p.vfmt == GC_C64) return reinterpret_cast<const float *>(p.autos)[(size_t)c * p.N + i];
+    return (float)reinterpret_cast<const int *>(p.autos)[(size_t)c * p.N + i];
+}
+
+// index of the pair (r_j + d_k, r_j) in the selection, or -1
+__device__ __forceinline__ int pair_index(const CalParams &p, int k, int xj, int yj) {
+    const int dx = p.types[2 * k], dy = p.types[2 * k + 1];
+    const int L = p.L;
+    const int xi = xj + dx, yi = yj + dy;
+    if (xj < 0 || xj >= L || yj < 0 || yj >= L || xi < 0 || xi >= L || yi < 0 || yi >= L) return -1;
+    const int xlo = max(0, -dx), ylo = max(0, -dy);
+    return p.type_ptr[k] + (yj - ylo) * (L - abs(dx)) + (xj - xlo);
+}
+
+template <class R>
+struct C2 {
+    R x, y;
+};
+template <class R>
+__device__ __forceinline__ C2<R> cm(C2<R> a, C2<R> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <class R>
+__device__ __forceinline__ C2<R> cj(C2<R> a) {
+    return {a.x, -a.y};
+}
+
+// ----------------------------------------------------------------- block reductions
+template <class R, int NV>
+__device__ void block_sum(R (&v)[NV], R *red /* smem [32][NV] */) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) red[w * NV + q] = v[q];
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        R s = 0;
+        for (int u = 0; u < nw; ++u) s += red[u * NV + q];
+        v[q] = s;
+    }
+    __syncthreads();
+}
+
+// ----------------------------------------------------------------- start point
+// Spanning-tree phases over the (1,0) and (0,1) types (arg V_(1,0) = arg V_(0,1)
+// = 0 fixes the slopes), unit amplitudes, V_alpha = group mean of V_p / (g_i g_j^*).
+template <class R>
+__device__ void start_point(const CalParams &p, int c, R *xg, R *xv, R *red) {
+    const int L = p.L, N = p.N;
+    R *phi = xv + 2 * p.n_ubl;   // scratch after xv: N reals
+    if (threadIdx.x == 0) {
+        phi[0] = 0;
+        for (int x = 1; x < L; ++x) {
+            const float2 v = vobs(p, c, pair_index(p, p.ax, x - 1, 0));
+            phi[x] = phi[x - 1] + (R)atan2f(v.y, v.x);
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < L; x += blockDim.x) {
+        R acc = phi[x];
+        for (int y = 1; y < L; ++y) {
+            const float2 v = vobs(p, c, pair_index(p, p.ay, x, y - 1));
+            acc += (R)atan2f(v.y, v.x);
+            phi[y * L + x] = acc;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        R s, co;
+        if (sizeof(R) == 8) {
+            double sd, cd;
+            sincos((double)phi[i], &sd, &cd);
+            s = (R)sd;
+            co = (R)cd;
+        } else {
+            float sf, cf;
+            sincosf((float)phi[i], &sf, &cf);
+            s = (R)sf;
+            co = (R)cf;
+        }
+        xg[2 * i] = co;
+        xg[2 * i + 1] = s;
+    }
+    __syncthreads();
+    // V_alpha: one warp per type
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = w; k < p.n_ubl; k += nw) {
+        R sx = 0, sy = 0;
+        for (int q = p.type_ptr[k] + lane; q < p.type_ptr[k + 1]; q += 32) {
+            const int i = p.pair_i[q], j = p.pair_j[q];
+            const float2 v = vobs(p, c, q);
+            C2<R> gi{xg[2 * i], xg[2 * i + 1]}, gj{xg[2 * j], xg[2 * j + 1]};
+            C2<R> e = cm(cj(gi), gj);   // 1 / (g_i g_j^*) for unit gains
+            C2<R> t = cm(C2<R>{(R)v.x, (R)v.y}, e);
+            sx += t.x;
+            sy += t.y;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        }
+        if (lane == 0) {
+            const R n = (R)(p.type_ptr[k + 1] - p.type_ptr[k]);
+            xv[2 * k] = sx / n;
+            xv[2 * k + 1] = sy / n;
+        }
+    }
+    __syncthreads();
+}
+
+// chi^2 = sum_p |V_p - g_i g_j^* V_alpha|^2 over all pairs (one visit each)
+template <class R>
+__device__ R chi2_of(const CalParams &p, int c, const R *xg, const R *xv, R *red) {
+    R s[1] = {0};
+    for (int q = threadIdx.x; q < p.P; q += blockDim.x) {
+        const int i = p.pair_i[q], j = p.pair_j[q], k = p.pair_type[q];
+        const float2 v = vobs(p, c, q);
+        C2<R> m = cm(cm(C2<R>{xg[2 * i], xg[2 * i + 1]}, cj(C2<R>{xg[2 * j], xg[2 * j + 1]})),
+                     C2<R>{xv[2 * k], xv[2 * k + 1]});
+        const R rx = (R)v.x - m.x, ry = (R)v.y - m.y;
+        s[0] += rx * rx + ry * ry;
+    }
+    block_sum<R, 1>(s, red);
+    return s[0];
+}
+
+// ----------------------------------------------------------------- lincal
+template <class R>
+struct GnWork {
+    R *xg, *xv, *band, *border, *rhs, *S, *xs, *tg, *tv, *delta, *trial;
+    int n, m, bw;
+};
+
+template <class R>
+__device__ GnWork<R> gn_layout(const CalParams &p, char *base) {
+    GnWork<R> w;
+    w.n = 2 * p.N;
+    w.m = 2 * p.n_ubl;
+    w.bw = p.bw;
+    R *q = reinterpret_cast<R *>(base);
+    auto take = [&](size_t cnt) {
+        R *r = q;
+        q += (cnt + 31) & ~size_t(31);
+        return r;
+    };
+    w.xg = take(w.n);
+    w.xv = take(w.m + p.N);          // + N scratch for the start point
+    w.band = take((size_t)w.n * (w.bw + 1));
+    w.border = take((size_t)w.m * w.n);
+    w.rhs = take(w.n + w.m);
+    w.S = take((size_t)w.m * w.m);
+    w.xs = take(w.n + w.m);
+    w.tg = take((size_t)4 * w.n);
+    w.tv = take((size_t)4 * w.m);
+    w.delta = take(w.n + w.m);
+    w.trial = take(w.n + w.m);
+    return w;
+}
+
+template <class R>
+size_t gn_bytes(int N, int n_ubl, int bw) {
+    auto r = [](size_t c) { return (c + 31) & ~size_t(31); };
+    const size_t n = 2 * (size_t)N, m = 2 * (size_t)n_ubl;
+    return sizeof(R) * (r(n) + r(m + N) + r(n * (bw + 1)) + r(m * n) + r(n + m) + r(m * m) + r(n + m) +
+                        r(4 * n) + r(4 * m) + r(n + m) + r(n + m));
+}
+
+// Jacobian blocks of one pair: dm/d(Re,Im g_i) = (a, i a), a = conj(g_j) V;
+// dm/d(Re,Im g_j) = (b, -i b), b = g_i V; dm/d(Re,Im V) = (e, i e), e = g_i conj(g_j).
+// As real 2x2 blocks acting on (Re x, Im x): columns are (Re z, Im z) and (Re(iz), Im(iz)).
+template <class R>
+struct Jb {
+    R c0x, c0y, c1x, c1y;   // column 0 = (c0x, c0y), column 1 = (c1x, c1y)
+};
+template <class R>
+__device__ __forceinline__ Jb<R> jb_plus(C2<R> z) {   // (z, i z)
+    return {z.x, z.y, -z.y, z.x};
+}
+template <class R>
+__device__ __forceinline__ Jb<R> jb_minus(C2<R> z) {  // (z, -i z)
+    return {z.x, z.y, z.y, -z.x};
+}
+// A^T B for 2x2 real blocks given by columns
+template <class R>
+__device__ __forceinline__ void atb(const Jb<R> &a, const Jb<R> &b, R (&o)[2][2]) {
+    o[0][0] = a.c0x * b.c0x + a.c0y * b.c0y;
+    o[0][1] = a.c0x * b.c1x + a.c0y * b.c1y;
+    o[1][0] = a.c1x * b.c0x + a.c1y * b.c0y;
+    o[1][1] = a.c1x * b.c1x + a.c1y * b.c1y;
+}
+
+// Assemble the banded normal equations; returns chi^2 and the largest diagonal.
+template <class R>
+__device__ void gn_assemble(const CalParams &p, int c, GnWork<R> &w, R *red, R &chi2, R &dmax) {
+    const int L = p.L, N = p.N, nu = p.n_ubl, bw = w.bw, n = w.n;
+    // zero border and rhs
+    for (size_t i = threadIdx.x; i < (size_t)w.m * n; i += blockDim.x) w.border[i] = 0;
+    for (int i = threadIdx.x; i < n + w.m; i += blockDim.x) w.rhs[i] = 0;
+    __syncthreads();
+    R loc_dmax = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        R *row0 = w.band + (size_t)(2 * i) * (bw + 1);
+        R *row1 = row0 + (bw + 1);
+        for (int o = 0; o <= bw; ++o) {
+            row0[o] = 0;
+            row1[o] = 0;
+        }
+        const int xi = i % L, yi = i / L;
+        const C2<R> gi{w.xg[2 * i], w.xg[2 * i + 1]};
+        R d00 = 0, d10 = 0, d11 = 0, b0 = 0, b1 = 0;
+        for (int k = 0; k < nu; ++k) {
+            const C2<R> V{w.xv[2 * k], w.xv[2 * k + 1]};
+            const int dx = p.types[2 * k], dy = p.types[2 * k + 1];
+            // role A: pair (i, j = i - d), i is i_p
+            {
+                const int q = pair_index(p, k, xi - dx, yi - dy);
+                if (q >= 0) {
+                    const int j = (yi - dy) * L + (xi - dx);
+                    const C2<R> gj{w.xg[2 * j], w.xg[2 * j + 1]};
+                    const C2<R> a = cm(cj(gj), V), b = cm(gi, V), e = cm(gi, cj(gj));
+                    const float2 v = vobs(p, c, q);
+                    const C2<R> mm = cm(e, V);
+                    const R rx = (R)v.x - mm.x, ry = (R)v.y - mm.y;
+                    const Jb<R> Ji = jb_plus(a), Jj = jb_minus(b), Jv = jb_plus(e);
+                    R o[2][2];
+                    atb(Ji, Ji, o);
+                    d00 += o[0][0];
+                    d10 += o[1][0];
+                    d11 += o[1][1];
+                    // off-diagonal block rows (2i, 2i+1) x cols (2j, 2j+1), j < i
+                    atb(Ji, Jj, o);
+                    const int off = 2 * i - 2 * j;   // band offset of (2i, 2j)
+                    row0[off] += o[0][0];
+                    row0[off - 1] += o[0][1];
+                    row1[off + 1] += o[1][0];
+                    row1[off] += o[1][1];
+                    // border (V_k rows) x (g_i cols)
+                    atb(Jv, Ji, o);
+                    w.border[(size_t)(2 * k) * n + 2 * i] += o[0][0];
+                    w.border[(size_t)(2 * k) * n + 2 * i + 1] += o[0][1];
+                    w.border[(size_t)(2 * k + 1) * n + 2 * i] += o[1][0];
+                    w.border[(size_t)(2 * k + 1) * n + 2 * i + 1] += o[1][1];
+                    b0 += Ji.c0x * rx + Ji.c0y * ry;
+                    b1 += Ji.c1x * rx + Ji.c1y * ry;
+                }
+            }
+            // role B: pair (i' = i + d, i), i is j_p
+            {
+                const int q = pair_index(p, k, xi, yi);
+                if (q >= 0) {
+                    const int ip = (yi + dy) * L + (xi + dx);
+                    const C2<R> gp{w.xg[2 * ip], w.xg[2 * ip + 1]};
+                    const C2<R> b = cm(gp, V), e = cm(gp, cj(gi));
+                    const float2 v = vobs(p, c, q);
+                    const C2<R> mm = cm(e, V);
+                    const R rx = (R)v.x - mm.x, ry = (R)v.y - mm.y;
+                    const Jb<R> Jj = jb_minus(b), Jv = jb_plus(e);
+                    R o[2][2];
+                    atb(Jj, Jj, o);
+                    d00 += o[0][0];
+                    d10 += o[1][0];
+                    d11 += o[1][1];
+                    atb(Jv, Jj, o);
+                    w.border[(size_t)(2 * k) * n + 2 * i] += o[0][0];
+                    w.border[(size_t)(2 * k) * n + 2 * i + 1] += o[0][1];
+                    w.border[(size_t)(2 * k + 1) * n + 2 * i] += o[1][0];
+                    w.border[(size_t)(2 * k + 1) * n + 2 * i + 1] += o[1][1];
+                    b0 += Jj.c0x * rx + Jj.c0y * ry;
+                    b1 += Jj.c1x * rx + Jj.c1y * ry;
+                }
+            }
+        }
+        row0[0] = d00;
+        row1[1] = d10;
+        row1[0] = d11;
+        w.rhs[2 * i] = b0;
+        w.rhs[2 * i + 1] = b1;
+        loc_dmax = fmax(loc_dmax, fmax(d00, d11));
+    }
+    // model-visibility block (2x2 per type), its rhs and chi^2: one warp per type
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    R csum = 0;
+    for (int k = wp; k < nu; k += nw) {
+        const C2<R> V{w.xv[2 * k], w.xv[2 * k + 1]};
+        R s00 = 0, s11 = 0, s10 = 0, r0 = 0, r1 = 0, cc = 0;
+        for (int q = p.type_ptr[k] + lane; q < p.type_ptr[k + 1]; q += 32) {
+            const int i = p.pair_i[q], j = p.pair_j[q];
+            const C2<R> e = cm(C2<R>{w.xg[2 * i], w.xg[2 * i + 1]}, cj(C2<R>{w.xg[2 * j], w.xg[2 * j + 1]}));
+            const float2 v = vobs(p, c, q);
+            const C2<R> mm = cm(e, V);
+            const R rx = (R)v.x - mm.x, ry = (R)v.y - mm.y;
+            const R e2 = e.x * e.x + e.y * e.y;
+            s00 += e2;
+            s11 += e2;
+            r0 += e.x * rx + e.y * ry;
+            r1 += -e.y * rx + e.x * ry;
+            cc += rx * rx + ry * ry;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s00 += __shfl_xor_sync(0xffffffffu, s00, o);
+            s11 += __shfl_xor_sync(0xffffffffu, s11, o);
+            r0 += __shfl_xor_sync(0xffffffffu, r0, o);
+            r1 += __shfl_xor_sync(0xffffffffu, r1, o);
+            cc += __shfl_xor_sync(0xffffffffu, cc, o);
+        }
+        (void)s10;
+        if (lane == 0) {
+            // S holds A_VV here (diagonal 2x2 blocks: Jv^T Jv = |e|^2 I)
+            w.S[(size_t)(2 * k) * w.m + 2 * k] = s00;
+            w.S[(size_t)(2 * k + 1) * w.m + 2 * k + 1] = s11;
+            w.S[(size_t)(2 * k + 1) * w.m + 2 * k] = 0;
+            w.S[(size_t)(2 * k) * w.m + 2 * k + 1] = 0;
+            w.rhs[n + 2 * k] = r0;
+            w.rhs[n + 2 * k + 1] = r1;
+        }
+        csum += lane == 0 ? cc : (R)0;
+    }
+    // zero the off-diagonal blocks of A_VV (types do not share a model visibility)
+    for (int idx = threadIdx.x; idx < w.m * w.m; idx += blockDim.x) {
+        const int a = idx / w.m, b = idx % w.m;
+        if ((a >> 1) != (b >> 1)) w.S[idx] = 0;
+    }
+    R v2[2] = {csum, loc_dmax};
+    // chi^2 sum; max via a separate reduction
+    R s1[1] = {csum};
+    block_sum<R, 1>(s1, red);
+    chi2 = s1[0];
+    // block max of diagonals
+    for (int o = 16; o > 0; o >>= 1) loc_dmax = fmax(loc_dmax, __shfl_xor_sync(0xffffffffu, loc_dmax, o));
+    if (lane == 0) red[wp] = loc_dmax;
+    __syncthreads();
+    R mx = 0;
+    for (int u = 0; u < nw; ++u) mx = fmax(mx, red[u]);
+    dmax = mx;
+    __syncthreads();
+    (void)v2;
+}
+
+// In-place banded Cholesky of the gain block with the forward solve of the
+// m border rows and the gain rhs riding along.  The diagonal keeps the
+// unscaled pivot B_kk (L_kk = sqrt(B_kk)); off-diagonal entries become L.
+// Column k is scaled during the pass of column k+1 (disjoint entries), so
+// each column costs one barrier.  Returns false if a pivot is not positive.
+template <class R>
+__device__ bool gn_factor_forward(GnWork<R> &w, R mu, R *s_flag) {
+    const int n = w.n, bw = w.bw, m = w.m;
+    R *B = w.band;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    auto at = [&](int r, int o) -> R & { return B[(size_t)r * (bw + 1) + o]; };
+    for (int r = threadIdx.x; r < n; r += blockDim.x) at(r, 0) += mu;
+    __syncthreads();
+    for (int k = 0; k <= n; ++k) {
+        if (k > 0) {
+            // finish column k-1: l_ik = B_ik / sqrt(B_kk), z_k = rhs_k / sqrt(B_kk)
+            const int kk = k - 1;
+            const R inv = (R)1 / sqrt(at(kk, 0));
+            const int wk = min(bw, n - 1 - kk);
+            for (int t = threadIdx.x; t < wk + m + 1; t += blockDim.x) {
+                if (t < wk) at(kk + 1 + t, t + 1) *= inv;
+                else if (t < wk + m) w.border[(size_t)(t - wk) * n + kk] *= inv;
+                else w.rhs[kk] *= inv;
+            }
+        }
+        if (k == n) break;
+        const R bkk = at(k, 0);
+        if (!(bkk > (R)0)) {
+            if (threadIdx.x == 0) s_flag[0] = 1;
+            return false;   // uniform: every thread read the same pivot
+        }
+        const R invb = (R)1 / bkk;
+        const int wk = min(bw, n - 1 - k);
+        // trailing update, one warp per row: B_ij -= B_ik B_jk / B_kk
+        for (int ti = wp; ti < wk; ti += nw) {
+            const int i = k + 1 + ti;
+            const R bik = at(i, ti + 1) * invb;
+            for (int tj = lane; tj <= ti; tj += 32) {
+                const int j = k + 1 + tj;
+                at(i, ti - tj) -= bik * at(j, tj + 1);
+            }
+        }
+        // forward elimination of the border rows and the gain rhs
+        for (int t = threadIdx.x; t < (m + 1) * wk; t += blockDim.x) {
+            const int q = t / wk, ti = t - q * wk;
+            const int i = k + 1 + ti;
+            const R lik = at(i, ti + 1) * invb;
+            if (q < m) w.border[(size_t)q * n + i] -= lik * w.border[(size_t)q * n + k];
+            else w.rhs[i] -= lik * w.rhs[k];
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    return true;
+}
+
+// Dense m x m Cholesky + solve by one warp (m <= 128); S is overwritten.
+template <class R>
+__device__ bool small_chol_solve(R *S, R *b, int m) {
+    bool ok = true;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (int k = 0; k < m; ++k) {
+            R d = S[(size_t)k * m + k];
+            if (!(d > (R)0)) ok = false;
+            d = sqrt(d > (R)0 ? d : (R)1);
+            __syncwarp();
+            for (int i = k + 1 + lane; i < m; i += 32) S[(size_t)i * m + k] /= d;
+            if (lane == 0) S[(size_t)k * m + k] = d;
+            __syncwarp();
+            for (int i = k + 1 + lane; i < m; i += 32)
+                for (int j = k + 1; j <= i; ++j) S[(size_t)i * m + j] -= S[(size_t)i * m + k] * S[(size_t)j * m + k];
+            __syncwarp();
+        }
+        if (lane == 0) {
+            for (int i = 0; i < m; ++i) {
+                R s = b[i];
+                for (int j = 0; j < i; ++j) s -= S[(size_t)i * m + j] * b[j];
+                b[i] = s / S[(size_t)i * m + i];
+            }
+            for (int i = m - 1; i >= 0; --i) {
+                R s = b[i];
+                for (int j = i + 1; j < m; ++j) s -= S[(size_t)j * m + i] * b[j];
+                b[i] = s / S[(size_t)i * m + i];
+            }
+        }
+    }
+    return ok;
+}
+
+template <class R>
+__device__ void gn_solve(GnWork<R> &w, R mu_rel, R *red) {
+    const int n = w.n, m = w.m, bw = w.bw;
+    // Schur complement S = A_VV - Z Z^T, rhs_V -= Z z  (Z = forward-solved border)
+    const int npairs = m * (m + 1) / 2;
+    for (int t = threadIdx.x; t < npairs + m; t += blockDim.x) {
+        if (t < npairs) {
+            int a = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+            while ((a + 1) * (a + 2) / 2 <= t) ++a;
+            while (a * (a + 1) / 2 > t) --a;
+            const int b = t - a * (a + 1) / 2;
+            R s = 0;
+            const R *za = w.border + (size_t)a * n, *zb = w.border + (size_t)b * n;
+            for (int i = 0; i < n; ++i) s += za[i] * zb[i];
+            w.S[(size_t)a * m + b] -= s;
+            if (a != b) w.S[(size_t)b * m + a] = w.S[(size_t)a * m + b];
+        } else {
+            const int a = t - npairs;
+            R s = 0;
+            const R *za = w.border + (size_t)a * n;
+            for (int i = 0; i < n; ++i) s += za[i] * w.rhs[i];
+            w.rhs[n + a] -= s;
+        }
+    }
+    __syncthreads();
+    // Levenberg term on the Schur block (its near-null directions are the
+    // amplitude and slope degeneracies)
+    if (threadIdx.x == 0) {
+        R mx = 0;
+        for (int a = 0; a < m; ++a) mx = fmax(mx, w.S[(size_t)a * m + a]);
+        for (int a = 0; a < m; ++a) w.S[(size_t)a * m + a] += mu_rel * mx;
+    }
+    __syncthreads();
+    small_chol_solve<R>(w.S, w.rhs + n, m);
+    __syncthreads();
+    // rhs_g = z - Z^T x_V, then back substitution with L^T
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        R s = w.rhs[i];
+        for (int a = 0; a < m; ++a) s -= w.border[(size_t)a * n + i] * w.rhs[n + a];
+        w.rhs[i] = s;
+    }
+    __syncthreads();
+    R *B = w.band;
+    for (int k = n - 1; k >= 0; --k) {
+        const R xk = w.rhs[k] / sqrt(B[(size_t)k * (bw + 1)]);
+        for (int t = threadIdx.x; t < bw; t += blockDim.x) {
+            const int j = k - 1 - t;
+            if (j >= 0) w.rhs[j] -= B[(size_t)k * (bw + 1) + (k - j)] * xk;
+        }
+        if (threadIdx.x == 0) w.xs[k] = xk;
+        __syncthreads();
+    }
+    for (int a = threadIdx.x; a < m; a += blockDim.x) w.xs[n + a] = w.rhs[n + a];
+    __syncthreads();
+    (void)red;
+}
+
+// Project the four degeneracy directions out of delta (Sec. 5.2).
+template <class R>
+__device__ void gn_project(const CalParams &p, GnWork<R> &w, R *red) {
+    const int n = w.n, m = w.m, L = p.L;
+    // tangent vectors at the current point
+    for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
+        const R gx = w.xg[2 * i], gy = w.xg[2 * i + 1];
+        const R xx = (R)(i % L), yy = (R)(i / L);
+        R *t = w.tg;
+        t[0 * n + 2 * i] = gx;          t[0 * n + 2 * i + 1] = gy;          // amplitude: g
+        t[1 * n + 2 * i] = -gy;         t[1 * n + 2 * i + 1] = gx;          // phase: i g
+        t[2 * n + 2 * i] = -xx * gy;    t[2 * n + 2 * i + 1] = xx * gx;     // x slope: i x g
+        t[3 * n + 2 * i] = -yy * gy;    t[3 * n + 2 * i + 1] = yy * gx;     // y slope: i y g
+    }
+    for (int k = threadIdx.x; k < p.n_ubl; k += blockDim.x) {
+        const R vx = w.xv[2 * k], vy = w.xv[2 * k + 1];
+        const R dx = (R)p.types[2 * k], dy = (R)p.types[2 * k + 1];
+        R *t = w.tv;
+        t[0 * m + 2 * k] = -2 * vx;     t[0 * m + 2 * k + 1] = -2 * vy;     // amplitude: -2 V
+        t[1 * m + 2 * k] = 0;           t[1 * m + 2 * k + 1] = 0;
+        t[2 * m + 2 * k] = dx * vy;     t[2 * m + 2 * k + 1] = -dx * vx;    // -i dx V
+        t[3 * m + 2 * k] = dy * vy;     t[3 * m + 2 * k + 1] = -dy * vx;
+    }
+    __syncthreads();
+    R acc[14];
+#pragma unroll
+    for (int q = 0; q < 14; ++q) acc[q] = 0;
+    for (int i = threadIdx.x; i < n + m; i += blockDim.x) {
+        R t[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) t[a] = i < n ? w.tg[a * n + i] : w.tv[a * m + (i - n)];
+        const R d = w.xs[i];
+        int q = 0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b <= a; ++b) acc[q++] += t[a] * t[b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[10 + a] += t[a] * d;
+    }
+    block_sum<R, 14>(acc, red);
+    // solve G c = r (4x4, symmetric PD unless a direction vanishes)
+    R G[4][4], r[4], cvec[4];
+    {
+        int q = 0;
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b <= a; ++b) {
+                G[a][b] = acc[q];
+                G[b][a] = acc[q];
+                ++q;
+            }
+        for (int a = 0; a < 4; ++a) r[a] = acc[10 + a];
+        // Cholesky with a guard
+        R Lm[4][4] = {};
+        bool ok = true;
+        for (int a = 0; a < 4 && ok; ++a) {
+            R s = G[a][a];
+            for (int b = 0; b < a; ++b) s -= Lm[a][b] * Lm[a][b];
+            if (!(s > (R)1e-30)) {
+                ok = false;
+                break;
+            }
+            Lm[a][a] = sqrt(s);
+            for (int i = a + 1; i < 4; ++i) {
+                R t = G[i][a];
+                for (int b = 0; b < a; ++b) t -= Lm[i][b] * Lm[a][b];
+                Lm[i][a] = t / Lm[a][a];
+            }
+        }
+        if (ok) {
+            R y[4];
+            for (int a = 0; a < 4; ++a) {
+                R s = r[a];
+                for (int b = 0; b < a; ++b) s -= Lm[a][b] * y[b];
+                y[a] = s / Lm[a][a];
+            }
+            for (int a = 3; a >= 0; --a) {
+                R s = y[a];
+                for (int b = a + 1; b < 4; ++b) s -= Lm[b][a] * cvec[b];
+                cvec[a] = s / Lm[a][a];
+            }
+        } else {
+            for (int a = 0; a < 4; ++a) cvec[a] = 0;
+        }
+    }
+    for (int i = threadIdx.x; i < n + m; i += blockDim.x) {
+        R d = w.xs[i];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) d -= cvec[a] * (i < n ? w.tg[a * n + i] : w.tv[a * m + (i - n)]);
+        w.delta[i] = d;
+    }
+    __syncthreads();
+}
+
+// Degeneracy convention of the output: mean ln|g| = 0, arg V_(1,0) =
+// arg V_(0,1) = 0, arg g_0 = 0.  Works on float2 gains in place.
+__device__ void output_convention(const CalParams &p, float2 *g, float2 *V, double *red) {
+    double s[1] = {0.0};
+    for (int i = threadIdx.x; i < p.N; i += blockDim.x) s[0] += log(hypot((double)g[i].x, (double)g[i].y));
+    block_sum<double, 1>(s, red);
+    const double sc = exp(s[0] / p.N);
+    const double kx = atan2((double)V[p.ax].y, (double)V[p.ax].x);
+    const double ky = atan2((double)V[p.ay].y, (double)V[p.ay].x);
+    __syncthreads();
+    for (int k = threadIdx.x; k < p.n_ubl; k += blockDim.x) {
+        const double ph = -(kx * p.types[2 * k] + ky * p.types[2 * k + 1]);
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        const double vx = V[k].x * sc * sc, vy = V[k].y * sc * sc;
+        V[k] = make_float2((float)(vx * cs - vy * sn), (float)(vx * sn + vy * cs));
+    }
+    // phase of g_0 after the slope change (x = y = 0 for antenna 0)
+    const double psi = atan2((double)g[0].y, (double)g[0].x);
+    __syncthreads();
+    for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
+        const double ph = kx * (i % p.L) + ky * (i / p.L) - psi;
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        const double gx = g[i].x / sc, gy = g[i].y / sc;
+        g[i] = make_float2((float)(gx * cs - gy * sn), (float)(gx * sn + gy * cs));
+    }
+    __syncthreads();
+}
+
+template <class R>
+__device__ void finish_channel(const CalParams &p, int c, const R *xg, const R *xv, int iters, int st,
+                               double *red) {
+    float2 *g = p.gains + (size_t)c * p.N;
+    float2 *V = p.vmodel + (size_t)c * p.n_ubl;
+    for (int i = threadIdx.x; i < p.N; i += blockDim.x) g[i] = make_float2((float)xg[2 * i], (float)xg[2 * i + 1]);
+    for (int k = threadIdx.x; k < p.n_ubl; k += blockDim.x) V[k] = make_float2((float)xv[2 * k], (float)xv[2 * k + 1]);
+    __syncthreads();
+    output_convention(p, g, V, red);
+    // chi^2 and chi^2_r (Eq. redchi, Eq. dof) at the output point
+    double acc[2] = {0.0, 0.0};
+    const double ta = (double)p.t_autos;
+    for (int q = threadIdx.x; q < p.P; q += blockDim.x) {
+        const int i = p.pair_i[q], j = p.pair_j[q], k = p.pair_type[q];
+        const float2 v = vobs(p, c, q);
+        const double gx = g[i].x, gy = g[i].y, hx = g[j].x, hy = -g[j].y;
+        const double ex = gx * hx - gy * hy, ey = gx * hy + gy * hx;
+        const double mx = ex * V[k].x - ey * V[k].y, my = ex * V[k].y + ey * V[k].x;
+        const double rx = v.x - mx, ry = v.y - my;
+        const double r2 = rx * rx + ry * ry;
+        acc[0] += r2;
+        const double tp = (double)(p.win_t1[k] - p.win_t0[k]);
+        const double s2 = (auto_of(p, c, i) / ta) * (auto_of(p, c, j) / ta) / tp;
+        acc[1] += r2 / s2;
+    }
+    block_sum<double, 2>(acc, red);
+    if (threadIdx.x == 0) {
+        gc_calstats s;
+        s.chi2 = acc[0];
+        s.dof = p.P - p.N - p.n_ubl + 2;
+        s.chi2r = p.autos && s.dof > 0 ? acc[1] / s.dof : -1.0;
+        s.iters = iters;
+        s.status = st;
+        s.reserved = 0;
+        p.stats[c] = s;
+    }
+    __syncthreads();
+}
+
+template <class R>
+__global__ void __launch_bounds__(kCThreads) lincal_kernel(const CalParams p) {
+    __shared__ R red[32 * 14];
+    __shared__ double redd[64];
+    __shared__ R s_flag[1];
+    GnWork<R> w = gn_layout<R>(p, p.work + (size_t)blockIdx.x * p.work_per_cta);
+    for (int c = blockIdx.x; c < p.C; c += gridDim.x) {
+        const uint64_t t_start = gc_globaltimer();
+        if (p.warm) {
+            for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
+                const float2 g = p.gains[(size_t)c * p.N + i];
+                w.xg[2 * i] = g.x;
+                w.xg[2 * i + 1] = g.y;
+            }
+            for (int k = threadIdx.x; k < p.n_ubl; k += blockDim.x) {
+                const float2 v = p.vmodel[(size_t)c * p.n_ubl + k];
+                w.xv[2 * k] = v.x;
+                w.xv[2 * k + 1] = v.y;
+            }
+            __syncthreads();
+        } else {
+            start_point<R>(p, c, w.xg, w.xv, red);
+        }
+        int st = GC_ENOCONV, it = 0;
+        for (it = 1; it <= p.max_iter; ++it) {
+            R chi2, dmax;
+            gn_assemble<R>(p, c, w, red, chi2, dmax);
+            const R mu = (R)p.mu_rel * dmax;
+            if (!gn_factor_forward<R>(w, mu, s_flag)) {
+                st = GC_EDEGEN;
+                break;
+            }
+            gn_solve<R>(w, (R)p.mu_rel, red);
+            gn_project<R>(p, w, red);
+            // norms for the convergence test
+            R nr[2] = {0, 0};
+            for (int i = threadIdx.x; i < w.n + w.m; i += blockDim.x) {
+                const R x = i < w.n ? w.xg[i] : w.xv[i - w.n];
+                nr[0] += x * x;
+                nr[1] += w.delta[i] * w.delta[i];
+            }
+            block_sum<R, 2>(nr, red);
+            // halving line search on chi^2
+            R step = 1;
+            for (int ls = 0; ls < 8; ++ls) {
+                for (int i = threadIdx.x; i < w.n + w.m; i += blockDim.x)
+                    w.trial[i] = (i < w.n ? w.xg[i] : w.xv[i - w.n]) + step * w.delta[i];
+                __syncthreads();
+                const R c2 = chi2_of<R>(p, c, w.trial, w.trial + w.n, red);
+                if (c2 <= chi2 * (R)(1 + 1e-12) + (R)1e-30 || ls == 7) break;
+                step *= (R)0.5;
+            }
+            for (int i = threadIdx.x; i < w.n + w.m; i += blockDim.x) {
+                if (i < w.n) w.xg[i] = w.trial[i];
+                else w.xv[i - w.n] = w.trial[i];
+            }
+            __syncthreads();
+            if (step * sqrt(nr[1]) <= (R)p.tol * sqrt(nr[0])) {
+                st = GC_OK;
+                break;
+            }
+            if (gc_globaltimer() - t_start > p.deadline_ns) {
+                st = GC_ETIMEOUT;
+                if (threadIdx.x == 0) atomicOr(p.status, GC_DEV_TIMEOUT_CAL);
+                break;
+            }
+        }
+        finish_channel<R>(p, c, w.xg, w.xv, min(it, p.max_iter), st, redd);
+    }
+}
+
+// ----------------------------------------------------------------- omnical (FP32)
+__global__ void __launch_bounds__(kCThreads) omnical_kernel(const CalParams p) {
+    __shared__ float red[32 * 2];
+    __shared__ double redd[64];
+    float *base = reinterpret_cast<float *>(p.work + (size_t)blockIdx.x * p.work_per_cta);
+    float *xg = base;                        // 2N
+    float *xv = xg + 2 * p.N;                // 2 n_ubl (+ N scratch for the start point)
+    float *ng = xv + 2 * p.n_ubl + p.N;      // 2N new gains
+    float *nv = ng + 2 * p.N;                // 2 n_ubl new model visibilities
+    const int L = p.L, nu = p.n_ubl;
+    const float a = (float)p.damping;
+    for (int c = blockIdx.x; c < p.C; c += gridDim.x) {
+        const uint64_t t_start = gc_globaltimer();
+        if (p.warm) {
+            for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
+                const float2 g = p.gains[(size_t)c * p.N + i];
+                xg[2 * i] = g.x;
+                xg[2 * i + 1] = g.y;
+            }
+            for (int k = threadIdx.x; k < nu; k += blockDim.x) {
+                const float2 v = p.vmodel[(size_t)c * nu + k];
+                xv[2 * k] = v.x;
+                xv[2 * k + 1] = v.y;
+            }
+            __syncthreads();
+        } else {
+            start_point<float>(p, c, xg, xv, red);
+        }
+        int st = GC_ENOCONV, it;
+        for (it = 1; it <= p.max_iter; ++it) {
+            // gains: gather over each antenna's pairs
+            for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
+                const int xi = i % L, yi = i / L;
+                float nx = 0.f, ny = 0.f, den = 0.f;
+                for (int k = 0; k < nu; ++k) {
+                    const float vx = xv[2 * k], vy = xv[2 * k + 1];
+                    const int dx = p.types[2 * k], dy = p.types[2 * k + 1];
+                    int q = pair_index(p, k, xi - dx, yi - dy);
+                    if (q >= 0) {   // i = i_p, partner j: z = conj(g_j) V
+                        const int j = (yi - dy) * L + (xi - dx);
+                        const float zx = xg[2 * j] * vx + xg[2 * j + 1] * vy;
+                        const float zy = xg[2 * j] * vy - xg[2 * j + 1] * vx;
+                        const float2 v = vobs(p, c, q);
+                        nx += v.x * zx + v.y * zy;     // V conj(z)
+                        ny += v.y * zx - v.x * zy;
+                        den += zx * zx + zy * zy;
+                    }
+                    q = pair_index(p, k, xi, yi);
+                    if (q >= 0) {   // i = j_p, partner i': z = g_i' V ; num += conj(V_p) z
+                        const int ip = (yi + dy) * L + (xi + dx);
+                        const float zx = xg[2 * ip] * vx - xg[2 * ip + 1] * vy;
+                        const float zy = xg[2 * ip] * vy + xg[2 * ip + 1] * vx;
+                        const float2 v = vobs(p, c, q);
+                        nx += v.x * zx + v.y * zy;
+                        ny += v.x * zy - v.y * zx;
+                        den += zx * zx + zy * zy;
+                    }
+                }
+                ng[2 * i] = den > 0.f ? nx / den : xg[2 * i];
+                ng[2 * i + 1] = den > 0.f ? ny / den : xg[2 * i + 1];
+            }
+            // model visibilities: one warp per type
+            const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            for (int k = wp; k < nu; k += nw) {
+                float sx = 0.f, sy = 0.f, sd = 0.f;
+                for (int q = p.type_ptr[k] + lane; q < p.type_ptr[k + 1]; q += 32) {
+                    const int i = p.pair_i[q], j = p.pair_j[q];
+                    const float ex = xg[2 * i] * xg[2 * j] + xg[2 * i + 1] * xg[2 * j + 1];
+                    const float ey = xg[2 * i + 1] * xg[2 * j] - xg[2 * i] * xg[2 * j + 1];
+                    const float2 v = vobs(p, c, q);
+                    sx += v.x * ex + v.y * ey;
+                    sy += v.y * ex - v.x * ey;
+                    sd += ex * ex + ey * ey;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                    sd += __shfl_xor_sync(0xffffffffu, sd, o);
+                }
+                if (lane == 0) {
+                    nv[2 * k] = sd > 0.f ? sx / sd : xv[2 * k];
+                    nv[2 * k + 1] = sd > 0.f ? sy / sd : xv[2 * k + 1];
+                }
+            }
+            __syncthreads();
+            float acc[2] = {0.f, 0.f};
+            for (int i = threadIdx.x; i < 2 * p.N + 2 * nu; i += blockDim.x) {
+                float *x = i < 2 * p.N ? &xg[i] : &xv[i - 2 * p.N];
+                const float xn = i < 2 * p.N ? ng[i] : nv[i - 2 * p.N];
+                const float d = xn - *x;
+                acc[0] += d * d;
+                acc[1] += (*x) * (*x);
+                *x = (1.f - a) * (*x) + a * xn;
+            }
+            block_sum<float, 2>(acc, red);
+            if (sqrtf(acc[0]) < (float)p.tol * sqrtf(acc[1])) {
+                st = GC_OK;
+                break;
+            }
+            if (gc_globaltimer() - t_start > p.deadline_ns) {
+                st = GC_ETIMEOUT;
+                if (threadIdx.x == 0) atomicOr(p.status, GC_DEV_TIMEOUT_CAL);
+                break;
+            }
+        }
+        finish_channel<float>(p, c, xg, xv, min(it, p.max_iter), st, redd);
+    }
+}
+
+}  // namespace
+
+extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, const gc_sel *csel, int C,
+                                  const void *autos, const gc_calopts *opts, float *gains, float *vmodel,
+                                  gc_calstats *stats, void *stream) {
+    if (!ctx) return GC_EINVAL;
+    ctx->last_error.clear();
+    gc_sel *sel = const_cast<gc_sel *>(csel);
+    if (!vreduced || !sel || !gains || !vmodel || !stats || C < 1)
+        return gc_fail(ctx, GC_EINVAL, "gc_calibrate: null argument");
+    if (vfmt != GC_C64 && vfmt != GC_I4C) return gc_fail(ctx, GC_EINVAL, "gc_calibrate: unknown format");
+    if (sel->null_dim != 4) return gc_fail(ctx, GC_EDEGEN, "gc_calibrate: selection has extra degeneracies");
+    gc_calopts o;
+    if (opts) o = *opts;
+    else {
+        o.solver = GC_LINCAL;
+        o.precision = GC_FP64;
+        o.max_iter = 0;
+        o.tol = 0.0;
+        o.damping = 0.3;
+        o.warm_start = 0;
+        o.time_limit_ms = 0;
+    }
+    if (o.solver != GC_LINCAL && o.solver != GC_OMNICAL) return gc_fail(ctx, GC_EINVAL, "gc_calibrate: solver");
+    if (o.precision != GC_FP64 && o.precision != GC_FP32) return gc_fail(ctx, GC_EINVAL, "gc_calibrate: precision");
+    int ax = -1, ay = -1;
+    int D = 0;
+    for (int k = 0; k < sel->n_ubl; ++k) {
+        const int dx = sel->types[2 * k], dy = sel->types[2 * k + 1];
+        if (dx == 1 && dy == 0) ax = k;
+        if (dx == 0 && dy == 1) ay = k;
+        D = std::max(D, std::abs(dy * sel->L + dx));
+    }
+    if (ax < 0 || ay < 0) return gc_fail(ctx, GC_EDEGEN, "gc_calibrate: the selection lacks the axis types");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaSetDevice");
+    gc_status st = gc_sel_upload(ctx, sel);
+    if (st != GC_OK) return st;
+
+    CalParams p;
+    p.vred = vreduced;
+    p.vfmt = vfmt;
+    p.autos = autos;
+    p.C = C;
+    p.L = sel->L;
+    p.N = sel->L * sel->L;
+    p.P = sel->P;
+    p.n_ubl = sel->n_ubl;
+    p.types = sel->d_types;
+    p.type_ptr = sel->d_type_ptr;
+    p.pair_i = sel->d_pair_i;
+    p.pair_j = sel->d_pair_j;
+    p.pair_type = sel->d_pair_type;
+    p.win_t0 = sel->d_win_t0;
+    p.win_t1 = sel->d_win_t1;
+    p.ax = ax;
+    p.ay = ay;
+    p.t_autos = sel->n_cycle * sel->t_int;
+    p.gains = reinterpret_cast<float2 *>(gains);
+    p.vmodel = reinterpret_cast<float2 *>(vmodel);
+    p.stats = stats;
+    p.solver = o.solver;
+    p.warm = o.warm_start;
+    p.damping = o.damping > 0.0 ? o.damping : 0.3;
+    p.status = ctx->status_dev;
+    p.deadline_ns = (unsigned long long)(o.time_limit_ms > 0 ? o.time_limit_ms : 10000) * 1000000ull;
+    p.bw = 2 * D + 1;
+    const bool fp64 = o.precision == GC_FP64;
+    p.tol = o.tol > 0.0 ? o.tol : (o.solver == GC_OMNICAL ? 1e-6 : (fp64 ? 1e-10 : 1e-6));
+    p.max_iter = o.max_iter > 0 ? o.max_iter : (o.solver == GC_OMNICAL ? 20000 : 50);
+    p.mu_rel = fp64 ? 1e-12 : 1e-7;
+
+    int occ = 0;
+    size_t per_cta;
+    const void *kfn;
+    if (o.solver == GC_LINCAL) {
+        if (sel->n_ubl > kMaxUbl)
+            return gc_fail(ctx, GC_EUNSUPPORTED,
+                           "gc_calibrate: lincal supports up to 64 baseline-types (use omnical for low-cadence)");
+        per_cta = fp64 ? gn_bytes<double>(p.N, p.n_ubl, p.bw) : gn_bytes<float>(p.N, p.n_ubl, p.bw);
+        kfn = fp64 ? (const void *)lincal_kernel<double> : (const void *)lincal_kernel<float>;
+    } else {
+        per_cta = sizeof(float) * (size_t)(2 * p.N + 2 * p.n_ubl + p.N + 2 * p.N + 2 * p.n_ubl + 64);
+        kfn = (const void *)omnical_kernel;
+    }
+    per_cta = (per_cta + 255) & ~size_t(255);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kCThreads, 0);
+    if (e != cudaSuccess || occ < 1) return gc_cuda_fail(ctx, e, "occupancy(calibration)");
+    const int grid = std::min(C, occ * ctx->sm_count);
+    st = gc_scratch_reserve(ctx, per_cta * grid);
+    if (st != GC_OK) return st;
+    p.work = static_cast<char *>(ctx->scratch);
+    p.work_per_cta = per_cta;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const char *name = o.solver == GC_LINCAL ? (fp64 ? "lincal_fp64" : "lincal_fp32") : "omnical";
+    int rec = gc_prof_begin(ctx, s, name);
+    if (o.solver == GC_LINCAL) {
+        if (fp64) lincal_kernel<double><<<grid, kCThreads, 0, s>>>(p);
+        else lincal_kernel<float><<<grid, kCThreads, 0, s>>>(p);
+    } else {
+        omnical_kernel<<<grid, kCThreads, 0, s>>>(p);
+    }
+    gc_prof_end(ctx, s, rec);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch calibration");
+    return GC_OK;
+}

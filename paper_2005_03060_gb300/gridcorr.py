@@ -66,6 +66,8 @@ _lib.gc_sel_arrays.argtypes = [_vp] + [_i32pp] * 6
 _lib.gc_sel_arrays.restype = _i
 _lib.gc_reduce.argtypes = [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp]
 _lib.gc_reduce.restype = _i
+_lib.gc_calibrate.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.gc_calibrate.restype = _i
 _lib.gc_quantize.argtypes = [_vp, _vp, _i, _i, _i, _vp, _vp, _vp]
 _lib.gc_quantize.restype = _i
 
@@ -177,6 +179,31 @@ class Context:
                                   _vp(_stream_ptr(volt.device))))
         return (out, a) if autos else out
 
+    # ------------------------------------------------------------------ calibrate
+    def calibrate(self, vred: torch.Tensor, sel: Selection, autos: torch.Tensor | None = None,
+                  solver: str = "lincal", precision: str = "fp64", max_iter: int = 0,
+                  tol: float = 0.0, damping: float = 0.0, time_limit_ms: int = 0,
+                  gains: torch.Tensor | None = None, vmodel: torch.Tensor | None = None,
+                  warm_start: bool = False, stats: torch.Tensor | None = None):
+        """Per-channel redundant calibration of V^reduced (gc_reduce output).
+        Returns (gains [C, N] complex64, vmodel [C, n_ubl] complex64, stats
+        as a uint8 device tensor [C, 32]; decode with `decode_stats`)."""
+        vfmt = GC_C64 if vred.dtype == torch.complex64 else GC_I4C
+        C = vred.shape[0]
+        N = sel.L * sel.L
+        dev = vred.device
+        gains = gains if gains is not None else torch.empty(C, N, dtype=torch.complex64, device=dev)
+        vmodel = vmodel if vmodel is not None else torch.empty(C, sel.n_ubl, dtype=torch.complex64, device=dev)
+        stats = stats if stats is not None else torch.empty(C, 32, dtype=torch.uint8, device=dev)
+        o = CalOpts(GC_LINCAL if solver == "lincal" else GC_OMNICAL,
+                    GC_FP64 if precision == "fp64" else GC_FP32, max_iter, 1 if warm_start else 0,
+                    tol, damping, time_limit_ms, 0)
+        self.check(_lib.gc_calibrate(self._h, _vp(vred.data_ptr()), vfmt, sel.handle, C,
+                                     _vp(autos.data_ptr() if autos is not None else None),
+                                     ctypes.byref(o), _vp(gains.data_ptr()), _vp(vmodel.data_ptr()),
+                                     _vp(stats.data_ptr()), _vp(_stream_ptr(dev))))
+        return gains, vmodel, stats
+
     # ------------------------------------------------------------------ quantise
     def quantize(self, volt: torch.Tensor, out=None, scales=None):
         """4+4-bit bytes [C, T, N] uint8 and per-channel float scales [C]."""
@@ -188,6 +215,20 @@ class Context:
         self.check(_lib.gc_quantize(self._h, _vp(volt.data_ptr()), C, T, N, _vp(out.data_ptr()),
                                     _vp(scales.data_ptr()), _vp(_stream_ptr(volt.device))))
         return out, scales
+
+
+GC_LINCAL, GC_OMNICAL = 0, 1
+GC_FP64, GC_FP32 = 0, 1
+
+
+class CalOpts(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("warm_start", ctypes.c_int), ("tol", ctypes.c_double), ("damping", ctypes.c_double),
+                ("time_limit_ms", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+STATS_DTYPE = [("chi2", "<f8"), ("chi2r", "<f8"), ("dof", "<i4"), ("iters", "<i4"),
+               ("status", "<i4"), ("reserved", "<i4")]
 
 
 class Selection:
@@ -236,6 +277,12 @@ class Selection:
             self.close()
         except Exception:
             pass
+
+
+def decode_stats(stats: torch.Tensor):
+    """uint8 [C, 32] gc_calstats -> numpy structured array."""
+    import numpy as np
+    return stats.cpu().numpy().reshape(-1).view(np.dtype(STATS_DTYPE))
 
 
 def fft_size(L: int) -> int:

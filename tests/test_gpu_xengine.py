@@ -78,7 +78,7 @@ def test_reduce_i4c_exact(gc, ctx, orc, scheme, L, C, T):
         ref = orc.xengine_i4c(b[c], sel.pair_i, sel.pair_j, sel.win_t0[pt], sel.win_t1[pt])
         assert np.array_equal(vr[c].astype(np.int64), ref)
         q = orc.unpack_i4c(b[c])
-        ref_a = np.sum(np.abs(q[:used]) ** 2, axis=0)
+        ref_a = np.sum(q[:used].real ** 2 + q[:used].imag ** 2, axis=0)
         assert np.array_equal(au[c].astype(np.int64), ref_a.astype(np.int64))
 
 
