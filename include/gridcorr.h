@@ -88,6 +88,12 @@ GC_API gc_status gc_profile_enable(gc_ctx *ctx, int enable);
 GC_API int gc_profile_read(gc_ctx *ctx, char *names, double *total_ms, int *launches,
                            int max_kinds);
 
+/* Arithmetic throughput probe (not part of the paper's method; used for
+ * roofline denominators).  kind 0: FP32 FMA, kind 1: FP64 FMA.  Launches a
+ * kernel of independent FMA chains on the context's device (legacy default
+ * stream), synchronises, and writes the achieved TFLOP/s (FMA = 2 flops). */
+GC_API gc_status gc_peak_probe(gc_ctx *ctx, int kind, double *tflops);
+
 /* Smallest FFT side M for an L x L grid: the smallest power of two >= 2L - 1,
  * so that the circular correlation of the zero-padded grid equals the
  * linear one (paper Sec. 1, convolution theorem).  gc_correlate uses
@@ -196,6 +202,10 @@ GC_API gc_status gc_quantize(gc_ctx *ctx, const float *volt, int C, int T, int N
  *              of each step; up to 64 baseline-types (subset selections).
  *   GC_OMNICAL damped simultaneous least-squares fixed point (damping 0.3
  *              by default, Sec. 3), FP32; any selection (low-cadence).
+ *   GC_LINCAL_CG Gauss-Newton with the step from Jacobi-preconditioned
+ *              conjugate gradients on J^T J, matrix-free (J v per pair, J^T u
+ *              by gather), FP32 products with FP64 reductions (CG stops at
+ *              relative residual 1e-4); any selection.
  * Start point (unless warm_start): spanning-tree phases over the (1,0) and
  * (0,1) types, unit amplitudes, group-mean model visibilities.  Warm start
  * reads gains and vmodel as given.
@@ -212,10 +222,10 @@ GC_API gc_status gc_quantize(gc_ctx *ctx, const float *volt, int C, int T, int N
  *             iters, status (GC_OK, GC_ENOCONV at max_iter, GC_ETIMEOUT past
  *             time_limit_ms, GC_EDEGEN on a non-positive pivot).
  * Zero-valued option fields select the defaults: max_iter 50 (lincal) /
- * 20000 (omnical), tol 1e-10 (lincal FP64) / 1e-6 (FP32, omnical), damping
+ * 20000 (omnical), tol 1e-10 (lincal FP64) / 1e-6 (otherwise), damping
  * 0.3, time_limit_ms 10000 per channel.  Uses the context workspace.
  */
-typedef enum gc_solver { GC_LINCAL = 0, GC_OMNICAL = 1 } gc_solver;
+typedef enum gc_solver { GC_LINCAL = 0, GC_OMNICAL = 1, GC_LINCAL_CG = 2 } gc_solver;
 typedef enum gc_precision { GC_FP64 = 0, GC_FP32 = 1 } gc_precision;
 typedef struct gc_calopts {
     int solver;        /* gc_solver */

@@ -794,6 +794,279 @@ __global__ void __launch_bounds__(kCThreads) lincal_kernel(const CalParams p) {
     }
 }
 
+// ----------------------------------------------------------------- lincal, matrix-free (mixed precision)
+// Gauss-Newton with the step from preconditioned conjugate gradients on
+// (J^T J + mu I) delta = J^T r, never forming J^T J: J v is evaluated per
+// pair, J^T u by gather per antenna and per type.  FP32 products, FP64
+// reductions.  The diagonal blocks of J^T J are |a|^2 I (gains) and |e|^2 I
+// (model visibilities), which give the Jacobi preconditioner.
+struct CgWork {
+    float *xg, *xv;          // state (xv followed by N scratch floats)
+    float *dg, *dv;          // preconditioner diagonals
+    float *b, *x, *r, *z, *pp, *q, *trial, *tg;   // n + m each (tg: 4 (n + m))
+    float2 *u;               // per-pair work [P]
+    int n, m;
+};
+
+__device__ CgWork cg_layout(const CalParams &p, char *base) {
+    CgWork w;
+    w.n = 2 * p.N;
+    w.m = 2 * p.n_ubl;
+    const size_t nm = w.n + w.m;
+    float *q = reinterpret_cast<float *>(base);
+    auto take = [&](size_t cnt) {
+        float *r = q;
+        q += (cnt + 63) & ~size_t(63);
+        return r;
+    };
+    w.xg = take(w.n);
+    w.xv = take(w.m + p.N);
+    w.dg = take(p.N);
+    w.dv = take(p.n_ubl);
+    w.b = take(nm);
+    w.x = take(nm);
+    w.r = take(nm);
+    w.z = take(nm);
+    w.pp = take(nm);
+    w.q = take(nm);
+    w.trial = take(nm);
+    w.tg = take(4 * nm);
+    w.u = reinterpret_cast<float2 *>(take(2 * (size_t)p.P));
+    return w;
+}
+
+size_t cg_bytes(int N, int n_ubl, int P) {
+    auto r = [](size_t c) { return (c + 63) & ~size_t(63); };
+    const size_t n = 2 * (size_t)N, m = 2 * (size_t)n_ubl, nm = n + m;
+    return sizeof(float) * (r(n) + r(m + N) + r(N) + r(n_ubl) + 7 * r(nm) + r(4 * nm) + r(2 * (size_t)P));
+}
+
+// u_p = a_p v_gi + b_p conj(v_gj) + e_p v_V  (J v as complex per pair), with
+// a = conj(g_j) V, b = g_i V, e = g_i conj(g_j).  When `resid` is set, u_p is
+// the residual V_p - g_i conj(g_j) V instead, and chi^2 is returned.
+__device__ double cg_pairs(const CalParams &p, int c, const CgWork &w, const float *v, bool resid,
+                           double *red) {
+    double s[1] = {0.0};
+    for (int q = threadIdx.x; q < p.P; q += blockDim.x) {
+        const int i = p.pair_i[q], j = p.pair_j[q], k = p.pair_type[q];
+        const float gix = w.xg[2 * i], giy = w.xg[2 * i + 1], gjx = w.xg[2 * j], gjy = w.xg[2 * j + 1];
+        const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
+        const float ex = gix * gjx + giy * gjy, ey = giy * gjx - gix * gjy;   // g_i conj(g_j)
+        if (resid) {
+            const float2 o = vobs(p, c, q);
+            const float rx = o.x - (ex * Vx - ey * Vy), ry = o.y - (ex * Vy + ey * Vx);
+            w.u[q] = make_float2(rx, ry);
+            s[0] += (double)rx * rx + (double)ry * ry;
+        } else {
+            const float ax = gjx * Vx + gjy * Vy, ay = gjx * Vy - gjy * Vx;   // conj(g_j) V
+            const float bx = gix * Vx - giy * Vy, by = gix * Vy + giy * Vx;   // g_i V
+            const float vix = v[2 * i], viy = v[2 * i + 1], vjx = v[2 * j], vjy = -v[2 * j + 1];
+            const float vvx = v[w.n + 2 * k], vvy = v[w.n + 2 * k + 1];
+            const float ux = ax * vix - ay * viy + bx * vjx - by * vjy + ex * vvx - ey * vvy;
+            const float uy = ax * viy + ay * vix + bx * vjy + by * vjx + ex * vvy + ey * vvx;
+            w.u[q] = make_float2(ux, uy);
+        }
+    }
+    if (resid) block_sum<double, 1>(s, red);
+    else __syncthreads();
+    return s[0];
+}
+
+// out = J^T u (+ mu v when v != null); also the preconditioner diagonals when diag is set.
+__device__ void cg_gather(const CalParams &p, const CgWork &w, float *out, const float *v, float mu, bool diag) {
+    const int L = p.L, nu = p.n_ubl;
+    for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
+        const int xi = i % L, yi = i / L;
+        const float gix = w.xg[2 * i], giy = w.xg[2 * i + 1];
+        float ox = 0.f, oy = 0.f, d = 0.f;
+        for (int k = 0; k < nu; ++k) {
+            const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
+            const int dx = p.types[2 * k], dy = p.types[2 * k + 1];
+            int q = pair_index(p, k, xi - dx, yi - dy);
+            if (q >= 0) {   // i = i_p: conj(a) u, a = conj(g_j) V
+                const int j = (yi - dy) * L + (xi - dx);
+                const float gjx = w.xg[2 * j], gjy = w.xg[2 * j + 1];
+                const float ax = gjx * Vx + gjy * Vy, ay = gjx * Vy - gjy * Vx;
+                const float2 u = w.u[q];
+                ox += ax * u.x + ay * u.y;
+                oy += ax * u.y - ay * u.x;
+                d += ax * ax + ay * ay;
+            }
+            q = pair_index(p, k, xi, yi);
+            if (q >= 0) {   // i = j_p: b conj(u), b = g_i' V
+                const int ip = (yi + dy) * L + (xi + dx);
+                const float gx = w.xg[2 * ip], gy = w.xg[2 * ip + 1];
+                const float bx = gx * Vx - gy * Vy, by = gx * Vy + gy * Vx;
+                const float2 u = w.u[q];
+                ox += bx * u.x + by * u.y;
+                oy += by * u.x - bx * u.y;
+                d += bx * bx + by * by;
+            }
+        }
+        if (v) {
+            ox += mu * v[2 * i];
+            oy += mu * v[2 * i + 1];
+        }
+        out[2 * i] = ox;
+        out[2 * i + 1] = oy;
+        if (diag) w.dg[i] = d;
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = wp; k < nu; k += nw) {
+        float sx = 0.f, sy = 0.f, sd = 0.f;
+        for (int q = p.type_ptr[k] + lane; q < p.type_ptr[k + 1]; q += 32) {
+            const int i = p.pair_i[q], j = p.pair_j[q];
+            const float ex = w.xg[2 * i] * w.xg[2 * j] + w.xg[2 * i + 1] * w.xg[2 * j + 1];
+            const float ey = w.xg[2 * i + 1] * w.xg[2 * j] - w.xg[2 * i] * w.xg[2 * j + 1];
+            const float2 u = w.u[q];
+            sx += ex * u.x + ey * u.y;
+            sy += ex * u.y - ey * u.x;
+            sd += ex * ex + ey * ey;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            sd += __shfl_xor_sync(0xffffffffu, sd, o);
+        }
+        if (lane == 0) {
+            if (v) {
+                sx += mu * v[w.n + 2 * k];
+                sy += mu * v[w.n + 2 * k + 1];
+            }
+            out[w.n + 2 * k] = sx;
+            out[w.n + 2 * k + 1] = sy;
+            if (diag) w.dv[k] = sd;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ float cg_prec(const CalParams &p, const CgWork &w, int idx, float mu) {
+    return idx < w.n ? 1.f / (w.dg[idx >> 1] + mu) : 1.f / (w.dv[(idx - w.n) >> 1] + mu);
+}
+
+__global__ void __launch_bounds__(kCThreads) lincal_cg_kernel(const CalParams p, double cg_tol, int cg_max) {
+    __shared__ double red[32 * 14];
+    __shared__ float redf[32 * 14];
+    CgWork w = cg_layout(p, p.work + (size_t)blockIdx.x * p.work_per_cta);
+    const int nm = w.n + w.m;
+    GnWork<float> gw;   // view for the shared projection helper
+    gw.xg = w.xg;
+    gw.xv = w.xv;
+    gw.tg = w.tg;
+    gw.tv = w.tg + 4 * w.n;
+    gw.xs = w.x;
+    gw.delta = w.z;
+    gw.n = w.n;
+    gw.m = w.m;
+    for (int c = blockIdx.x; c < p.C; c += gridDim.x) {
+        const uint64_t t_start = gc_globaltimer();
+        if (p.warm) {
+            for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
+                const float2 g = p.gains[(size_t)c * p.N + i];
+                w.xg[2 * i] = g.x;
+                w.xg[2 * i + 1] = g.y;
+            }
+            for (int k = threadIdx.x; k < p.n_ubl; k += blockDim.x) {
+                const float2 v = p.vmodel[(size_t)c * p.n_ubl + k];
+                w.xv[2 * k] = v.x;
+                w.xv[2 * k + 1] = v.y;
+            }
+            __syncthreads();
+        } else {
+            start_point<float>(p, c, w.xg, w.xv, redf);
+        }
+        int st = GC_ENOCONV, it;
+        for (it = 1; it <= p.max_iter; ++it) {
+            // residual, right-hand side J^T r and the Jacobi diagonals
+            const double chi2 = cg_pairs(p, c, w, nullptr, true, red);
+            cg_gather(p, w, w.b, nullptr, 0.f, true);
+            double dm[1] = {0.0};
+            for (int i = threadIdx.x; i < p.N; i += blockDim.x) dm[0] = fmax(dm[0], (double)w.dg[i]);
+            for (int o = 16; o > 0; o >>= 1) dm[0] = fmax(dm[0], __shfl_xor_sync(0xffffffffu, dm[0], o));
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dm[0];
+            __syncthreads();
+            double dmax = 0.0;
+            for (int u = 0; u < (int)(blockDim.x >> 5); ++u) dmax = fmax(dmax, red[u]);
+            __syncthreads();
+            const float mu = (float)(p.mu_rel * dmax);
+            // PCG from x = 0
+            double acc[2] = {0.0, 0.0};
+            for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+                const float bi = w.b[i];
+                const float zi = bi * cg_prec(p, w, i, mu);
+                w.x[i] = 0.f;
+                w.r[i] = bi;
+                w.z[i] = zi;
+                w.pp[i] = zi;
+                acc[0] += (double)bi * zi;
+                acc[1] += (double)bi * bi;
+            }
+            block_sum<double, 2>(acc, red);
+            double rz = acc[0];
+            const double bnorm2 = acc[1];
+            for (int k = 0; k < cg_max && bnorm2 > 0.0; ++k) {
+                cg_pairs(p, c, w, w.pp, false, red);
+                cg_gather(p, w, w.q, w.pp, mu, false);
+                double pq[1] = {0.0};
+                for (int i = threadIdx.x; i < nm; i += blockDim.x) pq[0] += (double)w.pp[i] * w.q[i];
+                block_sum<double, 1>(pq, red);
+                if (!(pq[0] > 0.0)) break;
+                const float alpha = (float)(rz / pq[0]);
+                double a2[2] = {0.0, 0.0};
+                for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+                    w.x[i] += alpha * w.pp[i];
+                    const float ri = w.r[i] - alpha * w.q[i];
+                    w.r[i] = ri;
+                    const float zi = ri * cg_prec(p, w, i, mu);
+                    w.z[i] = zi;
+                    a2[0] += (double)ri * zi;
+                    a2[1] += (double)ri * ri;
+                }
+                block_sum<double, 2>(a2, red);
+                if (a2[1] <= cg_tol * cg_tol * bnorm2) break;
+                const float beta = (float)(a2[0] / rz);
+                rz = a2[0];
+                for (int i = threadIdx.x; i < nm; i += blockDim.x) w.pp[i] = w.z[i] + beta * w.pp[i];
+                __syncthreads();
+            }
+            // project out the degeneracies (delta lands in w.z), line search, update
+            gn_project<float>(p, gw, redf);
+            double nr[2] = {0.0, 0.0};
+            for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+                const float x = i < w.n ? w.xg[i] : w.xv[i - w.n];
+                nr[0] += (double)x * x;
+                nr[1] += (double)w.z[i] * w.z[i];
+            }
+            block_sum<double, 2>(nr, red);
+            float step = 1.f;
+            for (int ls = 0; ls < 8; ++ls) {
+                for (int i = threadIdx.x; i < nm; i += blockDim.x)
+                    w.trial[i] = (i < w.n ? w.xg[i] : w.xv[i - w.n]) + step * w.z[i];
+                __syncthreads();
+                const float c2 = chi2_of<float>(p, c, w.trial, w.trial + w.n, redf);
+                if ((double)c2 <= chi2 * (1.0 + 1e-6) + 1e-30 || ls == 7) break;
+                step *= 0.5f;
+            }
+            for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+                if (i < w.n) w.xg[i] = w.trial[i];
+                else w.xv[i - w.n] = w.trial[i];
+            }
+            __syncthreads();
+            if ((double)step * sqrt(nr[1]) <= p.tol * sqrt(nr[0])) {
+                st = GC_OK;
+                break;
+            }
+            if (gc_globaltimer() - t_start > p.deadline_ns) {
+                st = GC_ETIMEOUT;
+                if (threadIdx.x == 0) atomicOr(p.status, GC_DEV_TIMEOUT_CAL);
+                break;
+            }
+        }
+        finish_channel<float>(p, c, w.xg, w.xv, min(it, p.max_iter), st, red);
+    }
+}
+
 // ----------------------------------------------------------------- omnical (FP32)
 __global__ void __launch_bounds__(kCThreads) omnical_kernel(const CalParams p) {
     __shared__ float red[32 * 2];
@@ -926,7 +1199,8 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
         o.warm_start = 0;
         o.time_limit_ms = 0;
     }
-    if (o.solver != GC_LINCAL && o.solver != GC_OMNICAL) return gc_fail(ctx, GC_EINVAL, "gc_calibrate: solver");
+    if (o.solver != GC_LINCAL && o.solver != GC_OMNICAL && o.solver != GC_LINCAL_CG)
+        return gc_fail(ctx, GC_EINVAL, "gc_calibrate: solver");
     if (o.precision != GC_FP64 && o.precision != GC_FP32) return gc_fail(ctx, GC_EINVAL, "gc_calibrate: precision");
     int ax = -1, ay = -1;
     int D = 0;
@@ -971,9 +1245,10 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
     p.deadline_ns = (unsigned long long)(o.time_limit_ms > 0 ? o.time_limit_ms : 10000) * 1000000ull;
     p.bw = 2 * D + 1;
     const bool fp64 = o.precision == GC_FP64;
-    p.tol = o.tol > 0.0 ? o.tol : (o.solver == GC_OMNICAL ? 1e-6 : (fp64 ? 1e-10 : 1e-6));
+    const bool fp64_ne = o.solver == GC_LINCAL && fp64;
+    p.tol = o.tol > 0.0 ? o.tol : (fp64_ne ? 1e-10 : 1e-6);
     p.max_iter = o.max_iter > 0 ? o.max_iter : (o.solver == GC_OMNICAL ? 20000 : 50);
-    p.mu_rel = fp64 ? 1e-12 : 1e-7;
+    p.mu_rel = fp64_ne ? 1e-12 : 1e-7;
 
     int occ = 0;
     size_t per_cta;
@@ -984,6 +1259,9 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
                            "gc_calibrate: lincal supports up to 64 baseline-types (use omnical for low-cadence)");
         per_cta = fp64 ? gn_bytes<double>(p.N, p.n_ubl, p.bw) : gn_bytes<float>(p.N, p.n_ubl, p.bw);
         kfn = fp64 ? (const void *)lincal_kernel<double> : (const void *)lincal_kernel<float>;
+    } else if (o.solver == GC_LINCAL_CG) {
+        per_cta = cg_bytes(p.N, p.n_ubl, p.P);
+        kfn = (const void *)lincal_cg_kernel;
     } else {
         per_cta = sizeof(float) * (size_t)(2 * p.N + 2 * p.n_ubl + p.N + 2 * p.N + 2 * p.n_ubl + 64);
         kfn = (const void *)omnical_kernel;
@@ -997,11 +1275,14 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
     p.work = static_cast<char *>(ctx->scratch);
     p.work_per_cta = per_cta;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const char *name = o.solver == GC_LINCAL ? (fp64 ? "lincal_fp64" : "lincal_fp32") : "omnical";
+    const char *name = o.solver == GC_LINCAL ? (fp64 ? "lincal_fp64" : "lincal_fp32")
+                       : (o.solver == GC_LINCAL_CG ? "lincal_cg" : "omnical");
     int rec = gc_prof_begin(ctx, s, name);
     if (o.solver == GC_LINCAL) {
         if (fp64) lincal_kernel<double><<<grid, kCThreads, 0, s>>>(p);
         else lincal_kernel<float><<<grid, kCThreads, 0, s>>>(p);
+    } else if (o.solver == GC_LINCAL_CG) {
+        lincal_cg_kernel<<<grid, kCThreads, 0, s>>>(p, 1e-4, 500);
     } else {
         omnical_kernel<<<grid, kCThreads, 0, s>>>(p);
     }

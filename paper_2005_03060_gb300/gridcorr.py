@@ -68,6 +68,8 @@ _lib.gc_reduce.argtypes = [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp]
 _lib.gc_reduce.restype = _i
 _lib.gc_calibrate.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.gc_calibrate.restype = _i
+_lib.gc_peak_probe.argtypes = [_vp, _i, ctypes.POINTER(ctypes.c_double)]
+_lib.gc_peak_probe.restype = _i
 _lib.gc_quantize.argtypes = [_vp, _vp, _i, _i, _i, _vp, _vp, _vp]
 _lib.gc_quantize.restype = _i
 
@@ -134,6 +136,12 @@ class Context:
             out[nm] = (ms[k], cnt[k])
         return out
 
+    def peak_probe(self, kind: str) -> float:
+        """Measured FMA throughput in TFLOP/s ('fp32' or 'fp64')."""
+        v = ctypes.c_double()
+        self.check(_lib.gc_peak_probe(self._h, 0 if kind == "fp32" else 1, ctypes.byref(v)))
+        return v.value
+
     # ------------------------------------------------------------------ correlate
     def correlate(self, volt: torch.Tensor, gains: torch.Tensor, L: int | None = None,
                   out: torch.Tensor | None = None) -> torch.Tensor:
@@ -195,7 +203,7 @@ class Context:
         gains = gains if gains is not None else torch.empty(C, N, dtype=torch.complex64, device=dev)
         vmodel = vmodel if vmodel is not None else torch.empty(C, sel.n_ubl, dtype=torch.complex64, device=dev)
         stats = stats if stats is not None else torch.empty(C, 32, dtype=torch.uint8, device=dev)
-        o = CalOpts(GC_LINCAL if solver == "lincal" else GC_OMNICAL,
+        o = CalOpts({"lincal": GC_LINCAL, "omnical": GC_OMNICAL, "lincal_cg": GC_LINCAL_CG}[solver],
                     GC_FP64 if precision == "fp64" else GC_FP32, max_iter, 1 if warm_start else 0,
                     tol, damping, time_limit_ms, 0)
         self.check(_lib.gc_calibrate(self._h, _vp(vred.data_ptr()), vfmt, sel.handle, C,
@@ -217,7 +225,7 @@ class Context:
         return out, scales
 
 
-GC_LINCAL, GC_OMNICAL = 0, 1
+GC_LINCAL, GC_OMNICAL, GC_LINCAL_CG = 0, 1, 2
 GC_FP64, GC_FP32 = 0, 1
 
 

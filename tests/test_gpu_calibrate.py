@@ -48,7 +48,10 @@ def rel_err(a, b):
     return float(np.max(np.abs(a - b) / np.abs(b)))
 
 
-@pytest.mark.parametrize("solver,precision", [("lincal", "fp64"), ("lincal", "fp32"), ("omnical", "fp32")])
+SOLVERS = [("lincal", "fp64"), ("lincal", "fp32"), ("lincal_cg", "fp32"), ("omnical", "fp32")]
+
+
+@pytest.mark.parametrize("solver,precision", SOLVERS)
 def test_noise_free_recovers_injected_gains(gc, ctx, solver, precision):
     """One noise-free point source is exactly redundant: the injected gains
     come back up to the four degeneracies (Sec. 5.2)."""
@@ -67,7 +70,7 @@ def test_noise_free_recovers_injected_gains(gc, ctx, solver, precision):
         assert rel_err(gf, gt) < GTOL
 
 
-@pytest.mark.parametrize("solver,precision", [("lincal", "fp64"), ("lincal", "fp32"), ("omnical", "fp32")])
+@pytest.mark.parametrize("solver,precision", SOLVERS)
 def test_tiny_config_matches_oracle(gc, ctx, orc, solver, precision):
     """8x8 grid, 32 channels, 256 samples, 20 sources, subset selection."""
     L, C, T = 8, 32, 256
@@ -90,12 +93,13 @@ def test_tiny_config_matches_oracle(gc, ctx, orc, solver, precision):
     assert 0.7 < float(np.median(stats["chi2r"])) < 1.4
 
 
-def test_lowcad_omnical_matches_oracle(gc, ctx, orc):
+@pytest.mark.parametrize("solver", ["omnical", "lincal_cg"])
+def test_lowcad_matches_oracle(gc, ctx, orc, solver):
     L, C, T = 6, 4, 400
     volt, gains, _ = synth.make_voltages(3, L, C, T, n_src=20)
     sel = gc.Selection("lowcad", L, T)
     vr, au = ctx.reduce(volt.cuda(), sel)
-    g, V, st = ctx.calibrate(vr, sel, au, solver="omnical")
+    g, V, st = ctx.calibrate(vr, sel, au, solver=solver)
     ctx.device_status()
     stats = gc.decode_stats(st)
     assert np.all(stats["status"] == gc.GC_OK), stats["status"]
@@ -155,18 +159,20 @@ def test_time_limit_reports_timeout(gc, ctx):
 
 def test_paper_scale_channel_matches_oracle(gc, ctx, orc):
     """32x32 grid, 256 channels, 4096 samples, 200 sources: the full GPU run
-    (the benchmark's configuration) against the oracle on one channel."""
+    (the benchmark's configuration, every solver) against the oracle on one
+    channel."""
     L, C, T = 32, 256, 4096
     sel = gc.Selection("subset", L, T)
     volt = torch.empty(C, T, L * L, dtype=torch.complex64, device="cuda")
     volt, gains, _ = synth.make_voltages(2, L, C, T, n_src=200, device="cuda", out=volt)
     vr, au = ctx.reduce(volt, sel)
-    g, V, st = ctx.calibrate(vr, sel, au)
-    ctx.device_status()
-    stats = gc.decode_stats(st)
-    assert np.all(stats["status"] == gc.GC_OK)
     c = 77
     gr, _, _, _ = oracle_gains(orc, volt[c].cpu().numpy().astype(np.complex128), "subset", L, T)
-    assert rel_err(g[c].cpu().numpy().astype(np.complex128), gr) < GTOL
+    for solver, precision in SOLVERS:
+        g, V, st = ctx.calibrate(vr, sel, au, solver=solver, precision=precision)
+        ctx.device_status()
+        stats = gc.decode_stats(st)
+        assert np.all(stats["status"] == gc.GC_OK), solver
+        assert rel_err(g[c].cpu().numpy().astype(np.complex128), gr) < GTOL, solver
     del volt
     torch.cuda.empty_cache()
