@@ -250,6 +250,28 @@ GC_API gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, const
                               gc_calstats *stats, void *stream);
 
 /*
+ * chi^2 of the redundant model and its adjoint (numerator of Eq. redchi;
+ * the differentiable form of the calibration objective).
+ *
+ *   chi2[c] = sum_p w_p |V_p - g_i conj(g_j) V_alpha(p)|^2,  V_p = S_p / t_p
+ *
+ *   vreduced  gc_reduce output for `sel`; gains [C][L*L] c64; vmodel
+ *   [C][n_ubl] c64; weights [C][P] float or NULL (uniform); chi2 [C] double.
+ * gc_chi2_backward writes, scaled by grad_out[c] (dL/dchi2_c; NULL = 1):
+ *   grad_gains[c][k]  = dchi2/dRe g_k + i dchi2/dIm g_k
+ *                     = -2 [sum_{i_p=k} w r g_j conj(V) + sum_{j_p=k} w conj(r) g_i V]
+ *   grad_vmodel[c][a] = -2 sum_{p in a} w r conj(g_i) g_j
+ * recomputing the residuals from (gains, vmodel).  FP32 products, FP64 sums.
+ */
+GC_API gc_status gc_chi2(gc_ctx *ctx, const void *vreduced, int vfmt, const gc_sel *sel, int C,
+                         const float *gains, const float *vmodel, const float *weights, double *chi2,
+                         void *stream);
+GC_API gc_status gc_chi2_backward(gc_ctx *ctx, const void *vreduced, int vfmt, const gc_sel *sel,
+                                  int C, const float *gains, const float *vmodel,
+                                  const float *weights, const double *grad_out, float *grad_gains,
+                                  float *grad_vmodel, void *stream);
+
+/*
  * FFT-correlator that allocates no device memory.  The paper has no
  * counterpart: this is an interface for callers that cannot call cudaMalloc
  * -- for example a real-time correlator process whose device memory is

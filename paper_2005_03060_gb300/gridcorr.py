@@ -70,6 +70,10 @@ _lib.gc_calibrate.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _v
 _lib.gc_calibrate.restype = _i
 _lib.gc_peak_probe.argtypes = [_vp, _i, ctypes.POINTER(ctypes.c_double)]
 _lib.gc_peak_probe.restype = _i
+_lib.gc_chi2.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp]
+_lib.gc_chi2.restype = _i
+_lib.gc_chi2_backward.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.gc_chi2_backward.restype = _i
 _lib.gc_quantize.argtypes = [_vp, _vp, _i, _i, _i, _vp, _vp, _vp]
 _lib.gc_quantize.restype = _i
 
@@ -212,6 +216,32 @@ class Context:
                                      _vp(stats.data_ptr()), _vp(_stream_ptr(dev))))
         return gains, vmodel, stats
 
+    # ------------------------------------------------------------------ chi^2 and adjoint
+    def chi2(self, vred, sel, gains, vmodel, weights=None, out=None):
+        """chi^2 per channel (float64 [C])."""
+        vfmt = GC_C64 if vred.dtype == torch.complex64 else GC_I4C
+        C = vred.shape[0]
+        out = out if out is not None else torch.empty(C, dtype=torch.float64, device=vred.device)
+        self.check(_lib.gc_chi2(self._h, _vp(vred.data_ptr()), vfmt, sel.handle, C,
+                                _vp(gains.data_ptr()), _vp(vmodel.data_ptr()),
+                                _vp(weights.data_ptr() if weights is not None else None),
+                                _vp(out.data_ptr()), _vp(_stream_ptr(vred.device))))
+        return out
+
+    def chi2_backward(self, vred, sel, gains, vmodel, grad_out=None, weights=None):
+        vfmt = GC_C64 if vred.dtype == torch.complex64 else GC_I4C
+        C = vred.shape[0]
+        dg = torch.empty_like(gains)
+        dv = torch.empty_like(vmodel)
+        go = grad_out.contiguous().to(torch.float64) if grad_out is not None else None
+        self.check(_lib.gc_chi2_backward(self._h, _vp(vred.data_ptr()), vfmt, sel.handle, C,
+                                         _vp(gains.data_ptr()), _vp(vmodel.data_ptr()),
+                                         _vp(weights.data_ptr() if weights is not None else None),
+                                         _vp(go.data_ptr() if go is not None else None),
+                                         _vp(dg.data_ptr()), _vp(dv.data_ptr()),
+                                         _vp(_stream_ptr(vred.device))))
+        return dg, dv
+
     # ------------------------------------------------------------------ quantise
     def quantize(self, volt: torch.Tensor, out=None, scales=None):
         """4+4-bit bytes [C, T, N] uint8 and per-channel float scales [C]."""
@@ -285,6 +315,32 @@ class Selection:
             self.close()
         except Exception:
             pass
+
+
+class Chi2Function(torch.autograd.Function):
+    """chi^2 per channel as a differentiable function of the complex gains
+    [C, N] and model visibilities [C, n_ubl] (complex64), with the gradient
+    from the library's adjoint kernel.  Only (gains, vmodel) are saved: the
+    backward pass recomputes the residuals (checkpointing)."""
+
+    @staticmethod
+    def forward(fctx, gains, vmodel, vred, sel, ctx, weights=None):
+        g = gains.detach().contiguous()
+        v = vmodel.detach().contiguous()
+        fctx.save_for_backward(g, v)
+        fctx.vred, fctx.sel, fctx.gctx, fctx.weights = vred, sel, ctx, weights
+        return ctx.chi2(vred, sel, g, v, weights)
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        g, v = fctx.saved_tensors
+        dg, dv = fctx.gctx.chi2_backward(fctx.vred, fctx.sel, g, v, grad_out, fctx.weights)
+        return dg, dv, None, None, None, None
+
+
+def chi2(gains, vmodel, vred, sel, ctx=None, weights=None):
+    ctx = ctx or default_context(gains.device)
+    return Chi2Function.apply(gains, vmodel, vred, sel, ctx, weights)
 
 
 def decode_stats(stats: torch.Tensor):
