@@ -250,6 +250,41 @@ GC_API gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, const
                               gc_calstats *stats, void *stream);
 
 /*
+ * Batched calibration: several arrays of different size (each with its own
+ * selection, channel count and buffers, as for gc_calibrate) in one
+ * persistent launch.  CTAs take (array, channel) work items from a device
+ * counter, arrays ordered by decreasing cost (pairs + 4 N) unless the
+ * "cal.order" tuning knob is 1.  The solver is GC_LINCAL_CG (other solver
+ * fields of opts are ignored); results equal those of gc_calibrate with
+ * GC_LINCAL_CG.  At most 32 arrays.  Enqueues a memset and one kernel, so
+ * after a first call that has sized the workspace the call can be captured
+ * into a CUDA graph.
+ */
+typedef struct gc_batch_item {
+    const gc_sel *sel;
+    int C;
+    int vfmt;
+    const void *vreduced;
+    const void *autos;
+    float *gains;
+    float *vmodel;
+    gc_calstats *stats;
+} gc_batch_item;
+GC_API gc_status gc_calibrate_batched(gc_ctx *ctx, int n_arrays, const gc_batch_item *items,
+                                      const gc_calopts *opts, void *stream);
+
+/*
+ * Tuning knobs of a context (0 = automatic), set by the autotuner:
+ *   "fft.chunk_len"    time samples per FFT-correlator work item
+ *   "xeng.tsplit"      time slices per X-engine window
+ *   "cal.ctas_per_sm"  resident calibration CTAs per SM (cap)
+ *   "cal.order"        batched work order: 0 largest first, 1 as given
+ * GC_EINVAL for an unknown name or a negative value.
+ */
+GC_API gc_status gc_set_tuning(gc_ctx *ctx, const char *name, int value);
+GC_API gc_status gc_get_tuning(const gc_ctx *ctx, const char *name, int *value);
+
+/*
  * chi^2 of the redundant model and its adjoint (numerator of Eq. redchi;
  * the differentiable form of the calibration objective).
  *

@@ -1,0 +1,62 @@
+"""Autotuner for the launch shapes of the hot path.
+
+Times the candidate values of each tuning knob of a context (see
+gc_set_tuning in include/gridcorr.h) on the caller's own data with CUDA
+events, keeps the fastest, and sets it on the context.  Knobs only change
+how work is split into launches and items, never the arithmetic, so every
+candidate computes the same result (the FFT chunking changes the order of
+the FP32 time sums; the tests bound that).
+"""
+from __future__ import annotations
+
+import torch
+
+
+def _time(fn, reps: int = 3) -> float:
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _sweep(ctx, knob: str, values, fn, reps: int) -> dict:
+    timings = {}
+    for v in values:
+        ctx.set_tuning(knob, v)
+        timings[v] = _time(fn, reps)
+    best = min(timings, key=timings.get)
+    ctx.set_tuning(knob, best)
+    return {"knob": knob, "best": best, "ms": timings}
+
+
+def tune_correlator(ctx, volt, gains, L=None, reps: int = 3) -> dict:
+    out = torch.empty(volt.shape[0], 2 * (L or int(round(volt.shape[2] ** 0.5))) - 1,
+                      2 * (L or int(round(volt.shape[2] ** 0.5))) - 1, dtype=torch.complex64,
+                      device=volt.device)
+    return _sweep(ctx, "fft.chunk_len", [0, 128, 256, 512, 1024],
+                  lambda: ctx.correlate(volt, gains, L, out=out), reps)
+
+
+def tune_xengine(ctx, volt, sel, reps: int = 3) -> dict:
+    vr, au = ctx.reduce(volt, sel)
+    return _sweep(ctx, "xeng.tsplit", [0, 1, 2, 4, 8],
+                  lambda: ctx.reduce(volt, sel, out=vr, out_autos=au), reps)
+
+
+def tune_calibration(ctx, arrays, reps: int = 2) -> dict:
+    """arrays: as for Context.calibrate_batched (outputs are reused)."""
+    outs = ctx.calibrate_batched(arrays)
+    for a, (g, v, s) in zip(arrays, outs):
+        a.setdefault("gains", g)
+        a.setdefault("vmodel", v)
+        a.setdefault("stats", s)
+    res = {"order": _sweep(ctx, "cal.order", [0, 1], lambda: ctx.calibrate_batched(arrays), reps)}
+    res["ctas"] = _sweep(ctx, "cal.ctas_per_sm", [0, 1, 2, 3],
+                         lambda: ctx.calibrate_batched(arrays), reps)
+    return res

@@ -27,6 +27,7 @@
 // baseline-type.
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "gc_sel.h"
@@ -877,7 +878,6 @@ __device__ void cg_gather(const CalParams &p, const CgWork &w, float *out, const
     const int L = p.L, nu = p.n_ubl;
     for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
         const int xi = i % L, yi = i / L;
-        const float gix = w.xg[2 * i], giy = w.xg[2 * i + 1];
         float ox = 0.f, oy = 0.f, d = 0.f;
         for (int k = 0; k < nu; ++k) {
             const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
@@ -945,10 +945,10 @@ __device__ __forceinline__ float cg_prec(const CalParams &p, const CgWork &w, in
     return idx < w.n ? 1.f / (w.dg[idx >> 1] + mu) : 1.f / (w.dv[(idx - w.n) >> 1] + mu);
 }
 
-__global__ void __launch_bounds__(kCThreads) lincal_cg_kernel(const CalParams p, double cg_tol, int cg_max) {
-    __shared__ double red[32 * 14];
-    __shared__ float redf[32 * 14];
-    CgWork w = cg_layout(p, p.work + (size_t)blockIdx.x * p.work_per_cta);
+// One channel of matrix-free Gauss-Newton (used by the per-selection and the
+// batched kernels).  All threads of the CTA call it.
+__device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg_tol, int cg_max, double *red,
+                                 float *redf) {
     const int nm = w.n + w.m;
     GnWork<float> gw;   // view for the shared projection helper
     gw.xg = w.xg;
@@ -959,111 +959,151 @@ __global__ void __launch_bounds__(kCThreads) lincal_cg_kernel(const CalParams p,
     gw.delta = w.z;
     gw.n = w.n;
     gw.m = w.m;
-    for (int c = blockIdx.x; c < p.C; c += gridDim.x) {
-        const uint64_t t_start = gc_globaltimer();
-        if (p.warm) {
-            for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
-                const float2 g = p.gains[(size_t)c * p.N + i];
-                w.xg[2 * i] = g.x;
-                w.xg[2 * i + 1] = g.y;
-            }
-            for (int k = threadIdx.x; k < p.n_ubl; k += blockDim.x) {
-                const float2 v = p.vmodel[(size_t)c * p.n_ubl + k];
-                w.xv[2 * k] = v.x;
-                w.xv[2 * k + 1] = v.y;
-            }
-            __syncthreads();
-        } else {
-            start_point<float>(p, c, w.xg, w.xv, redf);
+    const uint64_t t_start = gc_globaltimer();
+    if (p.warm) {
+        for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
+            const float2 g = p.gains[(size_t)c * p.N + i];
+            w.xg[2 * i] = g.x;
+            w.xg[2 * i + 1] = g.y;
         }
-        int st = GC_ENOCONV, it;
-        for (it = 1; it <= p.max_iter; ++it) {
-            // residual, right-hand side J^T r and the Jacobi diagonals
-            const double chi2 = cg_pairs(p, c, w, nullptr, true, red);
-            cg_gather(p, w, w.b, nullptr, 0.f, true);
-            double dm[1] = {0.0};
-            for (int i = threadIdx.x; i < p.N; i += blockDim.x) dm[0] = fmax(dm[0], (double)w.dg[i]);
-            for (int o = 16; o > 0; o >>= 1) dm[0] = fmax(dm[0], __shfl_xor_sync(0xffffffffu, dm[0], o));
-            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dm[0];
-            __syncthreads();
-            double dmax = 0.0;
-            for (int u = 0; u < (int)(blockDim.x >> 5); ++u) dmax = fmax(dmax, red[u]);
-            __syncthreads();
-            const float mu = (float)(p.mu_rel * dmax);
-            // PCG from x = 0
-            double acc[2] = {0.0, 0.0};
+        for (int k = threadIdx.x; k < p.n_ubl; k += blockDim.x) {
+            const float2 v = p.vmodel[(size_t)c * p.n_ubl + k];
+            w.xv[2 * k] = v.x;
+            w.xv[2 * k + 1] = v.y;
+        }
+        __syncthreads();
+    } else {
+        start_point<float>(p, c, w.xg, w.xv, redf);
+    }
+    int st = GC_ENOCONV, it;
+    for (it = 1; it <= p.max_iter; ++it) {
+        // residual, right-hand side J^T r and the Jacobi diagonals
+        const double chi2 = cg_pairs(p, c, w, nullptr, true, red);
+        cg_gather(p, w, w.b, nullptr, 0.f, true);
+        double dm = 0.0;
+        for (int i = threadIdx.x; i < p.N; i += blockDim.x) dm = fmax(dm, (double)w.dg[i]);
+        for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dm;
+        __syncthreads();
+        double dmax = 0.0;
+        for (int u = 0; u < (int)(blockDim.x >> 5); ++u) dmax = fmax(dmax, red[u]);
+        __syncthreads();
+        const float mu = (float)(p.mu_rel * dmax);
+        // PCG from x = 0
+        double acc[2] = {0.0, 0.0};
+        for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+            const float bi = w.b[i];
+            const float zi = bi * cg_prec(p, w, i, mu);
+            w.x[i] = 0.f;
+            w.r[i] = bi;
+            w.z[i] = zi;
+            w.pp[i] = zi;
+            acc[0] += (double)bi * zi;
+            acc[1] += (double)bi * bi;
+        }
+        block_sum<double, 2>(acc, red);
+        double rz = acc[0];
+        const double bnorm2 = acc[1];
+        for (int k = 0; k < cg_max && bnorm2 > 0.0; ++k) {
+            cg_pairs(p, c, w, w.pp, false, red);
+            cg_gather(p, w, w.q, w.pp, mu, false);
+            double pq[1] = {0.0};
+            for (int i = threadIdx.x; i < nm; i += blockDim.x) pq[0] += (double)w.pp[i] * w.q[i];
+            block_sum<double, 1>(pq, red);
+            if (!(pq[0] > 0.0)) break;
+            const float alpha = (float)(rz / pq[0]);
+            double a2[2] = {0.0, 0.0};
             for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-                const float bi = w.b[i];
-                const float zi = bi * cg_prec(p, w, i, mu);
-                w.x[i] = 0.f;
-                w.r[i] = bi;
+                w.x[i] += alpha * w.pp[i];
+                const float ri = w.r[i] - alpha * w.q[i];
+                w.r[i] = ri;
+                const float zi = ri * cg_prec(p, w, i, mu);
                 w.z[i] = zi;
-                w.pp[i] = zi;
-                acc[0] += (double)bi * zi;
-                acc[1] += (double)bi * bi;
+                a2[0] += (double)ri * zi;
+                a2[1] += (double)ri * ri;
             }
-            block_sum<double, 2>(acc, red);
-            double rz = acc[0];
-            const double bnorm2 = acc[1];
-            for (int k = 0; k < cg_max && bnorm2 > 0.0; ++k) {
-                cg_pairs(p, c, w, w.pp, false, red);
-                cg_gather(p, w, w.q, w.pp, mu, false);
-                double pq[1] = {0.0};
-                for (int i = threadIdx.x; i < nm; i += blockDim.x) pq[0] += (double)w.pp[i] * w.q[i];
-                block_sum<double, 1>(pq, red);
-                if (!(pq[0] > 0.0)) break;
-                const float alpha = (float)(rz / pq[0]);
-                double a2[2] = {0.0, 0.0};
-                for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-                    w.x[i] += alpha * w.pp[i];
-                    const float ri = w.r[i] - alpha * w.q[i];
-                    w.r[i] = ri;
-                    const float zi = ri * cg_prec(p, w, i, mu);
-                    w.z[i] = zi;
-                    a2[0] += (double)ri * zi;
-                    a2[1] += (double)ri * ri;
-                }
-                block_sum<double, 2>(a2, red);
-                if (a2[1] <= cg_tol * cg_tol * bnorm2) break;
-                const float beta = (float)(a2[0] / rz);
-                rz = a2[0];
-                for (int i = threadIdx.x; i < nm; i += blockDim.x) w.pp[i] = w.z[i] + beta * w.pp[i];
-                __syncthreads();
-            }
-            // project out the degeneracies (delta lands in w.z), line search, update
-            gn_project<float>(p, gw, redf);
-            double nr[2] = {0.0, 0.0};
-            for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-                const float x = i < w.n ? w.xg[i] : w.xv[i - w.n];
-                nr[0] += (double)x * x;
-                nr[1] += (double)w.z[i] * w.z[i];
-            }
-            block_sum<double, 2>(nr, red);
-            float step = 1.f;
-            for (int ls = 0; ls < 8; ++ls) {
-                for (int i = threadIdx.x; i < nm; i += blockDim.x)
-                    w.trial[i] = (i < w.n ? w.xg[i] : w.xv[i - w.n]) + step * w.z[i];
-                __syncthreads();
-                const float c2 = chi2_of<float>(p, c, w.trial, w.trial + w.n, redf);
-                if ((double)c2 <= chi2 * (1.0 + 1e-6) + 1e-30 || ls == 7) break;
-                step *= 0.5f;
-            }
-            for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-                if (i < w.n) w.xg[i] = w.trial[i];
-                else w.xv[i - w.n] = w.trial[i];
-            }
+            block_sum<double, 2>(a2, red);
+            if (a2[1] <= cg_tol * cg_tol * bnorm2) break;
+            const float beta = (float)(a2[0] / rz);
+            rz = a2[0];
+            for (int i = threadIdx.x; i < nm; i += blockDim.x) w.pp[i] = w.z[i] + beta * w.pp[i];
             __syncthreads();
-            if ((double)step * sqrt(nr[1]) <= p.tol * sqrt(nr[0])) {
-                st = GC_OK;
-                break;
-            }
-            if (gc_globaltimer() - t_start > p.deadline_ns) {
-                st = GC_ETIMEOUT;
-                if (threadIdx.x == 0) atomicOr(p.status, GC_DEV_TIMEOUT_CAL);
-                break;
-            }
         }
-        finish_channel<float>(p, c, w.xg, w.xv, min(it, p.max_iter), st, red);
+        // project out the degeneracies (delta lands in w.z), line search, update
+        gn_project<float>(p, gw, redf);
+        double nr[2] = {0.0, 0.0};
+        for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+            const float x = i < w.n ? w.xg[i] : w.xv[i - w.n];
+            nr[0] += (double)x * x;
+            nr[1] += (double)w.z[i] * w.z[i];
+        }
+        block_sum<double, 2>(nr, red);
+        float step = 1.f;
+        for (int ls = 0; ls < 8; ++ls) {
+            for (int i = threadIdx.x; i < nm; i += blockDim.x)
+                w.trial[i] = (i < w.n ? w.xg[i] : w.xv[i - w.n]) + step * w.z[i];
+            __syncthreads();
+            const float c2 = chi2_of<float>(p, c, w.trial, w.trial + w.n, redf);
+            if ((double)c2 <= chi2 * (1.0 + 1e-6) + 1e-30 || ls == 7) break;
+            step *= 0.5f;
+        }
+        for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+            if (i < w.n) w.xg[i] = w.trial[i];
+            else w.xv[i - w.n] = w.trial[i];
+        }
+        __syncthreads();
+        if ((double)step * sqrt(nr[1]) <= p.tol * sqrt(nr[0])) {
+            st = GC_OK;
+            break;
+        }
+        if (gc_globaltimer() - t_start > p.deadline_ns) {
+            st = GC_ETIMEOUT;
+            if (threadIdx.x == 0) atomicOr(p.status, GC_DEV_TIMEOUT_CAL);
+            break;
+        }
+    }
+    finish_channel<float>(p, c, w.xg, w.xv, min(it, p.max_iter), st, red);
+}
+
+__global__ void __launch_bounds__(kCThreads) lincal_cg_kernel(const CalParams p, double cg_tol, int cg_max) {
+    __shared__ double red[32 * 14];
+    __shared__ float redf[32 * 14];
+    CgWork w = cg_layout(p, p.work + (size_t)blockIdx.x * p.work_per_cta);
+    for (int c = blockIdx.x; c < p.C; c += gridDim.x) cg_solve_channel(p, c, w, cg_tol, cg_max, red, redf);
+}
+
+// Several arrays of different size in one persistent launch: CTAs take
+// (array, channel) items from a device counter, arrays in `order`
+// (largest first by default) so that long solves start early.
+constexpr int kMaxBatch = 32;
+struct BatchParams {
+    CalParams arr[kMaxBatch];
+    int order[kMaxBatch];
+    int prefix[kMaxBatch + 1];   // channel-count prefix sums in processing order
+    int n_arr, total;
+    unsigned int *counter;
+    char *work;
+    size_t work_per_cta;
+    double cg_tol;
+    int cg_max;
+};
+
+__global__ void __launch_bounds__(kCThreads) lincal_cg_batched(const __grid_constant__ BatchParams bp) {
+    __shared__ double red[32 * 14];
+    __shared__ float redf[32 * 14];
+    __shared__ int s_item;
+    char *base = bp.work + (size_t)blockIdx.x * bp.work_per_cta;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(bp.counter, 1u);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= bp.total) break;
+        int slot = 0;
+        while (slot + 1 < bp.n_arr && bp.prefix[slot + 1] <= item) ++slot;
+        const CalParams &p = bp.arr[bp.order[slot]];
+        CgWork w = cg_layout(p, base);
+        cg_solve_channel(p, item - bp.prefix[slot], w, bp.cg_tol, bp.cg_max, red, redf);
     }
 }
 
@@ -1178,27 +1218,12 @@ __global__ void __launch_bounds__(kCThreads) omnical_kernel(const CalParams p) {
 
 }  // namespace
 
-extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, const gc_sel *csel, int C,
-                                  const void *autos, const gc_calopts *opts, float *gains, float *vmodel,
-                                  gc_calstats *stats, void *stream) {
-    if (!ctx) return GC_EINVAL;
-    ctx->last_error.clear();
-    gc_sel *sel = const_cast<gc_sel *>(csel);
+static gc_status fill_params(gc_ctx *ctx, gc_sel *sel, int C, const void *vreduced, int vfmt, const void *autos,
+                             const gc_calopts &o, float *gains, float *vmodel, gc_calstats *stats, CalParams &p) {
     if (!vreduced || !sel || !gains || !vmodel || !stats || C < 1)
         return gc_fail(ctx, GC_EINVAL, "gc_calibrate: null argument");
     if (vfmt != GC_C64 && vfmt != GC_I4C) return gc_fail(ctx, GC_EINVAL, "gc_calibrate: unknown format");
     if (sel->null_dim != 4) return gc_fail(ctx, GC_EDEGEN, "gc_calibrate: selection has extra degeneracies");
-    gc_calopts o;
-    if (opts) o = *opts;
-    else {
-        o.solver = GC_LINCAL;
-        o.precision = GC_FP64;
-        o.max_iter = 0;
-        o.tol = 0.0;
-        o.damping = 0.3;
-        o.warm_start = 0;
-        o.time_limit_ms = 0;
-    }
     if (o.solver != GC_LINCAL && o.solver != GC_OMNICAL && o.solver != GC_LINCAL_CG)
         return gc_fail(ctx, GC_EINVAL, "gc_calibrate: solver");
     if (o.precision != GC_FP64 && o.precision != GC_FP32) return gc_fail(ctx, GC_EINVAL, "gc_calibrate: precision");
@@ -1211,12 +1236,8 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
         D = std::max(D, std::abs(dy * sel->L + dx));
     }
     if (ax < 0 || ay < 0) return gc_fail(ctx, GC_EDEGEN, "gc_calibrate: the selection lacks the axis types");
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaSetDevice");
     gc_status st = gc_sel_upload(ctx, sel);
     if (st != GC_OK) return st;
-
-    CalParams p;
     p.vred = vreduced;
     p.vfmt = vfmt;
     p.autos = autos;
@@ -1244,19 +1265,50 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
     p.status = ctx->status_dev;
     p.deadline_ns = (unsigned long long)(o.time_limit_ms > 0 ? o.time_limit_ms : 10000) * 1000000ull;
     p.bw = 2 * D + 1;
-    const bool fp64 = o.precision == GC_FP64;
-    const bool fp64_ne = o.solver == GC_LINCAL && fp64;
+    const bool fp64_ne = o.solver == GC_LINCAL && o.precision == GC_FP64;
     p.tol = o.tol > 0.0 ? o.tol : (fp64_ne ? 1e-10 : 1e-6);
     p.max_iter = o.max_iter > 0 ? o.max_iter : (o.solver == GC_OMNICAL ? 20000 : 50);
     p.mu_rel = fp64_ne ? 1e-12 : 1e-7;
+    p.work = nullptr;
+    p.work_per_cta = 0;
+    return GC_OK;
+}
 
+static gc_calopts default_opts(const gc_calopts *opts) {
+    gc_calopts o;
+    if (opts) return *opts;
+    o.solver = GC_LINCAL;
+    o.precision = GC_FP64;
+    o.max_iter = 0;
+    o.tol = 0.0;
+    o.damping = 0.3;
+    o.warm_start = 0;
+    o.time_limit_ms = 0;
+    o.reserved = 0;
+    return o;
+}
+
+extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, const gc_sel *csel, int C,
+                                  const void *autos, const gc_calopts *opts, float *gains, float *vmodel,
+                                  gc_calstats *stats, void *stream) {
+    if (!ctx) return GC_EINVAL;
+    ctx->last_error.clear();
+    gc_sel *sel = const_cast<gc_sel *>(csel);
+    const gc_calopts o = default_opts(opts);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaSetDevice");
+    CalParams p;
+    gc_status st = fill_params(ctx, sel, C, vreduced, vfmt, autos, o, gains, vmodel, stats, p);
+    if (st != GC_OK) return st;
+    const bool fp64 = o.precision == GC_FP64;
     int occ = 0;
     size_t per_cta;
     const void *kfn;
     if (o.solver == GC_LINCAL) {
         if (sel->n_ubl > kMaxUbl)
             return gc_fail(ctx, GC_EUNSUPPORTED,
-                           "gc_calibrate: lincal supports up to 64 baseline-types (use omnical for low-cadence)");
+                           "gc_calibrate: banded lincal supports up to 64 baseline-types "
+                           "(use GC_LINCAL_CG or omnical for low-cadence)");
         per_cta = fp64 ? gn_bytes<double>(p.N, p.n_ubl, p.bw) : gn_bytes<float>(p.N, p.n_ubl, p.bw);
         kfn = fp64 ? (const void *)lincal_kernel<double> : (const void *)lincal_kernel<float>;
     } else if (o.solver == GC_LINCAL_CG) {
@@ -1269,6 +1321,7 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
     per_cta = (per_cta + 255) & ~size_t(255);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kCThreads, 0);
     if (e != cudaSuccess || occ < 1) return gc_cuda_fail(ctx, e, "occupancy(calibration)");
+    if (ctx->tune[GC_TUNE_CAL_CTAS] > 0) occ = std::min(occ, ctx->tune[GC_TUNE_CAL_CTAS]);
     const int grid = std::min(C, occ * ctx->sm_count);
     st = gc_scratch_reserve(ctx, per_cta * grid);
     if (st != GC_OK) return st;
@@ -1289,5 +1342,61 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
     gc_prof_end(ctx, s, rec);
     e = cudaGetLastError();
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch calibration");
+    return GC_OK;
+}
+
+extern "C" gc_status gc_calibrate_batched(gc_ctx *ctx, int n_arrays, const gc_batch_item *items,
+                                          const gc_calopts *opts, void *stream) {
+    if (!ctx) return GC_EINVAL;
+    ctx->last_error.clear();
+    if (n_arrays < 1 || n_arrays > kMaxBatch || !items)
+        return gc_fail(ctx, GC_EINVAL, "gc_calibrate_batched: need 1..32 arrays");
+    gc_calopts o = default_opts(opts);
+    o.solver = GC_LINCAL_CG;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaSetDevice");
+    BatchParams bp;
+    memset(&bp, 0, sizeof bp);
+    size_t per_cta = 0;
+    std::vector<std::pair<double, int>> cost;
+    for (int a = 0; a < n_arrays; ++a) {
+        const gc_batch_item &it = items[a];
+        gc_status st = fill_params(ctx, const_cast<gc_sel *>(it.sel), it.C, it.vreduced, it.vfmt, it.autos, o,
+                                   it.gains, it.vmodel, it.stats, bp.arr[a]);
+        if (st != GC_OK) return st;
+        per_cta = std::max(per_cta, cg_bytes(bp.arr[a].N, bp.arr[a].n_ubl, bp.arr[a].P));
+        cost.push_back({(double)bp.arr[a].P + 4.0 * bp.arr[a].N, a});
+    }
+    if (ctx->tune[GC_TUNE_CAL_ORDER] == 0)
+        std::stable_sort(cost.begin(), cost.end(), [](const std::pair<double, int> &x,
+                                                      const std::pair<double, int> &y) { return x.first > y.first; });
+    bp.n_arr = n_arrays;
+    bp.prefix[0] = 0;
+    for (int k = 0; k < n_arrays; ++k) {
+        bp.order[k] = cost[k].second;
+        bp.prefix[k + 1] = bp.prefix[k] + bp.arr[cost[k].second].C;
+    }
+    bp.total = bp.prefix[n_arrays];
+    bp.cg_tol = 1e-4;
+    bp.cg_max = 500;
+    per_cta = (per_cta + 255) & ~size_t(255);
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lincal_cg_batched, kCThreads, 0);
+    if (e != cudaSuccess || occ < 1) return gc_cuda_fail(ctx, e, "occupancy(batched calibration)");
+    if (ctx->tune[GC_TUNE_CAL_CTAS] > 0) occ = std::min(occ, ctx->tune[GC_TUNE_CAL_CTAS]);
+    const int grid = std::min(bp.total, occ * ctx->sm_count);
+    gc_status st = gc_scratch_reserve(ctx, 256 + per_cta * grid);
+    if (st != GC_OK) return st;
+    bp.counter = static_cast<unsigned int *>(ctx->scratch);
+    bp.work = static_cast<char *>(ctx->scratch) + 256;
+    bp.work_per_cta = per_cta;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    e = cudaMemsetAsync(bp.counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "reset work counter");
+    int rec = gc_prof_begin(ctx, s, "lincal_cg_batched");
+    lincal_cg_batched<<<grid, kCThreads, 0, s>>>(bp);
+    gc_prof_end(ctx, s, rec);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch batched calibration");
     return GC_OK;
 }

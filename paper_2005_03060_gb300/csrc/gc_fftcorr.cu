@@ -480,6 +480,10 @@ struct Launcher {
                 best_len = len;
             }
         }
+        if (ctx->tune[GC_TUNE_FFT_CHUNK] > 0) {
+            best_len = ((std::min(ctx->tune[GC_TUNE_FFT_CHUNK], 4096) + step - 1) / step) * step;
+            best_n = (T + best_len - 1) / best_len;
+        }
         Params p;
         p.volt = volt;
         p.gains = reinterpret_cast<const float2 *>(gains);

@@ -199,6 +199,28 @@ int gc_profile_read(gc_ctx *ctx, char *names, double *total_ms, int *launches, i
     return n;
 }
 
+static int tune_index(const char *name) {
+    if (!name) return -1;
+    static const char *names[GC_TUNE_N] = {"fft.chunk_len", "xeng.tsplit", "cal.ctas_per_sm", "cal.order"};
+    for (int k = 0; k < GC_TUNE_N; ++k)
+        if (strcmp(name, names[k]) == 0) return k;
+    return -1;
+}
+
+gc_status gc_set_tuning(gc_ctx *ctx, const char *name, int value) {
+    const int k = tune_index(name);
+    if (!ctx || k < 0 || value < 0) return GC_EINVAL;
+    ctx->tune[k] = value;
+    return GC_OK;
+}
+
+gc_status gc_get_tuning(const gc_ctx *ctx, const char *name, int *value) {
+    const int k = tune_index(name);
+    if (!ctx || k < 0 || !value) return GC_EINVAL;
+    *value = ctx->tune[k];
+    return GC_OK;
+}
+
 int gc_fft_size(int L) {
     if (L < 1 || L > 128) return 0;
     int M = 1;

@@ -245,6 +245,7 @@ extern "C" gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, i
     int max_win = 0;
     for (int g = 0; g < sel->n_groups; ++g) max_win = std::max(max_win, sel->grp_t1[g] - sel->grp_t0[g]);
     while (base_items * n_tsplit < 2L * slots && n_tsplit < 16 && max_win / (n_tsplit * 2) >= 64) n_tsplit *= 2;
+    if (ctx->tune[GC_TUNE_XENG_TSPLIT] > 0) n_tsplit = std::min(ctx->tune[GC_TUNE_XENG_TSPLIT], 64);
     const size_t part_bytes = (size_t)n_tsplit * C * sel->P * sizeof(float2);
     const size_t apart_bytes = autos ? (size_t)sel->n_windows * n_tsplit * C * N * sizeof(float) : 0;
     st = gc_scratch_reserve(ctx, part_bytes + apart_bytes + 512);

@@ -74,6 +74,12 @@ _lib.gc_chi2.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp]
 _lib.gc_chi2.restype = _i
 _lib.gc_chi2_backward.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.gc_chi2_backward.restype = _i
+_lib.gc_calibrate_batched.argtypes = [_vp, _i, _vp, _vp, _vp]
+_lib.gc_calibrate_batched.restype = _i
+_lib.gc_set_tuning.argtypes = [_vp, ctypes.c_char_p, _i]
+_lib.gc_set_tuning.restype = _i
+_lib.gc_get_tuning.argtypes = [_vp, ctypes.c_char_p, ctypes.POINTER(_i)]
+_lib.gc_get_tuning.restype = _i
 _lib.gc_quantize.argtypes = [_vp, _vp, _i, _i, _i, _vp, _vp, _vp]
 _lib.gc_quantize.restype = _i
 
@@ -216,6 +222,42 @@ class Context:
                                      _vp(stats.data_ptr()), _vp(_stream_ptr(dev))))
         return gains, vmodel, stats
 
+    def calibrate_batched(self, arrays, max_iter: int = 0, tol: float = 0.0, time_limit_ms: int = 0):
+        """One persistent launch over several arrays.  `arrays` is a list of
+        dicts with keys vred, sel and optionally autos, gains, vmodel, stats
+        (outputs are allocated when missing).  Returns the list of
+        (gains, vmodel, stats) tuples."""
+        outs = []
+        items = (BatchItem * len(arrays))()
+        for k, a in enumerate(arrays):
+            vred, sel = a["vred"], a["sel"]
+            C = vred.shape[0]
+            dev = vred.device
+            g = a.get("gains")
+            g = g if g is not None else torch.empty(C, sel.L * sel.L, dtype=torch.complex64, device=dev)
+            v = a.get("vmodel")
+            v = v if v is not None else torch.empty(C, sel.n_ubl, dtype=torch.complex64, device=dev)
+            st = a.get("stats")
+            st = st if st is not None else torch.empty(C, 32, dtype=torch.uint8, device=dev)
+            au = a.get("autos")
+            items[k] = BatchItem(sel.handle.value if isinstance(sel.handle, _vp) else sel.handle, C,
+                                 GC_C64 if vred.dtype == torch.complex64 else GC_I4C, vred.data_ptr(),
+                                 au.data_ptr() if au is not None else None, g.data_ptr(), v.data_ptr(),
+                                 st.data_ptr())
+            outs.append((g, v, st))
+        o = CalOpts(GC_LINCAL_CG, GC_FP32, max_iter, 0, tol, 0.0, time_limit_ms, 0)
+        self.check(_lib.gc_calibrate_batched(self._h, len(arrays), ctypes.cast(items, _vp), ctypes.byref(o),
+                                             _vp(_stream_ptr(arrays[0]["vred"].device))))
+        return outs
+
+    def set_tuning(self, name: str, value: int):
+        self.check(_lib.gc_set_tuning(self._h, name.encode(), int(value)))
+
+    def get_tuning(self, name: str) -> int:
+        v = _i()
+        self.check(_lib.gc_get_tuning(self._h, name.encode(), ctypes.byref(v)))
+        return v.value
+
     # ------------------------------------------------------------------ chi^2 and adjoint
     def chi2(self, vred, sel, gains, vmodel, weights=None, out=None):
         """chi^2 per channel (float64 [C])."""
@@ -263,6 +305,12 @@ class CalOpts(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("tol", ctypes.c_double), ("damping", ctypes.c_double),
                 ("time_limit_ms", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("sel", ctypes.c_void_p), ("C", ctypes.c_int), ("vfmt", ctypes.c_int),
+                ("vreduced", ctypes.c_void_p), ("autos", ctypes.c_void_p), ("gains", ctypes.c_void_p),
+                ("vmodel", ctypes.c_void_p), ("stats", ctypes.c_void_p)]
 
 
 STATS_DTYPE = [("chi2", "<f8"), ("chi2r", "<f8"), ("dof", "<i4"), ("iters", "<i4"),

@@ -112,3 +112,39 @@ def make_voltages(seed: int, L: int, C: int, T: int, n_src: int, snr: float = 10
 def complex_to_interleaved(z: torch.Tensor) -> torch.Tensor:
     """complex64 [...] -> float32 [..., 2] view (re, im) without copying."""
     return torch.view_as_real(z)
+
+
+def make_visibilities(seed: int, L: int, C: int, pair_i, pair_j, pair_type, n_ubl: int, t_pair,
+                      snr: float = 10.0, amp_sigma: float = 0.05, device="cpu"):
+    """Visibility-level draw in the manner of the paper's own simulations
+    (Sec. 3): true visibilities of random amplitude, uncorrelated between
+    baseline-types and constant in time; gains with ~5 % amplitude scatter and
+    random phases; complex Gaussian noise at the given per-visibility SNR,
+    reduced by sqrt(t_p) for a pair integrated over t_p samples.
+
+    Returns (sums [C, P] complex64 = t_p * V_p, gains [C, N], vtrue [C, n_ubl])
+    so that the sums stand where the X-engine output would.
+    """
+    N = L * L
+    pi = torch.as_tensor(pair_i, dtype=torch.long, device=device)
+    pj = torch.as_tensor(pair_j, dtype=torch.long, device=device)
+    pt = torch.as_tensor(pair_type, dtype=torch.long, device=device)
+    tp = torch.as_tensor(t_pair, dtype=torch.float64, device=device)
+    P = pi.numel()
+    gains = make_gains(seed, C, N, device, amp_sigma)
+    out = torch.empty(C, P, dtype=torch.complex64, device=device)
+    vt = torch.empty(C, n_ubl, dtype=torch.complex64, device=device)
+    for c in range(C):
+        g = _gen(device, seed, c, 4)
+        amp = 0.5 + torch.rand(n_ubl, generator=g, device=device, dtype=torch.float64)
+        ph = (torch.rand(n_ubl, generator=g, device=device, dtype=torch.float64) * 2 - 1) * math.pi
+        V = torch.polar(amp, ph)
+        gc = gains[c].to(torch.complex128)
+        m = gc[pi] * gc[pj].conj() * V[pt]
+        sig = amp[pt] / snr / torch.sqrt(tp)
+        nre = torch.randn(P, generator=g, device=device, dtype=torch.float64)
+        nim = torch.randn(P, generator=g, device=device, dtype=torch.float64)
+        noise = torch.complex(nre, nim) * (sig / math.sqrt(2.0))
+        out[c] = ((m + noise) * tp).to(torch.complex64)
+        vt[c] = V.to(torch.complex64)
+    return out, gains, vt

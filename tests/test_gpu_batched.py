@@ -1,0 +1,110 @@
+"""Batched calibration of heterogeneous arrays (one persistent launch), its
+CUDA-graph capture and the autotuner.
+
+Inputs are the paper's own visibility-level simulation (Sec. 3) on the
+selections of arrays of different size.  The batched launch must give the
+same gains as a separate gc_calibrate(GC_LINCAL_CG) per array, and the
+small arrays must match the FP64 oracle (1e-3 on gains)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import calib as oc
+from oracle import select as osel
+from paper_2005_03060_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+GRIDS = [8, 12, 16, 24, 32, 40, 48, 64, 80, 96, 112, 128]
+
+
+@pytest.fixture(scope="module")
+def gc():
+    from paper_2005_03060_gb300 import gridcorr
+    return gridcorr
+
+
+@pytest.fixture(scope="module")
+def ctx(gc):
+    return gc.Context(0)
+
+
+def _arrays(gc, grids, chans, T=2048, seed=40):
+    arrays, truth = [], []
+    for k, (L, C) in enumerate(zip(grids, chans)):
+        sel = gc.Selection("subset", L, T)
+        pt = sel.pair_type()
+        tp = (sel.win_t1 - sel.win_t0)[pt]
+        s, g, v = synth.make_visibilities(seed + k, L, C, sel.pair_i, sel.pair_j, pt, sel.n_ubl, tp,
+                                          snr=10.0, device="cuda")
+        arrays.append({"vred": s.contiguous(), "sel": sel})
+        truth.append((g, v))
+    return arrays, truth
+
+
+def test_batched_equals_per_array(gc, ctx):
+    chans = [6, 5, 4, 4, 3, 3, 2, 2, 2, 1, 1, 1]
+    arrays, _ = _arrays(gc, GRIDS, chans)
+    outs = ctx.calibrate_batched(arrays)
+    ctx.device_status()
+    for a, (g, v, st) in zip(arrays, outs):
+        stats = gc.decode_stats(st)
+        assert np.all(stats["status"] == gc.GC_OK), (a["sel"].L, stats["status"])
+        g1, v1, st1 = ctx.calibrate(a["vred"], a["sel"], solver="lincal_cg")
+        ctx.device_status()
+        d = ((g - g1).abs() / g1.abs()).max().item()
+        assert d < 1e-5, (a["sel"].L, d)
+
+
+def test_batched_small_arrays_match_oracle(gc, ctx):
+    arrays, _ = _arrays(gc, [8, 12], [3, 2], T=1024, seed=7)
+    outs = ctx.calibrate_batched(arrays)
+    ctx.device_status()
+    for a, (g, v, st) in zip(arrays, outs):
+        L = a["sel"].L
+        osl = osel.subset(L, 1024)
+        pt = osl.pair_type()
+        t = (osl.win_t1 - osl.win_t0)[pt]
+        S = a["vred"].cpu().numpy().astype(np.complex128)
+        for c in range(S.shape[0]):
+            gr, Vr, it, ok = oc.calibrate(S[c] / t, osl.pair_i, osl.pair_j, pt, osl.types, L, "lincal")
+            assert ok
+            ge = g[c].cpu().numpy().astype(np.complex128)
+            assert np.max(np.abs(ge - gr) / np.abs(gr)) < 1e-3
+
+
+def test_batched_graph_capture_replays(gc, ctx):
+    arrays, _ = _arrays(gc, [8, 16, 32], [4, 3, 2], seed=90)
+    outs = ctx.calibrate_batched(arrays)          # sizes the workspace, uploads selections
+    torch.cuda.synchronize()
+    ref = [g.clone() for g, _, _ in outs]
+    for a, (g, v, st) in zip(arrays, outs):
+        a["gains"], a["vmodel"], a["stats"] = g, v, st
+        g.zero_()
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        ctx.calibrate_batched(arrays)
+    graph.replay()
+    torch.cuda.synchronize()
+    ctx.device_status()
+    for r, a in zip(ref, arrays):
+        assert torch.equal(r, a["gains"])
+
+
+def test_autotuner_sets_knobs(gc, ctx):
+    from paper_2005_03060_gb300 import autotune
+    arrays, _ = _arrays(gc, [8, 16], [4, 2], seed=11)
+    res = autotune.tune_calibration(ctx, arrays, reps=1)
+    assert ctx.get_tuning("cal.order") == res["order"]["best"]
+    assert ctx.get_tuning("cal.ctas_per_sm") == res["ctas"]["best"]
+    L, C, T = 16, 4, 512
+    volt, gains, _ = synth.make_voltages(4, L, C, T, n_src=10, device="cuda")
+    r = autotune.tune_correlator(ctx, volt, gains, reps=1)
+    assert ctx.get_tuning("fft.chunk_len") == r["best"]
+    sel = gc.Selection("subset", L, T)
+    r = autotune.tune_xengine(ctx, volt, sel, reps=1)
+    assert ctx.get_tuning("xeng.tsplit") == r["best"]
+    for k in ("fft.chunk_len", "xeng.tsplit", "cal.order", "cal.ctas_per_sm"):
+        ctx.set_tuning(k, 0)
+    with pytest.raises(gc.GridcorrError):
+        ctx.set_tuning("no.such.knob", 1)
