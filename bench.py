@@ -333,6 +333,7 @@ def run_ours(args, rank, world, local_rank):
         variants[name] = {"ms": ms, "chans_per_s": C / (ms * 1e-3),
                           "max_rel_gain_diff_vs_lincal_fp64": diff,
                           "mean_iters": float(np.mean(sv["iters"])),
+                          "mean_cg_iters": float(np.mean(sv["inner"])),
                           "converged": int(np.sum(sv["status"] == 0))}
 
     # ---- end to end through the public API with host buffers (pinned)

@@ -243,7 +243,7 @@ typedef struct gc_calstats {
     int dof;
     int iters;
     int status;
-    int reserved;
+    int inner;   /* GC_LINCAL_CG: total conjugate-gradient iterations; else 0 */
 } gc_calstats;
 GC_API gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, const gc_sel *sel, int C,
                               const void *autos, const gc_calopts *opts, float *gains, float *vmodel,

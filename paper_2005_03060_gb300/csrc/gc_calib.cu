@@ -35,6 +35,8 @@
 namespace {
 
 constexpr int kCThreads = 512;
+constexpr int kCgThreads = 512;   // matrix-free kernels
+constexpr size_t kCgSmemMax = 160u * 1024u;   // shared arena cap for the matrix-free kernels
 constexpr int kMaxUbl = 64;   // lincal border limit (2 * 64 reals)
 
 struct CalParams {
@@ -43,6 +45,7 @@ struct CalParams {
     const void *autos;           // c64 float | i4c int [C][N], or null
     int C, L, N, P, n_ubl;
     const int32_t *types, *type_ptr, *pair_i, *pair_j, *pair_type, *win_t0, *win_t1;
+    const int32_t *nbr;          // [2][n_ubl][N] neighbour table or null
     int ax, ay;                  // indices of types (1,0) and (0,1)
     int t_autos;                 // samples summed in autos
     float2 *gains;               // [C][N] (in: warm start when warm != 0)
@@ -687,7 +690,7 @@ __device__ void output_convention(const CalParams &p, float2 *g, float2 *V, doub
 
 template <class R>
 __device__ void finish_channel(const CalParams &p, int c, const R *xg, const R *xv, int iters, int st,
-                               double *red) {
+                               double *red, int inner = 0) {
     float2 *g = p.gains + (size_t)c * p.N;
     float2 *V = p.vmodel + (size_t)c * p.n_ubl;
     for (int i = threadIdx.x; i < p.N; i += blockDim.x) g[i] = make_float2((float)xg[2 * i], (float)xg[2 * i + 1]);
@@ -718,7 +721,7 @@ __device__ void finish_channel(const CalParams &p, int c, const R *xg, const R *
         s.chi2r = p.autos && s.dof > 0 ? acc[1] / s.dof : -1.0;
         s.iters = iters;
         s.status = st;
-        s.reserved = 0;
+        s.inner = inner;
         p.stats[c] = s;
     }
     __syncthreads();
@@ -797,151 +800,154 @@ __global__ void __launch_bounds__(kCThreads) lincal_kernel(const CalParams p) {
 
 // ----------------------------------------------------------------- lincal, matrix-free (mixed precision)
 // Gauss-Newton with the step from preconditioned conjugate gradients on
-// (J^T J + mu I) delta = J^T r, never forming J^T J: J v is evaluated per
-// pair, J^T u by gather per antenna and per type.  FP32 products, FP64
-// reductions.  The diagonal blocks of J^T J are |a|^2 I (gains) and |e|^2 I
-// (model visibilities), which give the Jacobi preconditioner.
+// (J^T J + mu I) delta = J^T r, never forming J^T J.  The operator is one pass
+// over the pairs: each pair evaluates its entry of J v,
+//   u_p = a_p v_gi + b_p conj(v_gj) + e_p v_V,  a = conj(g_j) V, b = g_i V, e = g_i conj(g_j),
+// and scatters J^T u -- conj(a) u to g_i, b conj(u) to g_j (shared-memory
+// atomics) and conj(e) u to V (warp-reduced when a warp's pairs share a type,
+// which the type-major pair order makes the common case).  The diagonal
+// blocks of J^T J are |a|^2 I and |e|^2 I, the Jacobi preconditioner.  FP32
+// products, FP64 reductions; the randomly accessed vectors (state, search
+// direction, operator output, diagonals) live in shared memory when they fit.
 struct CgWork {
-    float *xg, *xv;          // state (xv followed by N scratch floats)
-    float *dg, *dv;          // preconditioner diagonals
-    float *b, *x, *r, *z, *pp, *q, *trial, *tg;   // n + m each (tg: 4 (n + m))
-    float2 *u;               // per-pair work [P]
+    float *xg, *xv;          // state 2N; 2 n_ubl (+ N scratch for the start point)
+    float *pp, *acc;         // search direction and operator output (n + m)
+    float *dg, *dv;          // Jacobi diagonals (N, n_ubl)
+    float *b, *x, *r, *z, *trial, *tg;   // streaming vectors (global); tg: 4 (n + m)
     int n, m;
 };
 
-__device__ CgWork cg_layout(const CalParams &p, char *base) {
+__host__ __device__ inline size_t cg_hot_floats(int N, int n_ubl) { return 8 * (size_t)N + 7 * (size_t)n_ubl + 64; }
+
+__device__ CgWork cg_layout(const CalParams &p, char *base, float *smem_arena, bool use_smem) {
     CgWork w;
     w.n = 2 * p.N;
     w.m = 2 * p.n_ubl;
     const size_t nm = w.n + w.m;
-    float *q = reinterpret_cast<float *>(base);
-    auto take = [&](size_t cnt) {
-        float *r = q;
-        q += (cnt + 63) & ~size_t(63);
+    float *g = reinterpret_cast<float *>(base);
+    auto takeg = [&](size_t cnt) {
+        float *r = g;
+        g += (cnt + 63) & ~size_t(63);
         return r;
     };
-    w.xg = take(w.n);
-    w.xv = take(w.m + p.N);
-    w.dg = take(p.N);
-    w.dv = take(p.n_ubl);
-    w.b = take(nm);
-    w.x = take(nm);
-    w.r = take(nm);
-    w.z = take(nm);
-    w.pp = take(nm);
-    w.q = take(nm);
-    w.trial = take(nm);
-    w.tg = take(4 * nm);
-    w.u = reinterpret_cast<float2 *>(take(2 * (size_t)p.P));
+    float *h = use_smem ? smem_arena : takeg(cg_hot_floats(p.N, p.n_ubl));
+    w.xg = h;
+    h += 2 * p.N;
+    w.xv = h;
+    h += 2 * p.n_ubl + p.N;
+    w.pp = h;
+    h += nm;
+    w.acc = h;
+    h += nm;
+    w.dg = h;
+    h += p.N;
+    w.dv = h;
+    w.b = takeg(nm);
+    w.x = takeg(nm);
+    w.r = takeg(nm);
+    w.z = takeg(nm);
+    w.trial = takeg(nm);
+    w.tg = takeg(4 * nm);
     return w;
 }
 
-size_t cg_bytes(int N, int n_ubl, int P) {
+size_t cg_bytes(int N, int n_ubl, int /*P*/) {
     auto r = [](size_t c) { return (c + 63) & ~size_t(63); };
-    const size_t n = 2 * (size_t)N, m = 2 * (size_t)n_ubl, nm = n + m;
-    return sizeof(float) * (r(n) + r(m + N) + r(N) + r(n_ubl) + 7 * r(nm) + r(4 * nm) + r(2 * (size_t)P));
+    const size_t nm = 2 * (size_t)N + 2 * (size_t)n_ubl;
+    return sizeof(float) * (r(cg_hot_floats(N, n_ubl)) + 5 * r(nm) + r(4 * nm));
 }
 
-// u_p = a_p v_gi + b_p conj(v_gj) + e_p v_V  (J v as complex per pair), with
-// a = conj(g_j) V, b = g_i V, e = g_i conj(g_j).  When `resid` is set, u_p is
-// the residual V_p - g_i conj(g_j) V instead, and chi^2 is returned.
-__device__ double cg_pairs(const CalParams &p, int c, const CgWork &w, const float *v, bool resid,
-                           double *red) {
-    double s[1] = {0.0};
-    for (int q = threadIdx.x; q < p.P; q += blockDim.x) {
-        const int i = p.pair_i[q], j = p.pair_j[q], k = p.pair_type[q];
-        const float gix = w.xg[2 * i], giy = w.xg[2 * i + 1], gjx = w.xg[2 * j], gjy = w.xg[2 * j + 1];
-        const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
-        const float ex = gix * gjx + giy * gjy, ey = giy * gjx - gix * gjy;   // g_i conj(g_j)
-        if (resid) {
-            const float2 o = vobs(p, c, q);
-            const float rx = o.x - (ex * Vx - ey * Vy), ry = o.y - (ex * Vy + ey * Vx);
-            w.u[q] = make_float2(rx, ry);
-            s[0] += (double)rx * rx + (double)ry * ry;
+// One pass over the pairs.  resid: u = r (the residual), acc = J^T r, dg/dv
+// = diagonals, returns chi^2.  Otherwise u = J pp and acc = J^T u.
+// Each warp walks a contiguous chunk of the (type-major) pair list, so the
+// model-visibility terms accumulate in registers and are flushed with one
+// warp reduction per type boundary.
+__device__ double cg_pass(const CalParams &p, int c, const CgWork &w, bool resid, double *red) {
+    const int nm = w.n + w.m;
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) w.acc[i] = 0.f;
+    if (resid) {
+        for (int i = threadIdx.x; i < p.N; i += blockDim.x) w.dg[i] = 0.f;
+        for (int k = threadIdx.x; k < p.n_ubl; k += blockDim.x) w.dv[k] = 0.f;
+    }
+    __syncthreads();
+    float chi = 0.f;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int chunk = ((p.P + nw - 1) / nw + 31) & ~31;
+    const int q_lo = wp * chunk, q_hi = min(p.P, q_lo + chunk);
+    int k_cur = q_lo < q_hi ? p.pair_type[q_lo] : 0;
+    float vx = 0.f, vy = 0.f, vd = 0.f;
+    auto flush = [&](int k) {
+        float a = vx, b = vy, d = vd;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&w.acc[w.n + 2 * k], a);
+            atomicAdd(&w.acc[w.n + 2 * k + 1], b);
+            if (resid) atomicAdd(&w.dv[k], d);
+        }
+        vx = vy = vd = 0.f;
+    };
+    for (int q0 = q_lo; q0 < q_hi; q0 += 32) {
+        const int q = q0 + lane;
+        const bool valid = q < q_hi;
+        int k = k_cur;
+        float ux = 0.f, uy = 0.f, ex = 0.f, ey = 0.f;
+        if (valid) {
+            const int i = p.pair_i[q], j = p.pair_j[q];
+            k = p.pair_type[q];
+            const float gix = w.xg[2 * i], giy = w.xg[2 * i + 1], gjx = w.xg[2 * j], gjy = w.xg[2 * j + 1];
+            const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
+            ex = gix * gjx + giy * gjy;
+            ey = giy * gjx - gix * gjy;                                        // g_i conj(g_j)
+            const float ax = gjx * Vx + gjy * Vy, ay = gjx * Vy - gjy * Vx;    // conj(g_j) V
+            const float bx = gix * Vx - giy * Vy, by = gix * Vy + giy * Vx;    // g_i V
+            if (resid) {
+                const float2 o = vobs(p, c, q);
+                ux = o.x - (ex * Vx - ey * Vy);
+                uy = o.y - (ex * Vy + ey * Vx);
+                chi = fmaf(ux, ux, fmaf(uy, uy, chi));
+                atomicAdd(&w.dg[i], ax * ax + ay * ay);
+                atomicAdd(&w.dg[j], bx * bx + by * by);
+            } else {
+                const float vix = w.pp[2 * i], viy = w.pp[2 * i + 1];
+                const float vjx = w.pp[2 * j], vjy = -w.pp[2 * j + 1];
+                const float vvx = w.pp[w.n + 2 * k], vvy = w.pp[w.n + 2 * k + 1];
+                ux = ax * vix - ay * viy + bx * vjx - by * vjy + ex * vvx - ey * vvy;
+                uy = ax * viy + ay * vix + bx * vjy + by * vjx + ex * vvy + ey * vvx;
+            }
+            // conj(a) u -> g_i ; b conj(u) -> g_j
+            atomicAdd(&w.acc[2 * i], ax * ux + ay * uy);
+            atomicAdd(&w.acc[2 * i + 1], ax * uy - ay * ux);
+            atomicAdd(&w.acc[2 * j], bx * ux + by * uy);
+            atomicAdd(&w.acc[2 * j + 1], by * ux - bx * uy);
+        }
+        // conj(e) u -> V_k (and |e|^2 -> dv_k)
+        const float tx = ex * ux + ey * uy, ty = ex * uy - ey * ux, td = resid ? ex * ex + ey * ey : 0.f;
+        if (__all_sync(0xffffffffu, k == k_cur)) {
+            vx += tx;
+            vy += ty;
+            vd += td;
         } else {
-            const float ax = gjx * Vx + gjy * Vy, ay = gjx * Vy - gjy * Vx;   // conj(g_j) V
-            const float bx = gix * Vx - giy * Vy, by = gix * Vy + giy * Vx;   // g_i V
-            const float vix = v[2 * i], viy = v[2 * i + 1], vjx = v[2 * j], vjy = -v[2 * j + 1];
-            const float vvx = v[w.n + 2 * k], vvy = v[w.n + 2 * k + 1];
-            const float ux = ax * vix - ay * viy + bx * vjx - by * vjy + ex * vvx - ey * vvy;
-            const float uy = ax * viy + ay * vix + bx * vjy + by * vjx + ex * vvy + ey * vvx;
-            w.u[q] = make_float2(ux, uy);
+            flush(k_cur);
+            if (valid) {
+                atomicAdd(&w.acc[w.n + 2 * k], tx);
+                atomicAdd(&w.acc[w.n + 2 * k + 1], ty);
+                if (resid) atomicAdd(&w.dv[k], td);
+            }
+            k_cur = __shfl_sync(0xffffffffu, k, 31);
         }
     }
+    if (q_lo < q_hi) flush(k_cur);
+    double s[1] = {(double)chi};
     if (resid) block_sum<double, 1>(s, red);
     else __syncthreads();
     return s[0];
 }
 
-// out = J^T u (+ mu v when v != null); also the preconditioner diagonals when diag is set.
-__device__ void cg_gather(const CalParams &p, const CgWork &w, float *out, const float *v, float mu, bool diag) {
-    const int L = p.L, nu = p.n_ubl;
-    for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
-        const int xi = i % L, yi = i / L;
-        float ox = 0.f, oy = 0.f, d = 0.f;
-        for (int k = 0; k < nu; ++k) {
-            const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
-            const int dx = p.types[2 * k], dy = p.types[2 * k + 1];
-            int q = pair_index(p, k, xi - dx, yi - dy);
-            if (q >= 0) {   // i = i_p: conj(a) u, a = conj(g_j) V
-                const int j = (yi - dy) * L + (xi - dx);
-                const float gjx = w.xg[2 * j], gjy = w.xg[2 * j + 1];
-                const float ax = gjx * Vx + gjy * Vy, ay = gjx * Vy - gjy * Vx;
-                const float2 u = w.u[q];
-                ox += ax * u.x + ay * u.y;
-                oy += ax * u.y - ay * u.x;
-                d += ax * ax + ay * ay;
-            }
-            q = pair_index(p, k, xi, yi);
-            if (q >= 0) {   // i = j_p: b conj(u), b = g_i' V
-                const int ip = (yi + dy) * L + (xi + dx);
-                const float gx = w.xg[2 * ip], gy = w.xg[2 * ip + 1];
-                const float bx = gx * Vx - gy * Vy, by = gx * Vy + gy * Vx;
-                const float2 u = w.u[q];
-                ox += bx * u.x + by * u.y;
-                oy += by * u.x - bx * u.y;
-                d += bx * bx + by * by;
-            }
-        }
-        if (v) {
-            ox += mu * v[2 * i];
-            oy += mu * v[2 * i + 1];
-        }
-        out[2 * i] = ox;
-        out[2 * i + 1] = oy;
-        if (diag) w.dg[i] = d;
-    }
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = wp; k < nu; k += nw) {
-        float sx = 0.f, sy = 0.f, sd = 0.f;
-        for (int q = p.type_ptr[k] + lane; q < p.type_ptr[k + 1]; q += 32) {
-            const int i = p.pair_i[q], j = p.pair_j[q];
-            const float ex = w.xg[2 * i] * w.xg[2 * j] + w.xg[2 * i + 1] * w.xg[2 * j + 1];
-            const float ey = w.xg[2 * i + 1] * w.xg[2 * j] - w.xg[2 * i] * w.xg[2 * j + 1];
-            const float2 u = w.u[q];
-            sx += ex * u.x + ey * u.y;
-            sy += ex * u.y - ey * u.x;
-            sd += ex * ex + ey * ey;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            sx += __shfl_xor_sync(0xffffffffu, sx, o);
-            sy += __shfl_xor_sync(0xffffffffu, sy, o);
-            sd += __shfl_xor_sync(0xffffffffu, sd, o);
-        }
-        if (lane == 0) {
-            if (v) {
-                sx += mu * v[w.n + 2 * k];
-                sy += mu * v[w.n + 2 * k + 1];
-            }
-            out[w.n + 2 * k] = sx;
-            out[w.n + 2 * k + 1] = sy;
-            if (diag) w.dv[k] = sd;
-        }
-    }
-    __syncthreads();
-}
-
-__device__ __forceinline__ float cg_prec(const CalParams &p, const CgWork &w, int idx, float mu) {
+__device__ __forceinline__ float cg_prec(const CgWork &w, int idx, float mu) {
     return idx < w.n ? 1.f / (w.dg[idx >> 1] + mu) : 1.f / (w.dv[(idx - w.n) >> 1] + mu);
 }
 
@@ -975,11 +981,11 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
     } else {
         start_point<float>(p, c, w.xg, w.xv, redf);
     }
-    int st = GC_ENOCONV, it;
+    int st = GC_ENOCONV, it, inner = 0;
+    double grad0 = 0.0;
     for (it = 1; it <= p.max_iter; ++it) {
         // residual, right-hand side J^T r and the Jacobi diagonals
-        const double chi2 = cg_pairs(p, c, w, nullptr, true, red);
-        cg_gather(p, w, w.b, nullptr, 0.f, true);
+        const double chi2 = cg_pass(p, c, w, true, red);
         double dm = 0.0;
         for (int i = threadIdx.x; i < p.N; i += blockDim.x) dm = fmax(dm, (double)w.dg[i]);
         for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
@@ -989,41 +995,51 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
         for (int u = 0; u < (int)(blockDim.x >> 5); ++u) dmax = fmax(dmax, red[u]);
         __syncthreads();
         const float mu = (float)(p.mu_rel * dmax);
-        // PCG from x = 0
-        double acc[2] = {0.0, 0.0};
+        // PCG from x = 0; per-thread FP32 partials, FP64 block sums
+        float pa0 = 0.f, pa1 = 0.f;
         for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-            const float bi = w.b[i];
-            const float zi = bi * cg_prec(p, w, i, mu);
+            const float bi = w.acc[i];
+            const float zi = bi * cg_prec(w, i, mu);
+            w.b[i] = bi;
             w.x[i] = 0.f;
             w.r[i] = bi;
-            w.z[i] = zi;
             w.pp[i] = zi;
-            acc[0] += (double)bi * zi;
-            acc[1] += (double)bi * bi;
+            pa0 = fmaf(bi, zi, pa0);
+            pa1 = fmaf(bi, bi, pa1);
         }
+        double acc[2] = {(double)pa0, (double)pa1};
         block_sum<double, 2>(acc, red);
         double rz = acc[0];
         const double bnorm2 = acc[1];
+        // inexact Newton: loose linear solves while the gradient is large
+        if (it == 1) grad0 = bnorm2;
+        const double eta = fmin(0.1, fmax(cg_tol, sqrt(sqrt(bnorm2 / fmax(grad0, 1e-300)))));
         for (int k = 0; k < cg_max && bnorm2 > 0.0; ++k) {
-            cg_pairs(p, c, w, w.pp, false, red);
-            cg_gather(p, w, w.q, w.pp, mu, false);
-            double pq[1] = {0.0};
-            for (int i = threadIdx.x; i < nm; i += blockDim.x) pq[0] += (double)w.pp[i] * w.q[i];
+            ++inner;
+            cg_pass(p, c, w, false, red);
+            float pl = 0.f;
+            for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+                const float qi = w.acc[i] + mu * w.pp[i];
+                pl = fmaf(w.pp[i], qi, pl);
+            }
+            double pq[1] = {(double)pl};
             block_sum<double, 1>(pq, red);
             if (!(pq[0] > 0.0)) break;
             const float alpha = (float)(rz / pq[0]);
-            double a2[2] = {0.0, 0.0};
+            float b0 = 0.f, b1 = 0.f;
             for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-                w.x[i] += alpha * w.pp[i];
-                const float ri = w.r[i] - alpha * w.q[i];
+                const float pi_ = w.pp[i];
+                w.x[i] += alpha * pi_;
+                const float ri = w.r[i] - alpha * (w.acc[i] + mu * pi_);
                 w.r[i] = ri;
-                const float zi = ri * cg_prec(p, w, i, mu);
+                const float zi = ri * cg_prec(w, i, mu);
                 w.z[i] = zi;
-                a2[0] += (double)ri * zi;
-                a2[1] += (double)ri * ri;
+                b0 = fmaf(ri, zi, b0);
+                b1 = fmaf(ri, ri, b1);
             }
+            double a2[2] = {(double)b0, (double)b1};
             block_sum<double, 2>(a2, red);
-            if (a2[1] <= cg_tol * cg_tol * bnorm2) break;
+            if (a2[1] <= eta * eta * bnorm2) break;
             const float beta = (float)(a2[0] / rz);
             rz = a2[0];
             for (int i = threadIdx.x; i < nm; i += blockDim.x) w.pp[i] = w.z[i] + beta * w.pp[i];
@@ -1062,13 +1078,16 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
             break;
         }
     }
-    finish_channel<float>(p, c, w.xg, w.xv, min(it, p.max_iter), st, red);
+    finish_channel<float>(p, c, w.xg, w.xv, min(it, p.max_iter), st, red, inner);
 }
 
-__global__ void __launch_bounds__(kCThreads) lincal_cg_kernel(const CalParams p, double cg_tol, int cg_max) {
+__global__ void __launch_bounds__(kCgThreads, 2) lincal_cg_kernel(const CalParams p, double cg_tol, int cg_max,
+                                                              int smem_floats) {
     __shared__ double red[32 * 14];
     __shared__ float redf[32 * 14];
-    CgWork w = cg_layout(p, p.work + (size_t)blockIdx.x * p.work_per_cta);
+    extern __shared__ __align__(16) float arena[];
+    const bool use_smem = cg_hot_floats(p.N, p.n_ubl) <= (size_t)smem_floats;
+    CgWork w = cg_layout(p, p.work + (size_t)blockIdx.x * p.work_per_cta, arena, use_smem);
     for (int c = blockIdx.x; c < p.C; c += gridDim.x) cg_solve_channel(p, c, w, cg_tol, cg_max, red, redf);
 }
 
@@ -1086,12 +1105,14 @@ struct BatchParams {
     size_t work_per_cta;
     double cg_tol;
     int cg_max;
+    int smem_floats;
 };
 
-__global__ void __launch_bounds__(kCThreads) lincal_cg_batched(const __grid_constant__ BatchParams bp) {
+__global__ void __launch_bounds__(kCgThreads, 2) lincal_cg_batched(const __grid_constant__ BatchParams bp) {
     __shared__ double red[32 * 14];
     __shared__ float redf[32 * 14];
     __shared__ int s_item;
+    extern __shared__ __align__(16) float arena[];
     char *base = bp.work + (size_t)blockIdx.x * bp.work_per_cta;
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(bp.counter, 1u);
@@ -1102,7 +1123,8 @@ __global__ void __launch_bounds__(kCThreads) lincal_cg_batched(const __grid_cons
         int slot = 0;
         while (slot + 1 < bp.n_arr && bp.prefix[slot + 1] <= item) ++slot;
         const CalParams &p = bp.arr[bp.order[slot]];
-        CgWork w = cg_layout(p, base);
+        const bool use_smem = cg_hot_floats(p.N, p.n_ubl) <= (size_t)bp.smem_floats;
+        CgWork w = cg_layout(p, base, arena, use_smem);
         cg_solve_channel(p, item - bp.prefix[slot], w, bp.cg_tol, bp.cg_max, red, redf);
     }
 }
@@ -1144,9 +1166,9 @@ __global__ void __launch_bounds__(kCThreads) omnical_kernel(const CalParams p) {
                 for (int k = 0; k < nu; ++k) {
                     const float vx = xv[2 * k], vy = xv[2 * k + 1];
                     const int dx = p.types[2 * k], dy = p.types[2 * k + 1];
-                    int q = pair_index(p, k, xi - dx, yi - dy);
+                    int q = p.nbr ? p.nbr[(size_t)k * p.N + i] : pair_index(p, k, xi - dx, yi - dy);
                     if (q >= 0) {   // i = i_p, partner j: z = conj(g_j) V
-                        const int j = (yi - dy) * L + (xi - dx);
+                        const int j = i - (dy * L + dx);
                         const float zx = xg[2 * j] * vx + xg[2 * j + 1] * vy;
                         const float zy = xg[2 * j] * vy - xg[2 * j + 1] * vx;
                         const float2 v = vobs(p, c, q);
@@ -1154,9 +1176,9 @@ __global__ void __launch_bounds__(kCThreads) omnical_kernel(const CalParams p) {
                         ny += v.y * zx - v.x * zy;
                         den += zx * zx + zy * zy;
                     }
-                    q = pair_index(p, k, xi, yi);
+                    q = p.nbr ? p.nbr[(size_t)(nu + k) * p.N + i] : pair_index(p, k, xi, yi);
                     if (q >= 0) {   // i = j_p, partner i': z = g_i' V ; num += conj(V_p) z
-                        const int ip = (yi + dy) * L + (xi + dx);
+                        const int ip = i + (dy * L + dx);
                         const float zx = xg[2 * ip] * vx - xg[2 * ip + 1] * vy;
                         const float zy = xg[2 * ip] * vy + xg[2 * ip + 1] * vx;
                         const float2 v = vobs(p, c, q);
@@ -1253,6 +1275,7 @@ static gc_status fill_params(gc_ctx *ctx, gc_sel *sel, int C, const void *vreduc
     p.pair_type = sel->d_pair_type;
     p.win_t0 = sel->d_win_t0;
     p.win_t1 = sel->d_win_t1;
+    p.nbr = sel->d_nbr;
     p.ax = ax;
     p.ay = ay;
     p.t_autos = sel->n_cycle * sel->t_int;
@@ -1302,7 +1325,7 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
     if (st != GC_OK) return st;
     const bool fp64 = o.precision == GC_FP64;
     int occ = 0;
-    size_t per_cta;
+    size_t per_cta, cg_smem = 0;
     const void *kfn;
     if (o.solver == GC_LINCAL) {
         if (sel->n_ubl > kMaxUbl)
@@ -1314,12 +1337,17 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
     } else if (o.solver == GC_LINCAL_CG) {
         per_cta = cg_bytes(p.N, p.n_ubl, p.P);
         kfn = (const void *)lincal_cg_kernel;
+        const size_t hot = cg_hot_floats(p.N, p.n_ubl) * sizeof(float);
+        cg_smem = hot <= kCgSmemMax ? hot : 0;
+        e = cudaFuncSetAttribute(lincal_cg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCgSmemMax);
+        if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(lincal_cg)");
     } else {
         per_cta = sizeof(float) * (size_t)(2 * p.N + 2 * p.n_ubl + p.N + 2 * p.N + 2 * p.n_ubl + 64);
         kfn = (const void *)omnical_kernel;
     }
     per_cta = (per_cta + 255) & ~size_t(255);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kCThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, o.solver == GC_LINCAL_CG ? kCgThreads : kCThreads,
+                                                      cg_smem);
     if (e != cudaSuccess || occ < 1) return gc_cuda_fail(ctx, e, "occupancy(calibration)");
     if (ctx->tune[GC_TUNE_CAL_CTAS] > 0) occ = std::min(occ, ctx->tune[GC_TUNE_CAL_CTAS]);
     const int grid = std::min(C, occ * ctx->sm_count);
@@ -1335,7 +1363,7 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
         if (fp64) lincal_kernel<double><<<grid, kCThreads, 0, s>>>(p);
         else lincal_kernel<float><<<grid, kCThreads, 0, s>>>(p);
     } else if (o.solver == GC_LINCAL_CG) {
-        lincal_cg_kernel<<<grid, kCThreads, 0, s>>>(p, 1e-4, 500);
+        lincal_cg_kernel<<<grid, kCgThreads, cg_smem, s>>>(p, 1e-4, 500, (int)(cg_smem / sizeof(float)));
     } else {
         omnical_kernel<<<grid, kCThreads, 0, s>>>(p);
     }
@@ -1379,9 +1407,18 @@ extern "C" gc_status gc_calibrate_batched(gc_ctx *ctx, int n_arrays, const gc_ba
     bp.total = bp.prefix[n_arrays];
     bp.cg_tol = 1e-4;
     bp.cg_max = 500;
+    // shared arena: the largest array that fits the cap
+    size_t smem = 0;
+    for (int a = 0; a < n_arrays; ++a) {
+        const size_t hot = cg_hot_floats(bp.arr[a].N, bp.arr[a].n_ubl) * sizeof(float);
+        if (hot <= kCgSmemMax) smem = std::max(smem, hot);
+    }
+    bp.smem_floats = (int)(smem / sizeof(float));
+    e = cudaFuncSetAttribute(lincal_cg_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCgSmemMax);
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(lincal_cg_batched)");
     per_cta = (per_cta + 255) & ~size_t(255);
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lincal_cg_batched, kCThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lincal_cg_batched, kCgThreads, smem);
     if (e != cudaSuccess || occ < 1) return gc_cuda_fail(ctx, e, "occupancy(batched calibration)");
     if (ctx->tune[GC_TUNE_CAL_CTAS] > 0) occ = std::min(occ, ctx->tune[GC_TUNE_CAL_CTAS]);
     const int grid = std::min(bp.total, occ * ctx->sm_count);
@@ -1394,7 +1431,7 @@ extern "C" gc_status gc_calibrate_batched(gc_ctx *ctx, int n_arrays, const gc_ba
     e = cudaMemsetAsync(bp.counter, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "reset work counter");
     int rec = gc_prof_begin(ctx, s, "lincal_cg_batched");
-    lincal_cg_batched<<<grid, kCThreads, 0, s>>>(bp);
+    lincal_cg_batched<<<grid, kCgThreads, smem, s>>>(bp);
     gc_prof_end(ctx, s, rec);
     e = cudaGetLastError();
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch batched calibration");

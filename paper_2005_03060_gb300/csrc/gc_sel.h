@@ -16,6 +16,9 @@ struct gc_sel {
     std::vector<int32_t> type_ptr;   // [n_ubl + 1]
     std::vector<int32_t> pair_i, pair_j, pair_type;   // [P]
     std::vector<int32_t> win_t0, win_t1;              // [n_ubl]
+    // neighbour table [2][n_ubl][N]: pair index with antenna i as i_p (0) or
+    // as j_p (1), -1 if none; empty when it would exceed 16 M entries
+    std::vector<int32_t> nbr;
     // X-engine work groups (types sharing a window, <= GC_XENG_NTY each)
     int n_groups = 0, n_windows = 0;
     std::vector<int32_t> grp_types;  // type indices, grouped
@@ -27,7 +30,7 @@ struct gc_sel {
     int32_t *d_types = nullptr, *d_type_ptr = nullptr, *d_pair_i = nullptr, *d_pair_j = nullptr,
             *d_pair_type = nullptr, *d_win_t0 = nullptr, *d_win_t1 = nullptr, *d_grp_types = nullptr,
             *d_grp_off = nullptr, *d_grp_t0 = nullptr, *d_grp_t1 = nullptr, *d_grp_first = nullptr,
-            *d_grp_win = nullptr;
+            *d_grp_win = nullptr, *d_nbr = nullptr;
 };
 
 gc_status gc_sel_upload(gc_ctx *ctx, gc_sel *s);

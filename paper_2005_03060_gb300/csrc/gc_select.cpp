@@ -83,6 +83,16 @@ void fill_pairs(gc_sel *s) {
         s->type_ptr.push_back((int32_t)s->pair_i.size());
     }
     s->P = (int)s->pair_i.size();
+    const size_t N = (size_t)L * L;
+    s->nbr.clear();
+    if (2 * (size_t)s->n_ubl * N <= (16u << 20)) {
+        s->nbr.assign(2 * (size_t)s->n_ubl * N, -1);
+        for (int q = 0; q < s->P; ++q) {
+            const int k = s->pair_type[q];
+            s->nbr[(size_t)k * N + s->pair_i[q]] = q;
+            s->nbr[(size_t)(s->n_ubl + k) * N + s->pair_j[q]] = q;
+        }
+    }
 }
 
 // X-engine work groups: types that share a window, at most GC_XENG_NTY each.
@@ -140,8 +150,8 @@ gc_status gc_sel_upload(gc_ctx *ctx, gc_sel *s) {
     const std::vector<int32_t> *parts[] = {&s->types,   &s->type_ptr, &s->pair_i,    &s->pair_j,
                                            &s->pair_type, &s->win_t0, &s->win_t1,   &s->grp_types,
                                            &s->grp_off, &s->grp_t0,   &s->grp_t1,   &s->grp_first,
-                                           &s->grp_win};
-    constexpr int kParts = 13;
+                                           &s->grp_win,   &s->nbr};
+    constexpr int kParts = 14;
     size_t total = 0;
     size_t offs[kParts];
     for (int i = 0; i < kParts; ++i) {
@@ -166,8 +176,9 @@ gc_status gc_sel_upload(gc_ctx *ctx, gc_sel *s) {
     int32_t **dst[] = {&s->d_types,   &s->d_type_ptr, &s->d_pair_i,   &s->d_pair_j,
                        &s->d_pair_type, &s->d_win_t0, &s->d_win_t1,   &s->d_grp_types,
                        &s->d_grp_off, &s->d_grp_t0,   &s->d_grp_t1,   &s->d_grp_first,
-                       &s->d_grp_win};
+                       &s->d_grp_win,   &s->d_nbr};
     for (int i = 0; i < kParts; ++i) *dst[i] = reinterpret_cast<int32_t *>(static_cast<char *>(base) + offs[i]);
+    if (s->nbr.empty()) s->d_nbr = nullptr;
     s->d_base = base;
     s->device = ctx->device;
     return GC_OK;

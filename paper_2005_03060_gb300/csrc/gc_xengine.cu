@@ -94,8 +94,16 @@ __global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
         __syncthreads();
 
         float2 acc[GC_XENG_NTY];
+        int nb[GC_XENG_NTY];   // neighbour antenna r_j + d_k, or -1 (fixed for the item)
 #pragma unroll
-        for (int k = 0; k < GC_XENG_NTY; ++k) acc[k] = make_float2(0.f, 0.f);
+        for (int k = 0; k < GC_XENG_NTY; ++k) {
+            acc[k] = make_float2(0.f, 0.f);
+            nb[k] = -1;
+            if (k < ntype && own) {
+                const int xi = x + s_dx[k], yi = y + s_dy[k];
+                if (xi >= 0 && xi < L && yi >= 0 && yi < L) nb[k] = yi * L + xi;
+            }
+        }
         float aut = 0.f;
 
         for (int st = 0; st < n_st; ++st) {
@@ -127,14 +135,11 @@ __global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
                     aut = fmaf(b.x, b.x, fmaf(b.y, b.y, aut));
 #pragma unroll
                     for (int k = 0; k < GC_XENG_NTY; ++k) {
-                        if (k < ntype) {
-                            const int xi = x + s_dx[k], yi = y + s_dy[k];
-                            if (xi >= 0 && xi < L && yi >= 0 && yi < L) {
-                                const float2 a = ld_volt(sv, yi * L + xi, p.vfmt);
-                                // a * conj(b)
-                                acc[k].x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc[k].x));
-                                acc[k].y = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc[k].y));
-                            }
+                        if (nb[k] >= 0) {
+                            const float2 a = ld_volt(sv, nb[k], p.vfmt);
+                            // a * conj(b)
+                            acc[k].x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc[k].x));
+                            acc[k].y = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc[k].y));
                         }
                     }
                 }

@@ -314,7 +314,7 @@ class BatchItem(ctypes.Structure):
 
 
 STATS_DTYPE = [("chi2", "<f8"), ("chi2r", "<f8"), ("dof", "<i4"), ("iters", "<i4"),
-               ("status", "<i4"), ("reserved", "<i4")]
+               ("status", "<i4"), ("inner", "<i4")]
 
 
 class Selection:

@@ -87,8 +87,10 @@ def test_batched_graph_capture_replays(gc, ctx):
     graph.replay()
     torch.cuda.synchronize()
     ctx.device_status()
+    # the operator's shared-memory atomics make the last bits run-dependent;
+    # replay and eager agree to the solver's convergence tolerance
     for r, a in zip(ref, arrays):
-        assert torch.equal(r, a["gains"])
+        assert ((r - a["gains"]).abs() / r.abs()).max().item() < 1e-5
 
 
 def test_autotuner_sets_knobs(gc, ctx):
