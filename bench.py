@@ -405,9 +405,19 @@ def run_ours(args, rank, world, local_rank):
     if "lincal_cg" in kern:
         ms, n = kern["lincal_cg"]
         dur = ms / n * 1e-3
-        rl["lincal_cg"] = {"bound": "latency", "achieved": C / dur, "unit": "chans/s",
-                           "peak": None, "frac": None, "traffic": None,
-                           "note": "one CTA per channel; barrier/latency bound (see profiles)"}
+        cg_it = float(np.sum(st_last["inner"]))
+        gn_it = float(np.sum(st_last["iters"]))
+        nm = 2 * N + 2 * sel.n_ubl
+        # algorithmic FP32 flops: operator pass (~70 per pair) and vector updates (~12 per
+        # unknown) per CG iteration; residual/gradient pass, projection and line search
+        # (~90 per pair, ~40 per unknown) per Gauss-Newton iteration
+        flops = cg_it * (70.0 * sel.P + 12.0 * nm) + gn_it * (90.0 * sel.P + 40.0 * nm)
+        rl["lincal_cg"] = {"bound": "alu", "achieved": flops / dur / 1e12, "peak": fp32_peak,
+                           "unit": "TFLOP/s", "frac": flops / dur / 1e12 / fp32_peak, "traffic": None,
+                           "algorithmic_flops": flops, "cg_iterations": cg_it, "gn_iterations": gn_it,
+                           "chans_per_s": C / dur,
+                           "note": "one CTA per channel; latency bound at 2 channels per SM",
+                           "peak_source": "measured: gc_peak_probe FP32 FMA on this GPU"}
     if lname in kern:
         ms, n = kern[lname]
         dur = ms / n * 1e-3
