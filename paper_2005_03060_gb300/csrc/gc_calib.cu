@@ -36,7 +36,7 @@ namespace {
 
 constexpr int kCThreads = 512;
 constexpr int kCgThreads = 512;   // matrix-free kernels
-constexpr size_t kCgSmemMax = 160u * 1024u;   // shared arena cap for the matrix-free kernels
+constexpr size_t kCgSmemMax = 100u * 1024u;   // shared arena cap (two CTAs per SM)
 constexpr int kMaxUbl = 64;   // lincal border limit (2 * 64 reals)
 
 struct CalParams {
@@ -814,12 +814,31 @@ struct CgWork {
     float *pp, *acc;         // search direction and operator output (n + m)
     float *dg, *dv;          // Jacobi diagonals (N, n_ubl)
     float *b, *x, *r, *z, *trial, *tg;   // streaming vectors (global); tg: 4 (n + m)
+    // two-level preconditioner: patch-aggregation coarse space (see cg_coarse_setup)
+    float *Ca, *Cp;          // coarse amplitude / phase operators, then their inverses (nc x nc)
+    float *rc, *yc;          // coarse residual / solution (2 nc; shared memory)
     int n, m;
+    int B, npx, ncp, nc, cv; // patch side, patches per row, patches, coarse size, V in coarse space
 };
+
+constexpr int kMaxCoarse = 160;
+
+__host__ __device__ inline void cg_coarse_dims(int L, int n_ubl, int &B, int &npx, int &ncp, int &nc, int &cv) {
+    B = L >= 16 ? L / 8 : (L >= 4 ? 2 : 1);
+    npx = (L + B - 1) / B;
+    ncp = npx * npx;
+    cv = n_ubl <= 64 ? 1 : 0;
+    nc = ncp + (cv ? n_ubl : 0);
+    if (nc > kMaxCoarse) {   // keep the coarse system small
+        cv = 0;
+        nc = ncp;
+    }
+}
 
 __host__ __device__ inline size_t cg_hot_floats(int N, int n_ubl) { return 8 * (size_t)N + 7 * (size_t)n_ubl + 64; }
 
-__device__ CgWork cg_layout(const CalParams &p, char *base, float *smem_arena, bool use_smem) {
+__device__ CgWork cg_layout(const CalParams &p, char *base, float *smem_arena, bool use_smem,
+                            bool use_coarse_smem) {
     CgWork w;
     w.n = 2 * p.N;
     w.m = 2 * p.n_ubl;
@@ -831,6 +850,7 @@ __device__ CgWork cg_layout(const CalParams &p, char *base, float *smem_arena, b
         return r;
     };
     float *h = use_smem ? smem_arena : takeg(cg_hot_floats(p.N, p.n_ubl));
+    float *hot_end = h + cg_hot_floats(p.N, p.n_ubl);
     w.xg = h;
     h += 2 * p.N;
     w.xv = h;
@@ -848,13 +868,31 @@ __device__ CgWork cg_layout(const CalParams &p, char *base, float *smem_arena, b
     w.z = takeg(nm);
     w.trial = takeg(nm);
     w.tg = takeg(4 * nm);
+    cg_coarse_dims(p.L, p.n_ubl, w.B, w.npx, w.ncp, w.nc, w.cv);
+    if (use_coarse_smem) {
+        w.Ca = hot_end;
+        w.Cp = hot_end + (size_t)w.nc * w.nc;
+    } else {
+        w.Ca = takeg((size_t)w.nc * w.nc);
+        w.Cp = takeg((size_t)w.nc * w.nc);
+    }
     return w;
+}
+
+__host__ __device__ inline size_t cg_coarse_floats(int L, int n_ubl) {
+    int B, npx, ncp, nc, cv;
+    cg_coarse_dims(L, n_ubl, B, npx, ncp, nc, cv);
+    return 2 * (size_t)nc * nc;
 }
 
 size_t cg_bytes(int N, int n_ubl, int /*P*/) {
     auto r = [](size_t c) { return (c + 63) & ~size_t(63); };
     const size_t nm = 2 * (size_t)N + 2 * (size_t)n_ubl;
-    return sizeof(float) * (r(cg_hot_floats(N, n_ubl)) + 5 * r(nm) + r(4 * nm));
+    int B, npx, ncp, nc, cv;
+    const int L = (int)lround(sqrt((double)N));
+    cg_coarse_dims(L, n_ubl, B, npx, ncp, nc, cv);
+    const size_t c2 = (size_t)nc * nc;
+    return sizeof(float) * (r(cg_hot_floats(N, n_ubl)) + 5 * r(nm) + r(4 * nm) + 2 * r(c2));
 }
 
 // One pass over the pairs.  resid: u = r (the residual), acc = J^T r, dg/dv
@@ -864,12 +902,12 @@ size_t cg_bytes(int N, int n_ubl, int /*P*/) {
 // warp reduction per type boundary.
 __device__ double cg_pass(const CalParams &p, int c, const CgWork &w, bool resid, double *red) {
     const int nm = w.n + w.m;
-    for (int i = threadIdx.x; i < nm; i += blockDim.x) w.acc[i] = 0.f;
-    if (resid) {
+    if (resid) {   // the operator passes find acc already zeroed by the caller
+        for (int i = threadIdx.x; i < nm; i += blockDim.x) w.acc[i] = 0.f;
         for (int i = threadIdx.x; i < p.N; i += blockDim.x) w.dg[i] = 0.f;
         for (int k = threadIdx.x; k < p.n_ubl; k += blockDim.x) w.dv[k] = 0.f;
+        __syncthreads();
     }
-    __syncthreads();
     float chi = 0.f;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int chunk = ((p.P + nw - 1) / nw + 31) & ~31;
@@ -947,15 +985,168 @@ __device__ double cg_pass(const CalParams &p, int c, const CgWork &w, bool resid
     return s[0];
 }
 
-__device__ __forceinline__ float cg_prec(const CgWork &w, int idx, float mu) {
-    return idx < w.n ? 1.f / (w.dg[idx >> 1] + mu) : 1.f / (w.dv[(idx - w.n) >> 1] + mu);
+// Two-level preconditioner.  The coarse space scales each patch of B x B
+// antennas by one complex factor and (when there are few types) each model
+// visibility by another: dg_i = g_i c_P(i), dV_k = V_k c_k.  For a pair, J
+// applied to it gives u_p = m_p (c_Pi + conj(c_Pj) + c_k) with m_p the model,
+// so the coarse normal matrix splits into a real "amplitude" system
+// (Re c: c_Pi + c_Pj + c_k) and a real "phase" system (Im c: c_Pi - c_Pj + c_k),
+// each with entries sum |m_p|^2 -- the patch-level form of Eq. logcal.  The
+// coarse operators are inverted in FP64 once per Gauss-Newton iteration and
+// applied in FP32: M^-1 = D^-1 + R A_c^-1 R^T.
+__device__ __forceinline__ int patch_of(const CgWork &w, int i, int L) {
+    return ((i / L) / w.B) * w.npx + (i % L) / w.B;
+}
+
+// Single-barrier block sum (FP32 warp trees, fixed-order cross-warp sum):
+// buf holds two [32][NV] slots used alternately, so no trailing barrier is
+// needed before the next reduction.
+template <int NV>
+__device__ __forceinline__ void fast_sum(float (&v)[NV], float *buf, int &parity) {
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    float *b = buf + parity * 32 * NV;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) b[wp * NV + q] = v[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        float t = 0.f;
+        for (int u = 0; u < nw; ++u) t += b[u * NV + q];
+        v[q] = t;
+    }
+    parity ^= 1;
+}
+
+__device__ void cg_coarse_setup(const CalParams &p, const CgWork &w, float mu) {
+    const int nc = w.nc, L = p.L;
+    for (int t = threadIdx.x; t < nc * nc; t += blockDim.x) {
+        w.Ca[t] = 0.f;
+        w.Cp[t] = 0.f;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < p.P; q += blockDim.x) {
+        const int i = p.pair_i[q], j = p.pair_j[q], k = p.pair_type[q];
+        const float gix = w.xg[2 * i], giy = w.xg[2 * i + 1], gjx = w.xg[2 * j], gjy = w.xg[2 * j + 1];
+        const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
+        const float ex = gix * gjx + giy * gjy, ey = giy * gjx - gix * gjy;
+        const float wq = (ex * ex + ey * ey) * (Vx * Vx + Vy * Vy);   // |m_p|^2
+        const int a = patch_of(w, i, L), b = patch_of(w, j, L);
+        // upper triangle only (row <= col); symmetrised below
+        if (a == b) {
+            atomicAdd(&w.Ca[a * nc + a], 4.f * wq);
+        } else {
+            const int lo = min(a, b), hi = max(a, b);
+            atomicAdd(&w.Ca[a * nc + a], wq);
+            atomicAdd(&w.Ca[b * nc + b], wq);
+            atomicAdd(&w.Ca[lo * nc + hi], wq);
+            atomicAdd(&w.Cp[a * nc + a], wq);
+            atomicAdd(&w.Cp[b * nc + b], wq);
+            atomicAdd(&w.Cp[lo * nc + hi], -wq);
+        }
+        if (w.cv) {
+            const int kc = w.ncp + k;   // > every patch index
+            if (a == b) {
+                atomicAdd(&w.Ca[a * nc + kc], 2.f * wq);
+            } else {
+                atomicAdd(&w.Ca[a * nc + kc], wq);
+                atomicAdd(&w.Ca[b * nc + kc], wq);
+                atomicAdd(&w.Cp[a * nc + kc], wq);
+                atomicAdd(&w.Cp[b * nc + kc], -wq);
+            }
+        }
+    }
+    __syncthreads();
+    // Levenberg term mu R^T R: patch P gets mu sum |g_i|^2; the type diagonal
+    // is sum_p |m_p|^2 = |V_k|^2 dv_k (+ mu |V_k|^2)
+    for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
+        const int a = patch_of(w, i, L);
+        const float g2 = w.xg[2 * i] * w.xg[2 * i] + w.xg[2 * i + 1] * w.xg[2 * i + 1];
+        atomicAdd(&w.Ca[a * nc + a], mu * g2);
+        atomicAdd(&w.Cp[a * nc + a], mu * g2);
+    }
+    if (w.cv)
+        for (int k = threadIdx.x; k < p.n_ubl; k += blockDim.x) {
+            const int kc = w.ncp + k;
+            const float v2 = w.xv[2 * k] * w.xv[2 * k] + w.xv[2 * k + 1] * w.xv[2 * k + 1];
+            w.Ca[kc * nc + kc] = v2 * (w.dv[k] + mu);
+            w.Cp[kc * nc + kc] = v2 * (w.dv[k] + mu);
+        }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nc * nc; t += blockDim.x) {   // lower from upper
+        const int r = t / nc, cc = t % nc;
+        if (r > cc) {
+            w.Ca[t] = w.Ca[cc * nc + r];
+            w.Cp[t] = w.Cp[cc * nc + r];
+        }
+    }
+    __syncthreads();
+    // one warp per system: diagonal floor, Gauss-Jordan inversion in place
+    // (SPD, no pivoting), then the projection P A^-1 P that removes the exact
+    // coarse null direction n (amplitude: patches 1, types -2; phase: patches 1)
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (wp < 2) {
+        float *A = wp ? w.Cp : w.Ca;
+        float mx = 0.f;
+        for (int r = lane; r < nc; r += 32) mx = fmaxf(mx, A[r * nc + r]);
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        for (int r = lane; r < nc; r += 32) A[r * nc + r] += 1e-5f * mx;
+        __syncwarp();
+        for (int k = 0; k < nc; ++k) {
+            const float iv = 1.f / A[k * nc + k];
+            __syncwarp();
+            for (int e = lane; e < nc * nc; e += 32) {
+                const int r = e / nc, cc = e - r * nc;
+                if (r != k && cc != k) A[e] -= A[r * nc + k] * A[k * nc + cc] * iv;
+            }
+            __syncwarp();
+            for (int r = lane; r < nc; r += 32) {
+                if (r != k) {
+                    A[r * nc + k] *= -iv;
+                    A[k * nc + r] *= iv;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) A[k * nc + k] = iv;
+            __syncwarp();
+        }
+        const bool amp = wp == 0;
+        if (!amp || w.cv) {
+            // u = A n, c = n.A n, s = n.n
+            auto nv = [&](int t) -> float { return t < w.ncp ? 1.f : (amp ? -2.f : 0.f); };
+            float s_loc = 0.f;
+            for (int t = lane; t < nc; t += 32) s_loc += nv(t) * nv(t);
+            for (int o = 16; o > 0; o >>= 1) s_loc += __shfl_xor_sync(0xffffffffu, s_loc, o);
+            float *u = w.yc + wp * nc;    // scratch
+            float c_loc = 0.f;
+            for (int r = lane; r < nc; r += 32) {
+                float acc = 0.f;
+                for (int t = 0; t < nc; ++t) acc = fmaf(A[r * nc + t], nv(t), acc);
+                u[r] = acc;
+                c_loc += nv(r) * acc;
+            }
+            for (int o = 16; o > 0; o >>= 1) c_loc += __shfl_xor_sync(0xffffffffu, c_loc, o);
+            __syncwarp();
+            const float is = 1.f / s_loc;
+            for (int e = lane; e < nc * nc; e += 32) {
+                const int r = e / nc, t = e - r * nc;
+                A[e] += -u[r] * nv(t) * is - nv(r) * u[t] * is + nv(r) * nv(t) * c_loc * is * is;
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
 }
 
 // One channel of matrix-free Gauss-Newton (used by the per-selection and the
-// batched kernels).  All threads of the CTA call it.
+// batched kernels).  All threads of the CTA call it.  The CG iteration takes
+// four barriers (six with the coarse correction).
 __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg_tol, int cg_max, double *red,
                                  float *redf) {
-    const int nm = w.n + w.m;
+    const int nm = w.n + w.m, ne = p.N + p.n_ubl, L = p.L, nc = w.nc;
     GnWork<float> gw;   // view for the shared projection helper
     gw.xg = w.xg;
     gw.xv = w.xv;
@@ -965,6 +1156,9 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
     gw.delta = w.z;
     gw.n = w.n;
     gw.m = w.m;
+    __shared__ float sbuf[2 * 32 * 2];
+    int par = 0;
+    const bool coarse = nc > 0;
     const uint64_t t_start = gc_globaltimer();
     if (p.warm) {
         for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
@@ -981,6 +1175,51 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
     } else {
         start_point<float>(p, c, w.xg, w.xv, redf);
     }
+    // complex element e: antenna e < N, else model visibility e - N
+    auto base_of = [&](int e) { return e < p.N ? 2 * e : w.n + 2 * (e - p.N); };
+    auto dinv = [&](int e, float mu) { return e < p.N ? 1.f / (w.dg[e] + mu) : 1.f / (w.dv[e - p.N] + mu); };
+    auto cidx_of = [&](int e) { return e < p.N ? patch_of(w, e, L) : (w.cv ? w.ncp + (e - p.N) : -1); };
+    // z = D^-1 r (+ R y after the coarse solve); restriction rc += conj(s) r
+    auto precondition = [&](float mu) {
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+            const int b = base_of(e);
+            const float rx = w.r[b], ry = w.r[b + 1], iv = dinv(e, mu);
+            w.z[b] = rx * iv;
+            w.z[b + 1] = ry * iv;
+            if (coarse) {
+                const int ci = cidx_of(e);
+                if (ci >= 0) {
+                    const float sx = e < p.N ? w.xg[b] : w.xv[b - w.n];
+                    const float sy = e < p.N ? w.xg[b + 1] : w.xv[b - w.n + 1];
+                    atomicAdd(&w.rc[ci], sx * rx + sy * ry);
+                    atomicAdd(&w.rc[nc + ci], sx * ry - sy * rx);
+                }
+            }
+        }
+        if (!coarse) return;
+        __syncthreads();
+        for (int t = threadIdx.x; t < 2 * nc; t += blockDim.x) {
+            const int m = t / nc, row = t - m * nc;
+            const float *A = m ? w.Cp : w.Ca;
+            const float *rr = w.rc + m * nc;
+            float acc = 0.f;
+            for (int cc = 0; cc < nc; ++cc) acc = fmaf(A[row * nc + cc], rr[cc], acc);
+            w.yc[t] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+            const int ci = cidx_of(e);
+            if (ci < 0) continue;
+            const int b = base_of(e);
+            const float sx = e < p.N ? w.xg[b] : w.xv[b - w.n];
+            const float sy = e < p.N ? w.xg[b + 1] : w.xv[b - w.n + 1];
+            const float ya = w.yc[ci], yp = w.yc[nc + ci];
+            w.z[b] += sx * ya - sy * yp;
+            w.z[b + 1] += sx * yp + sy * ya;
+        }
+        for (int t = threadIdx.x; t < 2 * nc; t += blockDim.x) w.rc[t] = 0.f;   // for the next use
+    };
+    for (int t = threadIdx.x; t < 2 * kMaxCoarse; t += blockDim.x) w.rc[t] = 0.f;
     int st = GC_ENOCONV, it, inner = 0;
     double grad0 = 0.0;
     for (it = 1; it <= p.max_iter; ++it) {
@@ -995,56 +1234,74 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
         for (int u = 0; u < (int)(blockDim.x >> 5); ++u) dmax = fmax(dmax, red[u]);
         __syncthreads();
         const float mu = (float)(p.mu_rel * dmax);
-        // PCG from x = 0; per-thread FP32 partials, FP64 block sums
-        float pa0 = 0.f, pa1 = 0.f;
+        if (coarse && it <= 2) cg_coarse_setup(p, w, mu);   // later iterations reuse it
+        // PCG from x = 0
         for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-            const float bi = w.acc[i];
-            const float zi = bi * cg_prec(w, i, mu);
-            w.b[i] = bi;
+            w.b[i] = w.acc[i];
             w.x[i] = 0.f;
-            w.r[i] = bi;
-            w.pp[i] = zi;
-            pa0 = fmaf(bi, zi, pa0);
-            pa1 = fmaf(bi, bi, pa1);
+            w.r[i] = w.acc[i];
         }
-        double acc[2] = {(double)pa0, (double)pa1};
-        block_sum<double, 2>(acc, red);
-        double rz = acc[0];
-        const double bnorm2 = acc[1];
+        __syncthreads();
+        precondition(mu);
+        // vector loops walk complex elements so that each thread owns both
+        // halves of what it precondition()s -- no barrier between them
+        float v2[2] = {0.f, 0.f};
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+            const int b = base_of(e);
+            for (int h = 0; h < 2; ++h) {
+                const float ri = w.r[b + h], zi = w.z[b + h];
+                w.pp[b + h] = zi;
+                w.acc[b + h] = 0.f;
+                v2[0] = fmaf(ri, zi, v2[0]);
+                v2[1] = fmaf(ri, ri, v2[1]);
+            }
+        }
+        fast_sum<2>(v2, sbuf, par);
+        float rz = v2[0];
+        const float bnorm2 = v2[1];
         // inexact Newton: loose linear solves while the gradient is large
         if (it == 1) grad0 = bnorm2;
-        const double eta = fmin(0.1, fmax(cg_tol, sqrt(sqrt(bnorm2 / fmax(grad0, 1e-300)))));
-        for (int k = 0; k < cg_max && bnorm2 > 0.0; ++k) {
+        const float eta = (float)fmin(0.1, fmax(cg_tol, sqrt(sqrt((double)bnorm2 / fmax(grad0, 1e-300)))));
+        for (int k = 0; k < cg_max && bnorm2 > 0.f; ++k) {
             ++inner;
-            cg_pass(p, c, w, false, red);
-            float pl = 0.f;
-            for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-                const float qi = w.acc[i] + mu * w.pp[i];
-                pl = fmaf(w.pp[i], qi, pl);
+            cg_pass(p, c, w, false, red);                 // acc = J^T J pp (acc was zeroed)
+            float v1[1] = {0.f};
+            for (int i = threadIdx.x; i < nm; i += blockDim.x) v1[0] = fmaf(w.pp[i], w.acc[i] + mu * w.pp[i], v1[0]);
+            fast_sum<1>(v1, sbuf, par);
+            if (!(v1[0] > 0.f)) break;
+            const float alpha = rz / v1[0];
+            for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+                const int b = base_of(e);
+                for (int h = 0; h < 2; ++h) {
+                    const float pi_ = w.pp[b + h];
+                    w.x[b + h] += alpha * pi_;
+                    w.r[b + h] -= alpha * (w.acc[b + h] + mu * pi_);
+                }
             }
-            double pq[1] = {(double)pl};
-            block_sum<double, 1>(pq, red);
-            if (!(pq[0] > 0.0)) break;
-            const float alpha = (float)(rz / pq[0]);
-            float b0 = 0.f, b1 = 0.f;
-            for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-                const float pi_ = w.pp[i];
-                w.x[i] += alpha * pi_;
-                const float ri = w.r[i] - alpha * (w.acc[i] + mu * pi_);
-                w.r[i] = ri;
-                const float zi = ri * cg_prec(w, i, mu);
-                w.z[i] = zi;
-                b0 = fmaf(ri, zi, b0);
-                b1 = fmaf(ri, ri, b1);
+            precondition(mu);
+            float v3[2] = {0.f, 0.f};
+            for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+                const int b = base_of(e);
+                for (int h = 0; h < 2; ++h) {
+                    const float ri = w.r[b + h];
+                    v3[0] = fmaf(ri, w.z[b + h], v3[0]);
+                    v3[1] = fmaf(ri, ri, v3[1]);
+                }
             }
-            double a2[2] = {(double)b0, (double)b1};
-            block_sum<double, 2>(a2, red);
-            if (a2[1] <= eta * eta * bnorm2) break;
-            const float beta = (float)(a2[0] / rz);
-            rz = a2[0];
-            for (int i = threadIdx.x; i < nm; i += blockDim.x) w.pp[i] = w.z[i] + beta * w.pp[i];
+            fast_sum<2>(v3, sbuf, par);
+            if (v3[1] <= eta * eta * bnorm2) break;
+            const float beta = v3[0] / rz;
+            rz = v3[0];
+            for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+                const int b = base_of(e);
+                for (int h = 0; h < 2; ++h) {
+                    w.pp[b + h] = w.z[b + h] + beta * w.pp[b + h];
+                    w.acc[b + h] = 0.f;
+                }
+            }
             __syncthreads();
         }
+        __syncthreads();
         // project out the degeneracies (delta lands in w.z), line search, update
         gn_project<float>(p, gw, redf);
         double nr[2] = {0.0, 0.0};
@@ -1085,9 +1342,14 @@ __global__ void __launch_bounds__(kCgThreads, 2) lincal_cg_kernel(const CalParam
                                                               int smem_floats) {
     __shared__ double red[32 * 14];
     __shared__ float redf[32 * 14];
+    __shared__ float s_rc[2 * kMaxCoarse], s_yc[2 * kMaxCoarse];
     extern __shared__ __align__(16) float arena[];
     const bool use_smem = cg_hot_floats(p.N, p.n_ubl) <= (size_t)smem_floats;
-    CgWork w = cg_layout(p, p.work + (size_t)blockIdx.x * p.work_per_cta, arena, use_smem);
+    const bool coarse_smem =
+        use_smem && cg_hot_floats(p.N, p.n_ubl) + cg_coarse_floats(p.L, p.n_ubl) <= (size_t)smem_floats;
+    CgWork w = cg_layout(p, p.work + (size_t)blockIdx.x * p.work_per_cta, arena, use_smem, coarse_smem);
+    w.rc = s_rc;
+    w.yc = s_yc;
     for (int c = blockIdx.x; c < p.C; c += gridDim.x) cg_solve_channel(p, c, w, cg_tol, cg_max, red, redf);
 }
 
@@ -1112,6 +1374,7 @@ __global__ void __launch_bounds__(kCgThreads, 2) lincal_cg_batched(const __grid_
     __shared__ double red[32 * 14];
     __shared__ float redf[32 * 14];
     __shared__ int s_item;
+    __shared__ float s_rc[2 * kMaxCoarse], s_yc[2 * kMaxCoarse];
     extern __shared__ __align__(16) float arena[];
     char *base = bp.work + (size_t)blockIdx.x * bp.work_per_cta;
     for (;;) {
@@ -1124,7 +1387,11 @@ __global__ void __launch_bounds__(kCgThreads, 2) lincal_cg_batched(const __grid_
         while (slot + 1 < bp.n_arr && bp.prefix[slot + 1] <= item) ++slot;
         const CalParams &p = bp.arr[bp.order[slot]];
         const bool use_smem = cg_hot_floats(p.N, p.n_ubl) <= (size_t)bp.smem_floats;
-        CgWork w = cg_layout(p, base, arena, use_smem);
+        const bool coarse_smem =
+            use_smem && cg_hot_floats(p.N, p.n_ubl) + cg_coarse_floats(p.L, p.n_ubl) <= (size_t)bp.smem_floats;
+        CgWork w = cg_layout(p, base, arena, use_smem, coarse_smem);
+        w.rc = s_rc;
+        w.yc = s_yc;
         cg_solve_channel(p, item - bp.prefix[slot], w, bp.cg_tol, bp.cg_max, red, redf);
     }
 }
@@ -1338,7 +1605,8 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
         per_cta = cg_bytes(p.N, p.n_ubl, p.P);
         kfn = (const void *)lincal_cg_kernel;
         const size_t hot = cg_hot_floats(p.N, p.n_ubl) * sizeof(float);
-        cg_smem = hot <= kCgSmemMax ? hot : 0;
+        const size_t both = hot + cg_coarse_floats(p.L, p.n_ubl) * sizeof(float);
+        cg_smem = both <= kCgSmemMax ? both : (hot <= kCgSmemMax ? hot : 0);
         e = cudaFuncSetAttribute(lincal_cg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCgSmemMax);
         if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(lincal_cg)");
     } else {
@@ -1411,7 +1679,9 @@ extern "C" gc_status gc_calibrate_batched(gc_ctx *ctx, int n_arrays, const gc_ba
     size_t smem = 0;
     for (int a = 0; a < n_arrays; ++a) {
         const size_t hot = cg_hot_floats(bp.arr[a].N, bp.arr[a].n_ubl) * sizeof(float);
-        if (hot <= kCgSmemMax) smem = std::max(smem, hot);
+        const size_t both = hot + cg_coarse_floats(bp.arr[a].L, bp.arr[a].n_ubl) * sizeof(float);
+        if (both <= kCgSmemMax) smem = std::max(smem, both);
+        else if (hot <= kCgSmemMax) smem = std::max(smem, hot);
     }
     bp.smem_floats = (int)(smem / sizeof(float));
     e = cudaFuncSetAttribute(lincal_cg_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCgSmemMax);
