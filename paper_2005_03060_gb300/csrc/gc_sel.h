@@ -23,14 +23,14 @@ struct gc_sel {
     int n_groups = 0, n_windows = 0;
     std::vector<int32_t> grp_types;  // type indices, grouped
     std::vector<int32_t> grp_off;    // [n_groups + 1]
-    std::vector<int32_t> grp_t0, grp_t1, grp_first, grp_win;   // [n_groups]
+    std::vector<int32_t> grp_t0, grp_t1, grp_first, grp_win, grp_dymax;   // [n_groups]
     // device copies (one allocation, on `device`)
     int device = -1;
     void *d_base = nullptr;
     int32_t *d_types = nullptr, *d_type_ptr = nullptr, *d_pair_i = nullptr, *d_pair_j = nullptr,
             *d_pair_type = nullptr, *d_win_t0 = nullptr, *d_win_t1 = nullptr, *d_grp_types = nullptr,
             *d_grp_off = nullptr, *d_grp_t0 = nullptr, *d_grp_t1 = nullptr, *d_grp_first = nullptr,
-            *d_grp_win = nullptr, *d_nbr = nullptr;
+            *d_grp_win = nullptr, *d_nbr = nullptr, *d_grp_dymax = nullptr;
 };
 
 gc_status gc_sel_upload(gc_ctx *ctx, gc_sel *s);

@@ -103,6 +103,7 @@ void fill_groups(gc_sel *s) {
     s->grp_t1.clear();
     s->grp_first.clear();
     s->grp_win.clear();
+    s->grp_dymax.clear();
     std::vector<int> order(s->n_ubl);
     for (int k = 0; k < s->n_ubl; ++k) order[k] = k;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return s->win_t0[a] < s->win_t0[b]; });
@@ -112,12 +113,14 @@ void fill_groups(gc_sel *s) {
         const int t0 = s->win_t0[order[k]], t1 = s->win_t1[order[k]];
         bool first = true;
         while (k < s->n_ubl && s->win_t0[order[k]] == t0) {
-            int n = 0;
+            int n = 0, dymax = 0;
             while (k < s->n_ubl && s->win_t0[order[k]] == t0 && n < GC_XENG_NTY) {
                 s->grp_types.push_back(order[k]);
+                dymax = std::max(dymax, s->types[2 * order[k] + 1]);
                 ++k;
                 ++n;
             }
+            s->grp_dymax.push_back(dymax);
             s->grp_off.push_back((int32_t)s->grp_types.size());
             s->grp_t0.push_back(t0);
             s->grp_t1.push_back(t1);
@@ -150,8 +153,8 @@ gc_status gc_sel_upload(gc_ctx *ctx, gc_sel *s) {
     const std::vector<int32_t> *parts[] = {&s->types,   &s->type_ptr, &s->pair_i,    &s->pair_j,
                                            &s->pair_type, &s->win_t0, &s->win_t1,   &s->grp_types,
                                            &s->grp_off, &s->grp_t0,   &s->grp_t1,   &s->grp_first,
-                                           &s->grp_win,   &s->nbr};
-    constexpr int kParts = 14;
+                                           &s->grp_win,   &s->nbr,      &s->grp_dymax};
+    constexpr int kParts = 15;
     size_t total = 0;
     size_t offs[kParts];
     for (int i = 0; i < kParts; ++i) {
@@ -176,7 +179,7 @@ gc_status gc_sel_upload(gc_ctx *ctx, gc_sel *s) {
     int32_t **dst[] = {&s->d_types,   &s->d_type_ptr, &s->d_pair_i,   &s->d_pair_j,
                        &s->d_pair_type, &s->d_win_t0, &s->d_win_t1,   &s->d_grp_types,
                        &s->d_grp_off, &s->d_grp_t0,   &s->d_grp_t1,   &s->d_grp_first,
-                       &s->d_grp_win,   &s->d_nbr};
+                       &s->d_grp_win,   &s->d_nbr,      &s->d_grp_dymax};
     for (int i = 0; i < kParts; ++i) *dst[i] = reinterpret_cast<int32_t *>(static_cast<char *>(base) + offs[i]);
     if (s->nbr.empty()) s->d_nbr = nullptr;
     s->d_base = base;

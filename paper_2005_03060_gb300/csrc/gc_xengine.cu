@@ -30,25 +30,31 @@ struct XParams {
     float2 *part;             // [n_tsplit][C][P]
     float *apart;             // [n_windows * n_tsplit][C][N] (may be null)
     const int32_t *grp_win;   // window index per group
+    const int32_t *grp_dymax; // largest dy among the group's types
     unsigned int *status;
     int use_tma;
+    int rows_stage;           // 1: stage only the block's rows plus the dy halo
+    size_t stage_stride;      // bytes per stage buffer (ns staged samples)
 };
 
-__device__ __forceinline__ float2 ld_volt(const unsigned char *s, int idx, int vfmt) {
-    if (vfmt == GC_C64) return reinterpret_cast<const float2 *>(s)[idx];
+template <int VF>
+__device__ __forceinline__ float2 ld_volt(const unsigned char *s, int idx) {
+    if (VF == GC_C64) return reinterpret_cast<const float2 *>(s)[idx];
     const int b = (int)(signed char)s[idx];
     return make_float2((float)(b >> 4), (float)((int)(signed char)(b << 4) >> 4));
 }
 
+// VF: voltage format; NTY: type slots per thread (>= the largest group)
+template <int VF, int NTY>
 __global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[2];
     __shared__ int s_dx[GC_XENG_NTY], s_dy[GC_XENG_NTY], s_base[GC_XENG_NTY];
     __shared__ int s_err;
     const int tid = threadIdx.x;
-    const int esz = p.vfmt == GC_C64 ? 8 : 1;
+    constexpr int esz = VF == GC_C64 ? 8 : 1;
     const size_t sample_bytes = (size_t)p.N * esz;
-    const size_t stage_stride = ((sample_bytes * p.ns + 127) / 128) * 128;
+    const size_t stage_stride = p.stage_stride;
     const int L = p.L;
     if (tid == 0) {
         s_err = 0;
@@ -80,28 +86,41 @@ __global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
         const bool own = j < p.N;
         const unsigned char *vc = static_cast<const unsigned char *>(p.volt) + (size_t)c * p.T * sample_bytes;
         const int n_st = (tb - ta + p.ns - 1) / p.ns;
+        // staged part of each sample: rows [y_lo, y_hi) (whole sample without row staging)
+        const int y_lo = p.rows_stage ? (rb * kXThreads) / L : 0;
+        const int y_hi = p.rows_stage ? min(L, (min(p.N, (rb + 1) * kXThreads) - 1) / L + 1 + p.grp_dymax[g]) : L;
+        const size_t part_bytes = (size_t)(y_hi - y_lo) * L * esz;   // staged bytes per sample
+        const size_t src_off = (size_t)y_lo * L * esz;
+        auto issue = [&](int t, int cnt, uint32_t b) {
+            unsigned char *dst = smem + b * stage_stride;
+            gc_mbar_expect_tx(&bars[b], (uint32_t)(cnt * part_bytes));
+            if (part_bytes == sample_bytes) {
+                gc_bulk_load(dst, vc + (size_t)t * sample_bytes, (uint32_t)(cnt * sample_bytes), &bars[b]);
+            } else {
+                for (int u = 0; u < cnt; ++u)
+                    gc_bulk_load(dst + u * part_bytes, vc + (size_t)(t + u) * sample_bytes + src_off,
+                                 (uint32_t)part_bytes, &bars[b]);
+            }
+        };
         if (p.use_tma && tid == 0) {
             for (int k = 0; k < 2 && k < n_st; ++k) {
                 const int t = ta + k * p.ns;
-                const int cnt = min(p.ns, tb - t);
-                const uint32_t b = ld_count & 1u;
-                gc_mbar_expect_tx(&bars[b], (uint32_t)(cnt * sample_bytes));
-                gc_bulk_load(smem + b * stage_stride, vc + (size_t)t * sample_bytes, (uint32_t)(cnt * sample_bytes),
-                             &bars[b]);
+                issue(t, min(p.ns, tb - t), ld_count & 1u);
                 ++ld_count;
             }
         }
         __syncthreads();
 
-        float2 acc[GC_XENG_NTY];
-        int nb[GC_XENG_NTY];   // neighbour antenna r_j + d_k, or -1 (fixed for the item)
+        float2 acc[NTY];
+        int nb[NTY];   // neighbour antenna r_j + d_k, or -1 (fixed for the item)
+        const bool do_autos = p.apart && p.grp_first[g];
 #pragma unroll
-        for (int k = 0; k < GC_XENG_NTY; ++k) {
+        for (int k = 0; k < NTY; ++k) {
             acc[k] = make_float2(0.f, 0.f);
             nb[k] = -1;
             if (k < ntype && own) {
                 const int xi = x + s_dx[k], yi = y + s_dy[k];
-                if (xi >= 0 && xi < L && yi >= 0 && yi < L) nb[k] = yi * L + xi;
+                if (xi >= 0 && xi < L && yi >= 0 && yi < L) nb[k] = (yi - y_lo) * L + xi;
             }
         }
         float aut = 0.f;
@@ -123,20 +142,23 @@ __global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
                 if (s_err) break;
             } else {
                 // plain staging (sizes or alignment TMA cannot take)
-                for (size_t i = tid; i < cnt * sample_bytes; i += kXThreads)
-                    smem[i] = vc[(size_t)t * sample_bytes + i];
+                for (size_t i = tid; i < cnt * part_bytes; i += kXThreads) {
+                    const size_t u = i / part_bytes, o = i - u * part_bytes;
+                    smem[i] = vc[(size_t)(t + u) * sample_bytes + src_off + o];
+                }
                 stage = smem;
                 __syncthreads();
             }
             if (own) {
+                const int jl = j - y_lo * L;   // own antenna within the staged rows
                 for (int u = 0; u < cnt; ++u) {
-                    const unsigned char *sv = stage + u * sample_bytes;
-                    const float2 b = ld_volt(sv, j, p.vfmt);
-                    aut = fmaf(b.x, b.x, fmaf(b.y, b.y, aut));
+                    const unsigned char *sv = stage + u * part_bytes;
+                    const float2 b = ld_volt<VF>(sv, jl);
+                    if (do_autos) aut = fmaf(b.x, b.x, fmaf(b.y, b.y, aut));
 #pragma unroll
-                    for (int k = 0; k < GC_XENG_NTY; ++k) {
+                    for (int k = 0; k < NTY; ++k) {
                         if (nb[k] >= 0) {
-                            const float2 a = ld_volt(sv, nb[k], p.vfmt);
+                            const float2 a = ld_volt<VF>(sv, nb[k]);
                             // a * conj(b)
                             acc[k].x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc[k].x));
                             acc[k].y = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc[k].y));
@@ -148,11 +170,7 @@ __global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
             if (p.use_tma && tid == 0 && st + 2 < n_st) {
                 gc_fence_proxy_async();
                 const int t2 = ta + (st + 2) * p.ns;
-                const int cnt2 = min(p.ns, tb - t2);
-                const uint32_t b = ld_count & 1u;
-                gc_mbar_expect_tx(&bars[b], (uint32_t)(cnt2 * sample_bytes));
-                gc_bulk_load(smem + b * stage_stride, vc + (size_t)t2 * sample_bytes,
-                             (uint32_t)(cnt2 * sample_bytes), &bars[b]);
+                issue(t2, min(p.ns, tb - t2), ld_count & 1u);
                 ++ld_count;
             }
         }
@@ -160,7 +178,7 @@ __global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
         if (own) {
             float2 *out = p.part + ((size_t)ts * p.C + c) * p.P;
 #pragma unroll
-            for (int k = 0; k < GC_XENG_NTY; ++k) {
+            for (int k = 0; k < NTY; ++k) {
                 if (k < ntype) {
                     const int dx = s_dx[k], dy = s_dy[k];
                     const int xlo = max(0, -dx), ylo = max(0, -dy);
@@ -169,7 +187,7 @@ __global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
                         out[s_base[k] + (y - ylo) * (L - abs(dx)) + (x - xlo)] = acc[k];
                 }
             }
-            if (p.apart && p.grp_first[g]) {
+            if (do_autos) {
                 const int slot = p.grp_win[g] * p.n_tsplit + ts;
                 p.apart[((size_t)slot * p.C + c) * p.N + j] = aut;
             }
@@ -232,24 +250,51 @@ extern "C" gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, i
     const int N = L * L;
     const int esz = vfmt == GC_C64 ? 8 : 1;
     const size_t sample_bytes = (size_t)N * esz;
-    const int ns = (int)std::max<size_t>(1, std::min<size_t>(8, (32u << 10) / sample_bytes));
-    const size_t stage_stride = ((sample_bytes * ns + 127) / 128) * 128;
+    const bool tma = gc_aligned(volt, 16) && sample_bytes % 16 == 0;
+    const int n_rowblk = (N + kXThreads - 1) / kXThreads;
+    // stage row ranges when the halo is small (subset selections); a bulk copy
+    // per row range needs 16-byte aligned rows
+    int dymax_all = 0, ntmax = 0;
+    for (int k = 0; k < sel->n_ubl; ++k) dymax_all = std::max(dymax_all, sel->types[2 * k + 1]);
+    for (int g = 0; g < sel->n_groups; ++g) ntmax = std::max(ntmax, sel->grp_off[g + 1] - sel->grp_off[g]);
+    const int rows_stage = (n_rowblk > 1 && (kXThreads / L + 1 + dymax_all) < L &&
+                            (!tma || ((size_t)L * esz) % 16 == 0)) ? 1 : 0;
+    const size_t staged = rows_stage ? (size_t)std::min(L, kXThreads / L + 2 + dymax_all) * L * esz : sample_bytes;
+    const int ns = (int)std::max<size_t>(1, std::min<size_t>(16, (32u << 10) / staged));
+    const size_t stage_stride = ((staged * ns + 127) / 128) * 128;
     const size_t smem = 2 * stage_stride;
     if (smem > 200u * 1024u) return gc_fail(ctx, GC_EUNSUPPORTED, "gc_reduce: grid too large for the stage");
-    const bool tma = gc_aligned(volt, 16) && sample_bytes % 16 == 0;
-    e = cudaFuncSetAttribute(xeng_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int nty = ntmax <= 4 ? 4 : (ntmax <= 8 ? 8 : (ntmax <= 12 ? 12 : 16));
+    const void *kern;
+    if (vfmt == GC_C64)
+        kern = nty == 4 ? (const void *)xeng_accumulate<GC_C64, 4> : nty == 8 ? (const void *)xeng_accumulate<GC_C64, 8>
+             : nty == 12 ? (const void *)xeng_accumulate<GC_C64, 12> : (const void *)xeng_accumulate<GC_C64, 16>;
+    else
+        kern = nty == 4 ? (const void *)xeng_accumulate<GC_I4C, 4> : nty == 8 ? (const void *)xeng_accumulate<GC_I4C, 8>
+             : nty == 12 ? (const void *)xeng_accumulate<GC_I4C, 12> : (const void *)xeng_accumulate<GC_I4C, 16>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(xeng_accumulate)");
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, xeng_accumulate, kXThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kXThreads, smem);
     if (e != cudaSuccess || occ < 1) return gc_cuda_fail(ctx, e, "occupancy(xeng_accumulate)");
     const int slots = occ * ctx->sm_count;
-    const int n_rowblk = (N + kXThreads - 1) / kXThreads;
     const long base_items = (long)C * sel->n_groups * n_rowblk;
-    // split long windows in time until the work fills two waves (bounded)
-    int n_tsplit = 1;
+    // split long windows in time so that the items fill whole waves of the
+    // resident CTAs (slices of at least 64 samples)
     int max_win = 0;
     for (int g = 0; g < sel->n_groups; ++g) max_win = std::max(max_win, sel->grp_t1[g] - sel->grp_t0[g]);
-    while (base_items * n_tsplit < 2L * slots && n_tsplit < 16 && max_win / (n_tsplit * 2) >= 64) n_tsplit *= 2;
+    int n_tsplit = 1;
+    double best = -1.0;
+    for (int ts = 1; ts <= 16; ++ts) {
+        if (ts > 1 && max_win / ts < 64) break;
+        const long items = base_items * ts;
+        const long waves = (items + slots - 1) / slots;
+        const double eff = (double)items / ((double)waves * slots) - 0.01 * ts;   // prefer fewer slices
+        if (eff > best) {
+            best = eff;
+            n_tsplit = ts;
+        }
+    }
     if (ctx->tune[GC_TUNE_XENG_TSPLIT] > 0) n_tsplit = std::min(ctx->tune[GC_TUNE_XENG_TSPLIT], 64);
     const size_t part_bytes = (size_t)n_tsplit * C * sel->P * sizeof(float2);
     const size_t apart_bytes = autos ? (size_t)sel->n_windows * n_tsplit * C * N * sizeof(float) : 0;
@@ -283,11 +328,16 @@ extern "C" gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, i
     p.part = part;
     p.apart = apart;
     p.grp_win = sel->d_grp_win;
+    p.grp_dymax = sel->d_grp_dymax;
     p.status = ctx->status_dev;
     p.use_tma = tma ? 1 : 0;
+    p.rows_stage = rows_stage;
+    p.stage_stride = stage_stride;
     const int grid = (int)std::min<long>(p.n_items, slots);
     int rec = gc_prof_begin(ctx, s, "xeng_accumulate");
-    xeng_accumulate<<<grid, kXThreads, smem, s>>>(p);
+    void *args[] = {&p};
+    e = cudaLaunchKernel(kern, dim3(grid), dim3(kXThreads), args, smem, s);
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch xeng_accumulate");
     gc_prof_end(ctx, s, rec);
     e = cudaGetLastError();
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch xeng_accumulate");
