@@ -57,7 +57,11 @@ typedef enum gc_status {
 
 typedef enum gc_vfmt {
     GC_C64 = 0,           /* complex64: 8 bytes per antenna-sample */
-    GC_I4C = 1            /* 4+4-bit complex: 1 byte per antenna-sample */
+    GC_I4C = 1,           /* 4+4-bit complex: 1 byte per antenna-sample
+                             (two's-complement Re in the high nibble, Im in the low) */
+    GC_C32H = 2           /* binary16 pair (Re, Im): 4 bytes per antenna-sample; the
+                             FP16-storage variant -- arithmetic stays FP32.
+                             Accepted by gc_correlate only. */
 } gc_vfmt;
 
 typedef struct gc_ctx gc_ctx;
@@ -111,17 +115,20 @@ GC_API int gc_fft_size(int L);
  *   V^unique_c(d) = 1/(T N_d) sum_t sum_{r_i - r_j = d} w_i(t) w_j(t)^*,
  *   N_d = (L - |dx|)(L - |dy|).
  *
- *   volt     [C][T][L*L] c64 (8-byte aligned) or i4c (device)
+ *   volt     [C][T][L*L] c64 (8-byte aligned), c32h (4-byte aligned) or
+ *            i4c (device)
  *   gains    [C][L*L]    c64 (device); a zero gain gives inf/NaN output
  *   vunique  [C][2L-1][2L-1] c64 (device), index [dy + L - 1][dx + L - 1]
- *   1 <= L <= 64, C >= 1, T >= 1.
+ *   1 <= L <= 128, C >= 1, T >= 1 (GC_EINVAL otherwise); L > 64 (M = 256)
+ *   is built for i4c only (GC_EUNSUPPORTED for c64 / c32h).
  * Voltages are staged by TMA when the buffer is 16-byte aligned and a grid
- * row is a multiple of 16 bytes (c64: L even; i4c: L % 16 == 0), by plain
- * loads otherwise.
+ * row is a multiple of 16 bytes (c64: L even; c32h: L % 4 == 0; i4c:
+ * L % 16 == 0), by plain loads otherwise.
  *
  * Uses the context's scratch workspace for per-time-chunk power spectra
- * (C * chunks * M^2 * 4 bytes; grown with cudaMalloc on first need, which
- * synchronises the device).  Two kernels are enqueued on `stream`.
+ * (C * chunks * M^2 * 4 bytes, plus C * M * (2L-1) * 8 bytes for M = 256;
+ * grown with cudaMalloc on first need, which synchronises the device).  Two
+ * kernels (three for M = 256) are enqueued on `stream`.
  */
 GC_API gc_status gc_correlate(gc_ctx *ctx, const void *volt, int vfmt, int L, int C, int T,
                        const float *gains, float *vunique, void *stream);

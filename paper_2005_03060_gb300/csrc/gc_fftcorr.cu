@@ -16,7 +16,15 @@
 // both passes see only the L non-zero inputs (folds over L <= M/2 inputs).
 //
 // Kernel 2 (fftcorr_finalize) sums the chunk spectra (FP64), inverse-DFTs
-// the (2L-1)^2 lags that exist, and divides by T N_d.
+// the (2L-1)^2 lags that exist, and divides by T N_d.  For M = 256 the
+// spectrum no longer fits one CTA's shared memory and the inverse DFT runs as
+// two passes (fftcorr_finalize_rows / fftcorr_finalize_cols) through global
+// memory.
+//
+// Voltage formats: complex64 (8 B), binary16 pairs (4 B; the FP16-storage
+// variant, FP32 arithmetic) and 4+4-bit integers (1 B).
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <cstdio>
 
@@ -138,7 +146,7 @@ struct Cfg {
     static constexpr int NCOL = MX * S2;                // column items per group
     static constexpr int NTHREADS = G * NCOL;
     static constexpr int GNT = G * NT;                  // samples per iteration
-    static constexpr int ESZ = VF == GC_C64 ? 8 : 1;    // bytes per antenna-sample
+    static constexpr int ESZ = VF == GC_C64 ? 8 : (VF == GC_C32H ? 4 : 1);   // bytes per antenna-sample
     // padded stage row (bytes): the smallest odd number of 16-byte units
     // holding LMAX elements, so rows read by consecutive lanes hit distinct banks
     static constexpr int ROWU = (LMAX * ESZ + 15) / 16;
@@ -157,7 +165,7 @@ struct Cfg {
     static constexpr int SMEM = OFF_INTER + GNT * LMAX * IROW * 8;
     static_assert(MX % F1 == 0 && M % F2 == 0, "bad FFT split");
     static_assert(ROWB % 16 == 0 && (ROWB / 16) % 2 == 1, "stage row must be an odd number of 16B");
-    static_assert(F1 % 2 == 0 && (VF == GC_C64 || F1 % 16 == 0 || LMAX <= 16), "row reads");
+    static_assert(F1 % 4 == 0 && (VF != GC_I4C || F1 % 16 == 0 || LMAX <= 16), "row reads");
 };
 
 struct Params {
@@ -190,12 +198,22 @@ __device__ void stage_plain(const Params &p, unsigned char *stage, int c, int t)
             float2 v = make_float2(0.f, 0.f);
             if (ok) v = reinterpret_cast<const float2 *>(p.volt)[src];
             reinterpret_cast<float2 *>(stage)[(u * K::LMAX + y) * K::ROWE + x] = v;
+        } else if (K::VF == GC_C32H) {
+            unsigned int v = 0u;
+            if (ok) v = reinterpret_cast<const unsigned int *>(p.volt)[src];
+            reinterpret_cast<unsigned int *>(stage)[(u * K::LMAX + y) * K::ROWE + x] = v;
         } else {
             unsigned char v = 0;
             if (ok) v = reinterpret_cast<const unsigned char *>(p.volt)[src];
             stage[(u * K::LMAX + y) * K::ROWB + x] = v;
         }
     }
+}
+
+__device__ __forceinline__ float2 h2_to_f2(unsigned int bits) {
+    __half2 h;
+    *reinterpret_cast<unsigned int *>(&h) = bits;
+    return __half22float2(h);
 }
 
 __device__ __forceinline__ float2 i4c_to_f2(unsigned int byte) {
@@ -319,6 +337,24 @@ fftcorr_accumulate(const __grid_constant__ CUtensorMap tmap, const Params p) {
                                 const float2 w1 = cmul(make_float2(vv.z, vv.w), make_float2(cc.z, cc.w));
                                 b[xp] = cfma(b[xp], w0, tws[(k * x) & (K::M - 1)]);
                                 b[xp + 1] = cfma(b[xp + 1], w1, tws[(k * (x + 1)) & (K::M - 1)]);
+                            }
+                        }
+                    } else if (K::VF == GC_C32H) {
+#pragma unroll
+                        for (int xp = 0; xp < K::F1; xp += 4) {
+                            const int x = xp + K::F1 * j;
+                            if (x < K::LMAX) {
+                                const uint4 raw = *reinterpret_cast<const uint4 *>(srow + x * 4);
+                                const float4 c01 = *reinterpret_cast<const float4 *>(crow + x);
+                                const float4 c23 = *reinterpret_cast<const float4 *>(crow + x + 2);
+                                const float2 w0 = cmul(h2_to_f2(raw.x), make_float2(c01.x, c01.y));
+                                const float2 w1 = cmul(h2_to_f2(raw.y), make_float2(c01.z, c01.w));
+                                const float2 w2 = cmul(h2_to_f2(raw.z), make_float2(c23.x, c23.y));
+                                const float2 w3 = cmul(h2_to_f2(raw.w), make_float2(c23.z, c23.w));
+                                b[xp] = cfma(b[xp], w0, tws[(k * x) & (K::M - 1)]);
+                                b[xp + 1] = cfma(b[xp + 1], w1, tws[(k * (x + 1)) & (K::M - 1)]);
+                                b[xp + 2] = cfma(b[xp + 2], w2, tws[(k * (x + 2)) & (K::M - 1)]);
+                                b[xp + 3] = cfma(b[xp + 3], w3, tws[(k * (x + 3)) & (K::M - 1)]);
                             }
                         }
                     } else {
@@ -447,7 +483,84 @@ fftcorr_finalize(const float *__restrict__ ppart, int n_parts, float2 *__restric
     }
 }
 
+// Two-pass inverse DFT for large M (the M x M spectrum of one channel does
+// not fit in shared memory beside its partial transform).
+//   rows: Q[c][ky][dx] = sum_kx P[ky][kx] exp(+2 pi i kx dx / M),
+//         P = FP64 sum of the chunk spectra; kFinRows k_y rows per CTA.
+//   cols: V[c][dy][dx] = (1/M^2) sum_ky Q[ky][dx] exp(+2 pi i ky dy / M) / (T N_d);
+//         kFinCols lag columns per CTA.
+constexpr int kFinRows = 8;
+constexpr int kFinCols = 16;
+
+template <int M>
+__global__ void __launch_bounds__(256)
+fftcorr_finalize_rows(const float *__restrict__ ppart, int n_parts, float2 *__restrict__ Q, int L) {
+    __shared__ float P[kFinRows][M];
+    __shared__ float2 tws[M];
+    const int c = blockIdx.x, ky0 = blockIdx.y * kFinRows, W = 2 * L - 1;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) {
+        const cf w = c_tw.v[e * (256 / M)];
+        tws[e] = make_float2(w.x, w.y);
+    }
+    const float *src = ppart + (size_t)c * n_parts * M * M + (size_t)ky0 * M;
+    for (int k = threadIdx.x; k < kFinRows * M; k += blockDim.x) {
+        double s = 0.0;
+        for (int pp = 0; pp < n_parts; ++pp) s += (double)src[(size_t)pp * M * M + k];
+        P[k / M][k % M] = (float)s;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kFinRows * W; idx += blockDim.x) {
+        const int r = idx / W, dx = idx % W - (L - 1);
+        float re = 0.f, im = 0.f;
+        for (int kx = 0; kx < M; ++kx) {
+            const float2 w = tws[(kx * dx) & (M - 1)];
+            const float pv = P[r][kx];
+            re = fmaf(pv, w.x, re);
+            im = fmaf(-pv, w.y, im);
+        }
+        Q[((size_t)c * M + ky0 + r) * W + (dx + L - 1)] = make_float2(re, im);
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256)
+fftcorr_finalize_cols(const float2 *__restrict__ Q, float2 *__restrict__ vunique, int L, int T) {
+    __shared__ float2 Qs[M][kFinCols];
+    __shared__ float2 tws[M];
+    const int c = blockIdx.x, dx0 = blockIdx.y * kFinCols, W = 2 * L - 1;
+    const int ncol = min(kFinCols, W - dx0);
+    for (int e = threadIdx.x; e < M; e += blockDim.x) {
+        const cf w = c_tw.v[e * (256 / M)];
+        tws[e] = make_float2(w.x, w.y);
+    }
+    for (int k = threadIdx.x; k < M * kFinCols; k += blockDim.x) {
+        const int ky = k / kFinCols, j = k % kFinCols;
+        Qs[ky][j] = j < ncol ? Q[((size_t)c * M + ky) * W + dx0 + j] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < W * ncol; idx += blockDim.x) {
+        const int dyi = idx / ncol, j = idx % ncol;
+        const int dy = dyi - (L - 1), dxi = dx0 + j, dx = dxi - (L - 1);
+        float re = 0.f, im = 0.f;
+        for (int ky = 0; ky < M; ++ky) {
+            const float2 w = tws[(ky * dy) & (M - 1)];
+            const float2 qv = Qs[ky][j];
+            re = fmaf(qv.x, w.x, fmaf(qv.y, w.y, re));
+            im = fmaf(qv.y, w.x, fmaf(-qv.x, w.y, im));
+        }
+        const int nd = (L - (dx < 0 ? -dx : dx)) * (L - (dy < 0 ? -dy : dy));
+        const float s = (float)(1.0 / ((double)M * M * (double)T * nd));
+        vunique[(size_t)c * W * W + (size_t)dyi * W + dxi] = make_float2(re * s, im * s);
+    }
+}
+
 // ----------------------------------------------------------------- host side
+template <class K>
+CUtensorMapDataType tma_dtype() {
+    return K::VF == GC_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64
+                           : (K::VF == GC_C32H ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
+}
+
 template <class K>
 struct Launcher {
     static gc_status run(gc_ctx *ctx, const void *volt, int L, int C, int T, const float *gains,
@@ -494,8 +607,9 @@ struct Launcher {
         p.chunk_len = best_len;
         p.n_chunks = best_n;
         p.n_items = C * K::R * best_n;
-        const size_t need = (size_t)C * best_n * K::G * K::M * K::M * sizeof(float);
-        gc_status st = gc_scratch_reserve(ctx, need);
+        const size_t part_bytes = ((size_t)C * best_n * K::G * K::M * K::M * sizeof(float) + 255) / 256 * 256;
+        const size_t q_bytes = K::M > 128 ? (size_t)C * K::M * (2 * L - 1) * sizeof(float2) : 0;
+        gc_status st = gc_scratch_reserve(ctx, part_bytes + q_bytes);
         if (st != GC_OK) return st;
         p.ppart = reinterpret_cast<float *>(ctx->scratch);
 
@@ -506,9 +620,7 @@ struct Launcher {
             const uint64_t strides[3] = {(uint64_t)L * K::ESZ, (uint64_t)N * K::ESZ,
                                          (uint64_t)T * N * K::ESZ};
             const uint32_t box[4] = {(uint32_t)K::ROWE, (uint32_t)K::LMAX, (uint32_t)K::GNT, 1u};
-            st = gc_encode_tiled(ctx, &tmap,
-                                 K::VF == GC_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
-                                 4, const_cast<void *>(volt), dims, strides, box);
+            st = gc_encode_tiled(ctx, &tmap, tma_dtype<K>(), 4, const_cast<void *>(volt), dims, strides, box);
             if (st != GC_OK) return st;
         }
         const int grid = (int)std::min<long>(p.n_items, slots);
@@ -519,13 +631,22 @@ struct Launcher {
         if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch fftcorr_accumulate");
 
         const int W = 2 * L - 1;
-        const size_t fsmem = (size_t)K::M * K::M * 4 + (size_t)K::M * W * 8 + K::M * 8;
-        auto fin = fftcorr_finalize<K::M>;
-        e = cudaFuncSetAttribute(fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
-        if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(fftcorr_finalize)");
-        rec = gc_prof_begin(ctx, stream, "fftcorr_finalize");
-        fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n * K::G, reinterpret_cast<float2 *>(vunique), L, T);
-        gc_prof_end(ctx, stream, rec);
+        if constexpr (K::M > 128) {
+            float2 *Q = reinterpret_cast<float2 *>(static_cast<char *>(ctx->scratch) + part_bytes);
+            rec = gc_prof_begin(ctx, stream, "fftcorr_finalize");
+            fftcorr_finalize_rows<K::M><<<dim3(C, K::M / kFinRows), 256, 0, stream>>>(p.ppart, best_n * K::G, Q, L);
+            fftcorr_finalize_cols<K::M><<<dim3(C, (W + kFinCols - 1) / kFinCols), 256, 0, stream>>>(
+                Q, reinterpret_cast<float2 *>(vunique), L, T);
+            gc_prof_end(ctx, stream, rec);
+        } else {
+            const size_t fsmem = (size_t)K::M * K::M * 4 + (size_t)K::M * W * 8 + K::M * 8;
+            auto fin = fftcorr_finalize<K::M>;
+            e = cudaFuncSetAttribute(fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+            if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(fftcorr_finalize)");
+            rec = gc_prof_begin(ctx, stream, "fftcorr_finalize");
+            fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n * K::G, reinterpret_cast<float2 *>(vunique), L, T);
+            gc_prof_end(ctx, stream, rec);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch fftcorr_finalize");
         return GC_OK;
@@ -541,6 +662,15 @@ using CfgI16 = Cfg<16, 1, 16, 16, 2, 8, GC_I4C>;
 using CfgI32 = Cfg<32, 1, 32, 32, 2, 4, GC_I4C>;
 using CfgI64 = Cfg<64, 1, 32, 32, 2, 1, GC_I4C>;
 using CfgI128 = Cfg<128, 4, 32, 32, 2, 1, GC_I4C>;
+// M = 256 (L = 65..128): 4+4-bit only -- one complex64 or binary16 grid sample
+// (128 rows of 1 KB / 512 B) does not fit a double-buffered stage beside the
+// 133 KB coefficient table.  Eight k_x residues, one sample per iteration,
+// one CTA of 256 threads per SM (201 KB shared memory).
+using CfgI256 = Cfg<256, 8, 16, 32, 1, 1, GC_I4C>;
+using CfgH16 = Cfg<16, 1, 16, 16, 2, 8, GC_C32H>;
+using CfgH32 = Cfg<32, 1, 32, 32, 2, 4, GC_C32H>;
+using CfgH64 = Cfg<64, 1, 32, 32, 2, 1, GC_C32H>;
+using CfgH128 = Cfg<128, 4, 32, 32, 2, 1, GC_C32H>;
 
 }  // namespace
 
@@ -549,10 +679,14 @@ extern "C" gc_status gc_correlate(gc_ctx *ctx, const void *volt, int vfmt, int L
     if (!ctx) return GC_EINVAL;
     ctx->last_error.clear();
     if (!volt || !gains || !vunique) return gc_fail(ctx, GC_EINVAL, "gc_correlate: null buffer");
-    if (L < 1 || L > 64 || C < 1 || T < 1)
-        return gc_fail(ctx, GC_EINVAL, "gc_correlate: need 1 <= L <= 64, C >= 1, T >= 1");
-    if (vfmt != GC_C64 && vfmt != GC_I4C) return gc_fail(ctx, GC_EINVAL, "gc_correlate: unknown voltage format");
-    if (!gc_aligned(gains, 8) || !gc_aligned(vunique, 8) || (vfmt == GC_C64 && !gc_aligned(volt, 8)))
+    if (L < 1 || L > 128 || C < 1 || T < 1)
+        return gc_fail(ctx, GC_EINVAL, "gc_correlate: need 1 <= L <= 128, C >= 1, T >= 1");
+    if (vfmt != GC_C64 && vfmt != GC_I4C && vfmt != GC_C32H)
+        return gc_fail(ctx, GC_EINVAL, "gc_correlate: unknown voltage format");
+    if (L > 64 && vfmt != GC_I4C)
+        return gc_fail(ctx, GC_EUNSUPPORTED, "gc_correlate: L > 64 is built for 4+4-bit voltages only");
+    if (!gc_aligned(gains, 8) || !gc_aligned(vunique, 8) || (vfmt == GC_C64 && !gc_aligned(volt, 8)) ||
+        (vfmt == GC_C32H && !gc_aligned(volt, 4)))
         return gc_fail(ctx, GC_EINVAL, "gc_correlate: misaligned buffer");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaSetDevice");
@@ -565,12 +699,20 @@ extern "C" gc_status gc_correlate(gc_ctx *ctx, const void *volt, int vfmt, int L
             case 64: return Launcher<CfgC64>::run(ctx, volt, L, C, T, gains, vunique, s);
             case 128: return Launcher<CfgC128>::run(ctx, volt, L, C, T, gains, vunique, s);
         }
+    } else if (vfmt == GC_C32H) {
+        switch (M) {
+            case 16: return Launcher<CfgH16>::run(ctx, volt, L, C, T, gains, vunique, s);
+            case 32: return Launcher<CfgH32>::run(ctx, volt, L, C, T, gains, vunique, s);
+            case 64: return Launcher<CfgH64>::run(ctx, volt, L, C, T, gains, vunique, s);
+            case 128: return Launcher<CfgH128>::run(ctx, volt, L, C, T, gains, vunique, s);
+        }
     } else {
         switch (M) {
             case 16: return Launcher<CfgI16>::run(ctx, volt, L, C, T, gains, vunique, s);
             case 32: return Launcher<CfgI32>::run(ctx, volt, L, C, T, gains, vunique, s);
             case 64: return Launcher<CfgI64>::run(ctx, volt, L, C, T, gains, vunique, s);
             case 128: return Launcher<CfgI128>::run(ctx, volt, L, C, T, gains, vunique, s);
+            case 256: return Launcher<CfgI256>::run(ctx, volt, L, C, T, gains, vunique, s);
         }
     }
     return gc_fail(ctx, GC_EUNSUPPORTED, "gc_correlate: no kernel for this grid size");
@@ -690,7 +832,7 @@ gc_status noalloc_run(const NoallocDev &d, const void *volt, int L, int C, int T
         const cuuint32_t box[4] = {(cuuint32_t)K::ROWE, (cuuint32_t)K::LMAX, (cuuint32_t)K::GNT, 1u};
         const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
         CUresult r = reinterpret_cast<Fn>(g_noalloc_encode)(
-            &tmap, K::VF == GC_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 4,
+            &tmap, tma_dtype<K>(), 4,
             const_cast<void *>(volt), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return GC_ECUDA;
@@ -714,9 +856,9 @@ extern "C" gc_status gc_correlate_noalloc(const void *volt, int vfmt, int L, int
                                           float *vunique, unsigned int *status, void *stream) {
     if (!volt || !gains || !vunique) return GC_EINVAL;
     if (L < 1 || L > 64 || C < 1 || T < 1) return GC_EINVAL;
-    if (vfmt != GC_C64 && vfmt != GC_I4C) return GC_EINVAL;
+    if (vfmt != GC_C64 && vfmt != GC_I4C && vfmt != GC_C32H) return GC_EINVAL;
     if (!gc_aligned(gains, 8) || !gc_aligned(vunique, 8) || (vfmt == GC_C64 && !gc_aligned(volt, 8)) ||
-        (status && !gc_aligned(status, 4)))
+        (vfmt == GC_C32H && !gc_aligned(volt, 4)) || (status && !gc_aligned(status, 4)))
         return GC_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GC_ECUDA;
@@ -731,6 +873,13 @@ extern "C" gc_status gc_correlate_noalloc(const void *volt, int vfmt, int L, int
             case 32: return noalloc_run<CfgC32>(*d, volt, L, C, T, gains, vunique, status, s);
             case 64: return noalloc_run<CfgC64>(*d, volt, L, C, T, gains, vunique, status, s);
             case 128: return noalloc_run<CfgC128>(*d, volt, L, C, T, gains, vunique, status, s);
+        }
+    } else if (vfmt == GC_C32H) {
+        switch (M) {
+            case 16: return noalloc_run<CfgH16>(*d, volt, L, C, T, gains, vunique, status, s);
+            case 32: return noalloc_run<CfgH32>(*d, volt, L, C, T, gains, vunique, status, s);
+            case 64: return noalloc_run<CfgH64>(*d, volt, L, C, T, gains, vunique, status, s);
+            case 128: return noalloc_run<CfgH128>(*d, volt, L, C, T, gains, vunique, status, s);
         }
     } else {
         switch (M) {

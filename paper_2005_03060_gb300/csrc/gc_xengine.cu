@@ -10,6 +10,8 @@
 // and sums of those integers stay below 2^24, so FP32 sums are exact and the
 // int32 result is bit-exact.
 // xeng_reduce: sums the time slices (FP64) into V^reduced and the autos.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <cstdio>
 
@@ -40,6 +42,7 @@ struct XParams {
 template <int VF>
 __device__ __forceinline__ float2 ld_volt(const unsigned char *s, int idx) {
     if (VF == GC_C64) return reinterpret_cast<const float2 *>(s)[idx];
+    if (VF == GC_C32H) return __half22float2(reinterpret_cast<const __half2 *>(s)[idx]);
     const int b = (int)(signed char)s[idx];
     return make_float2((float)(b >> 4), (float)((int)(signed char)(b << 4) >> 4));
 }
@@ -52,7 +55,7 @@ __global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
     __shared__ int s_dx[GC_XENG_NTY], s_dy[GC_XENG_NTY], s_base[GC_XENG_NTY];
     __shared__ int s_err;
     const int tid = threadIdx.x;
-    constexpr int esz = VF == GC_C64 ? 8 : 1;
+    constexpr int esz = VF == GC_C64 ? 8 : (VF == GC_C32H ? 4 : 1);
     const size_t sample_bytes = (size_t)p.N * esz;
     const size_t stage_stride = p.stage_stride;
     const int L = p.L;
@@ -215,7 +218,7 @@ __global__ void xeng_reduce(const float2 *__restrict__ part, int n_tsplit, int C
                 re += v.x;
                 im += v.y;
             }
-            if (vfmt == GC_C64) {
+            if (vfmt != GC_I4C) {
                 reinterpret_cast<float2 *>(vred)[idx] = make_float2((float)re, (float)im);
             } else {
                 reinterpret_cast<int2 *>(vred)[idx] = make_int2((int)llrint(re), (int)llrint(im));
@@ -224,7 +227,7 @@ __global__ void xeng_reduce(const float2 *__restrict__ part, int n_tsplit, int C
             const size_t a = idx - total;
             double s = 0.0;
             for (int k = 0; k < n_aslots; ++k) s += apart[(size_t)k * C * N + a];
-            if (vfmt == GC_C64) reinterpret_cast<float *>(autos)[a] = (float)s;
+            if (vfmt != GC_I4C) reinterpret_cast<float *>(autos)[a] = (float)s;
             else reinterpret_cast<int *>(autos)[a] = (int)llrint(s);
         }
     }
@@ -238,17 +241,19 @@ extern "C" gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, i
     ctx->last_error.clear();
     gc_sel *sel = const_cast<gc_sel *>(csel);   // device copies are a cache of the immutable selection
     if (!volt || !sel || !vreduced) return gc_fail(ctx, GC_EINVAL, "gc_reduce: null argument");
-    if (vfmt != GC_C64 && vfmt != GC_I4C) return gc_fail(ctx, GC_EINVAL, "gc_reduce: unknown voltage format");
+    if (vfmt != GC_C64 && vfmt != GC_I4C && vfmt != GC_C32H)
+        return gc_fail(ctx, GC_EINVAL, "gc_reduce: unknown voltage format");
     if (L != sel->L || T < sel->T || C < 1)
         return gc_fail(ctx, GC_EINVAL, "gc_reduce: grid or integration does not match the selection");
-    if (!gc_aligned(vreduced, 8) || (autos && !gc_aligned(autos, 4)) || (vfmt == GC_C64 && !gc_aligned(volt, 8)))
+    if (!gc_aligned(vreduced, 8) || (autos && !gc_aligned(autos, 4)) || (vfmt == GC_C64 && !gc_aligned(volt, 8)) ||
+        (vfmt == GC_C32H && !gc_aligned(volt, 4)))
         return gc_fail(ctx, GC_EINVAL, "gc_reduce: misaligned buffer");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaSetDevice");
     gc_status st = gc_sel_upload(ctx, sel);
     if (st != GC_OK) return st;
     const int N = L * L;
-    const int esz = vfmt == GC_C64 ? 8 : 1;
+    const int esz = vfmt == GC_C64 ? 8 : (vfmt == GC_C32H ? 4 : 1);
     const size_t sample_bytes = (size_t)N * esz;
     const bool tma = gc_aligned(volt, 16) && sample_bytes % 16 == 0;
     const int n_rowblk = (N + kXThreads - 1) / kXThreads;
@@ -269,6 +274,9 @@ extern "C" gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, i
     if (vfmt == GC_C64)
         kern = nty == 4 ? (const void *)xeng_accumulate<GC_C64, 4> : nty == 8 ? (const void *)xeng_accumulate<GC_C64, 8>
              : nty == 12 ? (const void *)xeng_accumulate<GC_C64, 12> : (const void *)xeng_accumulate<GC_C64, 16>;
+    else if (vfmt == GC_C32H)
+        kern = nty == 4 ? (const void *)xeng_accumulate<GC_C32H, 4> : nty == 8 ? (const void *)xeng_accumulate<GC_C32H, 8>
+             : nty == 12 ? (const void *)xeng_accumulate<GC_C32H, 12> : (const void *)xeng_accumulate<GC_C32H, 16>;
     else
         kern = nty == 4 ? (const void *)xeng_accumulate<GC_I4C, 4> : nty == 8 ? (const void *)xeng_accumulate<GC_I4C, 8>
              : nty == 12 ? (const void *)xeng_accumulate<GC_I4C, 12> : (const void *)xeng_accumulate<GC_I4C, 16>;

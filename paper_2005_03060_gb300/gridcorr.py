@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libgridcorr.so")
 GC_OK, GC_EINVAL, GC_ENOMEM, GC_ECUDA, GC_ENOCONV, GC_ETIMEOUT, GC_EDEGEN, GC_EUNSUPPORTED = range(8)
 STATUS_NAMES = ["GC_OK", "GC_EINVAL", "GC_ENOMEM", "GC_ECUDA", "GC_ENOCONV", "GC_ETIMEOUT",
                 "GC_EDEGEN", "GC_EUNSUPPORTED"]
-GC_C64, GC_I4C = 0, 1
+GC_C64, GC_I4C, GC_C32H = 0, 1, 2
 
 
 class GridcorrError(RuntimeError):
@@ -82,6 +82,20 @@ _lib.gc_get_tuning.argtypes = [_vp, ctypes.c_char_p, ctypes.POINTER(_i)]
 _lib.gc_get_tuning.restype = _i
 _lib.gc_quantize.argtypes = [_vp, _vp, _i, _i, _i, _vp, _vp, _vp]
 _lib.gc_quantize.restype = _i
+
+
+def _volt_format(volt: torch.Tensor):
+    """(gc_vfmt, (C, T, N)) of a voltage tensor."""
+    if volt.dtype == torch.complex64 and volt.dim() == 3:
+        return GC_C64, tuple(volt.shape)
+    if volt.dtype in (torch.uint8, torch.int8) and volt.dim() == 3:
+        return GC_I4C, tuple(volt.shape)
+    if volt.dtype == torch.complex32 and volt.dim() == 3:
+        return GC_C32H, tuple(volt.shape)
+    if volt.dtype == torch.float16 and volt.dim() == 4 and volt.shape[-1] == 2:
+        return GC_C32H, tuple(volt.shape[:3])
+    raise TypeError("voltages must be complex64 [C, T, N], binary16 pairs (complex32 [C, T, N] or "
+                    "float16 [C, T, N, 2]) or 4+4-bit bytes (uint8/int8 [C, T, N])")
 
 
 def lib() -> ctypes.CDLL:
@@ -156,11 +170,9 @@ class Context:
     def correlate(self, volt: torch.Tensor, gains: torch.Tensor, L: int | None = None,
                   out: torch.Tensor | None = None) -> torch.Tensor:
         """V^unique [C, 2L-1, 2L-1] complex64 from voltages [C, T, L*L]
-        (complex64, or uint8/int8 4+4-bit) and gains [C, L*L] complex64."""
-        vfmt = GC_C64 if volt.dtype == torch.complex64 else GC_I4C
-        if vfmt == GC_I4C and volt.dtype not in (torch.uint8, torch.int8):
-            raise TypeError("voltages must be complex64 or 4+4-bit bytes (uint8/int8)")
-        C, T, N = volt.shape
+        (complex64; binary16 pairs as complex32 [C, T, L*L] or float16
+        [C, T, L*L, 2]; or uint8/int8 4+4-bit) and gains [C, L*L] complex64."""
+        vfmt, (C, T, N) = _volt_format(volt)
         L = L or int(round(N ** 0.5))
         if L * L != N:
             raise ValueError("the antenna axis must hold an L x L grid")
@@ -180,18 +192,18 @@ class Context:
     # ------------------------------------------------------------------ reduce
     def reduce(self, volt: torch.Tensor, sel: Selection, autos: bool = True, out=None, out_autos=None):
         """V^reduced raw pair sums: complex64 [C, P] for complex64 voltages,
-        int32 [C, P, 2] (exact) for 4+4-bit voltages; plus autos [C, N]."""
-        vfmt = GC_C64 if volt.dtype == torch.complex64 else GC_I4C
-        C, T, N = volt.shape
+        int32 [C, P, 2] (exact) for 4+4-bit voltages; plus autos [C, N].
+        Binary16 voltages (complex32 / float16 pairs) give complex64 sums."""
+        vfmt, (C, T, N) = _volt_format(volt)
         if not volt.is_cuda or not volt.is_contiguous():
             raise ValueError("voltages must be a contiguous CUDA tensor")
         if out is None:
-            out = (torch.empty(C, sel.P, dtype=torch.complex64, device=volt.device) if vfmt == GC_C64
+            out = (torch.empty(C, sel.P, dtype=torch.complex64, device=volt.device) if vfmt != GC_I4C
                    else torch.empty(C, sel.P, 2, dtype=torch.int32, device=volt.device))
         a = None
         if autos:
             a = out_autos if out_autos is not None else torch.empty(
-                C, N, dtype=torch.float32 if vfmt == GC_C64 else torch.int32, device=volt.device)
+                C, N, dtype=torch.float32 if vfmt != GC_I4C else torch.int32, device=volt.device)
         self.check(_lib.gc_reduce(self._h, _vp(volt.data_ptr()), vfmt, sel.L, C, T, sel.handle,
                                   _vp(out.data_ptr()), _vp(a.data_ptr() if a is not None else None),
                                   _vp(_stream_ptr(volt.device))))

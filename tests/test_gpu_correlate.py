@@ -74,6 +74,79 @@ def test_correlate_i4c(gc, orc, L, C, T):
         assert lag_err(got[c], ref, L) < TOL, (L, c)
 
 
+HALF_U = 2.0 ** -11   # unit roundoff of binary16
+
+
+def _half(volt):
+    """binary16 storage of complex64 voltages: float16 [C, T, N, 2] and the
+    complex128 values it holds exactly."""
+    h = torch.view_as_real(volt).to(torch.float16).contiguous()
+    return h, torch.view_as_complex(h.to(torch.float64)).numpy()
+
+
+@pytest.mark.parametrize("L,C,T", [(4, 1, 9), (8, 2, 40), (16, 1, 66), (30, 1, 20), (32, 2, 48),
+                                   (61, 1, 7), (64, 1, 10)])
+def test_correlate_c32h(gc, orc, L, C, T):
+    """FP16-storage variant: FP32 arithmetic on binary16 voltages.  Against the
+    oracle on the stored values: the FP32 bound.  Against FP64 on the
+    unrounded voltages: component rounding |dv| <= u |v| moves every product
+    w_i conj(w_j) by at most (2u + u^2)|w_i||w_j|, and by Cauchy-Schwarz the
+    pairs of one lag sum to at most R(0), so the lag-sum error is <= 2u + u^2
+    (u = 2^-11) plus the FP32 bound."""
+    volt, gains, _ = synth.make_voltages(300 + L, L, C, T, n_src=20)
+    h, held = _half(volt)
+    got = gc.correlate(h.cuda(), gains.cuda()).cpu().numpy()
+    gc.device_status()
+    # complex32 tensors take the same path
+    if hasattr(torch, "complex32"):
+        got2 = gc.correlate(torch.view_as_complex(h.float()).to(torch.complex32).cuda(), gains.cuda())
+        assert np.array_equal(got2.cpu().numpy(), got)
+    for c in range(C):
+        ref = orc.fx(held[c], gains[c].numpy(), L)
+        assert lag_err(got[c], ref, L) < TOL, (L, c)
+        ref64 = orc.fx(volt[c].numpy(), gains[c].numpy(), L)
+        assert lag_err(got[c], ref64, L) < 2 * HALF_U + HALF_U ** 2 + TOL, (L, c)
+
+
+@pytest.mark.parametrize("L,C,T", [(65, 1, 16), (80, 2, 8), (128, 1, 5)])
+def test_correlate_i4c_m256(gc, orc, L, C, T):
+    """Grids of 65..128 antennas a side (256 x 256 FFT): 4+4-bit voltages,
+    plain staging (L = 65) and TMA staging (L = 80, 128)."""
+    volt, gains, _ = synth.make_voltages(500 + L, L, C, T, n_src=20)
+    q = _quantised(volt)
+    out = gc.correlate(torch.from_numpy(q).cuda(), gains.cuda())
+    gc.device_status()
+    got = out.cpu().numpy()
+    for c in range(C):
+        ref = orc.fx(orc.unpack_i4c(q[c]), gains[c].numpy(), L)
+        assert lag_err(got[c], ref, L) < TOL, (L, c)
+
+
+def test_correlate_i4c_128_sampled(gc, orc):
+    """128x128 grid over several time chunks (T = 1100); sampled lags against
+    the oracle's one-lag definition."""
+    L, C, T = 128, 2, 1100
+    N = L * L
+    volt, gains, _ = synth.make_voltages(9, L, C, T, n_src=50)
+    qn = _quantised(volt)
+    del volt
+    out = gc.correlate(torch.from_numpy(qn).cuda(), gains.cuda())
+    gc.device_status()
+    got = out.cpu().numpy()
+    rng = np.random.default_rng(1)
+    for c in range(C):
+        v = orc.unpack_i4c(qn[c])
+        g = gains[c].numpy()
+        r0 = orc.lag(v, g, L, 0, 0)
+        lags = [(0, 0), (1, 0), (0, 1), (-127, 127), (127, 0), (0, -127)] + \
+            [tuple(rng.integers(-(L - 1), L, 2)) for _ in range(14)]
+        for dx, dy in lags:
+            ref = orc.lag(v, g, L, int(dx), int(dy))
+            nd = (L - abs(dx)) * (L - abs(dy))
+            e = abs(got[c, dy + L - 1, dx + L - 1] - ref) * nd / (N * abs(r0))
+            assert e < TOL, (c, dx, dy, e)
+
+
 def test_correlate_misaligned_plain_path(gc, orc):
     """A voltage buffer that is 8- but not 16-byte aligned takes the plain
     staging path and gives the same answer."""
@@ -90,11 +163,13 @@ def test_correlate_misaligned_plain_path(gc, orc):
 
 def test_correlate_rejects_bad_arguments(gc):
     from paper_2005_03060_gb300 import gridcorr
-    v = torch.zeros(1, 4, 65 * 65, dtype=torch.complex64, device="cuda")
-    g = torch.ones(1, 65 * 65, dtype=torch.complex64, device="cuda")
-    with pytest.raises(gridcorr.GridcorrError) as e:
-        gc.correlate(v, g)
-    assert e.value.status == gridcorr.GC_EINVAL
+    for L, dtype, status in [(65, torch.complex64, gridcorr.GC_EUNSUPPORTED),
+                             (129, torch.uint8, gridcorr.GC_EINVAL)]:
+        v = torch.zeros(1, 4, L * L, dtype=dtype, device="cuda")
+        g = torch.ones(1, L * L, dtype=torch.complex64, device="cuda")
+        with pytest.raises(gridcorr.GridcorrError) as e:
+            gc.correlate(v, g)
+        assert e.value.status == status
 
 
 def test_correlate_paper_scale_sampled(gc, orc):

@@ -62,6 +62,27 @@ def test_reduce_c64(gc, ctx, orc, scheme, L, C, T):
         assert np.max(np.abs(au[c] - ref_a) / ref_a) < TOL
 
 
+@pytest.mark.parametrize("scheme,L,C,T", [("subset", 8, 2, 256), ("lowcad", 8, 1, 256),
+                                          ("subset", 13, 1, 200), ("subset", 32, 1, 300)])
+def test_reduce_c32h(gc, ctx, orc, scheme, L, C, T):
+    """binary16-stored voltages (FP32 products and sums) against the oracle on
+    the stored values, with the complex64 bound; L = 13 takes the plain
+    staging path (a grid sample of 676 bytes is no multiple of 16)."""
+    sel = gc.Selection(scheme, L, T)
+    volt, gains, _ = synth.make_voltages(450 + L, L, C, T, n_src=20)
+    h = torch.view_as_real(volt).to(torch.float16).contiguous()
+    held = torch.view_as_complex(h.to(torch.float64)).numpy()
+    vr, au = ctx.reduce(h.cuda(), sel)
+    ctx.device_status()
+    assert vr.dtype == torch.complex64 and au.dtype == torch.float32
+    vr, au = vr.cpu().numpy(), au.cpu().numpy()
+    used = sel.n_cycle * sel.t_int
+    for c in range(C):
+        assert _check_c64(orc, held[c], sel, vr[c]) < TOL
+        ref_a = orc.autos(held[c], 0, used)
+        assert np.max(np.abs(au[c] - ref_a) / ref_a) < TOL
+
+
 @pytest.mark.parametrize("scheme,L,C,T", [("subset", 4, 2, 50), ("subset", 8, 2, 300),
                                           ("subset", 16, 1, 1000), ("lowcad", 8, 2, 256),
                                           ("lowcad", 16, 1, 2000), ("subset", 64, 1, 64)])
