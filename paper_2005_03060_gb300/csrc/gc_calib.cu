@@ -36,7 +36,10 @@ namespace {
 
 constexpr int kCThreads = 512;
 constexpr int kCgThreads = 512;   // matrix-free kernels
-constexpr size_t kCgSmemMax = 100u * 1024u;   // shared arena cap (two CTAs per SM)
+// shared arena cap: two CTAs per SM.  Arrays whose hot vectors need more keep
+// them in global memory (L2) at two CTAs per SM -- measured faster than one
+// CTA per SM with a larger arena (the solver is latency-bound).
+constexpr size_t kCgSmemMax = 100u * 1024u;
 constexpr int kMaxUbl = 64;   // lincal border limit (2 * 64 reals)
 
 struct CalParams {

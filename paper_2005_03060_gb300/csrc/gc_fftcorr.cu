@@ -216,9 +216,14 @@ __device__ __forceinline__ float2 h2_to_f2(unsigned int bits) {
     return __half22float2(h);
 }
 
+// 4-bit two's-complement nibble n -> float without an int-to-float
+// conversion: flipping the nibble's sign bit gives n + 8 in [0, 15]; placed in
+// the low mantissa bits of 2^23 that is the float 2^23 + n + 8 exactly, and
+// subtracting 2^23 + 8 leaves n.  Bits 7..4 of `byte` hold Re, bits 3..0 Im.
 __device__ __forceinline__ float2 i4c_to_f2(unsigned int byte) {
-    const int b = (int)(signed char)(byte & 0xFFu);
-    return make_float2((float)(b >> 4), (float)((int)(signed char)(byte << 4) >> 4));
+    const float re = __uint_as_float(((byte >> 4) & 0xFu) ^ 0x4B000008u) - 8388616.0f;
+    const float im = __uint_as_float((byte & 0xFu) ^ 0x4B000008u) - 8388616.0f;
+    return make_float2(re, im);
 }
 
 template <class K, bool kTMA>

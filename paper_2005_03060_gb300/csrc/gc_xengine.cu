@@ -6,9 +6,16 @@
 // antennas, time slice).  Samples of the whole grid are staged in shared
 // memory by 1-D bulk TMA copies (double-buffered); each thread owns one
 // reference antenna j and accumulates v_{j+d} conj(v_j) for every type d of
-// its group in registers.  4+4-bit voltages are unpacked to float: products
-// and sums of those integers stay below 2^24, so FP32 sums are exact and the
-// int32 result is bit-exact.
+// its group in registers.  complex64 and binary16 voltages accumulate in
+// FP32.  4+4-bit voltages take an integer path: each staged byte pair
+// (samples t, t+1 of one antenna) is expanded through a 256-entry table into
+// two words of signed bytes
+//   W  = (re_t, im_t, re_t1, im_t1),   Wc = (re_t, -im_t, re_t1, -im_t1),
+// and one 4-way byte dot product with int32 accumulation (dp4a) gives two
+// samples of each part of v_i conj(v_j):
+//   Re = re_i re_j + im_i im_j = dp4a(W_i, W_j),
+//   Im = im_i re_j - re_i im_j = dp4a(swap(W_i), Wc_j),
+// swap exchanging the two bytes of each (re, im) pair -- bit-exact sums.
 // xeng_reduce: sums the time slices (FP64) into V^reduced and the autos.
 #include <cuda_fp16.h>
 
@@ -29,14 +36,15 @@ struct XParams {
     int ns;                   // samples per stage
     const int32_t *types, *type_ptr, *grp_types, *grp_off, *grp_t0, *grp_t1, *grp_first;
     int P;
-    float2 *part;             // [n_tsplit][C][P]
-    float *apart;             // [n_windows * n_tsplit][C][N] (may be null)
+    float2 *part;             // [n_tsplit][C][P] (int2 for 4+4-bit voltages)
+    float *apart;             // [n_windows * n_tsplit][C][N] (int for 4+4-bit; may be null)
     const int32_t *grp_win;   // window index per group
     const int32_t *grp_dymax; // largest dy among the group's types
     unsigned int *status;
     int use_tma;
     int rows_stage;           // 1: stage only the block's rows plus the dy halo
     size_t stage_stride;      // bytes per stage buffer (ns staged samples)
+    int conv_recs;            // 4+4-bit: expanded antenna records (staged antennas + a zero record)
 };
 
 template <int VF>
@@ -47,18 +55,38 @@ __device__ __forceinline__ float2 ld_volt(const unsigned char *s, int idx) {
     return make_float2((float)(b >> 4), (float)((int)(signed char)(b << 4) >> 4));
 }
 
-// VF: voltage format; NTY: type slots per thread (>= the largest group)
-template <int VF, int NTY>
-__global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
+// VF: voltage format; NTY: type slots per thread (>= the largest group);
+// NP: sample pairs per stage for 4+4-bit voltages (8 with 16-sample stages, 1
+// with 2-sample stages for wide staged regions; 1 for the other formats).
+template <int VF, int NTY, int NP>
+__global__ void __launch_bounds__(kXThreads, 2) xeng_accumulate(const XParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[2];
     __shared__ int s_dx[GC_XENG_NTY], s_dy[GC_XENG_NTY], s_base[GC_XENG_NTY];
     __shared__ int s_err;
+    constexpr bool kI4 = VF == GC_I4C;
+    __shared__ uint32_t s_lut[kI4 ? 256 : 1];
     const int tid = threadIdx.x;
     constexpr int esz = VF == GC_C64 ? 8 : (VF == GC_C32H ? 4 : 1);
     const size_t sample_bytes = (size_t)p.N * esz;
     const size_t stage_stride = p.stage_stride;
     const int L = p.L;
+    // 4+4-bit: one record per staged antenna after the raw stages,
+    // [W of NP pairs | Wc of NP pairs | pad]; the pad makes the 16-byte record
+    // reads of consecutive antennas conflict-free.  The last record stays zero
+    // and stands in for neighbours outside the grid.
+    constexpr int kRec = NP == 8 ? 20 : 2;
+    uint32_t *conv = reinterpret_cast<uint32_t *>(smem + 2 * stage_stride);
+    if (kI4) {
+        for (int i = tid; i < kRec; i += kXThreads) conv[(size_t)(p.conv_recs - 1) * kRec + i] = 0u;
+        // byte -> (re, im, re, -im) as signed bytes
+        for (int b = tid; b < 256; b += kXThreads) {
+            const int re = (int)(signed char)b >> 4;
+            const int im = (int)(signed char)(b << 4) >> 4;
+            s_lut[b] = (uint32_t)(re & 0xFF) | ((uint32_t)(im & 0xFF) << 8) | ((uint32_t)(re & 0xFF) << 16) |
+                       ((uint32_t)(-im & 0xFF) << 24);
+        }
+    }
     if (tid == 0) {
         s_err = 0;
         gc_mbar_init(&bars[0], 1);
@@ -114,12 +142,18 @@ __global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
         }
         __syncthreads();
 
-        float2 acc[NTY];
+        float2 acc[kI4 ? 1 : NTY];
+        int ire[kI4 ? NTY : 1], iim[kI4 ? NTY : 1];
         int nb[NTY];   // neighbour antenna r_j + d_k, or -1 (fixed for the item)
         const bool do_autos = p.apart && p.grp_first[g];
 #pragma unroll
         for (int k = 0; k < NTY; ++k) {
-            acc[k] = make_float2(0.f, 0.f);
+            if (kI4) {
+                ire[k] = 0;
+                iim[k] = 0;
+            } else {
+                acc[k] = make_float2(0.f, 0.f);
+            }
             nb[k] = -1;
             if (k < ntype && own) {
                 const int xi = x + s_dx[k], yi = y + s_dy[k];
@@ -127,6 +161,15 @@ __global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
             }
         }
         float aut = 0.f;
+        int iaut = 0;
+        auto refill = [&](int st) {
+            if (p.use_tma && tid == 0 && st + 2 < n_st) {
+                gc_fence_proxy_async();
+                const int t2 = ta + (st + 2) * p.ns;
+                issue(t2, min(p.ns, tb - t2), ld_count & 1u);
+                ++ld_count;
+            }
+        };
 
         for (int st = 0; st < n_st; ++st) {
             const int t = ta + st * p.ns;
@@ -152,29 +195,97 @@ __global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
                 stage = smem;
                 __syncthreads();
             }
-            if (own) {
-                const int jl = j - y_lo * L;   // own antenna within the staged rows
-                for (int u = 0; u < cnt; ++u) {
-                    const unsigned char *sv = stage + u * part_bytes;
-                    const float2 b = ld_volt<VF>(sv, jl);
-                    if (do_autos) aut = fmaf(b.x, b.x, fmaf(b.y, b.y, aut));
+            if constexpr (kI4) {
+                // expand every staged antenna's bytes, sample pair by pair
+                // (samples beyond the copied count are zero)
+                // work unit = (antenna, two sample pairs); consecutive threads
+                // take consecutive antennas of one sample row
+                const int n_ant = (int)part_bytes;
+                constexpr int kQ = NP == 8 ? 4 : 1;   // units per antenna
+                for (int u = tid; u < kQ * n_ant; u += kXThreads) {
+                    const int qu = kQ == 1 ? 0 : u / n_ant;
+                    const int a = u - qu * n_ant;
+                    const int s0 = 4 * qu;             // first sample of the unit
+                    uint32_t e[4];
+#pragma unroll
+                    for (int i = 0; i < (NP == 8 ? 4 : 2); ++i)
+                        e[i] = s0 + i < cnt ? s_lut[stage[(size_t)(s0 + i) * part_bytes + a]] : 0u;
+                    uint32_t *rec = conv + (size_t)a * kRec;
+                    if constexpr (NP == 8) {
+                        *reinterpret_cast<uint2 *>(rec + 2 * qu) =
+                            make_uint2(__byte_perm(e[0], e[1], 0x5410), __byte_perm(e[2], e[3], 0x5410));
+                        *reinterpret_cast<uint2 *>(rec + 8 + 2 * qu) =
+                            make_uint2(__byte_perm(e[0], e[1], 0x7632), __byte_perm(e[2], e[3], 0x7632));
+                    } else {
+                        *reinterpret_cast<uint2 *>(rec) =
+                            make_uint2(__byte_perm(e[0], e[1], 0x5410), __byte_perm(e[0], e[1], 0x7632));
+                    }
+                }
+                __syncthreads();
+                refill(st);   // the raw stage is free again
+                if (own) {
+                    const int jl = j - y_lo * L;
+                    uint32_t wj[NP], wcj[NP];
+                    const uint32_t *rj = conv + (size_t)jl * kRec;
+                    if constexpr (NP == 8) {
+                        const uint4 *r4 = reinterpret_cast<const uint4 *>(rj);
+                        const uint4 a0 = r4[0], a1 = r4[1], b0 = r4[2], b1 = r4[3];
+                        wj[0] = a0.x; wj[1] = a0.y; wj[2] = a0.z; wj[3] = a0.w;
+                        wj[4] = a1.x; wj[5] = a1.y; wj[6] = a1.z; wj[7] = a1.w;
+                        wcj[0] = b0.x; wcj[1] = b0.y; wcj[2] = b0.z; wcj[3] = b0.w;
+                        wcj[4] = b1.x; wcj[5] = b1.y; wcj[6] = b1.z; wcj[7] = b1.w;
+                    } else {
+                        const uint2 r = *reinterpret_cast<const uint2 *>(rj);
+                        wj[0] = r.x;
+                        wcj[0] = r.y;
+                    }
+                    if (do_autos) {
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) iaut = __dp4a((int)wj[q], (int)wj[q], iaut);
+                    }
+                    // straight-line over the type slots (absent neighbours and
+                    // unused slots read the zero record) so that loads and the
+                    // dp4a chains of different types interleave
 #pragma unroll
                     for (int k = 0; k < NTY; ++k) {
-                        if (nb[k] >= 0) {
-                            const float2 a = ld_volt<VF>(sv, nb[k]);
-                            // a * conj(b)
-                            acc[k].x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc[k].x));
-                            acc[k].y = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc[k].y));
+                        const uint32_t *ri = conv + (size_t)(nb[k] >= 0 ? nb[k] : p.conv_recs - 1) * kRec;
+                        uint32_t wi[NP];
+                        if constexpr (NP == 8) {
+                            const uint4 *r4 = reinterpret_cast<const uint4 *>(ri);
+                            const uint4 a0 = r4[0], a1 = r4[1];
+                            wi[0] = a0.x; wi[1] = a0.y; wi[2] = a0.z; wi[3] = a0.w;
+                            wi[4] = a1.x; wi[5] = a1.y; wi[6] = a1.z; wi[7] = a1.w;
+                        } else {
+                            wi[0] = ri[0];
+                        }
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) {
+                            ire[k] = __dp4a((int)wi[q], (int)wj[q], ire[k]);
+                            iim[k] = __dp4a((int)__byte_perm(wi[q], 0u, 0x2301), (int)wcj[q], iim[k]);
                         }
                     }
                 }
-            }
-            __syncthreads();
-            if (p.use_tma && tid == 0 && st + 2 < n_st) {
-                gc_fence_proxy_async();
-                const int t2 = ta + (st + 2) * p.ns;
-                issue(t2, min(p.ns, tb - t2), ld_count & 1u);
-                ++ld_count;
+                __syncthreads();
+            } else {
+                if (own) {
+                    const int jl = j - y_lo * L;   // own antenna within the staged rows
+                    for (int u = 0; u < cnt; ++u) {
+                        const unsigned char *sv = stage + u * part_bytes;
+                        const float2 b = ld_volt<VF>(sv, jl);
+                        if (do_autos) aut = fmaf(b.x, b.x, fmaf(b.y, b.y, aut));
+#pragma unroll
+                        for (int k = 0; k < NTY; ++k) {
+                            if (nb[k] >= 0) {
+                                const float2 a = ld_volt<VF>(sv, nb[k]);
+                                // a * conj(b)
+                                acc[k].x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc[k].x));
+                                acc[k].y = fmaf(a.y, b.x, fmaf(-a.x, b.y, acc[k].y));
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+                refill(st);
             }
         }
         if (s_err) break;
@@ -186,13 +297,18 @@ __global__ void __launch_bounds__(kXThreads) xeng_accumulate(const XParams p) {
                     const int dx = s_dx[k], dy = s_dy[k];
                     const int xlo = max(0, -dx), ylo = max(0, -dy);
                     const int xi = x + dx, yi = y + dy;
-                    if (xi >= 0 && xi < L && yi >= 0 && yi < L)
-                        out[s_base[k] + (y - ylo) * (L - abs(dx)) + (x - xlo)] = acc[k];
+                    if (xi >= 0 && xi < L && yi >= 0 && yi < L) {
+                        const size_t o = s_base[k] + (y - ylo) * (L - abs(dx)) + (x - xlo);
+                        if constexpr (kI4) reinterpret_cast<int2 *>(out)[o] = make_int2(ire[k], iim[k]);
+                        else out[o] = acc[k];
+                    }
                 }
             }
             if (do_autos) {
                 const int slot = p.grp_win[g] * p.n_tsplit + ts;
-                p.apart[((size_t)slot * p.C + c) * p.N + j] = aut;
+                const size_t o = ((size_t)slot * p.C + c) * p.N + j;
+                if constexpr (kI4) reinterpret_cast<int *>(p.apart)[o] = iaut;
+                else p.apart[o] = aut;
             }
         }
         __syncthreads();
@@ -212,25 +328,42 @@ __global__ void xeng_reduce(const float2 *__restrict__ part, int n_tsplit, int C
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total + (size_t)C * N;
          idx += (size_t)gridDim.x * blockDim.x) {
         if (idx < total) {
-            double re = 0.0, im = 0.0;
-            for (int s = 0; s < n_tsplit; ++s) {
-                const float2 v = part[(size_t)s * total + idx];
-                re += v.x;
-                im += v.y;
-            }
             if (vfmt != GC_I4C) {
+                double re = 0.0, im = 0.0;
+                for (int s = 0; s < n_tsplit; ++s) {
+                    const float2 v = part[(size_t)s * total + idx];
+                    re += v.x;
+                    im += v.y;
+                }
                 reinterpret_cast<float2 *>(vred)[idx] = make_float2((float)re, (float)im);
             } else {
-                reinterpret_cast<int2 *>(vred)[idx] = make_int2((int)llrint(re), (int)llrint(im));
+                int re = 0, im = 0;
+                for (int s = 0; s < n_tsplit; ++s) {
+                    const int2 v = reinterpret_cast<const int2 *>(part)[(size_t)s * total + idx];
+                    re += v.x;
+                    im += v.y;
+                }
+                reinterpret_cast<int2 *>(vred)[idx] = make_int2(re, im);
             }
         } else if (autos) {
             const size_t a = idx - total;
-            double s = 0.0;
-            for (int k = 0; k < n_aslots; ++k) s += apart[(size_t)k * C * N + a];
-            if (vfmt != GC_I4C) reinterpret_cast<float *>(autos)[a] = (float)s;
-            else reinterpret_cast<int *>(autos)[a] = (int)llrint(s);
+            if (vfmt != GC_I4C) {
+                double s = 0.0;
+                for (int k = 0; k < n_aslots; ++k) s += apart[(size_t)k * C * N + a];
+                reinterpret_cast<float *>(autos)[a] = (float)s;
+            } else {
+                int s = 0;
+                for (int k = 0; k < n_aslots; ++k) s += reinterpret_cast<const int *>(apart)[(size_t)k * C * N + a];
+                reinterpret_cast<int *>(autos)[a] = s;
+            }
         }
     }
+}
+
+template <int VF, int NP>
+const void *pick_xeng(int nty) {
+    return nty == 4 ? (const void *)xeng_accumulate<VF, 4, NP> : nty == 8 ? (const void *)xeng_accumulate<VF, 8, NP>
+         : nty == 12 ? (const void *)xeng_accumulate<VF, 12, NP> : (const void *)xeng_accumulate<VF, 16, NP>;
 }
 
 }  // namespace
@@ -265,21 +398,21 @@ extern "C" gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, i
     const int rows_stage = (n_rowblk > 1 && (kXThreads / L + 1 + dymax_all) < L &&
                             (!tma || ((size_t)L * esz) % 16 == 0)) ? 1 : 0;
     const size_t staged = rows_stage ? (size_t)std::min(L, kXThreads / L + 2 + dymax_all) * L * esz : sample_bytes;
-    const int ns = (int)std::max<size_t>(1, std::min<size_t>(16, (32u << 10) / staged));
+    int ns = (int)std::max<size_t>(1, std::min<size_t>(16, (32u << 10) / staged));
+    if (vfmt == GC_I4C) ns = ns == 16 ? 16 : 2;   // 8 sample pairs per stage, or 1 for wide regions
     const size_t stage_stride = ((staged * ns + 127) / 128) * 128;
-    const size_t smem = 2 * stage_stride;
+    // 4+4-bit: one expanded record per staged antenna plus the zero record
+    const int conv_recs = vfmt == GC_I4C ? (int)staged + 1 : 0;
+    const size_t smem = 2 * stage_stride + (size_t)conv_recs * (ns == 16 ? 20 : 2) * 4;
     if (smem > 200u * 1024u) return gc_fail(ctx, GC_EUNSUPPORTED, "gc_reduce: grid too large for the stage");
     const int nty = ntmax <= 4 ? 4 : (ntmax <= 8 ? 8 : (ntmax <= 12 ? 12 : 16));
     const void *kern;
     if (vfmt == GC_C64)
-        kern = nty == 4 ? (const void *)xeng_accumulate<GC_C64, 4> : nty == 8 ? (const void *)xeng_accumulate<GC_C64, 8>
-             : nty == 12 ? (const void *)xeng_accumulate<GC_C64, 12> : (const void *)xeng_accumulate<GC_C64, 16>;
+        kern = pick_xeng<GC_C64, 1>(nty);
     else if (vfmt == GC_C32H)
-        kern = nty == 4 ? (const void *)xeng_accumulate<GC_C32H, 4> : nty == 8 ? (const void *)xeng_accumulate<GC_C32H, 8>
-             : nty == 12 ? (const void *)xeng_accumulate<GC_C32H, 12> : (const void *)xeng_accumulate<GC_C32H, 16>;
+        kern = pick_xeng<GC_C32H, 1>(nty);
     else
-        kern = nty == 4 ? (const void *)xeng_accumulate<GC_I4C, 4> : nty == 8 ? (const void *)xeng_accumulate<GC_I4C, 8>
-             : nty == 12 ? (const void *)xeng_accumulate<GC_I4C, 12> : (const void *)xeng_accumulate<GC_I4C, 16>;
+        kern = ns == 16 ? pick_xeng<GC_I4C, 8>(nty) : pick_xeng<GC_I4C, 1>(nty);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(xeng_accumulate)");
     int occ = 0;
@@ -341,6 +474,7 @@ extern "C" gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, i
     p.use_tma = tma ? 1 : 0;
     p.rows_stage = rows_stage;
     p.stage_stride = stage_stride;
+    p.conv_recs = conv_recs;
     const int grid = (int)std::min<long>(p.n_items, slots);
     int rec = gc_prof_begin(ctx, s, "xeng_accumulate");
     void *args[] = {&p};

@@ -82,16 +82,18 @@ def _cnormal(n_shape, var, g, device):
 
 def make_voltages(seed: int, L: int, C: int, T: int, n_src: int, snr: float = 10.0,
                   device="cpu", gains: torch.Tensor | None = None, noise: bool = True,
-                  out: torch.Tensor | None = None):
+                  out: torch.Tensor | None = None, channel0: int = 0):
     """Voltages [C, T, N] complex64 (row-major grid index), and the true gains.
 
     Returns (volt, gains, sky).  `out` may be a preallocated [C, T, N]
-    complex64 tensor (to fill device memory chunk by chunk).
+    complex64 tensor.  `channel0` offsets the channel index of the draws, so
+    that channels c0..c0+C-1 of a large workload can be generated chunk by
+    chunk (same sky for every chunk; pass that chunk's gains).
     """
     N = L * L
     sky = make_sky(seed, n_src, device)
     if gains is None:
-        gains = make_gains(seed, C, N, device)
+        gains = make_gains(seed, channel0 + C, N, device)[channel0:]
     pos = grid_positions(L, device)
     # steering phases e^{2 pi i r_i . l_k}: [K, N] complex64 (draw-time geometry)
     steer = torch.polar(torch.ones((), dtype=torch.float64, device=device),
@@ -100,7 +102,7 @@ def make_voltages(seed: int, L: int, C: int, T: int, n_src: int, snr: float = 10
     volt = out if out is not None else torch.empty(C, T, N, dtype=torch.complex64, device=device)
     flux32 = sky.flux.to(torch.float32)
     for c in range(C):
-        g = _gen(device, seed, c, 3)
+        g = _gen(device, seed, channel0 + c, 3)
         a = _cnormal((T, n_src), flux32, g, device)             # [T, K]
         sig = a @ steer                                         # [T, N]
         if noise:
