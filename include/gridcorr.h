@@ -93,9 +93,11 @@ GC_API int gc_profile_read(gc_ctx *ctx, char *names, double *total_ms, int *laun
                            int max_kinds);
 
 /* Arithmetic throughput probe (not part of the paper's method; used for
- * roofline denominators).  kind 0: FP32 FMA, kind 1: FP64 FMA.  Launches a
- * kernel of independent FMA chains on the context's device (legacy default
- * stream), synchronises, and writes the achieved TFLOP/s (FMA = 2 flops). */
+ * roofline denominators).  kind 0: FP32 FMA, kind 1: FP64 FMA, kind 2: 4-way
+ * signed 8-bit dot product with int32 accumulate (dp4a).  Launches a kernel
+ * of independent chains on the context's device (legacy default stream),
+ * synchronises, and writes the achieved tera-operations per second (FMA = 2
+ * flops; dp4a = 8 integer ops).  GC_EINVAL for another kind. */
 GC_API gc_status gc_peak_probe(gc_ctx *ctx, int kind, double *tflops);
 
 /* Smallest FFT side M for an L x L grid: the smallest power of two >= 2L - 1,

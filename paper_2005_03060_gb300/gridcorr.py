@@ -161,9 +161,10 @@ class Context:
         return out
 
     def peak_probe(self, kind: str) -> float:
-        """Measured FMA throughput in TFLOP/s ('fp32' or 'fp64')."""
+        """Measured throughput in tera-ops/s: 'fp32' / 'fp64' FMA (2 flops),
+        'dp4a' (8 integer ops)."""
         v = ctypes.c_double()
-        self.check(_lib.gc_peak_probe(self._h, 0 if kind == "fp32" else 1, ctypes.byref(v)))
+        self.check(_lib.gc_peak_probe(self._h, {"fp32": 0, "fp64": 1, "dp4a": 2}[kind], ctypes.byref(v)))
         return v.value
 
     # ------------------------------------------------------------------ correlate
