@@ -324,12 +324,13 @@ GC_API gc_status gc_chi2_backward(gc_ctx *ctx, const void *vreduced, int vfmt, c
  * telescope), or a host framework that owns every device allocation and
  * hands the library only the buffers it already holds.
  *
- * Same computation, arguments and layouts as gc_correlate, with no context:
+ * Same computation, arguments and layouts as gc_correlate (for 1 <= L <= 64),
+ * with no context:
  * the per-chunk power spectra live in a fixed 64 MiB array in the library's
  * device memory (every GPU that loads the library holds it until the
  * process exits).  The call is rejected with GC_EINVAL when
- *     C * ceil(T / 512) * G * M^2 * 4 bytes > 64 MiB
- * (M = max(16, gc_fft_size(L)); G = 8 for M = 16, 4 for M = 32, else 1);
+ *     C * ceil(T / 512) * M^2 * 4 bytes > 64 MiB
+ * (M = max(16, gc_fft_size(L)));
  * e.g. L = 32, T = 4096 allows up to 512 channels per call.
  *
  * The first call on a device (the current device) looks up the device

@@ -129,9 +129,8 @@ __device__ void block_sum(R (&v)[NV], R *red /* smem [32][NV] */) {
 // Spanning-tree phases over the (1,0) and (0,1) types (arg V_(1,0) = arg V_(0,1)
 // = 0 fixes the slopes), unit amplitudes, V_alpha = group mean of V_p / (g_i g_j^*).
 template <class R>
-__device__ void start_point(const CalParams &p, int c, R *xg, R *xv, R *red) {
+__device__ void start_point(const CalParams &p, int c, R *xg, R *xv, R *red, R *phi /* N reals of scratch */) {
     const int L = p.L, N = p.N;
-    R *phi = xv + 2 * p.n_ubl;   // scratch after xv: N reals
     if (threadIdx.x == 0) {
         phi[0] = 0;
         for (int x = 1; x < L; ++x) {
@@ -751,7 +750,7 @@ __global__ void __launch_bounds__(kCThreads) lincal_kernel(const CalParams p) {
             }
             __syncthreads();
         } else {
-            start_point<R>(p, c, w.xg, w.xv, red);
+            start_point<R>(p, c, w.xg, w.xv, red, w.xv + 2 * p.n_ubl);
         }
         int st = GC_ENOCONV, it = 0;
         for (it = 1; it <= p.max_iter; ++it) {
@@ -838,9 +837,15 @@ __host__ __device__ inline void cg_coarse_dims(int L, int n_ubl, int &B, int &np
     }
 }
 
-__host__ __device__ inline size_t cg_hot_floats(int N, int n_ubl) { return 8 * (size_t)N + 7 * (size_t)n_ubl + 64; }
+// Vectors read at random per pair (xg 2N, xv 2 n_ubl, pp and acc nm each, dv
+// n_ubl) and, when `with_dg`, the gain diagonal dg (N).
+__host__ __device__ inline size_t cg_hot_floats(int N, int n_ubl, bool with_dg) {
+    return 6 * (size_t)N + 7 * (size_t)n_ubl + (with_dg ? (size_t)N : 0) + 64;
+}
 
-__device__ CgWork cg_layout(const CalParams &p, char *base, float *smem_arena, bool use_smem,
+// hot_mode 2: hot vectors and dg in shared memory; 1: hot vectors in shared
+// memory, dg in global; 0: everything in global (L2-resident) memory.
+__device__ CgWork cg_layout(const CalParams &p, char *base, float *smem_arena, int hot_mode,
                             bool use_coarse_smem) {
     CgWork w;
     w.n = 2 * p.N;
@@ -852,19 +857,20 @@ __device__ CgWork cg_layout(const CalParams &p, char *base, float *smem_arena, b
         g += (cnt + 63) & ~size_t(63);
         return r;
     };
-    float *h = use_smem ? smem_arena : takeg(cg_hot_floats(p.N, p.n_ubl));
-    float *hot_end = h + cg_hot_floats(p.N, p.n_ubl);
+    float *ghot = takeg(cg_hot_floats(p.N, p.n_ubl, true));
+    float *h = hot_mode ? smem_arena : ghot;
+    float *hot_end = h + cg_hot_floats(p.N, p.n_ubl, hot_mode != 1);
     w.xg = h;
     h += 2 * p.N;
     w.xv = h;
-    h += 2 * p.n_ubl + p.N;
+    h += 2 * p.n_ubl;
     w.pp = h;
     h += nm;
     w.acc = h;
     h += nm;
-    w.dg = h;
-    h += p.N;
     w.dv = h;
+    h += p.n_ubl;
+    w.dg = hot_mode == 1 ? ghot : h;
     w.b = takeg(nm);
     w.x = takeg(nm);
     w.r = takeg(nm);
@@ -895,7 +901,28 @@ size_t cg_bytes(int N, int n_ubl, int /*P*/) {
     const int L = (int)lround(sqrt((double)N));
     cg_coarse_dims(L, n_ubl, B, npx, ncp, nc, cv);
     const size_t c2 = (size_t)nc * nc;
-    return sizeof(float) * (r(cg_hot_floats(N, n_ubl)) + 5 * r(nm) + r(4 * nm) + 2 * r(c2));
+    return sizeof(float) * (r(cg_hot_floats(N, n_ubl, true)) + 5 * r(nm) + r(4 * nm) + 2 * r(c2));
+}
+
+// Shared arena for one array: hot vectors with dg and the coarse operators if
+// they fit the cap, else the hot vectors alone, else nothing (0: global).
+// The split mode (hot vectors in shared memory, dg in global) is kept in the
+// kernel but not chosen: on the 4096-antenna array it measured slower than
+// the all-global layout, whose fire-and-forget L2 reductions do not stall
+// the issuing warps the way contended shared-memory atomics do.
+size_t cg_arena_bytes(int N, int n_ubl, int L, size_t cap) {
+    const size_t h2 = cg_hot_floats(N, n_ubl, true) * sizeof(float);
+    const size_t cf = cg_coarse_floats(L, n_ubl) * sizeof(float);
+    if (h2 + cf <= cap) return h2 + cf;
+    return h2 <= cap ? h2 : 0;
+}
+
+// the kernel side of the same choice, from the arena size it was given
+__device__ __forceinline__ void cg_modes(const CalParams &p, int smem_floats, int &hot_mode, bool &coarse_smem) {
+    const size_t h2 = cg_hot_floats(p.N, p.n_ubl, true), h1 = cg_hot_floats(p.N, p.n_ubl, false);
+    const size_t cf = cg_coarse_floats(p.L, p.n_ubl), sf = (size_t)smem_floats;
+    hot_mode = h2 <= sf ? 2 : (h1 <= sf ? 1 : 0);
+    coarse_smem = hot_mode != 0 && (hot_mode == 2 ? h2 : h1) + cf <= sf;
 }
 
 // One pass over the pairs.  resid: u = r (the residual), acc = J^T r, dg/dv
@@ -1176,7 +1203,7 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
         }
         __syncthreads();
     } else {
-        start_point<float>(p, c, w.xg, w.xv, redf);
+        start_point<float>(p, c, w.xg, w.xv, redf, w.z);
     }
     // complex element e: antenna e < N, else model visibility e - N
     auto base_of = [&](int e) { return e < p.N ? 2 * e : w.n + 2 * (e - p.N); };
@@ -1347,10 +1374,10 @@ __global__ void __launch_bounds__(kCgThreads, 2) lincal_cg_kernel(const CalParam
     __shared__ float redf[32 * 14];
     __shared__ float s_rc[2 * kMaxCoarse], s_yc[2 * kMaxCoarse];
     extern __shared__ __align__(16) float arena[];
-    const bool use_smem = cg_hot_floats(p.N, p.n_ubl) <= (size_t)smem_floats;
-    const bool coarse_smem =
-        use_smem && cg_hot_floats(p.N, p.n_ubl) + cg_coarse_floats(p.L, p.n_ubl) <= (size_t)smem_floats;
-    CgWork w = cg_layout(p, p.work + (size_t)blockIdx.x * p.work_per_cta, arena, use_smem, coarse_smem);
+    int hot_mode;
+    bool coarse_smem;
+    cg_modes(p, smem_floats, hot_mode, coarse_smem);
+    CgWork w = cg_layout(p, p.work + (size_t)blockIdx.x * p.work_per_cta, arena, hot_mode, coarse_smem);
     w.rc = s_rc;
     w.yc = s_yc;
     for (int c = blockIdx.x; c < p.C; c += gridDim.x) cg_solve_channel(p, c, w, cg_tol, cg_max, red, redf);
@@ -1389,10 +1416,10 @@ __global__ void __launch_bounds__(kCgThreads, 2) lincal_cg_batched(const __grid_
         int slot = 0;
         while (slot + 1 < bp.n_arr && bp.prefix[slot + 1] <= item) ++slot;
         const CalParams &p = bp.arr[bp.order[slot]];
-        const bool use_smem = cg_hot_floats(p.N, p.n_ubl) <= (size_t)bp.smem_floats;
-        const bool coarse_smem =
-            use_smem && cg_hot_floats(p.N, p.n_ubl) + cg_coarse_floats(p.L, p.n_ubl) <= (size_t)bp.smem_floats;
-        CgWork w = cg_layout(p, base, arena, use_smem, coarse_smem);
+        int hot_mode;
+        bool coarse_smem;
+        cg_modes(p, bp.smem_floats, hot_mode, coarse_smem);
+        CgWork w = cg_layout(p, base, arena, hot_mode, coarse_smem);
         w.rc = s_rc;
         w.yc = s_yc;
         cg_solve_channel(p, item - bp.prefix[slot], w, bp.cg_tol, bp.cg_max, red, redf);
@@ -1425,7 +1452,7 @@ __global__ void __launch_bounds__(kCThreads) omnical_kernel(const CalParams p) {
             }
             __syncthreads();
         } else {
-            start_point<float>(p, c, xg, xv, red);
+            start_point<float>(p, c, xg, xv, red, xv + 2 * p.n_ubl);
         }
         int st = GC_ENOCONV, it;
         for (it = 1; it <= p.max_iter; ++it) {
@@ -1607,9 +1634,7 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
     } else if (o.solver == GC_LINCAL_CG) {
         per_cta = cg_bytes(p.N, p.n_ubl, p.P);
         kfn = (const void *)lincal_cg_kernel;
-        const size_t hot = cg_hot_floats(p.N, p.n_ubl) * sizeof(float);
-        const size_t both = hot + cg_coarse_floats(p.L, p.n_ubl) * sizeof(float);
-        cg_smem = both <= kCgSmemMax ? both : (hot <= kCgSmemMax ? hot : 0);
+        cg_smem = cg_arena_bytes(p.N, p.n_ubl, p.L, kCgSmemMax);
         e = cudaFuncSetAttribute(lincal_cg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCgSmemMax);
         if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(lincal_cg)");
     } else {
@@ -1680,12 +1705,8 @@ extern "C" gc_status gc_calibrate_batched(gc_ctx *ctx, int n_arrays, const gc_ba
     bp.cg_max = 500;
     // shared arena: the largest array that fits the cap
     size_t smem = 0;
-    for (int a = 0; a < n_arrays; ++a) {
-        const size_t hot = cg_hot_floats(bp.arr[a].N, bp.arr[a].n_ubl) * sizeof(float);
-        const size_t both = hot + cg_coarse_floats(bp.arr[a].L, bp.arr[a].n_ubl) * sizeof(float);
-        if (both <= kCgSmemMax) smem = std::max(smem, both);
-        else if (hot <= kCgSmemMax) smem = std::max(smem, hot);
-    }
+    for (int a = 0; a < n_arrays; ++a)
+        smem = std::max(smem, cg_arena_bytes(bp.arr[a].N, bp.arr[a].n_ubl, bp.arr[a].L, kCgSmemMax));
     bp.smem_floats = (int)(smem / sizeof(float));
     e = cudaFuncSetAttribute(lincal_cg_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCgSmemMax);
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(lincal_cg_batched)");

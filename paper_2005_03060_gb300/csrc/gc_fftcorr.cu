@@ -134,9 +134,10 @@ __host__ __device__ constexpr int bitrev(int i) {
 }
 
 // ----------------------------------------------------------------- config
-template <int M_, int R_, int F1_, int F2_, int NT_, int G_, int VF_>
+template <int M_, int R_, int F1_, int F2_, int NT_, int G_, int VF_, int MINB_ = 1>
 struct Cfg {
     static constexpr int M = M_, R = R_, F1 = F1_, F2 = F2_, NT = NT_, G = G_, VF = VF_;
+    static constexpr int MINB = MINB_;                  // resident CTAs per SM the registers must allow
     static constexpr int LMAX = M / 2;
     static constexpr int MX = M / R;                    // k_x values per work item
     static constexpr int S1 = MX / F1;                  // row residues
@@ -166,12 +167,13 @@ struct Cfg {
     static_assert(MX % F1 == 0 && M % F2 == 0, "bad FFT split");
     static_assert(ROWB % 16 == 0 && (ROWB / 16) % 2 == 1, "stage row must be an odd number of 16B");
     static_assert(F1 % 4 == 0 && (VF != GC_I4C || F1 % 16 == 0 || LMAX <= 16), "row reads");
+    static_assert((G - 1) * NCOL * F2 * 4 <= GNT * LMAX * IROW * 8, "group partial spectra must fit the intermediate");
 };
 
 struct Params {
     const void *volt;        // [C][T][L*L]
     const float2 *gains;     // [C][L*L]
-    float *ppart;            // [C][n_chunks*G][M][M]
+    float *ppart;            // [C][n_chunks][M][M]
     unsigned int *status;
     int L, C, T;
     int chunk_len;           // multiple of G*NT
@@ -226,8 +228,39 @@ __device__ __forceinline__ float2 i4c_to_f2(unsigned int byte) {
     return make_float2(re, im);
 }
 
+// One row input into the fold: b += v c omega_M^{k x}.  With one row residue
+// per item (S1 == 1) the coefficient already carries the twiddle.
+template <class K>
+__device__ __forceinline__ void row_in(float2 &b, float2 v, float2 c, const float2 *tws, int k, int x) {
+    if constexpr (K::S1 == 1) b = cfma(b, v, c);
+    else b = cfma(b, cmul(v, c), tws[(k * x) & (K::M - 1)]);
+}
+
+// multiply by (-i)^R
+template <int R>
+__device__ __forceinline__ float2 rot_mi(float2 a) {
+    if (R == 0) return a;
+    if (R == 1) return make_float2(a.y, -a.x);
+    if (R == 2) return make_float2(-a.x, -a.y);
+    return make_float2(-a.y, a.x);
+}
+
+// Column fold for two folds (J2 == 2) and four column residues (M = 4 F2):
+// omega_M^{s2 (y + F2)} = omega_M^{s2 y} (-i)^{s2}, so the two inputs combine
+// with a trivial rotation before one twiddle multiply (none for s2 = 0).
+template <class K, int S2V>
+__device__ __forceinline__ void col_fold2(float2 (&b)[K::F2], const float2 *icol, const float2 *tws) {
+#pragma unroll
+    for (int yp = 0; yp < K::F2; ++yp) {
+        const float2 a0 = icol[yp * K::IROW];
+        const float2 r = rot_mi<S2V>(icol[(yp + K::F2) * K::IROW]);
+        const float2 t = make_float2(a0.x + r.x, a0.y + r.y);
+        b[yp] = S2V == 0 ? t : cmul(t, tws[(S2V * yp) & (K::M - 1)]);
+    }
+}
+
 template <class K, bool kTMA>
-__global__ void __launch_bounds__(K::NTHREADS)
+__global__ void __launch_bounds__(K::NTHREADS, K::MINB)
 fftcorr_accumulate(const __grid_constant__ CUtensorMap tmap, const Params p) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + K::OFF_BAR);
@@ -280,6 +313,9 @@ fftcorr_accumulate(const __grid_constant__ CUtensorMap tmap, const Params p) {
                 const float2 gg = p.gains[(size_t)c * L * L + y * L + x];
                 const float d = gg.x * gg.x + gg.y * gg.y;
                 cc = make_float2(gg.x / d, -gg.y / d);
+                // one row residue (k = q for the whole item): the row twiddle
+                // omega_M^{k x} rides on the coefficient
+                if (K::S1 == 1) cc = cmul(cc, tws[(q * x) & (K::M - 1)]);
             }
             coef[i] = cc;
         }
@@ -338,10 +374,8 @@ fftcorr_accumulate(const __grid_constant__ CUtensorMap tmap, const Params p) {
                             if (x < K::LMAX) {
                                 const float4 vv = *reinterpret_cast<const float4 *>(srow + x * 8);
                                 const float4 cc = *reinterpret_cast<const float4 *>(crow + x);
-                                const float2 w0 = cmul(make_float2(vv.x, vv.y), make_float2(cc.x, cc.y));
-                                const float2 w1 = cmul(make_float2(vv.z, vv.w), make_float2(cc.z, cc.w));
-                                b[xp] = cfma(b[xp], w0, tws[(k * x) & (K::M - 1)]);
-                                b[xp + 1] = cfma(b[xp + 1], w1, tws[(k * (x + 1)) & (K::M - 1)]);
+                                row_in<K>(b[xp], make_float2(vv.x, vv.y), make_float2(cc.x, cc.y), tws, k, x);
+                                row_in<K>(b[xp + 1], make_float2(vv.z, vv.w), make_float2(cc.z, cc.w), tws, k, x + 1);
                             }
                         }
                     } else if (K::VF == GC_C32H) {
@@ -352,14 +386,10 @@ fftcorr_accumulate(const __grid_constant__ CUtensorMap tmap, const Params p) {
                                 const uint4 raw = *reinterpret_cast<const uint4 *>(srow + x * 4);
                                 const float4 c01 = *reinterpret_cast<const float4 *>(crow + x);
                                 const float4 c23 = *reinterpret_cast<const float4 *>(crow + x + 2);
-                                const float2 w0 = cmul(h2_to_f2(raw.x), make_float2(c01.x, c01.y));
-                                const float2 w1 = cmul(h2_to_f2(raw.y), make_float2(c01.z, c01.w));
-                                const float2 w2 = cmul(h2_to_f2(raw.z), make_float2(c23.x, c23.y));
-                                const float2 w3 = cmul(h2_to_f2(raw.w), make_float2(c23.z, c23.w));
-                                b[xp] = cfma(b[xp], w0, tws[(k * x) & (K::M - 1)]);
-                                b[xp + 1] = cfma(b[xp + 1], w1, tws[(k * (x + 1)) & (K::M - 1)]);
-                                b[xp + 2] = cfma(b[xp + 2], w2, tws[(k * (x + 2)) & (K::M - 1)]);
-                                b[xp + 3] = cfma(b[xp + 3], w3, tws[(k * (x + 3)) & (K::M - 1)]);
+                                row_in<K>(b[xp], h2_to_f2(raw.x), make_float2(c01.x, c01.y), tws, k, x);
+                                row_in<K>(b[xp + 1], h2_to_f2(raw.y), make_float2(c01.z, c01.w), tws, k, x + 1);
+                                row_in<K>(b[xp + 2], h2_to_f2(raw.z), make_float2(c23.x, c23.y), tws, k, x + 2);
+                                row_in<K>(b[xp + 3], h2_to_f2(raw.w), make_float2(c23.z, c23.w), tws, k, x + 3);
                             }
                         }
                     } else {
@@ -374,8 +404,7 @@ fftcorr_accumulate(const __grid_constant__ CUtensorMap tmap, const Params p) {
                                     const int x = x0 + e;
                                     if (x < K::LMAX) {
                                         const float2 v = i4c_to_f2(words[e >> 2] >> (8 * (e & 3)));
-                                        const float2 w = cmul(v, crow[x]);
-                                        b[xp + e] = cfma(b[xp + e], w, tws[(k * x) & (K::M - 1)]);
+                                        row_in<K>(b[xp + e], v, crow[x], tws, k, x);
                                     }
                                 }
                             }
@@ -403,14 +432,24 @@ fftcorr_accumulate(const __grid_constant__ CUtensorMap tmap, const Params p) {
             for (int u = 0; u < K::NT; ++u) {
                 const float2 *icol = inter + ((g * K::NT + u) * K::LMAX) * K::IROW + kxl;
                 float2 b[K::F2];
+                if constexpr (K::J2 == 2 && K::S2 == 4 && K::LMAX == 2 * K::F2) {
+                    // s2 is uniform over each warp (MX >= 32 threads per residue)
+                    switch (s2) {
+                        case 0: col_fold2<K, 0>(b, icol, tws); break;
+                        case 1: col_fold2<K, 1>(b, icol, tws); break;
+                        case 2: col_fold2<K, 2>(b, icol, tws); break;
+                        default: col_fold2<K, 3>(b, icol, tws); break;
+                    }
+                } else {
 #pragma unroll
-                for (int i = 0; i < K::F2; ++i) b[i] = make_float2(0.f, 0.f);
+                    for (int i = 0; i < K::F2; ++i) b[i] = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int j = 0; j < K::J2; ++j) {
+                    for (int j = 0; j < K::J2; ++j) {
 #pragma unroll
-                    for (int yp = 0; yp < K::F2; ++yp) {
-                        const int y = yp + K::F2 * j;
-                        if (y < K::LMAX) b[yp] = cfma(b[yp], icol[y * K::IROW], tws[(s2 * y) & (K::M - 1)]);
+                        for (int yp = 0; yp < K::F2; ++yp) {
+                            const int y = yp + K::F2 * j;
+                            if (y < K::LMAX) b[yp] = cfma(b[yp], icol[y * K::IROW], tws[(s2 * y) & (K::M - 1)]);
+                        }
                     }
                 }
                 fft_reg<K::F2>(b);
@@ -421,11 +460,28 @@ fftcorr_accumulate(const __grid_constant__ CUtensorMap tmap, const Params p) {
         }
         if (s_err) break;
 
-        // chunk spectrum of this group: P[k_y][k_x]
-        float *out = p.ppart + ((size_t)c * p.n_chunks * K::G + (size_t)chunk * K::G + g) * K::M * K::M;
-        const int kx = q + K::R * kxl;
+        // chunk spectrum P[k_y][k_x]: the groups hold the same bins for
+        // different samples; groups 1.. park theirs in the (now idle)
+        // intermediate buffer and group 0 adds them up and stores
+        if constexpr (K::G > 1) {
+            float *park = reinterpret_cast<float *>(inter);
+            if (g > 0) {
 #pragma unroll
-        for (int i = 0; i < K::F2; ++i) out[(s2 + K::S2 * bitrev<K::F2>(i)) * K::M + kx] = acc[i];
+                for (int i = 0; i < K::F2; ++i) park[((g - 1) * K::F2 + i) * K::NCOL + col] = acc[i];
+            }
+            __syncthreads();
+            if (g == 0) {
+#pragma unroll
+                for (int i = 0; i < K::F2; ++i)
+                    for (int gg = 1; gg < K::G; ++gg) acc[i] += park[((gg - 1) * K::F2 + i) * K::NCOL + col];
+            }
+        }
+        if (g == 0) {
+            float *out = p.ppart + ((size_t)c * p.n_chunks + chunk) * K::M * K::M;
+            const int kx = q + K::R * kxl;
+#pragma unroll
+            for (int i = 0; i < K::F2; ++i) out[(s2 + K::S2 * bitrev<K::F2>(i)) * K::M + kx] = acc[i];
+        }
     }
 
     if (kTMA && s_err && tid == 0) {
@@ -612,7 +668,7 @@ struct Launcher {
         p.chunk_len = best_len;
         p.n_chunks = best_n;
         p.n_items = C * K::R * best_n;
-        const size_t part_bytes = ((size_t)C * best_n * K::G * K::M * K::M * sizeof(float) + 255) / 256 * 256;
+        const size_t part_bytes = ((size_t)C * best_n * K::M * K::M * sizeof(float) + 255) / 256 * 256;
         const size_t q_bytes = K::M > 128 ? (size_t)C * K::M * (2 * L - 1) * sizeof(float2) : 0;
         gc_status st = gc_scratch_reserve(ctx, part_bytes + q_bytes);
         if (st != GC_OK) return st;
@@ -639,7 +695,7 @@ struct Launcher {
         if constexpr (K::M > 128) {
             float2 *Q = reinterpret_cast<float2 *>(static_cast<char *>(ctx->scratch) + part_bytes);
             rec = gc_prof_begin(ctx, stream, "fftcorr_finalize");
-            fftcorr_finalize_rows<K::M><<<dim3(C, K::M / kFinRows), 256, 0, stream>>>(p.ppart, best_n * K::G, Q, L);
+            fftcorr_finalize_rows<K::M><<<dim3(C, K::M / kFinRows), 256, 0, stream>>>(p.ppart, best_n, Q, L);
             fftcorr_finalize_cols<K::M><<<dim3(C, (W + kFinCols - 1) / kFinCols), 256, 0, stream>>>(
                 Q, reinterpret_cast<float2 *>(vunique), L, T);
             gc_prof_end(ctx, stream, rec);
@@ -649,7 +705,7 @@ struct Launcher {
             e = cudaFuncSetAttribute(fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
             if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(fftcorr_finalize)");
             rec = gc_prof_begin(ctx, stream, "fftcorr_finalize");
-            fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n * K::G, reinterpret_cast<float2 *>(vunique), L, T);
+            fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n, reinterpret_cast<float2 *>(vunique), L, T);
             gc_prof_end(ctx, stream, rec);
         }
         e = cudaGetLastError();
@@ -666,7 +722,7 @@ using CfgC128 = Cfg<128, 4, 32, 32, 1, 1, GC_C64>;
 using CfgI16 = Cfg<16, 1, 16, 16, 2, 8, GC_I4C>;
 using CfgI32 = Cfg<32, 1, 32, 32, 2, 4, GC_I4C>;
 using CfgI64 = Cfg<64, 1, 32, 32, 2, 1, GC_I4C>;
-using CfgI128 = Cfg<128, 4, 32, 32, 2, 1, GC_I4C>;
+using CfgI128 = Cfg<128, 4, 32, 32, 1, 2, GC_I4C, 2>;   // two groups share the coefficients; 16 warps/SM
 // M = 256 (L = 65..128): 4+4-bit only -- one complex64 or binary16 grid sample
 // (128 rows of 1 KB / 512 B) does not fit a double-buffered stage beside the
 // 133 KB coefficient table.  Eight k_x residues, one sample per iteration,
@@ -675,7 +731,7 @@ using CfgI256 = Cfg<256, 8, 16, 32, 1, 1, GC_I4C>;
 using CfgH16 = Cfg<16, 1, 16, 16, 2, 8, GC_C32H>;
 using CfgH32 = Cfg<32, 1, 32, 32, 2, 4, GC_C32H>;
 using CfgH64 = Cfg<64, 1, 32, 32, 2, 1, GC_C32H>;
-using CfgH128 = Cfg<128, 4, 32, 32, 2, 1, GC_C32H>;
+using CfgH128 = Cfg<128, 4, 32, 32, 1, 2, GC_C32H>;
 
 }  // namespace
 
@@ -782,7 +838,7 @@ template <class K>
 gc_status noalloc_run(const NoallocDev &d, const void *volt, int L, int C, int T, const float *gains,
                       float *vunique, unsigned int *status, cudaStream_t stream) {
     const int N = L * L;
-    const size_t per_chunk = (size_t)C * K::G * K::M * K::M * sizeof(float);
+    const size_t per_chunk = (size_t)C * K::M * K::M * sizeof(float);
     const int n_min = std::max(1, (T + 511) / 512);      // chunks of <= 512 samples
     if (per_chunk * n_min > kNoallocScratchBytes) return GC_EINVAL;
     const int n_cap = (int)std::min<size_t>(kNoallocScratchBytes / per_chunk, (size_t)n_min + 64);
@@ -850,7 +906,7 @@ gc_status noalloc_run(const NoallocDev &d, const void *volt, int L, int C, int T
     auto fin = fftcorr_finalize<K::M>;
     if (cudaFuncSetAttribute(fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem) != cudaSuccess)
         return GC_ECUDA;
-    fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n * K::G, reinterpret_cast<float2 *>(vunique), L, T);
+    fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n, reinterpret_cast<float2 *>(vunique), L, T);
     if (cudaGetLastError() != cudaSuccess) return GC_ECUDA;
     return GC_OK;
 }

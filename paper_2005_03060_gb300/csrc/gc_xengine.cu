@@ -8,8 +8,8 @@
 // reference antenna j and accumulates v_{j+d} conj(v_j) for every type d of
 // its group in registers.  complex64 and binary16 voltages accumulate in
 // FP32.  4+4-bit voltages take an integer path: each staged byte pair
-// (samples t, t+1 of one antenna) is expanded through a 256-entry table into
-// two words of signed bytes
+// (samples t, t+1 of one antenna) is expanded by byte-parallel integer ops
+// into two words of signed bytes
 //   W  = (re_t, im_t, re_t1, im_t1),   Wc = (re_t, -im_t, re_t1, -im_t1),
 // and one 4-way byte dot product with int32 accumulation (dp4a) gives two
 // samples of each part of v_i conj(v_j):
@@ -65,7 +65,6 @@ __global__ void __launch_bounds__(kXThreads, 2) xeng_accumulate(const XParams p)
     __shared__ int s_dx[GC_XENG_NTY], s_dy[GC_XENG_NTY], s_base[GC_XENG_NTY];
     __shared__ int s_err;
     constexpr bool kI4 = VF == GC_I4C;
-    __shared__ uint32_t s_lut[kI4 ? 256 : 1];
     const int tid = threadIdx.x;
     constexpr int esz = VF == GC_C64 ? 8 : (VF == GC_C32H ? 4 : 1);
     const size_t sample_bytes = (size_t)p.N * esz;
@@ -79,13 +78,6 @@ __global__ void __launch_bounds__(kXThreads, 2) xeng_accumulate(const XParams p)
     uint32_t *conv = reinterpret_cast<uint32_t *>(smem + 2 * stage_stride);
     if (kI4) {
         for (int i = tid; i < kRec; i += kXThreads) conv[(size_t)(p.conv_recs - 1) * kRec + i] = 0u;
-        // byte -> (re, im, re, -im) as signed bytes
-        for (int b = tid; b < 256; b += kXThreads) {
-            const int re = (int)(signed char)b >> 4;
-            const int im = (int)(signed char)(b << 4) >> 4;
-            s_lut[b] = (uint32_t)(re & 0xFF) | ((uint32_t)(im & 0xFF) << 8) | ((uint32_t)(re & 0xFF) << 16) |
-                       ((uint32_t)(-im & 0xFF) << 24);
-        }
     }
     if (tid == 0) {
         s_err = 0;
@@ -206,19 +198,27 @@ __global__ void __launch_bounds__(kXThreads, 2) xeng_accumulate(const XParams p)
                     const int qu = kQ == 1 ? 0 : u / n_ant;
                     const int a = u - qu * n_ant;
                     const int s0 = 4 * qu;             // first sample of the unit
-                    uint32_t e[4];
+                    uint32_t X = 0u;                   // bytes of samples s0..s0+3 (0 past cnt)
 #pragma unroll
                     for (int i = 0; i < (NP == 8 ? 4 : 2); ++i)
-                        e[i] = s0 + i < cnt ? s_lut[stage[(size_t)(s0 + i) * part_bytes + a]] : 0u;
+                        if (s0 + i < cnt) X |= (uint32_t)stage[(size_t)(s0 + i) * part_bytes + a] << (8 * i);
+                    // sign-extend the nibbles byte-parallel: (n ^ 8) + 0x78 never
+                    // carries out of a byte and ^ 0x80 turns it into n as int8;
+                    // 0x88 - (n ^ 8), then ^ 0x80, gives -n
+                    const uint32_t ux = (X & 0x0F0F0F0Fu) ^ 0x08080808u;
+                    const uint32_t vx = ((X >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
+                    const uint32_t im = (ux + 0x78787878u) ^ 0x80808080u;
+                    const uint32_t nim = (0x88888888u - ux) ^ 0x80808080u;
+                    const uint32_t re = (vx + 0x78787878u) ^ 0x80808080u;
                     uint32_t *rec = conv + (size_t)a * kRec;
                     if constexpr (NP == 8) {
                         *reinterpret_cast<uint2 *>(rec + 2 * qu) =
-                            make_uint2(__byte_perm(e[0], e[1], 0x5410), __byte_perm(e[2], e[3], 0x5410));
+                            make_uint2(__byte_perm(re, im, 0x5140), __byte_perm(re, im, 0x7362));
                         *reinterpret_cast<uint2 *>(rec + 8 + 2 * qu) =
-                            make_uint2(__byte_perm(e[0], e[1], 0x7632), __byte_perm(e[2], e[3], 0x7632));
+                            make_uint2(__byte_perm(re, nim, 0x5140), __byte_perm(re, nim, 0x7362));
                     } else {
                         *reinterpret_cast<uint2 *>(rec) =
-                            make_uint2(__byte_perm(e[0], e[1], 0x5410), __byte_perm(e[0], e[1], 0x7632));
+                            make_uint2(__byte_perm(re, im, 0x5140), __byte_perm(re, nim, 0x5140));
                     }
                 }
                 __syncthreads();
