@@ -117,16 +117,30 @@ def fit_degeneracies(g_est, g_true, L):
 
 
 # --------------------------------------------------------------------------- start point
-def _lstsq_rows(n_var, rows_idx, rows_val, rhs):
-    A = np.zeros((len(rhs), n_var))
+def _lstsq_rows(n_var, rows_idx, rows_val, rhs, sparse=False):
+    """Minimum-norm least-squares solution of the rows given by (index,
+    value) lists: numpy's dense solver, or (sparse) LSQR started from zero,
+    which converges to the same minimum-norm solution."""
+    if not sparse:
+        A = np.zeros((len(rhs), n_var))
+        for r, (idx, val) in enumerate(zip(rows_idx, rows_val)):
+            for c, v in zip(idx, val):
+                A[r, c] += v
+        sol, *_ = np.linalg.lstsq(A, rhs, rcond=None)
+        return sol
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.linalg import lsqr
+    rr, cc, vv = [], [], []
     for r, (idx, val) in enumerate(zip(rows_idx, rows_val)):
         for c, v in zip(idx, val):
-            A[r, c] += v
-    sol, *_ = np.linalg.lstsq(A, rhs, rcond=None)
-    return sol
+            rr.append(r)
+            cc.append(c)
+            vv.append(v)
+    A = coo_matrix((vv, (rr, cc)), shape=(len(rhs), n_var)).tocsr()
+    return lsqr(A, rhs, atol=1e-15, btol=1e-15, conlim=1e15, iter_lim=50 * n_var)[0]
 
 
-def initial_solution(vobs, pi, pj, alpha, types, L):
+def initial_solution(vobs, pi, pj, alpha, types, L, sparse=False):
     """Phase tree + wrapped phase logcal + amplitude logcal (Eq. logcal)."""
     N = L * L
     nu = len(types)
@@ -145,10 +159,10 @@ def initial_solution(vobs, pi, pj, alpha, types, L):
     # wrapped residual phase logcal: dphi_i - dphi_j + theta_a = wrap(arg V - phi_i + phi_j)
     res = np.angle(vobs * np.exp(-1j * (phi[pi] - phi[pj])))
     idx = [(int(pi[p]), int(pj[p]), N + int(alpha[p])) for p in range(len(vobs))]
-    sol = _lstsq_rows(N + nu, idx, [(1.0, -1.0, 1.0)] * len(vobs), res)
+    sol = _lstsq_rows(N + nu, idx, [(1.0, -1.0, 1.0)] * len(vobs), res, sparse)
     phi = phi + sol[:N]
     # amplitude logcal: eta_i + eta_j + a_alpha = ln|V_p|
-    sol = _lstsq_rows(N + nu, idx, [(1.0, 1.0, 1.0)] * len(vobs), np.log(np.abs(vobs)))
+    sol = _lstsq_rows(N + nu, idx, [(1.0, 1.0, 1.0)] * len(vobs), np.log(np.abs(vobs)), sparse)
     g = np.exp(sol[:N] + 1j * phi)
     V = np.zeros(nu, np.complex128)
     cnt = np.zeros(nu)
@@ -187,6 +201,37 @@ def _jacobian(g, V, pi, pj, alpha):
     return J
 
 
+def _jacobian_sparse(g, V, pi, pj, alpha):
+    """The Jacobian of _jacobian as a scipy sparse matrix (same entries,
+    duplicates summed) for arrays too large for the dense form."""
+    from scipy.sparse import coo_matrix
+    N, nu, P = len(g), len(V), len(pi)
+    rows = np.arange(P)
+    dgi = np.conj(g[pj]) * V[alpha]
+    dgj = g[pi] * V[alpha]
+    dv = g[pi] * np.conj(g[pj])
+    R, Cc, X = [], [], []
+
+    def put(r, c, v):
+        R.append(r)
+        Cc.append(c)
+        X.append(v)
+    put(rows, pi, dgi.real)
+    put(P + rows, pi, dgi.imag)
+    put(rows, N + pi, -dgi.imag)
+    put(P + rows, N + pi, dgi.real)
+    put(rows, pj, dgj.real)
+    put(P + rows, pj, dgj.imag)
+    put(rows, N + pj, dgj.imag)
+    put(P + rows, N + pj, -dgj.real)
+    put(rows, 2 * N + alpha, dv.real)
+    put(P + rows, 2 * N + alpha, dv.imag)
+    put(rows, 2 * N + nu + alpha, -dv.imag)
+    put(P + rows, 2 * N + nu + alpha, dv.real)
+    return coo_matrix((np.concatenate(X), (np.concatenate(R), np.concatenate(Cc))),
+                      shape=(2 * P, 2 * N + 2 * nu)).tocsr()
+
+
 def _degenerate_directions(g, V, types_d, L):
     """Real tangent vectors of the four degeneracies at (g, V), in the
     ordering x = [Re g, Im g, Re V, Im V]: amplitude (g, -2V), phase (i g, 0)
@@ -199,20 +244,31 @@ def _degenerate_directions(g, V, types_d, L):
     return np.stack([np.concatenate([a.real, a.imag, b.real, b.imag]) for a, b in dirs], 1)
 
 
-def lincal(vobs, pi, pj, alpha, g, V, types, L, tol=1e-10, maxiter=200):
-    """Gauss-Newton on chi^2 about the current point (Sec. 2, lincal)."""
+def lincal(vobs, pi, pj, alpha, g, V, types, L, tol=1e-10, maxiter=200, sparse=False):
+    """Gauss-Newton on chi^2 about the current point (Sec. 2, lincal).
+    sparse: the same normal equations in scipy sparse form, solved by a
+    sparse direct factorisation (for arrays too large for the dense form)."""
     types_d = np.asarray(types, float)
     g = np.asarray(g, np.complex128).copy()
     V = np.asarray(V, np.complex128).copy()
     N, nu = len(g), len(V)
     for it in range(1, maxiter + 1):
         r = vobs - model(g, V, pi, pj, alpha)
-        J = _jacobian(g, V, pi, pj, alpha)
-        A = J.T @ J
-        b = J.T @ np.concatenate([r.real, r.imag])
-        A[np.diag_indices_from(A)] += 1e-12 * np.max(np.diag(A))
-        c = np.linalg.cholesky(A)
-        delta = np.linalg.solve(c.T, np.linalg.solve(c, b))
+        if sparse:
+            from scipy.sparse import identity
+            from scipy.sparse.linalg import spsolve
+            J = _jacobian_sparse(g, V, pi, pj, alpha)
+            A = (J.T @ J).tocsc()
+            b = J.T @ np.concatenate([r.real, r.imag])
+            A = A + (1e-12 * A.diagonal().max()) * identity(A.shape[0], format="csc")
+            delta = spsolve(A, b)
+        else:
+            J = _jacobian(g, V, pi, pj, alpha)
+            A = J.T @ J
+            b = J.T @ np.concatenate([r.real, r.imag])
+            A[np.diag_indices_from(A)] += 1e-12 * np.max(np.diag(A))
+            c = np.linalg.cholesky(A)
+            delta = np.linalg.solve(c.T, np.linalg.solve(c, b))
         # keep the four exact degeneracies (Sec. 5.2) out of the step
         Q, _ = np.linalg.qr(_degenerate_directions(g, V, types_d, L))
         delta -= Q @ (Q.T @ delta)
@@ -255,12 +311,14 @@ def omnical(vobs, pi, pj, alpha, g, V, damping=0.3, tol=1e-10, maxiter=100000):
     return g, V, maxiter, False
 
 
-def calibrate(vobs, pi, pj, alpha, types, L, solver="lincal", tol=1e-10, maxiter=None):
-    """Start point, solver and output convention for one channel."""
-    g0, V0 = initial_solution(vobs, pi, pj, alpha, types, L)
+def calibrate(vobs, pi, pj, alpha, types, L, solver="lincal", tol=1e-10, maxiter=None, sparse=False):
+    """Start point, solver and output convention for one channel.  sparse
+    (lincal only): sparse linear algebra for the start point and the
+    Gauss-Newton steps -- same equations, for large arrays."""
+    g0, V0 = initial_solution(vobs, pi, pj, alpha, types, L, sparse=sparse)
     if solver == "lincal":
         g, V, it, ok = lincal(vobs, pi, pj, alpha, g0, V0, types, L, tol=tol,
-                              maxiter=maxiter or 200)
+                              maxiter=maxiter or 200, sparse=sparse)
     elif solver == "omnical":
         g, V, it, ok = omnical(vobs, pi, pj, alpha, g0, V0, tol=tol, maxiter=maxiter or 100000)
     else:

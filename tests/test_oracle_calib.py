@@ -146,3 +146,27 @@ def test_voltages_to_gains_end_to_end(orc, solver):
     gf = oc.fit_degeneracies(ge, g_true, L)
     # float32 voltages: recovery to single precision
     assert np.max(np.abs(gf - g_true) / np.abs(g_true)) < 1e-5
+
+
+@pytest.mark.parametrize("L,sigma", [(4, 0.05), (6, 0.1), (8, 0.02)])
+def test_sparse_lincal_equals_dense(L, sigma):
+    """The sparse form of lincal solves the same Gauss-Newton normal
+    equations: same minimum, same gains after the output convention."""
+    sel, alpha, g, V, vobs = _problem(L, 40 + L, sigma=sigma)
+    a = oc.calibrate(vobs, sel.pair_i, sel.pair_j, alpha, sel.types, L, "lincal")
+    b = oc.calibrate(vobs, sel.pair_i, sel.pair_j, alpha, sel.types, L, "lincal", sparse=True)
+    assert a[3] and b[3]
+    assert np.max(np.abs(a[0] - b[0]) / np.abs(a[0])) < 1e-9
+    assert np.max(np.abs(a[1] - b[1]) / np.abs(a[1])) < 1e-9
+
+
+def test_sparse_lincal_noise_free_recovery_24x24():
+    """Exact recovery up to the four degeneracies (Sec. 5.2) on an array
+    the dense form would handle only slowly."""
+    L = 24
+    sel, alpha, g, V, vobs = _problem(L, 77, sel=osel.subset(L, 100))
+    ge, Ve, it, ok = oc.calibrate(vobs, sel.pair_i, sel.pair_j, alpha, sel.types, L, "lincal", sparse=True)
+    assert ok
+    assert oc.chi2(vobs, ge, Ve, sel.pair_i, sel.pair_j, alpha) < 1e-18 * len(vobs)
+    gf = oc.fit_degeneracies(ge, g, L)
+    assert np.max(np.abs(gf - g) / np.abs(g)) < 1e-8
