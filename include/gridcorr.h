@@ -316,6 +316,35 @@ GC_API gc_status gc_chi2_backward(gc_ctx *ctx, const void *vreduced, int vfmt, c
                                   float *grad_vmodel, void *stream);
 
 /*
+ * One integration of HOST-resident voltages through the whole cycle of the
+ * paper's Fig. 1: FFT-correlator (gc_correlate), reduced X-engine
+ * (gc_reduce) and calibration (gc_calibrate), streamed in chunks of
+ * `chunk` channels (0: automatic, about eight chunks).  The host->device
+ * copy of the next chunk, on a copy stream owned by the context, overlaps
+ * the kernels of the current one on `stream`; the calibration runs on groups
+ * of chunks as their V^reduced complete.  (No paper counterpart: this is the
+ * data path of a correlator whose voltages arrive from the host.)
+ *
+ *   h_volt    [C][T][L*L] host memory, c64 / c32h / i4c as gc_correlate;
+ *             page-locked memory lets the copies overlap (pageable memory
+ *             works, with synchronous copies)
+ *   gains_in  [C][L*L] c64 device: the gains the correlator applies
+ *   vunique   [C][2L-1][2L-1] c64 device (output)
+ *   vreduced, autos  device outputs as gc_reduce (autos may be NULL)
+ *   opts      calibration options (NULL: defaults); gains_out [C][L*L],
+ *             vmodel [C][n_ubl], stats [C]: device outputs as gc_calibrate
+ * The context allocates two device staging buffers of chunk * T * L*L
+ * voltage elements on first need (cudaMalloc, which synchronises the
+ * device) and keeps them.  Everything is enqueued; the call returns when
+ * the work is queued.  The staging buffers and h_volt must not be modified
+ * until `stream` has completed the call's work.  Errors as the three calls.
+ */
+GC_API gc_status gc_integrate_host(gc_ctx *ctx, const void *h_volt, int vfmt, int L, int C, int T,
+                                   const gc_sel *sel, const float *gains_in, float *vunique, void *vreduced,
+                                   void *autos, const gc_calopts *opts, float *gains_out, float *vmodel,
+                                   gc_calstats *stats, int chunk, void *stream);
+
+/*
  * FFT-correlator that allocates no device memory.  The paper has no
  * counterpart: this is an interface for callers that cannot call cudaMalloc
  * -- for example a real-time correlator process whose device memory is

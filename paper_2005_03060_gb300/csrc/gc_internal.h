@@ -40,6 +40,11 @@ struct gc_ctx {
     bool profile = false;
     std::vector<gc_prof_rec> prof;        // records since the last read
     std::vector<cudaEvent_t> event_pool;
+    // gc_integrate_host: copy stream, two device staging buffers, events
+    cudaStream_t copy_stream = nullptr;
+    void *stage[2] = {nullptr, nullptr};
+    size_t stage_bytes = 0;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr}, ev_entry = nullptr;
 };
 
 // launch timing helpers: no-ops unless profiling is enabled

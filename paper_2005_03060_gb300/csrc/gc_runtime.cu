@@ -134,6 +134,13 @@ void gc_destroy(gc_ctx *ctx) {
     cudaDeviceSynchronize();
     prof_clear(ctx);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    for (int b = 0; b < 2; ++b) {
+        if (ctx->stage[b]) cudaFree(ctx->stage[b]);
+        if (ctx->ev_copied[b]) cudaEventDestroy(ctx->ev_copied[b]);
+        if (ctx->ev_free[b]) cudaEventDestroy(ctx->ev_free[b]);
+    }
+    if (ctx->ev_entry) cudaEventDestroy(ctx->ev_entry);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->status_dev) cudaFree(ctx->status_dev);
     cudaSetDevice(prev);

@@ -82,6 +82,8 @@ _lib.gc_get_tuning.argtypes = [_vp, ctypes.c_char_p, ctypes.POINTER(_i)]
 _lib.gc_get_tuning.restype = _i
 _lib.gc_quantize.argtypes = [_vp, _vp, _i, _i, _i, _vp, _vp, _vp]
 _lib.gc_quantize.restype = _i
+_lib.gc_integrate_host.argtypes = [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp]
+_lib.gc_integrate_host.restype = _i
 
 
 def _volt_format(volt: torch.Tensor):
@@ -234,6 +236,31 @@ class Context:
                                      ctypes.byref(o), _vp(gains.data_ptr()), _vp(vmodel.data_ptr()),
                                      _vp(stats.data_ptr()), _vp(_stream_ptr(dev))))
         return gains, vmodel, stats
+
+    def integrate_host(self, h_volt: torch.Tensor, sel: "Selection", gains_in: torch.Tensor,
+                       vunique: torch.Tensor, vreduced: torch.Tensor, autos: torch.Tensor | None,
+                       gains_out: torch.Tensor, vmodel: torch.Tensor, stats: torch.Tensor,
+                       solver: str = "lincal_cg", precision: str = "fp32", chunk: int = 0):
+        """One integration of host-resident voltages (pinned CPU tensor of
+        any gc_vfmt layout) through correlate -> reduce -> calibrate,
+        streamed in channel chunks (gc_integrate_host); outputs are the
+        device tensors passed in, on the current stream."""
+        if h_volt.is_cuda or not h_volt.is_contiguous():
+            raise ValueError("h_volt must be a contiguous host tensor")
+        vfmt, (C, T, N) = _volt_format(h_volt)
+        dev = gains_in.device
+        for t in (gains_in, vunique, vreduced, gains_out, vmodel, stats) + ((autos,) if autos is not None else ()):
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("outputs and gains must be contiguous CUDA tensors")
+        o = CalOpts({"lincal": GC_LINCAL, "omnical": GC_OMNICAL, "lincal_cg": GC_LINCAL_CG}[solver],
+                    GC_FP64 if precision == "fp64" else GC_FP32, 0, 0, 0.0, 0.0, 0, 0)
+        self.check(_lib.gc_integrate_host(self._h, _vp(h_volt.data_ptr()), vfmt, sel.L, C, T, sel.handle,
+                                          _vp(gains_in.data_ptr()), _vp(vunique.data_ptr()),
+                                          _vp(vreduced.data_ptr()),
+                                          _vp(autos.data_ptr() if autos is not None else None),
+                                          ctypes.byref(o), _vp(gains_out.data_ptr()), _vp(vmodel.data_ptr()),
+                                          _vp(stats.data_ptr()), chunk, _vp(_stream_ptr(dev))))
+        return vunique, gains_out
 
     def calibrate_batched(self, arrays, max_iter: int = 0, tol: float = 0.0, time_limit_ms: int = 0):
         """One persistent launch over several arrays.  `arrays` is a list of
