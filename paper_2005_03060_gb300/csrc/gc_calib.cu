@@ -930,6 +930,9 @@ __device__ __forceinline__ void cg_modes(const CalParams &p, int smem_floats, in
 // Each warp walks a contiguous chunk of the (type-major) pair list, so the
 // model-visibility terms accumulate in registers and are flushed with one
 // warp reduction per type boundary.
+// kPipe: hot vectors in global memory -- pipeline the pair loads (a separate
+// instantiation: the pipeline's registers would slow the shared-memory form)
+template <bool kPipe>
 __device__ double cg_pass(const CalParams &p, int c, const CgWork &w, bool resid, double *red) {
     const int nm = w.n + w.m;
     if (resid) {   // the operator passes find acc already zeroed by the caller
@@ -958,31 +961,72 @@ __device__ double cg_pass(const CalParams &p, int c, const CgWork &w, bool resid
         }
         vx = vy = vd = 0.f;
     };
-    for (int q0 = q_lo; q0 < q_hi; q0 += 32) {
-        const int q = q0 + lane;
-        const bool valid = q < q_hi;
-        int k = k_cur;
+    // software pipeline over 32-pair batches: the index loads run two
+    // batches ahead and the gathers one batch ahead of the arithmetic and the
+    // reductions, so each warp keeps three batches of L2 traffic in flight
+    struct Idx {
+        int i, j, k, q;
+    };
+    struct Dat {
+        int i, j, k, q;
+        float gix, giy, gjx, gjy, Vx, Vy, a0, a1, a2, a3, a4, a5;
+    };
+    auto fetch_idx = [&](int q) {
+        Idx r{-1, -1, 0, q};
+        if (q < q_hi) {
+            r.i = p.pair_i[q];
+            r.j = p.pair_j[q];
+            r.k = p.pair_type[q];
+        }
+        return r;
+    };
+    auto fetch_dat = [&](const Idx &x) {
+        Dat d;
+        d.i = x.i;
+        d.j = x.j;
+        d.k = x.k;
+        d.q = x.q;
+        if (x.i >= 0) {
+            d.gix = w.xg[2 * x.i];
+            d.giy = w.xg[2 * x.i + 1];
+            d.gjx = w.xg[2 * x.j];
+            d.gjy = w.xg[2 * x.j + 1];
+            d.Vx = w.xv[2 * x.k];
+            d.Vy = w.xv[2 * x.k + 1];
+            if (resid) {
+                const float2 o = vobs(p, c, x.q);
+                d.a0 = o.x;
+                d.a1 = o.y;
+            } else {
+                d.a0 = w.pp[2 * x.i];
+                d.a1 = w.pp[2 * x.i + 1];
+                d.a2 = w.pp[2 * x.j];
+                d.a3 = w.pp[2 * x.j + 1];
+                d.a4 = w.pp[w.n + 2 * x.k];
+                d.a5 = w.pp[w.n + 2 * x.k + 1];
+            }
+        }
+        return d;
+    };
+    auto process = [&](const Dat &d) {
+        const bool valid = d.i >= 0;
+        const int k = valid ? d.k : k_cur;
         float ux = 0.f, uy = 0.f, ex = 0.f, ey = 0.f;
         if (valid) {
-            const int i = p.pair_i[q], j = p.pair_j[q];
-            k = p.pair_type[q];
-            const float gix = w.xg[2 * i], giy = w.xg[2 * i + 1], gjx = w.xg[2 * j], gjy = w.xg[2 * j + 1];
-            const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
+            const int i = d.i, j = d.j;
+            const float gix = d.gix, giy = d.giy, gjx = d.gjx, gjy = d.gjy, Vx = d.Vx, Vy = d.Vy;
             ex = gix * gjx + giy * gjy;
             ey = giy * gjx - gix * gjy;                                        // g_i conj(g_j)
             const float ax = gjx * Vx + gjy * Vy, ay = gjx * Vy - gjy * Vx;    // conj(g_j) V
             const float bx = gix * Vx - giy * Vy, by = gix * Vy + giy * Vx;    // g_i V
             if (resid) {
-                const float2 o = vobs(p, c, q);
-                ux = o.x - (ex * Vx - ey * Vy);
-                uy = o.y - (ex * Vy + ey * Vx);
+                ux = d.a0 - (ex * Vx - ey * Vy);
+                uy = d.a1 - (ex * Vy + ey * Vx);
                 chi = fmaf(ux, ux, fmaf(uy, uy, chi));
                 atomicAdd(&w.dg[i], ax * ax + ay * ay);
                 atomicAdd(&w.dg[j], bx * bx + by * by);
             } else {
-                const float vix = w.pp[2 * i], viy = w.pp[2 * i + 1];
-                const float vjx = w.pp[2 * j], vjy = -w.pp[2 * j + 1];
-                const float vvx = w.pp[w.n + 2 * k], vvy = w.pp[w.n + 2 * k + 1];
+                const float vix = d.a0, viy = d.a1, vjx = d.a2, vjy = -d.a3, vvx = d.a4, vvy = d.a5;
                 ux = ax * vix - ay * viy + bx * vjx - by * vjy + ex * vvx - ey * vvy;
                 uy = ax * viy + ay * vix + bx * vjy + by * vjx + ex * vvy + ey * vvx;
             }
@@ -1006,6 +1050,20 @@ __device__ double cg_pass(const CalParams &p, int c, const CgWork &w, bool resid
                 if (resid) atomicAdd(&w.dv[k], td);
             }
             k_cur = __shfl_sync(0xffffffffu, k, 31);
+        }
+    };
+    if (q_lo < q_hi) {
+        if constexpr (kPipe) {
+            Idx nxt = fetch_idx(q_lo + 32 + lane);
+            Dat cur = fetch_dat(fetch_idx(q_lo + lane));
+            for (int q0 = q_lo; q0 < q_hi; q0 += 32) {
+                const Dat d2 = fetch_dat(nxt);   // gathers of the next batch
+                nxt = fetch_idx(q0 + 64 + lane); // indices two batches ahead
+                process(cur);
+                cur = d2;
+            }
+        } else {   // shared-memory hot vectors: short latencies, no pipeline
+            for (int q0 = q_lo; q0 < q_hi; q0 += 32) process(fetch_dat(fetch_idx(q0 + lane)));
         }
     }
     if (q_lo < q_hi) flush(k_cur);
@@ -1174,6 +1232,7 @@ __device__ void cg_coarse_setup(const CalParams &p, const CgWork &w, float mu) {
 // One channel of matrix-free Gauss-Newton (used by the per-selection and the
 // batched kernels).  All threads of the CTA call it.  The CG iteration takes
 // four barriers (six with the coarse correction).
+template <bool kPipe>
 __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg_tol, int cg_max, double *red,
                                  float *redf) {
     const int nm = w.n + w.m, ne = p.N + p.n_ubl, L = p.L, nc = w.nc;
@@ -1254,7 +1313,7 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
     double grad0 = 0.0;
     for (it = 1; it <= p.max_iter; ++it) {
         // residual, right-hand side J^T r and the Jacobi diagonals
-        const double chi2 = cg_pass(p, c, w, true, red);
+        const double chi2 = cg_pass<kPipe>(p, c, w, true, red);
         double dm = 0.0;
         for (int i = threadIdx.x; i < p.N; i += blockDim.x) dm = fmax(dm, (double)w.dg[i]);
         for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
@@ -1294,7 +1353,7 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
         const float eta = (float)fmin(0.1, fmax(cg_tol, sqrt(sqrt((double)bnorm2 / fmax(grad0, 1e-300)))));
         for (int k = 0; k < cg_max && bnorm2 > 0.f; ++k) {
             ++inner;
-            cg_pass(p, c, w, false, red);                 // acc = J^T J pp (acc was zeroed)
+            cg_pass<kPipe>(p, c, w, false, red);          // acc = J^T J pp (acc was zeroed)
             float v1[1] = {0.f};
             for (int i = threadIdx.x; i < nm; i += blockDim.x) v1[0] = fmaf(w.pp[i], w.acc[i] + mu * w.pp[i], v1[0]);
             fast_sum<1>(v1, sbuf, par);
@@ -1368,6 +1427,7 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
     finish_channel<float>(p, c, w.xg, w.xv, min(it, p.max_iter), st, red, inner);
 }
 
+template <bool kPipe>
 __global__ void __launch_bounds__(kCgThreads, 2) lincal_cg_kernel(const CalParams p, double cg_tol, int cg_max,
                                                               int smem_floats) {
     __shared__ double red[32 * 14];
@@ -1380,7 +1440,7 @@ __global__ void __launch_bounds__(kCgThreads, 2) lincal_cg_kernel(const CalParam
     CgWork w = cg_layout(p, p.work + (size_t)blockIdx.x * p.work_per_cta, arena, hot_mode, coarse_smem);
     w.rc = s_rc;
     w.yc = s_yc;
-    for (int c = blockIdx.x; c < p.C; c += gridDim.x) cg_solve_channel(p, c, w, cg_tol, cg_max, red, redf);
+    for (int c = blockIdx.x; c < p.C; c += gridDim.x) cg_solve_channel<kPipe>(p, c, w, cg_tol, cg_max, red, redf);
 }
 
 // Several arrays of different size in one persistent launch: CTAs take
@@ -1422,7 +1482,7 @@ __global__ void __launch_bounds__(kCgThreads, 2) lincal_cg_batched(const __grid_
         CgWork w = cg_layout(p, base, arena, hot_mode, coarse_smem);
         w.rc = s_rc;
         w.yc = s_yc;
-        cg_solve_channel(p, item - bp.prefix[slot], w, bp.cg_tol, bp.cg_max, red, redf);
+        cg_solve_channel<false>(p, item - bp.prefix[slot], w, bp.cg_tol, bp.cg_max, red, redf);
     }
 }
 
@@ -1633,9 +1693,9 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
         kfn = fp64 ? (const void *)lincal_kernel<double> : (const void *)lincal_kernel<float>;
     } else if (o.solver == GC_LINCAL_CG) {
         per_cta = cg_bytes(p.N, p.n_ubl, p.P);
-        kfn = (const void *)lincal_cg_kernel;
         cg_smem = cg_arena_bytes(p.N, p.n_ubl, p.L, kCgSmemMax);
-        e = cudaFuncSetAttribute(lincal_cg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCgSmemMax);
+        kfn = cg_smem ? (const void *)lincal_cg_kernel<false> : (const void *)lincal_cg_kernel<true>;
+        e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCgSmemMax);
         if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(lincal_cg)");
     } else {
         per_cta = sizeof(float) * (size_t)(2 * p.N + 2 * p.n_ubl + p.N + 2 * p.N + 2 * p.n_ubl + 64);
@@ -1659,7 +1719,8 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
         if (fp64) lincal_kernel<double><<<grid, kCThreads, 0, s>>>(p);
         else lincal_kernel<float><<<grid, kCThreads, 0, s>>>(p);
     } else if (o.solver == GC_LINCAL_CG) {
-        lincal_cg_kernel<<<grid, kCgThreads, cg_smem, s>>>(p, 1e-4, 500, (int)(cg_smem / sizeof(float)));
+        if (cg_smem) lincal_cg_kernel<false><<<grid, kCgThreads, cg_smem, s>>>(p, 1e-4, 500, (int)(cg_smem / sizeof(float)));
+        else lincal_cg_kernel<true><<<grid, kCgThreads, 0, s>>>(p, 1e-4, 500, 0);
     } else {
         omnical_kernel<<<grid, kCThreads, 0, s>>>(p);
     }
