@@ -351,6 +351,9 @@ def gain_variance_prediction(L, types, pi, pj, alpha):
     """
     N = L * L
     A, B = logcal_matrices(L, types, pi, pj, alpha)
-    ca = np.linalg.pinv(A.T @ A)
-    cb = np.linalg.pinv(B.T @ B)
+    # the exact degeneracies (Sec. 5.2) are singular values at rounding level;
+    # a relative cut-off of 1e-9 leaves them out (the smallest physical
+    # singular values of these normal matrices are ~1e-4 of the largest)
+    ca = np.linalg.pinv(A.T @ A, rcond=1e-9, hermitian=True)
+    cb = np.linalg.pinv(B.T @ B, rcond=1e-9, hermitian=True)
     return np.diag(ca)[:N], np.diag(cb)[:N]
