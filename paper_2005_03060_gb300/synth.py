@@ -117,7 +117,7 @@ def complex_to_interleaved(z: torch.Tensor) -> torch.Tensor:
 
 
 def make_visibilities(seed: int, L: int, C: int, pair_i, pair_j, pair_type, n_ubl: int, t_pair,
-                      snr: float = 10.0, amp_sigma: float = 0.05, device="cpu"):
+                      snr: float = 10.0, amp_sigma: float = 0.05, device="cpu", unit_amp: bool = False):
     """Visibility-level draw in the manner of the paper's own simulations
     (Sec. 3): true visibilities of random amplitude, uncorrelated between
     baseline-types and constant in time; gains with ~5 % amplitude scatter and
@@ -125,7 +125,9 @@ def make_visibilities(seed: int, L: int, C: int, pair_i, pair_j, pair_type, n_ub
     reduced by sqrt(t_p) for a pair integrated over t_p samples.
 
     Returns (sums [C, P] complex64 = t_p * V_p, gains [C, N], vtrue [C, n_ubl])
-    so that the sums stand where the X-engine output would.
+    so that the sums stand where the X-engine output would.  unit_amp: every
+    baseline-type has |V| = 1 (the same SNR for all types, the setting of the
+    paper's gain-variance curves); otherwise |V| ~ U(0.5, 1.5).
     """
     N = L * L
     pi = torch.as_tensor(pair_i, dtype=torch.long, device=device)
@@ -139,6 +141,8 @@ def make_visibilities(seed: int, L: int, C: int, pair_i, pair_j, pair_type, n_ub
     for c in range(C):
         g = _gen(device, seed, c, 4)
         amp = 0.5 + torch.rand(n_ubl, generator=g, device=device, dtype=torch.float64)
+        if unit_amp:
+            amp = torch.ones_like(amp)
         ph = (torch.rand(n_ubl, generator=g, device=device, dtype=torch.float64) * 2 - 1) * math.pi
         V = torch.polar(amp, ph)
         gc = gains[c].to(torch.complex128)
