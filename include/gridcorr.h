@@ -316,6 +316,22 @@ GC_API gc_status gc_chi2_backward(gc_ctx *ctx, const void *vreduced, int vfmt, c
                                   float *grad_vmodel, void *stream);
 
 /*
+ * Checkpointed form of the pair above: gc_chi2_ckpt also stores the
+ * residuals r_p = V_p - g_i conj(g_j) V_alpha (unweighted, c64 [C][P],
+ * device, 8-byte aligned), and gc_chi2_backward_ckpt computes the same
+ * gradients from them instead of re-evaluating the model (V^reduced is not
+ * read).  The residuals cost 8 * P * C bytes, e.g. 0.92 GB for 512 channels
+ * of the 128x128 subset selection.  GC_EINVAL for null outputs.
+ */
+GC_API gc_status gc_chi2_ckpt(gc_ctx *ctx, const void *vreduced, int vfmt, const gc_sel *sel, int C,
+                              const float *gains, const float *vmodel, const float *weights, double *chi2,
+                              float *residuals, void *stream);
+GC_API gc_status gc_chi2_backward_ckpt(gc_ctx *ctx, const float *residuals, const gc_sel *sel, int C,
+                                       const float *gains, const float *vmodel, const float *weights,
+                                       const double *grad_out, float *grad_gains, float *grad_vmodel,
+                                       void *stream);
+
+/*
  * One integration of HOST-resident voltages through the whole cycle of the
  * paper's Fig. 1: FFT-correlator (gc_correlate), reduced X-engine
  * (gc_reduce) and calibration (gc_calibrate), streamed in chunks of

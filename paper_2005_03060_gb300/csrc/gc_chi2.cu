@@ -8,7 +8,9 @@
 //   dchi2/dg_k     = -2 [ sum_{p: i_p = k} w r g_j conj(V) + sum_{p: j_p = k} w conj(r) g_i V ]
 //   dchi2/dV_alpha = -2 sum_{p in alpha} w r conj(g_i) g_j
 // The backward pass recomputes the residuals from (g, V) -- nothing but the
-// inputs is kept between forward and backward.  FP32 products, FP64 sums.
+// inputs is kept between forward and backward -- or, in the checkpointed
+// form, reads the residuals the forward pass stored.  FP32 products, FP64
+// sums.
 #include <algorithm>
 
 #include "gc_sel.h"
@@ -26,6 +28,8 @@ struct Chi2Params {
     double *chi2;            // [C]
     const double *gout;      // [C] dL/dchi2 (backward)
     float2 *dg, *dV;         // [C][N], [C][n_ubl]
+    float2 *resid_out;       // [C][P] residuals stored by the forward pass, or null
+    const float2 *resid_in;  // [C][P] residuals the backward pass reads, or null (recompute)
 };
 
 __device__ __forceinline__ float2 obs(const Chi2Params &p, int c, int q) {
@@ -48,6 +52,12 @@ __device__ __forceinline__ float2 resid(const Chi2Params &p, int c, int q, int i
     return make_float2(o.x - (ex * V.x - ey * V.y), o.y - (ex * V.y + ey * V.x));
 }
 
+// residual for the backward pass: stored, or recomputed from (g, V)
+__device__ __forceinline__ float2 resid_b(const Chi2Params &p, int c, int q, int i, int j, int k) {
+    if (p.resid_in) return p.resid_in[(size_t)c * p.P + q];
+    return resid(p, c, q, i, j, k);
+}
+
 __device__ __forceinline__ int pidx(const Chi2Params &p, int k, int xj, int yj) {
     const int dx = p.types[2 * k], dy = p.types[2 * k + 1], L = p.L;
     const int xi = xj + dx, yi = yj + dy;
@@ -61,6 +71,7 @@ __global__ void __launch_bounds__(kKThreads) chi2_fwd(const Chi2Params p) {
         double s = 0.0;
         for (int q = threadIdx.x; q < p.P; q += blockDim.x) {
             const float2 r = resid(p, c, q, p.pair_i[q], p.pair_j[q], p.pair_type[q]);
+            if (p.resid_out) p.resid_out[(size_t)c * p.P + q] = r;
             const float wq = p.w ? p.w[(size_t)c * p.P + q] : 1.0f;
             s += (double)wq * ((double)r.x * r.x + (double)r.y * r.y);
         }
@@ -90,7 +101,7 @@ __global__ void __launch_bounds__(kKThreads) chi2_bwd(const Chi2Params p) {
                 int q = pidx(p, k, xi - dx, yi - dy);
                 if (q >= 0) {   // i = i_p: w r g_j conj(V)
                     const int j = (yi - dy) * L + (xi - dx);
-                    const float2 r = resid(p, c, q, i, j, k);
+                    const float2 r = resid_b(p, c, q, i, j, k);
                     const float2 gj = p.g[(size_t)c * p.N + j];
                     const float wq = p.w ? p.w[(size_t)c * p.P + q] : 1.0f;
                     const float tx = gj.x * V.x + gj.y * V.y, ty = gj.y * V.x - gj.x * V.y;   // g_j conj(V)
@@ -100,7 +111,7 @@ __global__ void __launch_bounds__(kKThreads) chi2_bwd(const Chi2Params p) {
                 q = pidx(p, k, xi, yi);
                 if (q >= 0) {   // i = j_p: w conj(r) g_i' V
                     const int ip = (yi + dy) * L + (xi + dx);
-                    const float2 r = resid(p, c, q, ip, i, k);
+                    const float2 r = resid_b(p, c, q, ip, i, k);
                     const float2 gp = p.g[(size_t)c * p.N + ip];
                     const float wq = p.w ? p.w[(size_t)c * p.P + q] : 1.0f;
                     const float tx = gp.x * V.x - gp.y * V.y, ty = gp.x * V.y + gp.y * V.x;   // g_i' V
@@ -116,7 +127,7 @@ __global__ void __launch_bounds__(kKThreads) chi2_bwd(const Chi2Params p) {
             double sx = 0.0, sy = 0.0;
             for (int q = p.type_ptr[k] + lane; q < p.type_ptr[k + 1]; q += 32) {
                 const int i = p.pair_i[q], j = p.pair_j[q];
-                const float2 r = resid(p, c, q, i, j, k);
+                const float2 r = resid_b(p, c, q, i, j, k);
                 const float2 gi = p.g[(size_t)c * p.N + i], gj = p.g[(size_t)c * p.N + j];
                 const float tx = gi.x * gj.x + gi.y * gj.y, ty = gi.x * gj.y - gi.y * gj.x;   // conj(g_i) g_j
                 const float wq = p.w ? p.w[(size_t)c * p.P + q] : 1.0f;
@@ -165,6 +176,8 @@ gc_status chi2_setup(gc_ctx *ctx, const void *vred, int vfmt, const gc_sel *csel
     p.chi2 = nullptr;
     p.gout = nullptr;
     p.dg = p.dV = nullptr;
+    p.resid_out = nullptr;
+    p.resid_in = nullptr;
     return GC_OK;
 }
 
@@ -199,6 +212,50 @@ extern "C" gc_status gc_chi2_backward(gc_ctx *ctx, const void *vreduced, int vfm
     p.gout = grad_out;
     p.dg = reinterpret_cast<float2 *>(grad_gains);
     p.dV = reinterpret_cast<float2 *>(grad_vmodel);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int grid = std::min(C, ctx->sm_count * 8);
+    int rec = gc_prof_begin(ctx, s, "chi2_bwd");
+    chi2_bwd<<<grid, kKThreads, 0, s>>>(p);
+    gc_prof_end(ctx, s, rec);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch chi2_bwd");
+    return GC_OK;
+}
+
+extern "C" gc_status gc_chi2_ckpt(gc_ctx *ctx, const void *vreduced, int vfmt, const gc_sel *sel, int C,
+                                  const float *gains, const float *vmodel, const float *weights, double *chi2,
+                                  float *residuals, void *stream) {
+    Chi2Params p;
+    gc_status st = chi2_setup(ctx, vreduced, vfmt, sel, C, gains, vmodel, weights, p);
+    if (st != GC_OK) return st;
+    if (!chi2 || !residuals || !gc_aligned(residuals, 8))
+        return gc_fail(ctx, GC_EINVAL, "gc_chi2_ckpt: null or misaligned output");
+    p.chi2 = chi2;
+    p.resid_out = reinterpret_cast<float2 *>(residuals);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int grid = std::min(C, ctx->sm_count * 8);
+    int rec = gc_prof_begin(ctx, s, "chi2_fwd");
+    chi2_fwd<<<grid, kKThreads, 0, s>>>(p);
+    gc_prof_end(ctx, s, rec);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch chi2_fwd");
+    return GC_OK;
+}
+
+extern "C" gc_status gc_chi2_backward_ckpt(gc_ctx *ctx, const float *residuals, const gc_sel *sel, int C,
+                                           const float *gains, const float *vmodel, const float *weights,
+                                           const double *grad_out, float *grad_gains, float *grad_vmodel,
+                                           void *stream) {
+    Chi2Params p;
+    // the stored residuals stand in for V^reduced, which the backward pass no longer reads
+    gc_status st = chi2_setup(ctx, residuals, GC_C64, sel, C, gains, vmodel, weights, p);
+    if (st != GC_OK) return st;
+    if (!grad_gains || !grad_vmodel || !gc_aligned(residuals, 8))
+        return gc_fail(ctx, GC_EINVAL, "gc_chi2_backward_ckpt: null output or misaligned residuals");
+    p.gout = grad_out;
+    p.dg = reinterpret_cast<float2 *>(grad_gains);
+    p.dV = reinterpret_cast<float2 *>(grad_vmodel);
+    p.resid_in = reinterpret_cast<const float2 *>(residuals);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int grid = std::min(C, ctx->sm_count * 8);
     int rec = gc_prof_begin(ctx, s, "chi2_bwd");

@@ -82,6 +82,10 @@ _lib.gc_get_tuning.argtypes = [_vp, ctypes.c_char_p, ctypes.POINTER(_i)]
 _lib.gc_get_tuning.restype = _i
 _lib.gc_quantize.argtypes = [_vp, _vp, _i, _i, _i, _vp, _vp, _vp]
 _lib.gc_quantize.restype = _i
+_lib.gc_chi2_ckpt.argtypes = [_vp, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.gc_chi2_ckpt.restype = _i
+_lib.gc_chi2_backward_ckpt.argtypes = [_vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.gc_chi2_backward_ckpt.restype = _i
 _lib.gc_integrate_host.argtypes = [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp]
 _lib.gc_integrate_host.restype = _i
 
@@ -299,16 +303,39 @@ class Context:
         return v.value
 
     # ------------------------------------------------------------------ chi^2 and adjoint
-    def chi2(self, vred, sel, gains, vmodel, weights=None, out=None):
-        """chi^2 per channel (float64 [C])."""
+    def chi2(self, vred, sel, gains, vmodel, weights=None, out=None, residuals=None):
+        """chi^2 per channel (float64 [C]).  residuals: a complex64 [C, P]
+        tensor that receives r_p (the checkpointed form, gc_chi2_ckpt)."""
         vfmt = GC_C64 if vred.dtype == torch.complex64 else GC_I4C
         C = vred.shape[0]
         out = out if out is not None else torch.empty(C, dtype=torch.float64, device=vred.device)
-        self.check(_lib.gc_chi2(self._h, _vp(vred.data_ptr()), vfmt, sel.handle, C,
-                                _vp(gains.data_ptr()), _vp(vmodel.data_ptr()),
-                                _vp(weights.data_ptr() if weights is not None else None),
-                                _vp(out.data_ptr()), _vp(_stream_ptr(vred.device))))
+        w = _vp(weights.data_ptr() if weights is not None else None)
+        if residuals is None:
+            self.check(_lib.gc_chi2(self._h, _vp(vred.data_ptr()), vfmt, sel.handle, C,
+                                    _vp(gains.data_ptr()), _vp(vmodel.data_ptr()), w,
+                                    _vp(out.data_ptr()), _vp(_stream_ptr(vred.device))))
+        else:
+            if residuals.dtype != torch.complex64 or tuple(residuals.shape) != (C, sel.P):
+                raise ValueError("residuals must be complex64 [C, P]")
+            self.check(_lib.gc_chi2_ckpt(self._h, _vp(vred.data_ptr()), vfmt, sel.handle, C,
+                                         _vp(gains.data_ptr()), _vp(vmodel.data_ptr()), w,
+                                         _vp(out.data_ptr()), _vp(residuals.data_ptr()),
+                                         _vp(_stream_ptr(vred.device))))
         return out
+
+    def chi2_backward_ckpt(self, residuals, sel, gains, vmodel, grad_out=None, weights=None):
+        """Gradients from residuals stored by chi2(..., residuals=)."""
+        C = residuals.shape[0]
+        dg = torch.empty_like(gains)
+        dv = torch.empty_like(vmodel)
+        go = grad_out.contiguous().to(torch.float64) if grad_out is not None else None
+        self.check(_lib.gc_chi2_backward_ckpt(self._h, _vp(residuals.data_ptr()), sel.handle, C,
+                                              _vp(gains.data_ptr()), _vp(vmodel.data_ptr()),
+                                              _vp(weights.data_ptr() if weights is not None else None),
+                                              _vp(go.data_ptr() if go is not None else None),
+                                              _vp(dg.data_ptr()), _vp(dv.data_ptr()),
+                                              _vp(_stream_ptr(residuals.device))))
+        return dg, dv
 
     def chi2_backward(self, vred, sel, gains, vmodel, grad_out=None, weights=None):
         vfmt = GC_C64 if vred.dtype == torch.complex64 else GC_I4C
@@ -408,27 +435,39 @@ class Selection:
 class Chi2Function(torch.autograd.Function):
     """chi^2 per channel as a differentiable function of the complex gains
     [C, N] and model visibilities [C, n_ubl] (complex64), with the gradient
-    from the library's adjoint kernel.  Only (gains, vmodel) are saved: the
-    backward pass recomputes the residuals (checkpointing)."""
+    from the library's adjoint kernel.  checkpoint=False saves only (gains,
+    vmodel) and the backward pass recomputes the residuals; checkpoint=True
+    saves the per-channel residuals (8 P bytes per channel) and the backward
+    pass reads them."""
 
     @staticmethod
-    def forward(fctx, gains, vmodel, vred, sel, ctx, weights=None):
+    def forward(fctx, gains, vmodel, vred, sel, ctx, weights=None, checkpoint=False):
         g = gains.detach().contiguous()
         v = vmodel.detach().contiguous()
-        fctx.save_for_backward(g, v)
         fctx.vred, fctx.sel, fctx.gctx, fctx.weights = vred, sel, ctx, weights
+        fctx.checkpoint = checkpoint
+        if checkpoint:
+            r = torch.empty(vred.shape[0], sel.P, dtype=torch.complex64, device=vred.device)
+            out = ctx.chi2(vred, sel, g, v, weights, residuals=r)
+            fctx.save_for_backward(g, v, r)
+            return out
+        fctx.save_for_backward(g, v)
         return ctx.chi2(vred, sel, g, v, weights)
 
     @staticmethod
     def backward(fctx, grad_out):
-        g, v = fctx.saved_tensors
-        dg, dv = fctx.gctx.chi2_backward(fctx.vred, fctx.sel, g, v, grad_out, fctx.weights)
-        return dg, dv, None, None, None, None
+        if fctx.checkpoint:
+            g, v, r = fctx.saved_tensors
+            dg, dv = fctx.gctx.chi2_backward_ckpt(r, fctx.sel, g, v, grad_out, fctx.weights)
+        else:
+            g, v = fctx.saved_tensors
+            dg, dv = fctx.gctx.chi2_backward(fctx.vred, fctx.sel, g, v, grad_out, fctx.weights)
+        return dg, dv, None, None, None, None, None
 
 
-def chi2(gains, vmodel, vred, sel, ctx=None, weights=None):
+def chi2(gains, vmodel, vred, sel, ctx=None, weights=None, checkpoint=False):
     ctx = ctx or default_context(gains.device)
-    return Chi2Function.apply(gains, vmodel, vred, sel, ctx, weights)
+    return Chi2Function.apply(gains, vmodel, vred, sel, ctx, weights, checkpoint)
 
 
 def decode_stats(stats: torch.Tensor):
