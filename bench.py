@@ -429,10 +429,13 @@ def calibration_variants(w: Workload, Cs: int, reps_fast: int):
     ctx, sel = w.ctx, w.sel
     vr, au = w.vr[:Cs].contiguous(), w.au[:Cs].contiguous()
     out, g64 = {}, None
-    for name, solver, prec, allc in [("lincal_fp64", "lincal", "fp64", False),
-                                     ("lincal_fp32", "lincal", "fp32", False),
-                                     ("omnical_fp32", "omnical", "fp32", False),
-                                     ("lincal_cg_mixed", "lincal_cg", "fp32", True)]:
+    # op: the matrix-free operator ("cal.operator": 0 gather over the grid, 1 pair-list scatter)
+    for name, solver, prec, allc, op in [("lincal_fp64", "lincal", "fp64", False, 0),
+                                         ("lincal_fp32", "lincal", "fp32", False, 0),
+                                         ("omnical_fp32", "omnical", "fp32", False, 0),
+                                         ("lincal_cg_mixed", "lincal_cg", "fp32", True, 0),
+                                         ("lincal_cg_mixed_pair_scatter", "lincal_cg", "fp32", True, 1)]:
+        ctx.set_tuning("cal.operator", op)
         v_in, a_in = (w.vr, w.au) if allc else (vr, au)
         Cn = w.C if allc else Cs
         reps = reps_fast if allc else 1
@@ -454,6 +457,7 @@ def calibration_variants(w: Workload, Cs: int, reps_fast: int):
                      "max_rel_gain_diff_vs_lincal_fp64": diff,
                      "mean_iters": float(np.mean(sv["iters"])), "mean_cg_iters": float(np.mean(sv["inner"])),
                      "converged": int(np.sum(sv["status"] == 0))}
+    ctx.set_tuning("cal.operator", 0)
     return out
 
 

@@ -288,6 +288,9 @@ GC_API gc_status gc_calibrate_batched(gc_ctx *ctx, int n_arrays, const gc_batch_
  *   "xeng.tsplit"      time slices per X-engine window
  *   "cal.ctas_per_sm"  resident calibration CTAs per SM (cap)
  *   "cal.order"        batched work order: 0 largest first, 1 as given
+ *   "cal.operator"     GC_LINCAL_CG operator: 0 per-antenna gather over the
+ *                      grid (selections of <= 16 baseline-types; others
+ *                      fall back to 1), 1 scatter over the pair list
  * GC_EINVAL for an unknown name or a negative value.
  */
 GC_API gc_status gc_set_tuning(gc_ctx *ctx, const char *name, int value);

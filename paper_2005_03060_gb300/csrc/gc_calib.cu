@@ -35,7 +35,9 @@
 namespace {
 
 constexpr int kCThreads = 512;
-constexpr int kCgThreads = 512;   // matrix-free kernels
+constexpr int kCgThreads = 512;   // matrix-free kernels, pair-scatter operator
+constexpr int kCgStThreads = 256; // matrix-free kernels, stencil operator (128 registers a thread)
+constexpr int kStencilTypes = 16; // baseline-types the stencil operator holds in registers
 // shared arena cap: two CTAs per SM.  Arrays whose hot vectors need more keep
 // them in global memory (L2) at two CTAs per SM -- measured faster than one
 // CTA per SM with a larger arena (the solver is latency-bound).
@@ -50,6 +52,7 @@ struct CalParams {
     const int32_t *types, *type_ptr, *pair_i, *pair_j, *pair_type, *win_t0, *win_t1;
     const int32_t *nbr;          // [2][n_ubl][N] neighbour table or null
     int ax, ay;                  // indices of types (1,0) and (0,1)
+    int stencil;                 // matrix-free operator by per-antenna gather (<= kStencilTypes types)
     int t_autos;                 // samples summed in autos
     float2 *gains;               // [C][N] (in: warm start when warm != 0)
     float2 *vmodel;              // [C][n_ubl]
@@ -819,6 +822,8 @@ struct CgWork {
     // two-level preconditioner: patch-aggregation coarse space (see cg_coarse_setup)
     float *Ca, *Cp;          // coarse amplitude / phase operators, then their inverses (nc x nc)
     float *rc, *yc;          // coarse residual / solution (2 nc; shared memory)
+    float *cscr;             // shared-memory scratch for one nc x nc system (or null)
+    int coarse_gather;       // every type offset within one patch side: gather assembly
     int n, m;
     int B, npx, ncp, nc, cv; // patch side, patches per row, patches, coarse size, V in coarse space
 };
@@ -843,9 +848,16 @@ __host__ __device__ inline size_t cg_hot_floats(int N, int n_ubl, bool with_dg) 
     return 6 * (size_t)N + 7 * (size_t)n_ubl + (with_dg ? (size_t)N : 0) + 64;
 }
 
+// Vectors the stencil operator gathers (xg 2N, xv 2 n_ubl, pp n + m); its
+// outputs (acc, dg, dv) are written once by their owning thread.
+__host__ __device__ inline size_t cg_sten_floats(int N, int n_ubl) {
+    return 4 * (size_t)N + 4 * (size_t)n_ubl + 64;
+}
+
 // hot_mode 2: hot vectors and dg in shared memory; 1: hot vectors in shared
-// memory, dg in global; 0: everything in global (L2-resident) memory.
-__device__ CgWork cg_layout(const CalParams &p, char *base, float *smem_arena, int hot_mode,
+// memory, dg in global; 0: everything in global (L2-resident) memory;
+// 3 (stencil operator): xg, xv and pp in shared memory, the rest in global.
+__device__ CgWork cg_layout(const CalParams &p, char *base, float *smem_arena, int smem_floats, int hot_mode,
                             bool use_coarse_smem) {
     CgWork w;
     w.n = 2 * p.N;
@@ -858,8 +870,9 @@ __device__ CgWork cg_layout(const CalParams &p, char *base, float *smem_arena, i
         return r;
     };
     float *ghot = takeg(cg_hot_floats(p.N, p.n_ubl, true));
-    float *h = hot_mode ? smem_arena : ghot;
-    float *hot_end = h + cg_hot_floats(p.N, p.n_ubl, hot_mode != 1);
+    float *h = hot_mode == 1 || hot_mode == 2 ? smem_arena : ghot;
+    float *hot_end = hot_mode == 3 ? smem_arena + cg_sten_floats(p.N, p.n_ubl)
+                                   : h + cg_hot_floats(p.N, p.n_ubl, hot_mode != 1);
     w.xg = h;
     h += 2 * p.N;
     w.xv = h;
@@ -871,6 +884,11 @@ __device__ CgWork cg_layout(const CalParams &p, char *base, float *smem_arena, i
     w.dv = h;
     h += p.n_ubl;
     w.dg = hot_mode == 1 ? ghot : h;
+    if (hot_mode == 3) {   // the gathered vectors move to shared memory
+        w.xg = smem_arena;
+        w.xv = w.xg + 2 * p.N;
+        w.pp = w.xv + 2 * p.n_ubl;
+    }
     w.b = takeg(nm);
     w.x = takeg(nm);
     w.r = takeg(nm);
@@ -884,6 +902,14 @@ __device__ CgWork cg_layout(const CalParams &p, char *base, float *smem_arena, i
     } else {
         w.Ca = takeg((size_t)w.nc * w.nc);
         w.Cp = takeg((size_t)w.nc * w.nc);
+    }
+    w.coarse_gather = 1;
+    for (int k = 0; k < p.n_ubl; ++k)
+        if (abs(p.types[2 * k]) > w.B || abs(p.types[2 * k + 1]) > w.B) w.coarse_gather = 0;
+    w.cscr = nullptr;
+    if (!use_coarse_smem && smem_floats > 0) {   // room for one system beside the hot vectors?
+        float *sc = hot_mode == 0 ? smem_arena : hot_end;
+        if (sc + (size_t)w.nc * w.nc <= smem_arena + smem_floats) w.cscr = sc;
     }
     return w;
 }
@@ -910,17 +936,28 @@ size_t cg_bytes(int N, int n_ubl, int /*P*/) {
 // kernel but not chosen: on the 4096-antenna array it measured slower than
 // the all-global layout, whose fire-and-forget L2 reductions do not stall
 // the issuing warps the way contended shared-memory atomics do.
-size_t cg_arena_bytes(int N, int n_ubl, int L, size_t cap) {
-    const size_t h2 = cg_hot_floats(N, n_ubl, true) * sizeof(float);
+// With the stencil operator the arena holds only the gathered vectors (and
+// the coarse operators when they fit beside them).
+size_t cg_arena_bytes(int N, int n_ubl, int L, size_t cap, bool stencil) {
+    const size_t h2 = (stencil ? cg_sten_floats(N, n_ubl) : cg_hot_floats(N, n_ubl, true)) * sizeof(float);
     const size_t cf = cg_coarse_floats(L, n_ubl) * sizeof(float);
+    const size_t c1 = cf / 2;   // one system: the inversion's shared-memory scratch
     if (h2 + cf <= cap) return h2 + cf;
-    return h2 <= cap ? h2 : 0;
+    if (h2 + c1 <= cap) return h2 + c1;
+    if (h2 <= cap) return h2;
+    return c1 <= cap ? c1 : 0;
 }
 
 // the kernel side of the same choice, from the arena size it was given
 __device__ __forceinline__ void cg_modes(const CalParams &p, int smem_floats, int &hot_mode, bool &coarse_smem) {
-    const size_t h2 = cg_hot_floats(p.N, p.n_ubl, true), h1 = cg_hot_floats(p.N, p.n_ubl, false);
     const size_t cf = cg_coarse_floats(p.L, p.n_ubl), sf = (size_t)smem_floats;
+    if (p.stencil) {
+        const size_t hs = cg_sten_floats(p.N, p.n_ubl);
+        hot_mode = hs <= sf ? 3 : 0;
+        coarse_smem = hot_mode != 0 && hs + cf <= sf;
+        return;
+    }
+    const size_t h2 = cg_hot_floats(p.N, p.n_ubl, true), h1 = cg_hot_floats(p.N, p.n_ubl, false);
     hot_mode = h2 <= sf ? 2 : (h1 <= sf ? 1 : 0);
     coarse_smem = hot_mode != 0 && (hot_mode == 2 ? h2 : h1) + cf <= sf;
 }
@@ -1073,6 +1110,144 @@ __device__ double cg_pass(const CalParams &p, int c, const CgWork &w, bool resid
     return s[0];
 }
 
+// The same operator as cg_pass, as a gather over the grid.  Every selection
+// here takes baseline-types whole, so antenna m meets each type d_k at most
+// twice: as the first member of the pair (m, m - d_k) and as the second
+// member of (m + d_k, m), both found by arithmetic on the grid (pair_index
+// order).  The thread owning m evaluates both pairs and sums its own row of
+// J^T u in registers: every pair is evaluated twice (once by each antenna)
+// and nothing is scattered, so there are no atomics and the result does not
+// depend on the schedule.  The model-visibility rows, conj(e) u (and |e|^2),
+// are summed per type over the first-member evaluations in registers and
+// reduced across the CTA once per pass.  Neighbour gathers of consecutive
+// threads hit consecutive addresses (shared memory when the arena holds xg,
+// xv and pp).  Same outputs and return value as cg_pass.
+__device__ double cg_pass_stencil(const CalParams &p, int c, const CgWork &w, bool resid, double *red) {
+    constexpr int KT = kStencilTypes;
+    __shared__ float s_tsum[(kCgStThreads / 32) * 3 * KT];
+    const int L = p.L, nu = p.n_ubl;
+    float tvx[KT], tvy[KT], tvd[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) tvx[k] = tvy[k] = tvd[k] = 0.f;
+    float chi = 0.f;
+    const float2 *xg = reinterpret_cast<const float2 *>(w.xg);
+    const float2 *pg = reinterpret_cast<const float2 *>(w.pp);
+    const float2 *vobs2 = reinterpret_cast<const float2 *>(p.vred) + (size_t)c * p.P;
+    const int2 *vobsi = reinterpret_cast<const int2 *>(p.vred) + (size_t)c * p.P;
+    for (int m = threadIdx.x; m < p.N; m += blockDim.x) {
+        const int x = m % L, y = m / L;
+        const float2 gm = xg[m];
+        const float2 pm = resid ? make_float2(0.f, 0.f) : pg[m];
+        float sx = 0.f, sy = 0.f, dgm = 0.f;
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            if (k >= nu) break;
+            const int dx = __ldg(p.types + 2 * k), dy = __ldg(p.types + 2 * k + 1);
+            const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
+            float pvx = 0.f, pvy = 0.f, inv = 0.f;
+            int qb = 0;
+            if (resid) {
+                inv = 1.0f / (float)(__ldg(p.win_t1 + k) - __ldg(p.win_t0 + k));
+                qb = __ldg(p.type_ptr + k);
+            } else {
+                pvx = w.pp[2 * p.N + 2 * k];
+                pvy = w.pp[2 * p.N + 2 * k + 1];
+            }
+            const int W = L - abs(dx), xlo = max(0, -dx), ylo = max(0, -dy);
+            const int off = dy * L + dx;
+            auto vo = [&](int q) {
+                if (p.vfmt == GC_C64) {
+                    const float2 v = vobs2[q];
+                    return make_float2(v.x * inv, v.y * inv);
+                }
+                const int2 v = vobsi[q];
+                return make_float2((float)v.x * inv, (float)v.y * inv);
+            };
+            // m first: pair (m, j = m - d_k)
+            {
+                const int xj = x - dx, yj = y - dy;
+                if (xj >= 0 && xj < L && yj >= 0 && yj < L) {
+                    const float2 gj = xg[m - off];
+                    const float ex = gm.x * gj.x + gm.y * gj.y, ey = gm.y * gj.x - gm.x * gj.y;   // g_m conj(g_j)
+                    const float ax = gj.x * Vx + gj.y * Vy, ay = gj.x * Vy - gj.y * Vx;         // conj(g_j) V
+                    float ux, uy;
+                    if (resid) {
+                        const float2 o = vo(qb + (yj - ylo) * W + (xj - xlo));
+                        ux = o.x - (ex * Vx - ey * Vy);
+                        uy = o.y - (ex * Vy + ey * Vx);
+                        chi = fmaf(ux, ux, fmaf(uy, uy, chi));
+                        dgm += ax * ax + ay * ay;
+                        tvd[k] += ex * ex + ey * ey;
+                    } else {
+                        const float bx = gm.x * Vx - gm.y * Vy, by = gm.x * Vy + gm.y * Vx;     // g_m V
+                        const float2 pj = pg[m - off];
+                        ux = ax * pm.x - ay * pm.y + bx * pj.x + by * pj.y + ex * pvx - ey * pvy;
+                        uy = ax * pm.y + ay * pm.x - bx * pj.y + by * pj.x + ex * pvy + ey * pvx;
+                    }
+                    sx += ax * ux + ay * uy;          // conj(a) u
+                    sy += ax * uy - ay * ux;
+                    tvx[k] += ex * ux + ey * uy;      // conj(e) u
+                    tvy[k] += ex * uy - ey * ux;
+                }
+            }
+            // m second: pair (i = m + d_k, m)
+            {
+                const int xi = x + dx, yi = y + dy;
+                if (xi >= 0 && xi < L && yi >= 0 && yi < L) {
+                    const float2 gi = xg[m + off];
+                    const float ex = gi.x * gm.x + gi.y * gm.y, ey = gi.y * gm.x - gi.x * gm.y;   // g_i conj(g_m)
+                    const float bx = gi.x * Vx - gi.y * Vy, by = gi.x * Vy + gi.y * Vx;         // g_i V
+                    float ux, uy;
+                    if (resid) {
+                        const float2 o = vo(qb + (y - ylo) * W + (x - xlo));
+                        ux = o.x - (ex * Vx - ey * Vy);
+                        uy = o.y - (ex * Vy + ey * Vx);
+                        dgm += bx * bx + by * by;
+                    } else {
+                        const float ax = gm.x * Vx + gm.y * Vy, ay = gm.x * Vy - gm.y * Vx;     // conj(g_m) V
+                        const float2 pi_ = pg[m + off];
+                        ux = ax * pi_.x - ay * pi_.y + bx * pm.x + by * pm.y + ex * pvx - ey * pvy;
+                        uy = ax * pi_.y + ay * pi_.x - bx * pm.y + by * pm.x + ex * pvy + ey * pvx;
+                    }
+                    sx += bx * ux + by * uy;          // b conj(u)
+                    sy += by * ux - bx * uy;
+                }
+            }
+        }
+        w.acc[2 * m] = sx;
+        w.acc[2 * m + 1] = sy;
+        if (resid) w.dg[m] = dgm;
+    }
+    // per-type sums: warp trees, then a fixed-order sum over the warps
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        if (k >= nu) break;
+        for (int o = 16; o > 0; o >>= 1) {
+            tvx[k] += __shfl_xor_sync(0xffffffffu, tvx[k], o);
+            tvy[k] += __shfl_xor_sync(0xffffffffu, tvy[k], o);
+            if (resid) tvd[k] += __shfl_xor_sync(0xffffffffu, tvd[k], o);
+        }
+        if (lane == 0) {
+            s_tsum[(wp * 3 + 0) * KT + k] = tvx[k];
+            s_tsum[(wp * 3 + 1) * KT + k] = tvy[k];
+            s_tsum[(wp * 3 + 2) * KT + k] = tvd[k];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * nu; t += blockDim.x) {
+        const int comp = t / nu, k = t - comp * nu;
+        float a = 0.f;
+        for (int u = 0; u < nw; ++u) a += s_tsum[(u * 3 + comp) * KT + k];
+        if (comp < 2) w.acc[2 * p.N + 2 * k + comp] = a;
+        else if (resid) w.dv[k] = a;
+    }
+    double s[1] = {(double)chi};
+    if (resid) block_sum<double, 1>(s, red);
+    else __syncthreads();
+    return s[0];
+}
+
 // Two-level preconditioner.  The coarse space scales each patch of B x B
 // antennas by one complex factor and (when there are few types) each model
 // visibility by another: dg_i = g_i c_P(i), dV_k = V_k c_k.  For a pair, J
@@ -1109,7 +1284,9 @@ __device__ __forceinline__ void fast_sum(float (&v)[NV], float *buf, int &parity
     parity ^= 1;
 }
 
-__device__ void cg_coarse_setup(const CalParams &p, const CgWork &w, float mu) {
+// Scatter assembly over the pair list (shared or global atomics), for any
+// selection; the upper triangle is accumulated and mirrored.
+__device__ void coarse_assemble_scatter(const CalParams &p, const CgWork &w, float mu) {
     const int nc = w.nc, L = p.L;
     for (int t = threadIdx.x; t < nc * nc; t += blockDim.x) {
         w.Ca[t] = 0.f;
@@ -1172,61 +1349,224 @@ __device__ void cg_coarse_setup(const CalParams &p, const CgWork &w, float mu) {
         }
     }
     __syncthreads();
-    // one warp per system: diagonal floor, Gauss-Jordan inversion in place
-    // (SPD, no pivoting), then the projection P A^-1 P that removes the exact
-    // coarse null direction n (amplitude: patches 1, types -2; phase: patches 1)
-    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (wp < 2) {
-        float *A = wp ? w.Cp : w.Ca;
-        float mx = 0.f;
-        for (int r = lane; r < nc; r += 32) mx = fmaxf(mx, A[r * nc + r]);
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        for (int r = lane; r < nc; r += 32) A[r * nc + r] += 1e-5f * mx;
-        __syncwarp();
-        for (int k = 0; k < nc; ++k) {
-            const float iv = 1.f / A[k * nc + k];
-            __syncwarp();
-            for (int e = lane; e < nc * nc; e += 32) {
-                const int r = e / nc, cc = e - r * nc;
-                if (r != k && cc != k) A[e] -= A[r * nc + k] * A[k * nc + cc] * iv;
-            }
-            __syncwarp();
-            for (int r = lane; r < nc; r += 32) {
-                if (r != k) {
-                    A[r * nc + k] *= -iv;
-                    A[k * nc + r] *= iv;
+}
+
+// Gather assembly: one warp per patch a walks the patch's antennas and, for
+// every type, the antenna's pair as first and as second member (the same
+// grid arithmetic as cg_pass_stencil), summing row a of both coarse
+// operators in registers: the patch itself, its eight neighbour patches
+// (pairs never reach further when every type offset is within one patch
+// side) and the model-visibility columns.  A pair inside the patch is met
+// twice and adds half its weight at each visit.  Rows are written whole
+// (no atomics, no mirroring); the type rows take their patch columns from
+// the same sums and a diagonal of |V_k|^2 (dv_k + mu).
+__device__ void coarse_assemble_gather(const CalParams &p, const CgWork &w, float mu) {
+    constexpr int KT = kStencilTypes;
+    const int nc = w.nc, L = p.L, B = w.B, npx = w.npx, ncp = w.ncp, nu = p.n_ubl;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const float2 *xg = reinterpret_cast<const float2 *>(w.xg);
+    for (int a = wp; a < ncp; a += nw) {
+        const int ax = a % npx, ay = a / npx;
+        float sa[9], sp[9], ta[KT], tp[KT];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) sa[q] = sp[q] = 0.f;
+#pragma unroll
+        for (int k = 0; k < KT; ++k) ta[k] = tp[k] = 0.f;
+        const int x0 = ax * B, y0 = ay * B;
+        const int bw = min(B, L - x0), bh = min(B, L - y0);
+        for (int t = lane; t < bw * bh; t += 32) {
+            const int x = x0 + t % bw, y = y0 + t / bw, m = y * L + x;
+            const float2 gm = xg[m];
+            const float gm2 = gm.x * gm.x + gm.y * gm.y;
+            sa[4] += mu * gm2;
+            sp[4] += mu * gm2;
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                if (k >= nu) break;
+                const int dx = __ldg(p.types + 2 * k), dy = __ldg(p.types + 2 * k + 1);
+                const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
+                const float v2 = Vx * Vx + Vy * Vy;
+#pragma unroll
+                for (int role = 0; role < 2; ++role) {
+                    const int xo = role == 0 ? x - dx : x + dx, yo = role == 0 ? y - dy : y + dy;
+                    if (xo < 0 || xo >= L || yo < 0 || yo >= L) continue;
+                    const float2 go = xg[yo * L + xo];
+                    const float wq = gm2 * (go.x * go.x + go.y * go.y) * v2;   // |m_p|^2
+                    const int px = xo / B - ax, py = yo / B - ay;              // in -1..1
+                    if (px == 0 && py == 0) {
+                        sa[4] += 2.f * wq;
+                        ta[k] += wq;
+                    } else {
+                        const int slot = (py + 1) * 3 + (px + 1);
+                        sa[4] += wq;
+                        sp[4] += wq;
+#pragma unroll
+                        for (int q = 0; q < 9; ++q)
+                            if (q == slot) {
+                                sa[q] += wq;
+                                sp[q] -= wq;
+                            }
+                        ta[k] += wq;
+                        tp[k] += role == 0 ? wq : -wq;
+                    }
                 }
             }
-            __syncwarp();
-            if (lane == 0) A[k * nc + k] = iv;
-            __syncwarp();
         }
-        const bool amp = wp == 0;
-        if (!amp || w.cv) {
-            // u = A n, c = n.A n, s = n.n
-            auto nv = [&](int t) -> float { return t < w.ncp ? 1.f : (amp ? -2.f : 0.f); };
-            float s_loc = 0.f;
-            for (int t = lane; t < nc; t += 32) s_loc += nv(t) * nv(t);
-            for (int o = 16; o > 0; o >>= 1) s_loc += __shfl_xor_sync(0xffffffffu, s_loc, o);
-            float *u = w.yc + wp * nc;    // scratch
-            float c_loc = 0.f;
-            for (int r = lane; r < nc; r += 32) {
-                float acc = 0.f;
-                for (int t = 0; t < nc; ++t) acc = fmaf(A[r * nc + t], nv(t), acc);
-                u[r] = acc;
-                c_loc += nv(r) * acc;
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            for (int o = 16; o > 0; o >>= 1) {
+                sa[q] += __shfl_xor_sync(0xffffffffu, sa[q], o);
+                sp[q] += __shfl_xor_sync(0xffffffffu, sp[q], o);
             }
-            for (int o = 16; o > 0; o >>= 1) c_loc += __shfl_xor_sync(0xffffffffu, c_loc, o);
-            __syncwarp();
-            const float is = 1.f / s_loc;
-            for (int e = lane; e < nc * nc; e += 32) {
-                const int r = e / nc, t = e - r * nc;
-                A[e] += -u[r] * nv(t) * is - nv(r) * u[t] * is + nv(r) * nv(t) * c_loc * is * is;
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            if (k >= nu) break;
+            for (int o = 16; o > 0; o >>= 1) {
+                ta[k] += __shfl_xor_sync(0xffffffffu, ta[k], o);
+                tp[k] += __shfl_xor_sync(0xffffffffu, tp[k], o);
             }
-            __syncwarp();
+        }
+        // row a (every lane holds every sum)
+        for (int cc = lane; cc < nc; cc += 32) {
+            float va = 0.f, vp = 0.f;
+            if (cc < ncp) {
+                const int px = cc % npx - ax, py = cc / npx - ay;
+                if (px >= -1 && px <= 1 && py >= -1 && py <= 1) {
+                    const int slot = (py + 1) * 3 + (px + 1);
+#pragma unroll
+                    for (int q = 0; q < 9; ++q)
+                        if (q == slot) {
+                            va = sa[q];
+                            vp = sp[q];
+                        }
+                }
+            } else {
+                const int k = cc - ncp;
+#pragma unroll
+                for (int q = 0; q < KT; ++q)
+                    if (q == k) {
+                        va = ta[q];
+                        vp = tp[q];
+                    }
+            }
+            w.Ca[a * nc + cc] = va;
+            w.Cp[a * nc + cc] = vp;
+        }
+        // column a of the type rows
+        if (w.cv)
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                if (k >= nu) break;
+                if (lane == k) {
+                    w.Ca[(ncp + k) * nc + a] = ta[k];
+                    w.Cp[(ncp + k) * nc + a] = tp[k];
+                }
+            }
+    }
+    if (w.cv)
+        for (int t = threadIdx.x; t < nu * nu; t += blockDim.x) {
+            const int k = t / nu, k2 = t - k * nu, r = ncp + k, cc = ncp + k2;
+            float d = 0.f;
+            if (k == k2) d = (w.xv[2 * k] * w.xv[2 * k] + w.xv[2 * k + 1] * w.xv[2 * k + 1]) * (w.dv[k] + mu);
+            w.Ca[r * nc + cc] = d;
+            w.Cp[r * nc + cc] = d;
+        }
+    __syncthreads();
+}
+
+// Block-wide max / sum of one float (all threads get the result).
+__device__ __forceinline__ float block_allreduce(float v, bool is_max, float *buf /* [32] */) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float t = __shfl_xor_sync(0xffffffffu, v, o);
+        v = is_max ? fmaxf(v, t) : v + t;
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) buf[wp] = v;
+    __syncthreads();
+    float r = buf[0];
+    for (int u = 1; u < nw; ++u) r = is_max ? fmaxf(r, buf[u]) : r + buf[u];
+    return r;
+}
+
+// Invert one coarse system in place with the whole CTA: diagonal floor,
+// Gauss-Jordan without pivoting (SPD), two barriers per pivot, then the
+// projection P A^-1 P that removes the exact coarse null direction n
+// (amplitude: patches 1, types -2; phase: patches 1, types 0).
+__device__ void coarse_invert(float *A, int nc, int ncp, bool amp, bool cv, float *u /* nc */, float *buf) {
+    const int tid = threadIdx.x, nt = blockDim.x, nn = nc * nc;
+    float mx = 0.f;
+    for (int r = tid; r < nc; r += nt) mx = fmaxf(mx, A[r * nc + r]);
+    mx = block_allreduce(mx, true, buf);
+    for (int r = tid; r < nc; r += nt) A[r * nc + r] += 1e-5f * mx;
+    __syncthreads();
+    const int dr = nt / nc, dc = nt - dr * nc;
+    for (int k = 0; k < nc; ++k) {
+        const float iv = 1.f / A[k * nc + k];
+        int r = tid / nc, c = tid - r * nc;
+        for (int e = tid; e < nn; e += nt) {
+            if (r != k && c != k) A[e] -= A[r * nc + k] * A[k * nc + c] * iv;
+            c += dc;
+            r += dr;
+            if (c >= nc) {
+                c -= nc;
+                ++r;
+            }
+        }
+        __syncthreads();
+        for (int q = tid; q < nc; q += nt)
+            if (q != k) {
+                A[q * nc + k] *= -iv;
+                A[k * nc + q] *= iv;
+            }
+        if (tid == 0) A[k * nc + k] = iv;
+        __syncthreads();
+    }
+    if (amp && !cv) return;
+    auto nv = [&](int t) -> float { return t < ncp ? 1.f : (amp ? -2.f : 0.f); };
+    float cl = 0.f, sl = 0.f;
+    for (int r = tid; r < nc; r += nt) {
+        float acc = 0.f;
+        for (int t = 0; t < nc; ++t) acc = fmaf(A[r * nc + t], nv(t), acc);
+        u[r] = acc;
+        cl += nv(r) * acc;
+        sl += nv(r) * nv(r);
+    }
+    const float cs = block_allreduce(cl, false, buf);
+    const float ss = block_allreduce(sl, false, buf);   // its barriers also publish u
+    const float is = 1.f / ss;
+    int r = tid / nc, c = tid - r * nc;
+    for (int e = tid; e < nn; e += nt) {
+        A[e] += -u[r] * nv(c) * is - nv(r) * u[c] * is + nv(r) * nv(c) * cs * is * is;
+        c += dc;
+        r += dr;
+        if (c >= nc) {
+            c -= nc;
+            ++r;
         }
     }
     __syncthreads();
+}
+
+// Build and invert the coarse operators (Gauss-Newton iterations 1 and 2).
+__device__ void cg_coarse_setup(const CalParams &p, const CgWork &w, float mu) {
+    __shared__ float s_buf[32];
+    if (p.stencil && w.coarse_gather) coarse_assemble_gather(p, w, mu);
+    else coarse_assemble_scatter(p, w, mu);
+    const int nn = w.nc * w.nc;
+    for (int m = 0; m < 2; ++m) {
+        float *A = m ? w.Cp : w.Ca;
+        float *W = w.cscr ? w.cscr : A;   // invert in shared memory when there is room
+        if (W != A) {
+            for (int e = threadIdx.x; e < nn; e += blockDim.x) W[e] = A[e];
+            __syncthreads();
+        }
+        coarse_invert(W, w.nc, w.ncp, m == 0, w.cv != 0, w.yc, s_buf);
+        if (W != A) {
+            for (int e = threadIdx.x; e < nn; e += blockDim.x) A[e] = W[e];
+            __syncthreads();
+        }
+    }
 }
 
 // One channel of matrix-free Gauss-Newton (used by the per-selection and the
@@ -1313,7 +1653,7 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
     double grad0 = 0.0;
     for (it = 1; it <= p.max_iter; ++it) {
         // residual, right-hand side J^T r and the Jacobi diagonals
-        const double chi2 = cg_pass<kPipe>(p, c, w, true, red);
+        const double chi2 = p.stencil ? cg_pass_stencil(p, c, w, true, red) : cg_pass<kPipe>(p, c, w, true, red);
         double dm = 0.0;
         for (int i = threadIdx.x; i < p.N; i += blockDim.x) dm = fmax(dm, (double)w.dg[i]);
         for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
@@ -1353,7 +1693,8 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
         const float eta = (float)fmin(0.1, fmax(cg_tol, sqrt(sqrt((double)bnorm2 / fmax(grad0, 1e-300)))));
         for (int k = 0; k < cg_max && bnorm2 > 0.f; ++k) {
             ++inner;
-            cg_pass<kPipe>(p, c, w, false, red);          // acc = J^T J pp (acc was zeroed)
+            if (p.stencil) cg_pass_stencil(p, c, w, false, red);   // acc = J^T J pp
+            else cg_pass<kPipe>(p, c, w, false, red);              // (acc was zeroed)
             float v1[1] = {0.f};
             for (int i = threadIdx.x; i < nm; i += blockDim.x) v1[0] = fmaf(w.pp[i], w.acc[i] + mu * w.pp[i], v1[0]);
             fast_sum<1>(v1, sbuf, par);
@@ -1427,9 +1768,10 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
     finish_channel<float>(p, c, w.xg, w.xv, min(it, p.max_iter), st, red, inner);
 }
 
-template <bool kPipe>
-__global__ void __launch_bounds__(kCgThreads, 2) lincal_cg_kernel(const CalParams p, double cg_tol, int cg_max,
-                                                              int smem_floats) {
+// kSten: the stencil operator (p.stencil set), launched with kCgStThreads
+template <bool kPipe, bool kSten>
+__global__ void __launch_bounds__(kSten ? kCgStThreads : kCgThreads, 2)
+lincal_cg_kernel(const CalParams p, double cg_tol, int cg_max, int smem_floats) {
     __shared__ double red[32 * 14];
     __shared__ float redf[32 * 14];
     __shared__ float s_rc[2 * kMaxCoarse], s_yc[2 * kMaxCoarse];
@@ -1437,7 +1779,7 @@ __global__ void __launch_bounds__(kCgThreads, 2) lincal_cg_kernel(const CalParam
     int hot_mode;
     bool coarse_smem;
     cg_modes(p, smem_floats, hot_mode, coarse_smem);
-    CgWork w = cg_layout(p, p.work + (size_t)blockIdx.x * p.work_per_cta, arena, hot_mode, coarse_smem);
+    CgWork w = cg_layout(p, p.work + (size_t)blockIdx.x * p.work_per_cta, arena, smem_floats, hot_mode, coarse_smem);
     w.rc = s_rc;
     w.yc = s_yc;
     for (int c = blockIdx.x; c < p.C; c += gridDim.x) cg_solve_channel<kPipe>(p, c, w, cg_tol, cg_max, red, redf);
@@ -1460,7 +1802,9 @@ struct BatchParams {
     int smem_floats;
 };
 
-__global__ void __launch_bounds__(kCgThreads, 2) lincal_cg_batched(const __grid_constant__ BatchParams bp) {
+template <bool kSten>
+__global__ void __launch_bounds__(kSten ? kCgStThreads : kCgThreads, 2)
+lincal_cg_batched(const __grid_constant__ BatchParams bp) {
     __shared__ double red[32 * 14];
     __shared__ float redf[32 * 14];
     __shared__ int s_item;
@@ -1479,7 +1823,7 @@ __global__ void __launch_bounds__(kCgThreads, 2) lincal_cg_batched(const __grid_
         int hot_mode;
         bool coarse_smem;
         cg_modes(p, bp.smem_floats, hot_mode, coarse_smem);
-        CgWork w = cg_layout(p, base, arena, hot_mode, coarse_smem);
+        CgWork w = cg_layout(p, base, arena, bp.smem_floats, hot_mode, coarse_smem);
         w.rc = s_rc;
         w.yc = s_yc;
         cg_solve_channel<false>(p, item - bp.prefix[slot], w, bp.cg_tol, bp.cg_max, red, redf);
@@ -1635,6 +1979,8 @@ static gc_status fill_params(gc_ctx *ctx, gc_sel *sel, int C, const void *vreduc
     p.nbr = sel->d_nbr;
     p.ax = ax;
     p.ay = ay;
+    // both selection builders take baseline-types whole, in pair_index order
+    p.stencil = ctx->tune[GC_TUNE_CAL_OP] == 0 && sel->n_ubl <= kStencilTypes ? 1 : 0;
     p.t_autos = sel->n_cycle * sel->t_int;
     p.gains = reinterpret_cast<float2 *>(gains);
     p.vmodel = reinterpret_cast<float2 *>(vmodel);
@@ -1683,6 +2029,7 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
     const bool fp64 = o.precision == GC_FP64;
     int occ = 0;
     size_t per_cta, cg_smem = 0;
+    bool pipe = false;
     const void *kfn;
     if (o.solver == GC_LINCAL) {
         if (sel->n_ubl > kMaxUbl)
@@ -1693,8 +2040,12 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
         kfn = fp64 ? (const void *)lincal_kernel<double> : (const void *)lincal_kernel<float>;
     } else if (o.solver == GC_LINCAL_CG) {
         per_cta = cg_bytes(p.N, p.n_ubl, p.P);
-        cg_smem = cg_arena_bytes(p.N, p.n_ubl, p.L, kCgSmemMax);
-        kfn = cg_smem ? (const void *)lincal_cg_kernel<false> : (const void *)lincal_cg_kernel<true>;
+        cg_smem = cg_arena_bytes(p.N, p.n_ubl, p.L, kCgSmemMax, p.stencil != 0);
+        // pair-scatter operator with its hot vectors in global memory: the pipelined pass
+        pipe = !p.stencil && cg_hot_floats(p.N, p.n_ubl, false) * sizeof(float) > cg_smem;
+        kfn = p.stencil ? (const void *)lincal_cg_kernel<false, true>
+                        : (pipe ? (const void *)lincal_cg_kernel<true, false>
+                                : (const void *)lincal_cg_kernel<false, false>);
         e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCgSmemMax);
         if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(lincal_cg)");
     } else {
@@ -1702,8 +2053,8 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
         kfn = (const void *)omnical_kernel;
     }
     per_cta = (per_cta + 255) & ~size_t(255);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, o.solver == GC_LINCAL_CG ? kCgThreads : kCThreads,
-                                                      cg_smem);
+    const int nthr = o.solver == GC_LINCAL_CG ? (p.stencil ? kCgStThreads : kCgThreads) : kCThreads;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, nthr, cg_smem);
     if (e != cudaSuccess || occ < 1) return gc_cuda_fail(ctx, e, "occupancy(calibration)");
     if (ctx->tune[GC_TUNE_CAL_CTAS] > 0) occ = std::min(occ, ctx->tune[GC_TUNE_CAL_CTAS]);
     const int grid = std::min(C, occ * ctx->sm_count);
@@ -1719,8 +2070,10 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
         if (fp64) lincal_kernel<double><<<grid, kCThreads, 0, s>>>(p);
         else lincal_kernel<float><<<grid, kCThreads, 0, s>>>(p);
     } else if (o.solver == GC_LINCAL_CG) {
-        if (cg_smem) lincal_cg_kernel<false><<<grid, kCgThreads, cg_smem, s>>>(p, 1e-4, 500, (int)(cg_smem / sizeof(float)));
-        else lincal_cg_kernel<true><<<grid, kCgThreads, 0, s>>>(p, 1e-4, 500, 0);
+        const int sf = (int)(cg_smem / sizeof(float));
+        if (p.stencil) lincal_cg_kernel<false, true><<<grid, kCgStThreads, cg_smem, s>>>(p, 1e-4, 500, sf);
+        else if (!pipe) lincal_cg_kernel<false, false><<<grid, kCgThreads, cg_smem, s>>>(p, 1e-4, 500, sf);
+        else lincal_cg_kernel<true, false><<<grid, kCgThreads, cg_smem, s>>>(p, 1e-4, 500, sf);
     } else {
         omnical_kernel<<<grid, kCThreads, 0, s>>>(p);
     }
@@ -1766,14 +2119,20 @@ extern "C" gc_status gc_calibrate_batched(gc_ctx *ctx, int n_arrays, const gc_ba
     bp.cg_max = 500;
     // shared arena: the largest array that fits the cap
     size_t smem = 0;
-    for (int a = 0; a < n_arrays; ++a)
-        smem = std::max(smem, cg_arena_bytes(bp.arr[a].N, bp.arr[a].n_ubl, bp.arr[a].L, kCgSmemMax));
+    bool sten = false;   // the stencil kernel (256 threads) when any array uses the stencil operator
+    for (int a = 0; a < n_arrays; ++a) {
+        smem = std::max(smem, cg_arena_bytes(bp.arr[a].N, bp.arr[a].n_ubl, bp.arr[a].L, kCgSmemMax,
+                                             bp.arr[a].stencil != 0));
+        sten = sten || bp.arr[a].stencil;
+    }
     bp.smem_floats = (int)(smem / sizeof(float));
-    e = cudaFuncSetAttribute(lincal_cg_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCgSmemMax);
+    const void *kfn = sten ? (const void *)lincal_cg_batched<true> : (const void *)lincal_cg_batched<false>;
+    const int nthr = sten ? kCgStThreads : kCgThreads;
+    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCgSmemMax);
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(lincal_cg_batched)");
     per_cta = (per_cta + 255) & ~size_t(255);
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lincal_cg_batched, kCgThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, nthr, smem);
     if (e != cudaSuccess || occ < 1) return gc_cuda_fail(ctx, e, "occupancy(batched calibration)");
     if (ctx->tune[GC_TUNE_CAL_CTAS] > 0) occ = std::min(occ, ctx->tune[GC_TUNE_CAL_CTAS]);
     const int grid = std::min(bp.total, occ * ctx->sm_count);
@@ -1786,7 +2145,8 @@ extern "C" gc_status gc_calibrate_batched(gc_ctx *ctx, int n_arrays, const gc_ba
     e = cudaMemsetAsync(bp.counter, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "reset work counter");
     int rec = gc_prof_begin(ctx, s, "lincal_cg_batched");
-    lincal_cg_batched<<<grid, kCgThreads, smem, s>>>(bp);
+    if (sten) lincal_cg_batched<true><<<grid, kCgStThreads, smem, s>>>(bp);
+    else lincal_cg_batched<false><<<grid, kCgThreads, smem, s>>>(bp);
     gc_prof_end(ctx, s, rec);
     e = cudaGetLastError();
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch batched calibration");

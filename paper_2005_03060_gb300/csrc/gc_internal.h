@@ -25,11 +25,18 @@ struct gc_prof_rec {
 };
 
 // tuning knobs (gc_set_tuning); 0 = automatic
-enum { GC_TUNE_FFT_CHUNK = 0, GC_TUNE_XENG_TSPLIT = 1, GC_TUNE_CAL_CTAS = 2, GC_TUNE_CAL_ORDER = 3, GC_TUNE_N = 4 };
+enum {
+    GC_TUNE_FFT_CHUNK = 0,
+    GC_TUNE_XENG_TSPLIT = 1,
+    GC_TUNE_CAL_CTAS = 2,
+    GC_TUNE_CAL_ORDER = 3,
+    GC_TUNE_CAL_OP = 4,
+    GC_TUNE_N = 5
+};
 
 struct gc_ctx {
     int device = 0;
-    int tune[GC_TUNE_N] = {0, 0, 0, 0};
+    int tune[GC_TUNE_N] = {0, 0, 0, 0, 0};
     int sm_count = 0;
     unsigned int *status_dev = nullptr;   // device error word
     void *scratch = nullptr;              // grow-only workspace
