@@ -570,48 +570,12 @@ __device__ void gn_solve(GnWork<R> &w, R mu_rel, R *red) {
 }
 
 // Project the four degeneracy directions out of delta (Sec. 5.2).
+// Solve G c = r for the 4 degeneracy coefficients from the packed lower
+// triangle of the Gram matrix (acc[0..9]) and the right-hand side acc[10..13]
+// (Cholesky; c = 0 when a direction vanishes).
 template <class R>
-__device__ void gn_project(const CalParams &p, GnWork<R> &w, R *red) {
-    const int n = w.n, m = w.m, L = p.L;
-    // tangent vectors at the current point
-    for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
-        const R gx = w.xg[2 * i], gy = w.xg[2 * i + 1];
-        const R xx = (R)(i % L), yy = (R)(i / L);
-        R *t = w.tg;
-        t[0 * n + 2 * i] = gx;          t[0 * n + 2 * i + 1] = gy;          // amplitude: g
-        t[1 * n + 2 * i] = -gy;         t[1 * n + 2 * i + 1] = gx;          // phase: i g
-        t[2 * n + 2 * i] = -xx * gy;    t[2 * n + 2 * i + 1] = xx * gx;     // x slope: i x g
-        t[3 * n + 2 * i] = -yy * gy;    t[3 * n + 2 * i + 1] = yy * gx;     // y slope: i y g
-    }
-    for (int k = threadIdx.x; k < p.n_ubl; k += blockDim.x) {
-        const R vx = w.xv[2 * k], vy = w.xv[2 * k + 1];
-        const R dx = (R)p.types[2 * k], dy = (R)p.types[2 * k + 1];
-        R *t = w.tv;
-        t[0 * m + 2 * k] = -2 * vx;     t[0 * m + 2 * k + 1] = -2 * vy;     // amplitude: -2 V
-        t[1 * m + 2 * k] = 0;           t[1 * m + 2 * k + 1] = 0;
-        t[2 * m + 2 * k] = dx * vy;     t[2 * m + 2 * k + 1] = -dx * vx;    // -i dx V
-        t[3 * m + 2 * k] = dy * vy;     t[3 * m + 2 * k + 1] = -dy * vx;
-    }
-    __syncthreads();
-    R acc[14];
-#pragma unroll
-    for (int q = 0; q < 14; ++q) acc[q] = 0;
-    for (int i = threadIdx.x; i < n + m; i += blockDim.x) {
-        R t[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) t[a] = i < n ? w.tg[a * n + i] : w.tv[a * m + (i - n)];
-        const R d = w.xs[i];
-        int q = 0;
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b <= a; ++b) acc[q++] += t[a] * t[b];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) acc[10 + a] += t[a] * d;
-    }
-    block_sum<R, 14>(acc, red);
-    // solve G c = r (4x4, symmetric PD unless a direction vanishes)
-    R G[4][4], r[4], cvec[4];
+__device__ void solve_gram4(const R (&acc)[14], R (&cvec)[4]) {
+    R G[4][4], r[4];
     {
         int q = 0;
         for (int a = 0; a < 4; ++a)
@@ -654,6 +618,50 @@ __device__ void gn_project(const CalParams &p, GnWork<R> &w, R *red) {
             for (int a = 0; a < 4; ++a) cvec[a] = 0;
         }
     }
+}
+
+template <class R>
+__device__ void gn_project(const CalParams &p, GnWork<R> &w, R *red) {
+    const int n = w.n, m = w.m, L = p.L;
+    // tangent vectors at the current point
+    for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
+        const R gx = w.xg[2 * i], gy = w.xg[2 * i + 1];
+        const R xx = (R)(i % L), yy = (R)(i / L);
+        R *t = w.tg;
+        t[0 * n + 2 * i] = gx;          t[0 * n + 2 * i + 1] = gy;          // amplitude: g
+        t[1 * n + 2 * i] = -gy;         t[1 * n + 2 * i + 1] = gx;          // phase: i g
+        t[2 * n + 2 * i] = -xx * gy;    t[2 * n + 2 * i + 1] = xx * gx;     // x slope: i x g
+        t[3 * n + 2 * i] = -yy * gy;    t[3 * n + 2 * i + 1] = yy * gx;     // y slope: i y g
+    }
+    for (int k = threadIdx.x; k < p.n_ubl; k += blockDim.x) {
+        const R vx = w.xv[2 * k], vy = w.xv[2 * k + 1];
+        const R dx = (R)p.types[2 * k], dy = (R)p.types[2 * k + 1];
+        R *t = w.tv;
+        t[0 * m + 2 * k] = -2 * vx;     t[0 * m + 2 * k + 1] = -2 * vy;     // amplitude: -2 V
+        t[1 * m + 2 * k] = 0;           t[1 * m + 2 * k + 1] = 0;
+        t[2 * m + 2 * k] = dx * vy;     t[2 * m + 2 * k + 1] = -dx * vx;    // -i dx V
+        t[3 * m + 2 * k] = dy * vy;     t[3 * m + 2 * k + 1] = -dy * vx;
+    }
+    __syncthreads();
+    R acc[14];
+#pragma unroll
+    for (int q = 0; q < 14; ++q) acc[q] = 0;
+    for (int i = threadIdx.x; i < n + m; i += blockDim.x) {
+        R t[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) t[a] = i < n ? w.tg[a * n + i] : w.tv[a * m + (i - n)];
+        const R d = w.xs[i];
+        int q = 0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b <= a; ++b) acc[q++] += t[a] * t[b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[10 + a] += t[a] * d;
+    }
+    block_sum<R, 14>(acc, red);
+    R cvec[4];
+    solve_gram4<R>(acc, cvec);
     for (int i = threadIdx.x; i < n + m; i += blockDim.x) {
         R d = w.xs[i];
 #pragma unroll
@@ -823,6 +831,10 @@ struct CgWork {
     float *Ca, *Cp;          // coarse amplitude / phase operators, then their inverses (nc x nc)
     float *rc, *yc;          // coarse residual / solution (2 nc; shared memory)
     float *cscr;             // shared-memory scratch for one nc x nc system (or null)
+    // relative-coordinate solver (stencil operator): |g_i|^2 then |V_k|^2, the
+    // diagonal of J^T J in those coordinates, and the coarse index per element
+    float *G, *D;
+    unsigned short *cid;
     int coarse_gather;       // every type offset within one patch side: gather assembly
     int n, m;
     int B, npx, ncp, nc, cv; // patch side, patches per row, patches, coarse size, V in coarse space
@@ -848,10 +860,12 @@ __host__ __device__ inline size_t cg_hot_floats(int N, int n_ubl, bool with_dg) 
     return 6 * (size_t)N + 7 * (size_t)n_ubl + (with_dg ? (size_t)N : 0) + 64;
 }
 
-// Vectors the stencil operator gathers (xg 2N, xv 2 n_ubl, pp n + m); its
-// outputs (acc, dg, dv) are written once by their owning thread.
+// Shared-memory vectors of the relative-coordinate solver: the search
+// direction q (gathered by the operator), G = |g|^2 / |V|^2 (gathered), the
+// Jacobi diagonal D and the coarse index of every element.
 __host__ __device__ inline size_t cg_sten_floats(int N, int n_ubl) {
-    return 4 * (size_t)N + 4 * (size_t)n_ubl + 64;
+    const size_t ne = (size_t)N + n_ubl;
+    return 2 * ne + 2 * ne + (ne + 1) / 2 + 64;   // q, G, D, coarse index (16 bit)
 }
 
 // hot_mode 2: hot vectors and dg in shared memory; 1: hot vectors in shared
@@ -884,10 +898,14 @@ __device__ CgWork cg_layout(const CalParams &p, char *base, float *smem_arena, i
     w.dv = h;
     h += p.n_ubl;
     w.dg = hot_mode == 1 ? ghot : h;
-    if (hot_mode == 3) {   // the gathered vectors move to shared memory
-        w.xg = smem_arena;
-        w.xv = w.xg + 2 * p.N;
-        w.pp = w.xv + 2 * p.n_ubl;
+    // relative-coordinate vectors: in the arena (mode 3) or in global memory
+    {
+        float *rb = hot_mode == 3 ? smem_arena : takeg(cg_sten_floats(p.N, p.n_ubl));
+        const int ne = p.N + p.n_ubl;
+        if (hot_mode == 3) w.pp = rb;   // q replaces the search direction
+        w.G = rb + 2 * ne;
+        w.D = w.G + ne;
+        w.cid = reinterpret_cast<unsigned short *>(w.D + ne);
     }
     w.b = takeg(nm);
     w.x = takeg(nm);
@@ -927,7 +945,8 @@ size_t cg_bytes(int N, int n_ubl, int /*P*/) {
     const int L = (int)lround(sqrt((double)N));
     cg_coarse_dims(L, n_ubl, B, npx, ncp, nc, cv);
     const size_t c2 = (size_t)nc * nc;
-    return sizeof(float) * (r(cg_hot_floats(N, n_ubl, true)) + 5 * r(nm) + r(4 * nm) + 2 * r(c2));
+    return sizeof(float) * (r(cg_hot_floats(N, n_ubl, true)) + 5 * r(nm) + r(4 * nm) + 2 * r(c2) +
+                            r(cg_sten_floats(N, n_ubl)));
 }
 
 // Shared arena for one array: hot vectors with dg and the coarse operators if
@@ -1110,49 +1129,85 @@ __device__ double cg_pass(const CalParams &p, int c, const CgWork &w, bool resid
     return s[0];
 }
 
-// The same operator as cg_pass, as a gather over the grid.  Every selection
-// here takes baseline-types whole, so antenna m meets each type d_k at most
-// twice: as the first member of the pair (m, m - d_k) and as the second
-// member of (m + d_k, m), both found by arithmetic on the grid (pair_index
-// order).  The thread owning m evaluates both pairs and sums its own row of
-// J^T u in registers: every pair is evaluated twice (once by each antenna)
-// and nothing is scattered, so there are no atomics and the result does not
-// depend on the schedule.  The model-visibility rows, conj(e) u (and |e|^2),
-// are summed per type over the first-member evaluations in registers and
-// reduced across the CTA once per pass.  Neighbour gathers of consecutive
-// threads hit consecutive addresses (shared memory when the arena holds xg,
-// xv and pp).  Same outputs and return value as cg_pass.
-__device__ double cg_pass_stencil(const CalParams &p, int c, const CgWork &w, bool resid, double *red) {
+// Relative coordinates.  With the step written as dg_i = g_i q_i and
+// dV_k = V_k w_k, the linearised model of pair p = (i, j) of type k is
+//   dM_p = m_p (q_i + conj(q_j) + w_k),   m_p = g_i conj(g_j) V_k,
+// so in (q, w) the Gauss-Newton matrix is a weighted graph operator with the
+// real weights W_p = |m_p|^2 = |g_i|^2 |g_j|^2 |V_k|^2:
+//   (A q)_i = sum_{p: i first} W_p s_p + sum_{p: i second} W_p conj(s_p),
+//   (A q)_k = sum_{p in k} W_p s_p,     s_p = q_i + conj(q_j) + w_k,
+// the right-hand side is sum conj(m_p) r_p (first) + m_p conj(r_p) (second),
+// and the Levenberg term mu I becomes mu |g_i|^2 / mu |V_k|^2.  This is the
+// same system as the (g, V) form under the diagonal change of variables, so
+// preconditioned CG takes the same steps (the Jacobi and patch-level coarse
+// spaces map onto themselves), but an operator evaluation costs a handful
+// of adds and multiplies instead of three complex products.
+//
+// The thread owning antenna m evaluates its pairs as first member (m, m - d_k)
+// and as second member (m + d_k, m), found by grid arithmetic (every
+// selection takes baseline-types whole, in pair_index order), and sums its
+// own row in registers: every pair is visited by both antennas and nothing
+// is scattered, so there are no atomics and the result does not depend on
+// the schedule.  The model-visibility rows are summed per type over the
+// first-member visits in registers and reduced across the CTA once per pass.
+template <int KT>
+__device__ __forceinline__ void rel_type_reduce(float (&tx)[KT], float (&ty)[KT], float (&td)[KT], bool with_d,
+                                                int nu, float *out_x /* stride 2 */, float *out_d, float *s_tsum) {
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        if (k >= nu) break;
+        for (int o = 16; o > 0; o >>= 1) {
+            tx[k] += __shfl_xor_sync(0xffffffffu, tx[k], o);
+            ty[k] += __shfl_xor_sync(0xffffffffu, ty[k], o);
+            if (with_d) td[k] += __shfl_xor_sync(0xffffffffu, td[k], o);
+        }
+        if (lane == 0) {
+            s_tsum[(wp * 3 + 0) * KT + k] = tx[k];
+            s_tsum[(wp * 3 + 1) * KT + k] = ty[k];
+            s_tsum[(wp * 3 + 2) * KT + k] = td[k];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * nu; t += blockDim.x) {
+        const int comp = t / nu, k = t - comp * nu;
+        float a = 0.f;
+        for (int u = 0; u < nw; ++u) a += s_tsum[(u * 3 + comp) * KT + k];
+        if (comp < 2) out_x[2 * k + comp] = a;
+        else if (with_d) out_d[k] = a;
+    }
+}
+
+// Residual pass at the current (g, V): chi^2 (returned), the right-hand side
+// in relative coordinates (acc), G, the diagonal D of A and, for the coarse
+// operators, dv_k = D_k / |V_k|^2.  Also returns, in *dmax, the largest
+// (g, V)-form gain diagonal D_i / G_i that scales the Levenberg term.
+__device__ double rel_resid_pass(const CalParams &p, int c, const CgWork &w, double *red, float *dmax) {
     constexpr int KT = kStencilTypes;
     __shared__ float s_tsum[(kCgStThreads / 32) * 3 * KT];
-    const int L = p.L, nu = p.n_ubl;
+    const int L = p.L, nu = p.n_ubl, N = p.N;
+    // the gains are gathered from a copy in the q area (free between CG solves)
+    float2 *xg = reinterpret_cast<float2 *>(w.pp);
+    for (int m = threadIdx.x; m < N; m += blockDim.x) xg[m] = reinterpret_cast<const float2 *>(w.xg)[m];
+    __syncthreads();
+    const float2 *vobs2 = reinterpret_cast<const float2 *>(p.vred) + (size_t)c * p.P;
+    const int2 *vobsi = reinterpret_cast<const int2 *>(p.vred) + (size_t)c * p.P;
     float tvx[KT], tvy[KT], tvd[KT];
 #pragma unroll
     for (int k = 0; k < KT; ++k) tvx[k] = tvy[k] = tvd[k] = 0.f;
-    float chi = 0.f;
-    const float2 *xg = reinterpret_cast<const float2 *>(w.xg);
-    const float2 *pg = reinterpret_cast<const float2 *>(w.pp);
-    const float2 *vobs2 = reinterpret_cast<const float2 *>(p.vred) + (size_t)c * p.P;
-    const int2 *vobsi = reinterpret_cast<const int2 *>(p.vred) + (size_t)c * p.P;
-    for (int m = threadIdx.x; m < p.N; m += blockDim.x) {
+    float chi = 0.f, dm = 0.f;
+    for (int m = threadIdx.x; m < N; m += blockDim.x) {
         const int x = m % L, y = m / L;
         const float2 gm = xg[m];
-        const float2 pm = resid ? make_float2(0.f, 0.f) : pg[m];
-        float sx = 0.f, sy = 0.f, dgm = 0.f;
+        const float Gm = gm.x * gm.x + gm.y * gm.y;
+        float sx = 0.f, sy = 0.f, dsum = 0.f;
 #pragma unroll
         for (int k = 0; k < KT; ++k) {
             if (k >= nu) break;
             const int dx = __ldg(p.types + 2 * k), dy = __ldg(p.types + 2 * k + 1);
             const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
-            float pvx = 0.f, pvy = 0.f, inv = 0.f;
-            int qb = 0;
-            if (resid) {
-                inv = 1.0f / (float)(__ldg(p.win_t1 + k) - __ldg(p.win_t0 + k));
-                qb = __ldg(p.type_ptr + k);
-            } else {
-                pvx = w.pp[2 * p.N + 2 * k];
-                pvy = w.pp[2 * p.N + 2 * k + 1];
-            }
+            const float inv = 1.0f / (float)(__ldg(p.win_t1 + k) - __ldg(p.win_t0 + k));
+            const int qb = __ldg(p.type_ptr + k);
             const int W = L - abs(dx), xlo = max(0, -dx), ylo = max(0, -dy);
             const int off = dy * L + dx;
             auto vo = [&](int q) {
@@ -1163,62 +1218,114 @@ __device__ double cg_pass_stencil(const CalParams &p, int c, const CgWork &w, bo
                 const int2 v = vobsi[q];
                 return make_float2((float)v.x * inv, (float)v.y * inv);
             };
-            // m first: pair (m, j = m - d_k)
-            {
+            {   // m first: pair (m, j = m - d_k)
                 const int xj = x - dx, yj = y - dy;
                 if (xj >= 0 && xj < L && yj >= 0 && yj < L) {
                     const float2 gj = xg[m - off];
                     const float ex = gm.x * gj.x + gm.y * gj.y, ey = gm.y * gj.x - gm.x * gj.y;   // g_m conj(g_j)
-                    const float ax = gj.x * Vx + gj.y * Vy, ay = gj.x * Vy - gj.y * Vx;         // conj(g_j) V
-                    float ux, uy;
-                    if (resid) {
-                        const float2 o = vo(qb + (yj - ylo) * W + (xj - xlo));
-                        ux = o.x - (ex * Vx - ey * Vy);
-                        uy = o.y - (ex * Vy + ey * Vx);
-                        chi = fmaf(ux, ux, fmaf(uy, uy, chi));
-                        dgm += ax * ax + ay * ay;
-                        tvd[k] += ex * ex + ey * ey;
-                    } else {
-                        const float bx = gm.x * Vx - gm.y * Vy, by = gm.x * Vy + gm.y * Vx;     // g_m V
-                        const float2 pj = pg[m - off];
-                        ux = ax * pm.x - ay * pm.y + bx * pj.x + by * pj.y + ex * pvx - ey * pvy;
-                        uy = ax * pm.y + ay * pm.x - bx * pj.y + by * pj.x + ex * pvy + ey * pvx;
-                    }
-                    sx += ax * ux + ay * uy;          // conj(a) u
-                    sy += ax * uy - ay * ux;
-                    tvx[k] += ex * ux + ey * uy;      // conj(e) u
-                    tvy[k] += ex * uy - ey * ux;
+                    const float mx = ex * Vx - ey * Vy, my = ex * Vy + ey * Vx;                 // model m_p
+                    const float2 o = vo(qb + (yj - ylo) * W + (xj - xlo));
+                    const float rx = o.x - mx, ry = o.y - my;
+                    chi = fmaf(rx, rx, fmaf(ry, ry, chi));
+                    const float Wp = mx * mx + my * my;
+                    dsum += Wp;
+                    tvd[k] += Wp;
+                    const float hx = mx * rx + my * ry, hy = mx * ry - my * rx;   // conj(m) r
+                    sx += hx;
+                    sy += hy;
+                    tvx[k] += hx;
+                    tvy[k] += hy;
                 }
             }
-            // m second: pair (i = m + d_k, m)
-            {
+            {   // m second: pair (i = m + d_k, m)
                 const int xi = x + dx, yi = y + dy;
                 if (xi >= 0 && xi < L && yi >= 0 && yi < L) {
                     const float2 gi = xg[m + off];
                     const float ex = gi.x * gm.x + gi.y * gm.y, ey = gi.y * gm.x - gi.x * gm.y;   // g_i conj(g_m)
-                    const float bx = gi.x * Vx - gi.y * Vy, by = gi.x * Vy + gi.y * Vx;         // g_i V
-                    float ux, uy;
-                    if (resid) {
-                        const float2 o = vo(qb + (y - ylo) * W + (x - xlo));
-                        ux = o.x - (ex * Vx - ey * Vy);
-                        uy = o.y - (ex * Vy + ey * Vx);
-                        dgm += bx * bx + by * by;
-                    } else {
-                        const float ax = gm.x * Vx + gm.y * Vy, ay = gm.x * Vy - gm.y * Vx;     // conj(g_m) V
-                        const float2 pi_ = pg[m + off];
-                        ux = ax * pi_.x - ay * pi_.y + bx * pm.x + by * pm.y + ex * pvx - ey * pvy;
-                        uy = ax * pi_.y + ay * pi_.x - bx * pm.y + by * pm.x + ex * pvy + ey * pvx;
-                    }
-                    sx += bx * ux + by * uy;          // b conj(u)
-                    sy += by * ux - bx * uy;
+                    const float mx = ex * Vx - ey * Vy, my = ex * Vy + ey * Vx;
+                    const float2 o = vo(qb + (y - ylo) * W + (x - xlo));
+                    const float rx = o.x - mx, ry = o.y - my;
+                    dsum += mx * mx + my * my;
+                    sx += mx * rx + my * ry;      // m conj(r)
+                    sy += my * rx - mx * ry;
                 }
             }
         }
         w.acc[2 * m] = sx;
         w.acc[2 * m + 1] = sy;
-        if (resid) w.dg[m] = dgm;
+        w.G[m] = Gm;
+        w.D[m] = dsum;
+        dm = fmaxf(dm, Gm > 0.f ? dsum / Gm : 0.f);
     }
-    // per-type sums: warp trees, then a fixed-order sum over the warps
+    rel_type_reduce<KT>(tvx, tvy, tvd, true, nu, w.acc + 2 * N, w.D + N, s_tsum);
+    for (int k = threadIdx.x; k < nu; k += blockDim.x) {
+        const float Uk = w.xv[2 * k] * w.xv[2 * k] + w.xv[2 * k + 1] * w.xv[2 * k + 1];
+        w.G[N + k] = Uk;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nu; k += blockDim.x) w.dv[k] = w.G[N + k] > 0.f ? w.D[N + k] / w.G[N + k] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    double s[1] = {(double)chi};
+    block_sum<double, 1>(s, red);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)dm;
+    __syncthreads();
+    double mx = 0.0;
+    for (int u = 0; u < (int)(blockDim.x >> 5); ++u) mx = fmax(mx, red[u]);
+    __syncthreads();
+    *dmax = (float)mx;
+    return s[0];
+}
+
+// acc = A q (relative coordinates, no Levenberg term): the search direction
+// q is w.pp, G and q are gathered (shared memory when the arena holds them).
+// Returns this thread's part of q.(A q + mu G q), the CG curvature; acc and
+// the partial sums are complete after the caller's next block reduction.
+__device__ float rel_op_pass(const CalParams &p, const CgWork &w, float mu) {
+    constexpr int KT = kStencilTypes;
+    __shared__ float s_tsum[(kCgStThreads / 32) * 2 * KT];
+    const int L = p.L, nu = p.n_ubl, N = p.N;
+    const float2 *q = reinterpret_cast<const float2 *>(w.pp);
+    const float *G = w.G;
+    float tvx[KT], tvy[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) tvx[k] = tvy[k] = 0.f;
+    float curv = 0.f;
+    for (int m = threadIdx.x; m < N; m += blockDim.x) {
+        const int x = m % L, y = m / L;
+        const float2 qm = q[m];
+        const float Gm = G[m];
+        float sx = 0.f, sy = 0.f;
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            if (k >= nu) break;
+            const int dx = __ldg(p.types + 2 * k), dy = __ldg(p.types + 2 * k + 1);
+            const float2 wk = q[N + k];
+            const float GU = Gm * G[N + k];
+            const int off = dy * L + dx;
+            // m first: s = q_m + conj(q_j) + w_k
+            if (x - dx >= 0 && x - dx < L && y - dy >= 0 && y - dy < L) {
+                const float2 qj = q[m - off];
+                const float Wp = GU * G[m - off];
+                const float ax = qm.x + wk.x + qj.x, ay = qm.y + wk.y - qj.y;
+                sx = fmaf(Wp, ax, sx);
+                sy = fmaf(Wp, ay, sy);
+                tvx[k] = fmaf(Wp, ax, tvx[k]);
+                tvy[k] = fmaf(Wp, ay, tvy[k]);
+            }
+            // m second: conj(s) = conj(q_i) + q_m + conj(w_k)
+            if (x + dx >= 0 && x + dx < L && y + dy >= 0 && y + dy < L) {
+                const float2 qi = q[m + off];
+                const float Wp = GU * G[m + off];
+                sx = fmaf(Wp, qi.x + qm.x + wk.x, sx);
+                sy = fmaf(Wp, qm.y - qi.y - wk.y, sy);
+            }
+        }
+        w.acc[2 * m] = sx;
+        w.acc[2 * m + 1] = sy;
+        const float mg = mu * Gm;
+        curv = fmaf(qm.x, sx + mg * qm.x, fmaf(qm.y, sy + mg * qm.y, curv));
+    }
+    // per-type rows: warp trees, then one thread per type sums over the warps
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
@@ -1226,25 +1333,66 @@ __device__ double cg_pass_stencil(const CalParams &p, int c, const CgWork &w, bo
         for (int o = 16; o > 0; o >>= 1) {
             tvx[k] += __shfl_xor_sync(0xffffffffu, tvx[k], o);
             tvy[k] += __shfl_xor_sync(0xffffffffu, tvy[k], o);
-            if (resid) tvd[k] += __shfl_xor_sync(0xffffffffu, tvd[k], o);
         }
         if (lane == 0) {
-            s_tsum[(wp * 3 + 0) * KT + k] = tvx[k];
-            s_tsum[(wp * 3 + 1) * KT + k] = tvy[k];
-            s_tsum[(wp * 3 + 2) * KT + k] = tvd[k];
+            s_tsum[(wp * 2 + 0) * KT + k] = tvx[k];
+            s_tsum[(wp * 2 + 1) * KT + k] = tvy[k];
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 3 * nu; t += blockDim.x) {
-        const int comp = t / nu, k = t - comp * nu;
-        float a = 0.f;
-        for (int u = 0; u < nw; ++u) a += s_tsum[(u * 3 + comp) * KT + k];
-        if (comp < 2) w.acc[2 * p.N + 2 * k + comp] = a;
-        else if (resid) w.dv[k] = a;
+    for (int k = threadIdx.x; k < nu; k += blockDim.x) {
+        float ax = 0.f, ay = 0.f;
+        for (int u = 0; u < nw; ++u) {
+            ax += s_tsum[(u * 2 + 0) * KT + k];
+            ay += s_tsum[(u * 2 + 1) * KT + k];
+        }
+        w.acc[2 * (N + k)] = ax;
+        w.acc[2 * (N + k) + 1] = ay;
+        const float2 wk = q[N + k];
+        const float mg = mu * G[N + k];
+        curv = fmaf(wk.x, ax + mg * wk.x, fmaf(wk.y, ay + mg * wk.y, curv));
     }
-    double s[1] = {(double)chi};
-    if (resid) block_sum<double, 1>(s, red);
-    else __syncthreads();
+    return curv;
+}
+
+// chi^2 at a trial point (g, V) (global memory), each pair once: the thread
+// owning antenna m takes the pairs (m, m - d_k).
+__device__ float rel_chi2(const CalParams &p, int c, const float *tg, const float *tv, float *red) {
+    constexpr int KT = kStencilTypes;
+    const int L = p.L, nu = p.n_ubl;
+    const float2 *g = reinterpret_cast<const float2 *>(tg);
+    const float2 *vobs2 = reinterpret_cast<const float2 *>(p.vred) + (size_t)c * p.P;
+    const int2 *vobsi = reinterpret_cast<const int2 *>(p.vred) + (size_t)c * p.P;
+    float s[1] = {0.f};
+    for (int m = threadIdx.x; m < p.N; m += blockDim.x) {
+        const int x = m % L, y = m / L;
+        const float2 gm = g[m];
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            if (k >= nu) break;
+            const int dx = __ldg(p.types + 2 * k), dy = __ldg(p.types + 2 * k + 1);
+            const int xj = x - dx, yj = y - dy;
+            if (xj < 0 || xj >= L || yj < 0 || yj >= L) continue;
+            const float inv = 1.0f / (float)(__ldg(p.win_t1 + k) - __ldg(p.win_t0 + k));
+            const int q = __ldg(p.type_ptr + k) + (yj - max(0, -dy)) * (L - abs(dx)) + (xj - max(0, -dx));
+            float ox, oy;
+            if (p.vfmt == GC_C64) {
+                const float2 v = vobs2[q];
+                ox = v.x * inv;
+                oy = v.y * inv;
+            } else {
+                const int2 v = vobsi[q];
+                ox = (float)v.x * inv;
+                oy = (float)v.y * inv;
+            }
+            const float2 gj = g[m - (dy * L + dx)];
+            const float Vx = tv[2 * k], Vy = tv[2 * k + 1];
+            const float ex = gm.x * gj.x + gm.y * gj.y, ey = gm.y * gj.x - gm.x * gj.y;
+            const float rx = ox - (ex * Vx - ey * Vy), ry = oy - (ex * Vy + ey * Vx);
+            s[0] = fmaf(rx, rx, fmaf(ry, ry, s[0]));
+        }
+    }
+    block_sum<float, 1>(s, red);
     return s[0];
 }
 
@@ -1264,13 +1412,15 @@ __device__ __forceinline__ int patch_of(const CgWork &w, int i, int L) {
 // Single-barrier block sum (FP32 warp trees, fixed-order cross-warp sum):
 // buf holds two [32][NV] slots used alternately, so no trailing barrier is
 // needed before the next reduction.
+constexpr int kFastSumMax = 3;   // values per fast_sum; buf holds 2 x 32 x kFastSumMax floats
 template <int NV>
 __device__ __forceinline__ void fast_sum(float (&v)[NV], float *buf, int &parity) {
+    static_assert(NV <= kFastSumMax, "fast_sum slot size");
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int q = 0; q < NV; ++q)
         for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-    float *b = buf + parity * 32 * NV;
+    float *b = buf + parity * 32 * kFastSumMax;   // fixed slots: sums of any size alternate safely
     if (lane == 0)
 #pragma unroll
         for (int q = 0; q < NV; ++q) b[wp * NV + q] = v[q];
@@ -1353,7 +1503,7 @@ __device__ void coarse_assemble_scatter(const CalParams &p, const CgWork &w, flo
 
 // Gather assembly: one warp per patch a walks the patch's antennas and, for
 // every type, the antenna's pair as first and as second member (the same
-// grid arithmetic as cg_pass_stencil), summing row a of both coarse
+// grid arithmetic as rel_op_pass, weights from G), summing row a of both coarse
 // operators in registers: the patch itself, its eight neighbour patches
 // (pairs never reach further when every type offset is within one patch
 // side) and the model-visibility columns.  A pair inside the patch is met
@@ -1364,7 +1514,7 @@ __device__ void coarse_assemble_gather(const CalParams &p, const CgWork &w, floa
     constexpr int KT = kStencilTypes;
     const int nc = w.nc, L = p.L, B = w.B, npx = w.npx, ncp = w.ncp, nu = p.n_ubl;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const float2 *xg = reinterpret_cast<const float2 *>(w.xg);
+    const float *G = w.G;   // |g_i|^2, then |V_k|^2 (relative-coordinate residual pass)
     for (int a = wp; a < ncp; a += nw) {
         const int ax = a % npx, ay = a / npx;
         float sa[9], sp[9], ta[KT], tp[KT];
@@ -1376,22 +1526,19 @@ __device__ void coarse_assemble_gather(const CalParams &p, const CgWork &w, floa
         const int bw = min(B, L - x0), bh = min(B, L - y0);
         for (int t = lane; t < bw * bh; t += 32) {
             const int x = x0 + t % bw, y = y0 + t / bw, m = y * L + x;
-            const float2 gm = xg[m];
-            const float gm2 = gm.x * gm.x + gm.y * gm.y;
+            const float gm2 = G[m];
             sa[4] += mu * gm2;
             sp[4] += mu * gm2;
 #pragma unroll
             for (int k = 0; k < KT; ++k) {
                 if (k >= nu) break;
                 const int dx = __ldg(p.types + 2 * k), dy = __ldg(p.types + 2 * k + 1);
-                const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
-                const float v2 = Vx * Vx + Vy * Vy;
+                const float v2 = G[p.N + k];
 #pragma unroll
                 for (int role = 0; role < 2; ++role) {
                     const int xo = role == 0 ? x - dx : x + dx, yo = role == 0 ? y - dy : y + dy;
                     if (xo < 0 || xo >= L || yo < 0 || yo >= L) continue;
-                    const float2 go = xg[yo * L + xo];
-                    const float wq = gm2 * (go.x * go.x + go.y * go.y) * v2;   // |m_p|^2
+                    const float wq = gm2 * G[yo * L + xo] * v2;   // |m_p|^2
                     const int px = xo / B - ax, py = yo / B - ay;              // in -1..1
                     if (px == 0 && py == 0) {
                         sa[4] += 2.f * wq;
@@ -1585,7 +1732,7 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
     gw.delta = w.z;
     gw.n = w.n;
     gw.m = w.m;
-    __shared__ float sbuf[2 * 32 * 2];
+    __shared__ float sbuf[2 * 32 * kFastSumMax];
     int par = 0;
     const bool coarse = nc > 0;
     const uint64_t t_start = gc_globaltimer();
@@ -1653,7 +1800,7 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
     double grad0 = 0.0;
     for (it = 1; it <= p.max_iter; ++it) {
         // residual, right-hand side J^T r and the Jacobi diagonals
-        const double chi2 = p.stencil ? cg_pass_stencil(p, c, w, true, red) : cg_pass<kPipe>(p, c, w, true, red);
+        const double chi2 = cg_pass<kPipe>(p, c, w, true, red);
         double dm = 0.0;
         for (int i = threadIdx.x; i < p.N; i += blockDim.x) dm = fmax(dm, (double)w.dg[i]);
         for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
@@ -1693,8 +1840,7 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
         const float eta = (float)fmin(0.1, fmax(cg_tol, sqrt(sqrt((double)bnorm2 / fmax(grad0, 1e-300)))));
         for (int k = 0; k < cg_max && bnorm2 > 0.f; ++k) {
             ++inner;
-            if (p.stencil) cg_pass_stencil(p, c, w, false, red);   // acc = J^T J pp
-            else cg_pass<kPipe>(p, c, w, false, red);              // (acc was zeroed)
+            cg_pass<kPipe>(p, c, w, false, red);          // acc = J^T J pp (acc was zeroed)
             float v1[1] = {0.f};
             for (int i = threadIdx.x; i < nm; i += blockDim.x) v1[0] = fmaf(w.pp[i], w.acc[i] + mu * w.pp[i], v1[0]);
             fast_sum<1>(v1, sbuf, par);
@@ -1768,6 +1914,278 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
     finish_channel<float>(p, c, w.xg, w.xv, min(it, p.max_iter), st, red, inner);
 }
 
+// One channel of matrix-free Gauss-Newton in relative coordinates (the
+// stencil operator; see rel_op_pass).  Same outer iteration, forcing terms,
+// preconditioner, projection, line search and stopping rule as
+// cg_solve_channel; the CG vectors hold (q, w) and the search direction q
+// lives in shared memory beside G, D and the coarse indices.  Convergence
+// tests use the (g, V)-form norms, |r|^2 / G per element.
+__device__ void cg_solve_channel_rel(const CalParams &p, int c, CgWork &w, double cg_tol, int cg_max, double *red,
+                                     float *redf) {
+    const int ne = p.N + p.n_ubl, L = p.L, nc = w.nc, N = p.N;
+    __shared__ float sbuf[2 * 32 * kFastSumMax];
+    int par = 0;
+    const bool coarse = nc > 0;
+    const uint64_t t_start = gc_globaltimer();
+    if (p.warm) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const float2 g = p.gains[(size_t)c * N + i];
+            w.xg[2 * i] = g.x;
+            w.xg[2 * i + 1] = g.y;
+        }
+        for (int k = threadIdx.x; k < p.n_ubl; k += blockDim.x) {
+            const float2 v = p.vmodel[(size_t)c * p.n_ubl + k];
+            w.xv[2 * k] = v.x;
+            w.xv[2 * k + 1] = v.y;
+        }
+        __syncthreads();
+    } else {
+        start_point<float>(p, c, w.xg, w.xv, redf, w.z);
+    }
+    // coarse index of every element (0xffff: none)
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        int ci = -1;
+        if (coarse) ci = e < N ? patch_of(w, e, L) : (w.cv ? w.ncp + (e - N) : -1);
+        w.cid[e] = ci < 0 ? (unsigned short)0xffff : (unsigned short)ci;
+    }
+    float2 *q = reinterpret_cast<float2 *>(w.pp);
+    float2 *acc = reinterpret_cast<float2 *>(w.acc);
+    float2 *xs = reinterpret_cast<float2 *>(w.x);
+    float2 *rs = reinterpret_cast<float2 *>(w.r);
+    float2 *zs = reinterpret_cast<float2 *>(w.z);
+    float2 *bs = reinterpret_cast<float2 *>(w.b);
+    // Preconditioner M^-1 r = (D + mu G)^-1 r + R A_c^-1 R^T r, split so that
+    // each CG step streams the global vectors three times: jacobi() applies
+    // the diagonal, restricts r to the coarse space (rc) and returns the
+    // partial dots r.z_j and |r|^2 (in (g, V)-form norm); coarse() solves
+    // y = A_c^-1 rc and returns y.rc (= r.R y), so r.z = r.z_j + y.rc without
+    // another pass; the prolongation z = z_j + R y rides on the q update.
+    // (called by every lane of a warp, e >= ne with r = 0: the restriction
+    // sums each run of equal coarse index across the warp -- consecutive
+    // antennas share a patch -- and the run's first lane adds it once)
+    auto jacobi = [&](int e, float2 r, float mu, float &rzj, float &rr) {
+        int ci = -1;
+        if (e < ne) {
+            const float iv = 1.f / (w.D[e] + mu * w.G[e]);
+            const float2 z = make_float2(r.x * iv, r.y * iv);
+            zs[e] = z;
+            rzj = fmaf(r.x, z.x, fmaf(r.y, z.y, rzj));
+            rr += (r.x * r.x + r.y * r.y) / w.G[e];
+            const unsigned cu = w.cid[e];
+            ci = cu == 0xffffu ? -1 : (int)cu;
+        }
+        if (!coarse) return;
+        const int lane = threadIdx.x & 31;
+        const int kprev = __shfl_up_sync(0xffffffffu, ci, 1);
+        const bool head = lane == 0 || kprev != ci;
+        const int run = __popc(__ballot_sync(0xffffffffu, head) & (0xffffffffu >> (31 - lane)));
+        float qx = r.x, qy = r.y;
+        for (int o = 1; o < 32; o <<= 1) {
+            const float tx = __shfl_down_sync(0xffffffffu, qx, o);
+            const float ty = __shfl_down_sync(0xffffffffu, qy, o);
+            const int tr = __shfl_down_sync(0xffffffffu, run, o);
+            if (lane + o < 32 && tr == run) {
+                qx += tx;
+                qy += ty;
+            }
+        }
+        if (head && ci >= 0) {
+            atomicAdd(&w.rc[ci], qx);
+            atomicAdd(&w.rc[nc + ci], qy);
+        }
+    };
+    auto coarse_solve = [&]() {   // after a barrier that completes rc
+        float ry = 0.f;
+        if (!coarse) return ry;
+        for (int t2 = threadIdx.x; t2 < 2 * nc; t2 += blockDim.x) {
+            const int m = t2 / nc, row = t2 - m * nc;
+            const float *Am = m ? w.Cp : w.Ca;
+            const float *rr = w.rc + m * nc;
+            float a = 0.f;
+            for (int cc = 0; cc < nc; ++cc) a = fmaf(Am[row * nc + cc], rr[cc], a);
+            w.yc[t2] = a;
+            ry = fmaf(a, w.rc[t2], ry);
+        }
+        return ry;
+    };
+    // q = z_j + R y + beta q (q is not read when first: the arena may hold
+    // anything, NaN patterns included, before the first update); rc is
+    // cleared for the next restriction
+    auto update_q = [&](float beta, bool first) {
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+            float2 z = zs[e];
+            if (coarse) {
+                const unsigned ci = w.cid[e];
+                if (ci != 0xffffu) {
+                    z.x += w.yc[ci];
+                    z.y += w.yc[nc + ci];
+                }
+            }
+            if (first) {
+                q[e] = z;
+            } else {
+                const float2 pq = q[e];
+                q[e] = make_float2(z.x + beta * pq.x, z.y + beta * pq.y);
+            }
+        }
+        for (int t2 = threadIdx.x; t2 < 2 * nc; t2 += blockDim.x) w.rc[t2] = 0.f;
+        __syncthreads();
+    };
+    for (int t2 = threadIdx.x; t2 < 2 * kMaxCoarse; t2 += blockDim.x) w.rc[t2] = 0.f;
+    int st = GC_ENOCONV, it, inner = 0;
+    double grad0 = 0.0;
+    for (it = 1; it <= p.max_iter; ++it) {
+        // residual, right-hand side, G, D and the Levenberg scale
+        float dmax = 0.f;
+        const double chi2 = rel_resid_pass(p, c, w, red, &dmax);
+        const float mu = (float)(p.mu_rel * (double)dmax);
+        if (coarse && it == 1) cg_coarse_setup(p, w, mu);   // later iterations reuse it
+        // PCG from x = 0: r = b, q = M^-1 r
+        float v2[3] = {0.f, 0.f, 0.f};
+        const int lane0 = threadIdx.x & 31;
+        for (int e0 = threadIdx.x - lane0; e0 < ne; e0 += blockDim.x) {   // warp-uniform trip count
+            const int e = e0 + lane0;
+            float2 a = make_float2(0.f, 0.f);
+            if (e < ne) {
+                a = acc[e];
+                bs[e] = a;
+                xs[e] = make_float2(0.f, 0.f);
+                rs[e] = a;
+            }
+            jacobi(e, a, mu, v2[0], v2[1]);
+        }
+        __syncthreads();
+        v2[2] = coarse_solve();
+        fast_sum<3>(v2, sbuf, par);
+        float rz = v2[0] + v2[2];
+        const float bnorm2 = v2[1];
+        update_q(0.f, true);
+        // inexact Newton: loose linear solves while the gradient is large
+        if (it == 1) grad0 = bnorm2;
+        const float eta = (float)fmin(0.1, fmax(cg_tol, sqrt(sqrt((double)bnorm2 / fmax(grad0, 1e-300)))));
+        for (int k = 0; k < cg_max && bnorm2 > 0.f; ++k) {
+            ++inner;
+            float v1[1] = {rel_op_pass(p, w, mu)};   // acc = A q; q.(A + mu G) q
+            fast_sum<1>(v1, sbuf, par);
+            if (!(v1[0] > 0.f)) break;
+            const float alpha = rz / v1[0];
+            float v3[3] = {0.f, 0.f, 0.f};
+            for (int e0 = threadIdx.x - lane0; e0 < ne; e0 += blockDim.x) {
+                const int e = e0 + lane0;
+                float2 rn = make_float2(0.f, 0.f);
+                if (e < ne) {
+                    const float2 pq = q[e], a = acc[e], x = xs[e], r = rs[e];
+                    const float mg = mu * w.G[e];
+                    xs[e] = make_float2(x.x + alpha * pq.x, x.y + alpha * pq.y);
+                    rn = make_float2(r.x - alpha * (a.x + mg * pq.x), r.y - alpha * (a.y + mg * pq.y));
+                    rs[e] = rn;
+                }
+                jacobi(e, rn, mu, v3[0], v3[1]);
+            }
+            __syncthreads();
+            v3[2] = coarse_solve();
+            fast_sum<3>(v3, sbuf, par);
+            if (v3[1] <= eta * eta * bnorm2) break;
+            const float rzn = v3[0] + v3[2];
+            const float beta = rzn / rz;
+            rz = rzn;
+            update_q(beta, false);
+        }
+        __syncthreads();
+        for (int t2 = threadIdx.x; t2 < 2 * nc; t2 += blockDim.x) w.rc[t2] = 0.f;
+        // Project the four degeneracy directions out of the step (Sec. 5.2),
+        // orthogonally in the (g, V) metric, which in relative coordinates
+        // weighs element e by G_e.  The directions have closed forms there:
+        // amplitude (1 | -2), phase (i | 0), slopes (i x | -i d_x) and
+        // (i y | -i d_y) for (antennas | types).
+        auto degen = [&](int e, float2 (&qa)[4]) {
+            if (e < N) {
+                const float X = (float)(e % L), Y = (float)(e / L);
+                qa[0] = make_float2(1.f, 0.f);
+                qa[1] = make_float2(0.f, 1.f);
+                qa[2] = make_float2(0.f, X);
+                qa[3] = make_float2(0.f, Y);
+            } else {
+                const float dx = (float)__ldg(p.types + 2 * (e - N)), dy = (float)__ldg(p.types + 2 * (e - N) + 1);
+                qa[0] = make_float2(-2.f, 0.f);
+                qa[1] = make_float2(0.f, 0.f);
+                qa[2] = make_float2(0.f, -dx);
+                qa[3] = make_float2(0.f, -dy);
+            }
+        };
+        float pacc[14];
+#pragma unroll
+        for (int u = 0; u < 14; ++u) pacc[u] = 0.f;
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+            float2 qa[4];
+            degen(e, qa);
+            const float2 x = xs[e];
+            const float Ge = w.G[e];
+            int u = 0;
+#pragma unroll
+            for (int a2 = 0; a2 < 4; ++a2) {
+#pragma unroll
+                for (int b2 = 0; b2 <= a2; ++b2) pacc[u++] += Ge * (qa[a2].x * qa[b2].x + qa[a2].y * qa[b2].y);
+                pacc[10 + a2] += Ge * (qa[a2].x * x.x + qa[a2].y * x.y);
+            }
+        }
+        block_sum<float, 14>(pacc, redf);
+        float cvec[4];
+        solve_gram4<float>(pacc, cvec);
+        // delta = s (x - sum_a c_a q_a) in the (g, V) form, into w.z
+        double nr[2] = {0.0, 0.0};
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+            float2 qa[4];
+            degen(e, qa);
+            float2 d = xs[e];
+#pragma unroll
+            for (int a2 = 0; a2 < 4; ++a2) {
+                d.x -= cvec[a2] * qa[a2].x;
+                d.y -= cvec[a2] * qa[a2].y;
+            }
+            const float2 sv = e < N ? reinterpret_cast<const float2 *>(w.xg)[e]
+                                    : reinterpret_cast<const float2 *>(w.xv)[e - N];
+            const float2 dp = make_float2(sv.x * d.x - sv.y * d.y, sv.x * d.y + sv.y * d.x);
+            zs[e] = dp;
+            nr[0] += (double)sv.x * sv.x + (double)sv.y * sv.y;
+            nr[1] += (double)dp.x * dp.x + (double)dp.y * dp.y;
+        }
+        block_sum<double, 2>(nr, red);
+        // halving line search on chi^2; each trial point is staged in the
+        // q area (free once the CG loop is done) for the pair gathers
+        float step = 1.f;
+        float2 *stage = q;
+        for (int ls = 0; ls < 8; ++ls) {
+            for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+                const float2 sv = e < N ? reinterpret_cast<const float2 *>(w.xg)[e]
+                                        : reinterpret_cast<const float2 *>(w.xv)[e - N];
+                const float2 dp = zs[e];
+                stage[e] = make_float2(sv.x + step * dp.x, sv.y + step * dp.y);
+            }
+            __syncthreads();
+            const float c2 = rel_chi2(p, c, reinterpret_cast<const float *>(stage),
+                                      reinterpret_cast<const float *>(stage + N), redf);
+            if ((double)c2 <= chi2 * (1.0 + 1e-6) + 1e-30 || ls == 7) break;
+            step *= 0.5f;
+        }
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+            if (e < N) reinterpret_cast<float2 *>(w.xg)[e] = stage[e];
+            else reinterpret_cast<float2 *>(w.xv)[e - N] = stage[e];
+        }
+        __syncthreads();
+        if ((double)step * sqrt(nr[1]) <= p.tol * sqrt(nr[0])) {
+            st = GC_OK;
+            break;
+        }
+        if (gc_globaltimer() - t_start > p.deadline_ns) {
+            st = GC_ETIMEOUT;
+            if (threadIdx.x == 0) atomicOr(p.status, GC_DEV_TIMEOUT_CAL);
+            break;
+        }
+    }
+    finish_channel<float>(p, c, w.xg, w.xv, min(it, p.max_iter), st, red, inner);
+}
+
 // kSten: the stencil operator (p.stencil set), launched with kCgStThreads
 template <bool kPipe, bool kSten>
 __global__ void __launch_bounds__(kSten ? kCgStThreads : kCgThreads, 2)
@@ -1782,7 +2200,15 @@ lincal_cg_kernel(const CalParams p, double cg_tol, int cg_max, int smem_floats) 
     CgWork w = cg_layout(p, p.work + (size_t)blockIdx.x * p.work_per_cta, arena, smem_floats, hot_mode, coarse_smem);
     w.rc = s_rc;
     w.yc = s_yc;
-    for (int c = blockIdx.x; c < p.C; c += gridDim.x) cg_solve_channel<kPipe>(p, c, w, cg_tol, cg_max, red, redf);
+    for (int c = blockIdx.x; c < p.C; c += gridDim.x) {
+        if constexpr (kSten) {
+            if (p.stencil) {
+                cg_solve_channel_rel(p, c, w, cg_tol, cg_max, red, redf);
+                continue;
+            }
+        }
+        cg_solve_channel<kPipe>(p, c, w, cg_tol, cg_max, red, redf);
+    }
 }
 
 // Several arrays of different size in one persistent launch: CTAs take
@@ -1826,6 +2252,12 @@ lincal_cg_batched(const __grid_constant__ BatchParams bp) {
         CgWork w = cg_layout(p, base, arena, bp.smem_floats, hot_mode, coarse_smem);
         w.rc = s_rc;
         w.yc = s_yc;
+        if constexpr (kSten) {
+            if (p.stencil) {
+                cg_solve_channel_rel(p, item - bp.prefix[slot], w, bp.cg_tol, bp.cg_max, red, redf);
+                continue;
+            }
+        }
         cg_solve_channel<false>(p, item - bp.prefix[slot], w, bp.cg_tol, bp.cg_max, red, redf);
     }
 }
