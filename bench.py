@@ -291,14 +291,14 @@ class Workload:
     def __init__(self, wl: dict, C: int, dev, ctx, rank: int):
         import torch
 
-        from paper_2005_03060_gb300 import gridcorr, synth
+        from paper_2005_03060_gb300 import gridcorr, shard, synth
 
         self.wl, self.C, self.dev, self.ctx = wl, C, dev, ctx
         L, T = wl["L"], wl["T"]
         N = L * L
         self.L, self.T, self.N = L, T, N
         self.M = max(16, gridcorr.fft_size(L))
-        seed = wl["seed"] + 1000 * rank
+        seed = shard.rank_seed(wl["seed"], rank)
         gains = synth.make_gains(seed, C, N, device=dev)
         if wl["vfmt"] == "i4c":
             volt = torch.empty(C, T, N, dtype=torch.uint8, device=dev)
@@ -465,7 +465,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
 
-    from paper_2005_03060_gb300 import gridcorr
+    from paper_2005_03060_gb300 import gridcorr, shard
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -498,11 +498,8 @@ def run_ours(args, rank, world, local_rank):
     ctx.profile(False)
     ctx.device_status()
     st_last = gridcorr.decode_stats(w.stats)
-    t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_step = float(t.item()) / args.steps
-    value = w.units * world / (ms_step * 1e-3)
+    ms_step = shard.max_over_ranks(ms_total, dev) / args.steps
+    value = shard.job_rate(w.units, world, ms_step)
 
     # ---- calibration variants on the same V^reduced (equal-error comparison)
     variants = calibration_variants(w, min(C, 16 if wl["L"] > 32 else C), max(1, min(5, args.steps // 4)))
@@ -529,11 +526,8 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(2):
         e2e_step()
     e2e_ms = _timed(e2e_step, e2e_steps, stream, barrier) / e2e_steps
-    t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(t.item())
-    e2e = {"value": w.units * world / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+    e2e_ms = shard.max_over_ranks(e2e_ms, dev)
+    e2e = {"value": shard.job_rate(w.units, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
            "h2d_bytes_per_step": h_volt.numel() * h_volt.element_size() + h_gains.numel() * 8,
            "d2h_bytes_per_step": h_vu.numel() * 8 + h_g.numel() * 8,
            "path": ("gc_integrate_host: pinned host voltages streamed in channel chunks, each copy "
