@@ -404,16 +404,21 @@ def rooflines(w: Workload, kern: dict, st_last, peaks: dict, probes: dict):
         dur = ms / n * 1e-3
         cg_it = float(np.sum(st_last["inner"]))
         gn_it = float(np.sum(st_last["iters"]))
-        nm = 2 * N + 2 * sel.n_ubl
-        # algorithmic FP32 flops: operator pass (~70 per pair) and vector updates (~12 per
-        # unknown) per CG iteration; residual/gradient pass, projection and line search
-        # (~90 per pair, ~40 per unknown) per Gauss-Newton iteration
-        flops = cg_it * (70.0 * sel.P + 12.0 * nm) + gn_it * (90.0 * sel.P + 40.0 * nm)
+        ne = N + sel.n_ubl
+        # algorithmic FP32 flops of the matrix-free Gauss-Newton in relative
+        # coordinates (each pair once, in its cheapest form): per CG iteration
+        # the operator (s_p = q_i + conj(q_j) + w_k, weight |m_p|^2, three row
+        # updates: ~14 per pair) and the vector updates (~20 per complex
+        # unknown); per Gauss-Newton iteration the residual pass (model,
+        # residual, right-hand side, diagonal: ~50 per pair), the projection,
+        # line search and update (~60 per unknown)
+        flops = cg_it * (14.0 * sel.P + 20.0 * ne) + gn_it * (50.0 * sel.P + 60.0 * ne)
         rl["lincal_cg"] = {"bound": "alu", "achieved": flops / dur / 1e12, "peak": probes["fp32"],
                            "unit": "TFLOP/s", "frac": flops / dur / 1e12 / probes["fp32"], "traffic": None,
                            "algorithmic_flops": flops, "cg_iterations": cg_it, "gn_iterations": gn_it,
                            "chans_per_s": C / dur,
-                           "note": "one CTA per channel, two per SM; latency-bound (barriers per CG step)",
+                           "note": ("one 256-thread CTA per channel, two per SM; each pair is evaluated by "
+                                    "both of its antennas (no atomics); bound by block barriers and latency"),
                            "peak_source": "measured: gc_peak_probe FP32 FMA on this GPU"}
     return rl
 
