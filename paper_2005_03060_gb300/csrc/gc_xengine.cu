@@ -10,12 +10,12 @@
 // FP32.  4+4-bit voltages take an integer path: each staged byte pair
 // (samples t, t+1 of one antenna) is expanded by byte-parallel integer ops
 // into two words of signed bytes
-//   W  = (re_t, im_t, re_t1, im_t1),   Wc = (re_t, -im_t, re_t1, -im_t1),
+//   W  = (re_t, im_t, re_t1, im_t1),   Wx = (-im_t, re_t, -im_t1, re_t1),
 // and one 4-way byte dot product with int32 accumulation (dp4a) gives two
 // samples of each part of v_i conj(v_j):
 //   Re = re_i re_j + im_i im_j = dp4a(W_i, W_j),
-//   Im = im_i re_j - re_i im_j = dp4a(swap(W_i), Wc_j),
-// swap exchanging the two bytes of each (re, im) pair -- bit-exact sums.
+//   Im = im_i re_j - re_i im_j = dp4a(W_i, Wx_j),
+// so a neighbour contributes its W words unchanged -- bit-exact sums.
 // xeng_reduce: sums the time slices (FP64) into V^reduced and the autos.
 #include <cuda_fp16.h>
 
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kXThreads, 2) xeng_accumulate(const XParams p)
     const size_t stage_stride = p.stage_stride;
     const int L = p.L;
     // 4+4-bit: one record per staged antenna after the raw stages,
-    // [W of NP pairs | Wc of NP pairs | pad]; the pad makes the 16-byte record
+    // [W of NP pairs | Wx of NP pairs | pad]; the pad makes the 16-byte record
     // reads of consecutive antennas conflict-free.  The last record stays zero
     // and stands in for neighbours outside the grid.
     constexpr int kRec = NP == 8 ? 20 : 2;
@@ -215,29 +215,29 @@ __global__ void __launch_bounds__(kXThreads, 2) xeng_accumulate(const XParams p)
                         *reinterpret_cast<uint2 *>(rec + 2 * qu) =
                             make_uint2(__byte_perm(re, im, 0x5140), __byte_perm(re, im, 0x7362));
                         *reinterpret_cast<uint2 *>(rec + 8 + 2 * qu) =
-                            make_uint2(__byte_perm(re, nim, 0x5140), __byte_perm(re, nim, 0x7362));
+                            make_uint2(__byte_perm(nim, re, 0x5140), __byte_perm(nim, re, 0x7362));
                     } else {
                         *reinterpret_cast<uint2 *>(rec) =
-                            make_uint2(__byte_perm(re, im, 0x5140), __byte_perm(re, nim, 0x5140));
+                            make_uint2(__byte_perm(re, im, 0x5140), __byte_perm(nim, re, 0x5140));
                     }
                 }
                 __syncthreads();
                 refill(st);   // the raw stage is free again
                 if (own) {
                     const int jl = j - y_lo * L;
-                    uint32_t wj[NP], wcj[NP];
+                    uint32_t wj[NP], wxj[NP];
                     const uint32_t *rj = conv + (size_t)jl * kRec;
                     if constexpr (NP == 8) {
                         const uint4 *r4 = reinterpret_cast<const uint4 *>(rj);
                         const uint4 a0 = r4[0], a1 = r4[1], b0 = r4[2], b1 = r4[3];
                         wj[0] = a0.x; wj[1] = a0.y; wj[2] = a0.z; wj[3] = a0.w;
                         wj[4] = a1.x; wj[5] = a1.y; wj[6] = a1.z; wj[7] = a1.w;
-                        wcj[0] = b0.x; wcj[1] = b0.y; wcj[2] = b0.z; wcj[3] = b0.w;
-                        wcj[4] = b1.x; wcj[5] = b1.y; wcj[6] = b1.z; wcj[7] = b1.w;
+                        wxj[0] = b0.x; wxj[1] = b0.y; wxj[2] = b0.z; wxj[3] = b0.w;
+                        wxj[4] = b1.x; wxj[5] = b1.y; wxj[6] = b1.z; wxj[7] = b1.w;
                     } else {
                         const uint2 r = *reinterpret_cast<const uint2 *>(rj);
                         wj[0] = r.x;
-                        wcj[0] = r.y;
+                        wxj[0] = r.y;
                     }
                     if (do_autos) {
 #pragma unroll
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kXThreads, 2) xeng_accumulate(const XParams p)
 #pragma unroll
                         for (int q = 0; q < NP; ++q) {
                             ire[k] = __dp4a((int)wi[q], (int)wj[q], ire[k]);
-                            iim[k] = __dp4a((int)__byte_perm(wi[q], 0u, 0x2301), (int)wcj[q], iim[k]);
+                            iim[k] = __dp4a((int)wi[q], (int)wxj[q], iim[k]);
                         }
                     }
                 }
