@@ -338,11 +338,15 @@ GC_API gc_status gc_chi2_backward_ckpt(gc_ctx *ctx, const float *residuals, cons
  * One integration of HOST-resident voltages through the whole cycle of the
  * paper's Fig. 1: FFT-correlator (gc_correlate), reduced X-engine
  * (gc_reduce) and calibration (gc_calibrate), streamed in chunks of
- * `chunk` channels (0: automatic, about eight chunks).  The host->device
- * copy of the next chunk, on a copy stream owned by the context, overlaps
- * the kernels of the current one on `stream`; the calibration runs on groups
- * of chunks as their V^reduced complete.  (No paper counterpart: this is the
- * data path of a correlator whose voltages arrive from the host.)
+ * `chunk` channels (0: automatic, about eight chunks; the first chunk is a
+ * quarter of `chunk`, so that little copy time precedes the first kernel).
+ * The host->device copy of the next chunk, on a copy stream owned by the
+ * context, overlaps the kernels of the current one on `stream`; one
+ * calibration launch over all C channels follows the last chunk.  A staging
+ * buffer is refilled as soon as the last kernel that read it has finished,
+ * so the first copies of the next call overlap this call's calibration.  (No
+ * paper counterpart: this is the data path of a correlator whose voltages
+ * arrive from the host.)
  *
  *   h_volt    [C][T][L*L] host memory, c64 / c32h / i4c as gc_correlate;
  *             page-locked memory lets the copies overlap (pageable memory

@@ -2,10 +2,13 @@
 // paper's Fig. 1 (FFT-correlator, reduced X-engine, calibration), streamed
 // channel chunk by channel chunk: the host->device copy of chunk i+1 (on the
 // context's copy stream) overlaps the correlator and X-engine kernels of
-// chunk i (on the caller's stream); calibration runs on groups of chunks as
-// their V^reduced complete, so that each launch still fills the GPU.
+// chunk i (on the caller's stream).  The first chunk is a quarter of the
+// others, so that little copy time is exposed before the first kernel; the
+// calibration is one launch over all channels at the end (the kernels share
+// one stream, so splitting it would only leave partial waves of CTAs).
 // Host code only: every step is one of the library's own kernels.
 #include <algorithm>
+#include <vector>
 
 #include "gc_sel.h"
 
@@ -23,8 +26,6 @@ gc_status ensure_streaming(gc_ctx *ctx, size_t stage_bytes) {
                 (e = cudaEventCreateWithFlags(&ctx->ev_free[b], cudaEventDisableTiming)) != cudaSuccess)
                 return gc_cuda_fail(ctx, e, "cudaEventCreate");
         }
-        e = cudaEventCreateWithFlags(&ctx->ev_entry, cudaEventDisableTiming);
-        if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaEventCreate");
     }
     if (stage_bytes > ctx->stage_bytes) {
         // the old buffers may still be read by queued kernels
@@ -71,21 +72,22 @@ extern "C" gc_status gc_integrate_host(gc_ctx *ctx, const void *h_volt, int vfmt
     gc_status st = ensure_streaming(ctx, (size_t)chunk * per_ch);
     if (st != GC_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    // calibration groups: whole chunks, about two resident CTAs per SM's worth
-    const int cal_group = std::max(1, (2 * ctx->sm_count + chunk - 1) / chunk);
-    // the staging buffers may still be read by work queued earlier on `stream`
-    if ((e = cudaEventRecord(ctx->ev_entry, s)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_entry, 0)) != cudaSuccess)
-        return gc_cuda_fail(ctx, e, "order the copy stream");
     const size_t vr_pair_bytes = 8;   // float2 sums or int2 exact sums per pair
     const size_t au_bytes = 4;
-    const int n_chunks = (C + chunk - 1) / chunk;
-    int cal_from = 0;
+    // chunk boundaries: a short first chunk, then full ones
+    std::vector<int> bounds{0};
+    if (chunk < C) bounds.push_back(std::max(1, chunk / 4));
+    while (bounds.back() < C) bounds.push_back(std::min(C, bounds.back() + chunk));
+    const int n_chunks = (int)bounds.size() - 1;
     const char *h = static_cast<const char *>(h_volt);
     for (int i = 0; i < n_chunks; ++i) {
         const int b = i & 1;
-        const int c0 = i * chunk, cc = std::min(chunk, C - c0);
-        if (i >= 2 && (e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b], 0)) != cudaSuccess)
+        const int c0 = bounds[i], cc = bounds[i + 1] - c0;
+        // a staging buffer is refilled once the last kernel that read it --
+        // of this call, or of the previous call for the first two chunks --
+        // is done, so the next integration's first copies overlap this one's
+        // calibration (an event never recorded makes the wait a no-op)
+        if ((e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b], 0)) != cudaSuccess)
             return gc_cuda_fail(ctx, e, "wait for a free staging buffer");
         e = cudaMemcpyAsync(ctx->stage[b], h + (size_t)c0 * per_ch, (size_t)cc * per_ch, cudaMemcpyHostToDevice,
                             ctx->copy_stream);
@@ -102,17 +104,7 @@ extern "C" gc_status gc_integrate_host(gc_ctx *ctx, const void *h_volt, int vfmt
         if (st != GC_OK) return st;
         if ((e = cudaEventRecord(ctx->ev_free[b], s)) != cudaSuccess)
             return gc_cuda_fail(ctx, e, "record staging release");
-        if ((i + 1) % cal_group == 0 || i + 1 == n_chunks) {
-            const int c1 = c0 + cc, n = c1 - cal_from;
-            const int cfmt = vfmt == GC_I4C ? GC_I4C : GC_C64;   // X-engine output format
-            st = gc_calibrate(ctx, static_cast<const char *>(vreduced) + (size_t)cal_from * sel->P * vr_pair_bytes,
-                              cfmt, sel, n,
-                              autos ? static_cast<const char *>(autos) + (size_t)cal_from * N * au_bytes : nullptr,
-                              opts, gains_out + (size_t)cal_from * N * 2, vmodel + (size_t)cal_from * sel->n_ubl * 2,
-                              stats + cal_from, stream);
-            if (st != GC_OK) return st;
-            cal_from = c1;
-        }
     }
-    return GC_OK;
+    const int cfmt = vfmt == GC_I4C ? GC_I4C : GC_C64;   // X-engine output format
+    return gc_calibrate(ctx, vreduced, cfmt, sel, C, autos, opts, gains_out, vmodel, stats, stream);
 }

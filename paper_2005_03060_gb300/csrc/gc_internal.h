@@ -51,7 +51,7 @@ struct gc_ctx {
     cudaStream_t copy_stream = nullptr;
     void *stage[2] = {nullptr, nullptr};
     size_t stage_bytes = 0;
-    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr}, ev_entry = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
 };
 
 // launch timing helpers: no-ops unless profiling is enabled

@@ -139,7 +139,6 @@ void gc_destroy(gc_ctx *ctx) {
         if (ctx->ev_copied[b]) cudaEventDestroy(ctx->ev_copied[b]);
         if (ctx->ev_free[b]) cudaEventDestroy(ctx->ev_free[b]);
     }
-    if (ctx->ev_entry) cudaEventDestroy(ctx->ev_entry);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->status_dev) cudaFree(ctx->status_dev);
