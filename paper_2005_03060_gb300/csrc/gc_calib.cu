@@ -813,8 +813,11 @@ __global__ void __launch_bounds__(kCThreads) lincal_kernel(const CalParams p) {
 
 // ----------------------------------------------------------------- lincal, matrix-free (mixed precision)
 // Gauss-Newton with the step from preconditioned conjugate gradients on
-// (J^T J + mu I) delta = J^T r, never forming J^T J.  The operator is one pass
-// over the pairs: each pair evaluates its entry of J v,
+// (J^T J + mu I) delta = J^T r, never forming J^T J.  Two operator forms: the
+// gather over the grid in relative coordinates (rel_op_pass and
+// cg_solve_channel_rel, for selections of <= kStencilTypes types) and the
+// pair-list scatter below (cg_pass and cg_solve_channel, any selection).
+// The scatter form is one pass over the pairs: each pair evaluates its entry of J v,
 //   u_p = a_p v_gi + b_p conj(v_gj) + e_p v_V,  a = conj(g_j) V, b = g_i V, e = g_i conj(g_j),
 // and scatters J^T u -- conj(a) u to g_i, b conj(u) to g_j (shared-memory
 // atomics) and conj(e) u to V (warp-reduced when a warp's pairs share a type,
