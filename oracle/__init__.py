@@ -181,3 +181,28 @@ def unpack_i4c(b):
     hi = np.where(hi >= 8, hi - 16, hi)
     lo = np.where(lo >= 8, lo - 16, lo)
     return hi.astype(np.float64) + 1j * lo.astype(np.float64)
+
+
+def fx_masked(volt, gains, mask, L):
+    """V^unique of an array on a partly occupied L x L lattice grid (Eq.
+    modelvis by definition, numpy): w = v / g on the occupied points; for
+    every separation d = r_i - r_j of two occupied points, the time average
+    of w_i conj(w_j) summed over those pairs and divided by their number N_d.
+    Returns (V [(2L-1), (2L-1)] indexed [dy + L - 1][dx + L - 1], N_d); lags
+    without a pair are 0."""
+    v = _c128(volt)
+    T = v.shape[0]
+    occ = np.flatnonzero(np.asarray(mask))
+    w = v[:, occ] / _c128(gains)[occ][None, :]
+    S = w.T @ np.conj(w) / T                       # S[i, j] = <w_i conj(w_j)>
+    x, y = occ % L, occ // L
+    dx = (x[:, None] - x[None, :]) + (L - 1)
+    dy = (y[:, None] - y[None, :]) + (L - 1)
+    W = 2 * L - 1
+    out = np.zeros((W, W), np.complex128)
+    nd = np.zeros((W, W), np.int64)
+    np.add.at(out, (dy.ravel(), dx.ravel()), S.ravel())
+    np.add.at(nd, (dy.ravel(), dx.ravel()), 1)
+    nz = nd > 0
+    out[nz] /= nd[nz]
+    return out, nd

@@ -79,6 +79,18 @@ def _axis_types(types):
     return types.index((1, 0)), types.index((0, 1))
 
 
+def _pos(L, N):
+    """Lattice coordinates [N, 2] of the antennas: the L x L grid (i = y L + x)
+    when L is an int, else L itself -- an [N, 2] array of lattice coordinates
+    for arrays that do not fill a square grid (e.g. hexagonal ones, Sec. 3);
+    every degeneracy and convention below is linear in these coordinates."""
+    if isinstance(L, (int, np.integer)):
+        return np.stack([np.arange(L * L) % L, np.arange(L * L) // L], 1).astype(float)
+    p = np.asarray(L, float)
+    assert p.shape == (N, 2)
+    return p
+
+
 def project(g, V, types, L):
     """Fix the four degeneracies (Sec. 5.2) to the output convention."""
     g = np.asarray(g, np.complex128).copy()
@@ -90,7 +102,7 @@ def project(g, V, types, L):
     # phase slopes: g_i -> g_i e^{i k.r_i}, V_a -> V_a e^{-i k.d_a}
     ax, ay = _axis_types(types)
     k = np.array([np.angle(V[ax]), np.angle(V[ay])])
-    pos = np.stack([np.arange(L * L) % L, np.arange(L * L) // L], 1).astype(float)
+    pos = _pos(L, len(g))
     g *= np.exp(1j * pos @ k)
     d = np.asarray(types, float)
     V *= np.exp(-1j * d @ k)
@@ -107,10 +119,17 @@ def fit_degeneracies(g_est, g_true, L):
     """
     q = g_true / g_est
     amp = np.exp(np.mean(np.log(np.abs(q))))
-    qq = q.reshape(L, L)
-    kx = np.angle(np.sum(qq[:, 1:] * np.conj(qq[:, :-1]))) if L > 1 else 0.0
-    ky = np.angle(np.sum(qq[1:, :] * np.conj(qq[:-1, :]))) if L > 1 else 0.0
-    pos = np.stack([np.arange(L * L) % L, np.arange(L * L) // L], 1).astype(float)
+    if isinstance(L, (int, np.integer)):
+        qq = q.reshape(L, L)
+        kx = np.angle(np.sum(qq[:, 1:] * np.conj(qq[:, :-1]))) if L > 1 else 0.0
+        ky = np.angle(np.sum(qq[1:, :] * np.conj(qq[:-1, :]))) if L > 1 else 0.0
+    else:   # mean increments over the antenna pairs one lattice step apart
+        pos = _pos(L, len(q))
+        at = {(int(a), int(b)): n for n, (a, b) in enumerate(pos)}
+        sx = sum(q[at[(a + 1, b)]] * np.conj(q[n]) for (a, b), n in at.items() if (a + 1, b) in at)
+        sy = sum(q[at[(a, b + 1)]] * np.conj(q[n]) for (a, b), n in at.items() if (a, b + 1) in at)
+        kx, ky = float(np.angle(sx)), float(np.angle(sy))
+    pos = _pos(L, len(q))
     ramp = np.exp(1j * (pos @ np.array([kx, ky])))
     phi0 = np.angle(np.sum(q * np.conj(ramp)))
     return g_est * amp * ramp * np.exp(1j * phi0)
@@ -142,20 +161,40 @@ def _lstsq_rows(n_var, rows_idx, rows_val, rhs, sparse=False):
 
 def initial_solution(vobs, pi, pj, alpha, types, L, sparse=False):
     """Phase tree + wrapped phase logcal + amplitude logcal (Eq. logcal)."""
-    N = L * L
     nu = len(types)
     ax, ay = _axis_types(types)
     lookup = {}
     for p in range(len(vobs)):
         if alpha[p] in (ax, ay):
             lookup[(int(pi[p]), int(pj[p]))] = vobs[p]
-    phi = np.zeros(N)
-    for x in range(1, L):                       # along the first row
-        phi[x] = phi[x - 1] + np.angle(lookup[(x, x - 1)])
-    for y in range(1, L):                       # up every column
-        for x in range(L):
-            i, j = y * L + x, (y - 1) * L + x
-            phi[i] = phi[j] + np.angle(lookup[(i, j)])
+    if isinstance(L, (int, np.integer)):
+        N = L * L
+        phi = np.zeros(N)
+        for x in range(1, L):                       # along the first row
+            phi[x] = phi[x - 1] + np.angle(lookup[(x, x - 1)])
+        for y in range(1, L):                       # up every column
+            for x in range(L):
+                i, j = y * L + x, (y - 1) * L + x
+                phi[i] = phi[j] + np.angle(lookup[(i, j)])
+    else:
+        # breadth-first tree over the axis-type pairs from antenna 0:
+        # phi_i - phi_j = arg V_p for p = (i, j) (arg V of both axis types is 0)
+        N = len(L)
+        phi = np.zeros(N)
+        nbrs = [[] for _ in range(N)]
+        for (i, j), vp in lookup.items():
+            nbrs[j].append((i, np.angle(vp)))
+            nbrs[i].append((j, -np.angle(vp)))
+        seen = np.zeros(N, bool)
+        seen[0] = True
+        queue = [0]
+        for a in queue:
+            for b, dphi in nbrs[a]:
+                if not seen[b]:
+                    seen[b] = True
+                    phi[b] = phi[a] + dphi
+                    queue.append(b)
+        assert seen.all(), "the axis types do not connect the array"
     # wrapped residual phase logcal: dphi_i - dphi_j + theta_a = wrap(arg V - phi_i + phi_j)
     res = np.angle(vobs * np.exp(-1j * (phi[pi] - phi[pj])))
     idx = [(int(pi[p]), int(pj[p]), N + int(alpha[p])) for p in range(len(vobs))]
@@ -237,8 +276,8 @@ def _degenerate_directions(g, V, types_d, L):
     ordering x = [Re g, Im g, Re V, Im V]: amplitude (g, -2V), phase (i g, 0)
     and the two slopes (i x_i g_i, -i dx_a V_a), (i y_i g_i, -i dy_a V_a)."""
     N = len(g)
-    xs = np.arange(N) % L
-    ys = np.arange(N) // L
+    pos = _pos(L, N)
+    xs, ys = pos[:, 0], pos[:, 1]
     dirs = [(g, -2.0 * V), (1j * g, 0.0 * V),
             (1j * xs * g, -1j * types_d[:, 0] * V), (1j * ys * g, -1j * types_d[:, 1] * V)]
     return np.stack([np.concatenate([a.real, a.imag, b.real, b.imag]) for a, b in dirs], 1)
@@ -314,7 +353,8 @@ def omnical(vobs, pi, pj, alpha, g, V, damping=0.3, tol=1e-10, maxiter=100000):
 def calibrate(vobs, pi, pj, alpha, types, L, solver="lincal", tol=1e-10, maxiter=None, sparse=False):
     """Start point, solver and output convention for one channel.  sparse
     (lincal only): sparse linear algebra for the start point and the
-    Gauss-Newton steps -- same equations, for large arrays."""
+    Gauss-Newton steps -- same equations, for large arrays.  L: the grid side,
+    or the [N, 2] lattice coordinates of the antennas (see _pos)."""
     g0, V0 = initial_solution(vobs, pi, pj, alpha, types, L, sparse=sparse)
     if solver == "lincal":
         g, V, it, ok = lincal(vobs, pi, pj, alpha, g0, V0, types, L, tol=tol,

@@ -220,3 +220,114 @@ def n_ubl_per_ant(sel: Selection) -> float:
         a |= set(sel.pair_j[sel.type_ptr[k]:sel.type_ptr[k + 1]].tolist())
         tot += len(a)
     return tot / N
+
+
+# --------------------------------------------------------------------------- lattice layouts
+# Arrays on a lattice that is not fully occupied -- the paper's own arrays
+# are hexagonal (Sec. 3) -- are held as an L x L bounding grid of lattice
+# points (index i = y L + x) with a mask of the occupied points.  Lattice
+# "square": unit spacing; "triangular": basis (1, 0), (1/2, sqrt(3)/2), so a
+# type (dx, dy) has squared length dx^2 + dx dy + dy^2 and physical angle
+# atan2(dy sqrt(3)/2, dx + dy/2).  The canonical half-plane rule
+# (dy > 0, or dy == 0 and dx > 0) is the same on both lattices.
+
+def hex_mask(s: int):
+    """Hexagonal array of side s (3 s (s - 1) + 1 antennas) on a triangular
+    lattice: axial coordinates (a, b) with |a|, |b|, |a + b| <= s - 1, held in
+    the (2 s - 1)^2 bounding grid at x = a + s - 1, y = b + s - 1.  Returns
+    (L, mask[L * L] uint8)."""
+    L = 2 * s - 1
+    m = np.zeros(L * L, np.uint8)
+    for y in range(L):
+        for x in range(L):
+            if s - 1 <= x + y <= 3 * s - 3:
+                m[y * L + x] = 1
+    return L, m
+
+
+def type_length2(d, lattice: str):
+    dx, dy = d
+    return dx * dx + dx * dy + dy * dy if lattice == "triangular" else dx * dx + dy * dy
+
+
+def type_angle(d, lattice: str):
+    dx, dy = d
+    if lattice == "triangular":
+        return math.atan2(dy * math.sqrt(3.0) / 2.0, dx + dy / 2.0)
+    return math.atan2(dy, dx)
+
+
+def masked_type_pairs(L: int, mask, d):
+    """(i, j) pairs of type d between occupied points, r_j row-major."""
+    return [(i, j) for i, j in type_pairs(L, d) if mask[i] and mask[j]]
+
+
+def layout_types(L: int, mask, lattice: str):
+    """Baseline-types with at least one occupied pair, shortest first (ties
+    by physical angle), with their pair counts."""
+    ts = [d for d in canonical_types(L) if masked_type_pairs(L, mask, d)]
+    ts.sort(key=lambda d: (type_length2(d, lattice), type_angle(d, lattice)))
+    return ts, [len(masked_type_pairs(L, mask, d)) for d in ts]
+
+
+def masked_null_space_dim(L: int, mask, types) -> int:
+    """null_space_dim over the occupied antennas only (dense SVD rank)."""
+    occ = np.flatnonzero(np.asarray(mask))
+    col = {int(a): c for c, a in enumerate(occ)}
+    N, nu = len(occ), len(types)
+    rows_a, rows_p = [], []
+    for k, d in enumerate(types):
+        for i, j in masked_type_pairs(L, mask, d):
+            ra = np.zeros(N + nu)
+            ra[col[i]] += 1.0
+            ra[col[j]] += 1.0
+            ra[N + k] += 1.0
+            rp = np.zeros(N + nu)
+            rp[col[i]] += 1.0
+            rp[col[j]] -= 1.0
+            rp[N + k] += 1.0
+            rows_a.append(ra)
+            rows_p.append(rp)
+    A = np.asarray(rows_a)
+    B = np.asarray(rows_p)
+    return (N + nu - np.linalg.matrix_rank(A)) + (N + nu - np.linalg.matrix_rank(B))
+
+
+def subset_layout(L: int, mask, lattice: str, T: int, p: float = 1.0, log_base: float = 2.0) -> Selection:
+    """Subset redundant calibration (Sec. 5) on a masked lattice: whole types
+    in ascending physical length until the pair count is the whole number of
+    groups closest to p N log N (N = occupied antennas), extended if needed
+    until exactly four degeneracies remain (Sec. 5.2, exact SVD rank)."""
+    mask = np.asarray(mask, np.uint8)
+    N = int(mask.sum())
+    ordered, counts = layout_types(L, mask, lattice)
+    target = budget(N, p, log_base)
+    cum, best_k, best_err = 0, 1, None
+    for k, n in enumerate(counts, start=1):
+        cum += n
+        err = abs(cum - target)
+        if best_err is None or err < best_err:
+            best_k, best_err = k, err
+    k = best_k
+    while masked_null_space_dim(L, mask, ordered[:k]) != 4:
+        k += 1
+    types = ordered[:k]
+    ptr, pi, pj = [0], [], []
+    for d in types:
+        prs = masked_type_pairs(L, mask, d)
+        pi += [a for a, _ in prs]
+        pj += [b for _, b in prs]
+        ptr.append(len(pi))
+    return Selection(L, types, np.asarray(ptr, np.int32), np.asarray(pi, np.int32), np.asarray(pj, np.int32),
+                     np.zeros(k, np.int32), np.full(k, T, np.int32), n_cycle=1, t_int=T, null_dim=4,
+                     extra=dict(target=target, k_budget=best_k, mask=mask, lattice=lattice, N=N))
+
+
+def compact(sel: Selection, mask):
+    """Pairs and lattice coordinates in the occupied-antenna numbering:
+    (pair_i, pair_j, pos [N_occ x 2]) for the oracle's calibration."""
+    occ = np.flatnonzero(np.asarray(mask))
+    col = -np.ones(len(mask), np.int64)
+    col[occ] = np.arange(len(occ))
+    pos = np.stack([occ % sel.L, occ // sel.L], 1).astype(float)
+    return col[sel.pair_i], col[sel.pair_j], pos
