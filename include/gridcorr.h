@@ -160,8 +160,30 @@ GC_API gc_status gc_correlate(gc_ctx *ctx, const void *volt, int vfmt, int L, in
 typedef struct gc_sel gc_sel;
 GC_API gc_status gc_selection_subset(int L, int T, double p, double log_base, gc_sel **out);
 GC_API gc_status gc_selection_lowcad(int L, int T, double p, double log_base, gc_sel **out);
+
+/*
+ * Subset selection for an array on a partly occupied lattice -- the paper's
+ * own arrays are hexagonal (Sec. 3; Fig. 13's 331 antennas).  The array is
+ * held as the L x L bounding grid of lattice points (point i = y L + x) with
+ * mask[i] = 1 where an antenna sits (host, L*L bytes); voltages and gains
+ * keep the grid layout, with anything at unoccupied points ignored.
+ * lattice GC_LATTICE_SQUARE: unit spacing; GC_LATTICE_TRIANGULAR: basis
+ * (1, 0), (1/2, sqrt(3)/2), so type (dx, dy) has squared length
+ * dx^2 + dx dy + dy^2.  Types with a pair between occupied points are taken
+ * whole, shortest first (ties by angle in [0, pi)), stopping at the count
+ * closest to p N log N with N the occupied points, then extended until the
+ * criterion of Sec. 5.2 holds: both axis types, and dx + dy even (square) or
+ * (-1, 1) (triangular).  GC_EDEGEN when no prefix satisfies it or the axis
+ * types do not connect the array; GC_EINVAL for a NULL mask, fewer than 3
+ * antennas or the size limits of gc_selection_subset.  Works with
+ * gc_reduce, gc_calibrate (GC_LINCAL_CG) and gc_correlate_masked.
+ */
+typedef enum gc_lattice { GC_LATTICE_SQUARE = 0, GC_LATTICE_TRIANGULAR = 1 } gc_lattice;
+GC_API gc_status gc_selection_subset_masked(int L, int T, double p, double log_base, const uint8_t *mask,
+                                            int lattice, gc_sel **out);
 GC_API void gc_sel_free(gc_sel *sel);
-/* info[8] = {L, T, P (pairs), n_ubl (types), n_cycle, t_int, null_dim, scheme (0 subset, 1 low-cadence)} */
+/* info[11] = {L, T, P (pairs), n_ubl (types), n_cycle, t_int, null_dim,
+ *             scheme (0 subset, 1 low-cadence), masked, lattice, antennas} */
 GC_API gc_status gc_sel_info(const gc_sel *sel, int32_t *info);
 /* Host arrays owned by the selection (valid until gc_sel_free): types [n_ubl][2],
  * type_ptr [n_ubl + 1] (pairs of type k are [type_ptr[k], type_ptr[k+1])),

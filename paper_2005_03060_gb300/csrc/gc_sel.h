@@ -24,13 +24,23 @@ struct gc_sel {
     std::vector<int32_t> grp_types;  // type indices, grouped
     std::vector<int32_t> grp_off;    // [n_groups + 1]
     std::vector<int32_t> grp_t0, grp_t1, grp_first, grp_win, grp_dymax;   // [n_groups]
+    // arrays on a partly occupied lattice (gc_selection_subset_masked)
+    int lattice = 0;                 // 0 square, 1 triangular
+    int masked = 0;                  // 1: only the points of `mask` hold antennas
+    int n_occ = 0;                   // antennas (L * L when unmasked)
+    std::vector<int32_t> mask;       // [L * L] 0 / 1 (masked only)
+    // start-point tree over the (1,0) and (0,1) types (masked only), in
+    // breadth-first order: antenna, the pair linking it to its parent (-1 for
+    // the root) and +1 / -1 when the antenna is that pair's first / second member
+    std::vector<int32_t> tree_ant, tree_pair, tree_sign;
     // device copies (one allocation, on `device`)
     int device = -1;
     void *d_base = nullptr;
     int32_t *d_types = nullptr, *d_type_ptr = nullptr, *d_pair_i = nullptr, *d_pair_j = nullptr,
             *d_pair_type = nullptr, *d_win_t0 = nullptr, *d_win_t1 = nullptr, *d_grp_types = nullptr,
             *d_grp_off = nullptr, *d_grp_t0 = nullptr, *d_grp_t1 = nullptr, *d_grp_first = nullptr,
-            *d_grp_win = nullptr, *d_nbr = nullptr, *d_grp_dymax = nullptr;
+            *d_grp_win = nullptr, *d_nbr = nullptr, *d_grp_dymax = nullptr, *d_mask = nullptr,
+            *d_tree_ant = nullptr, *d_tree_pair = nullptr, *d_tree_sign = nullptr;
 };
 
 gc_status gc_sel_upload(gc_ctx *ctx, gc_sel *s);

@@ -76,6 +76,7 @@ void fill_pairs(gc_sel *s) {
             for (int x = 0; x < L; ++x) {
                 const int xi = x + dx, yi = y + dy;
                 if (xi < 0 || xi >= L || yi < 0 || yi >= L) continue;
+                if (s->masked && !(s->mask[yi * L + xi] && s->mask[y * L + x])) continue;
                 s->pair_i.push_back(yi * L + xi);
                 s->pair_j.push_back(y * L + x);
                 s->pair_type.push_back(k);
@@ -133,6 +134,75 @@ void fill_groups(gc_sel *s) {
     s->n_groups = (int)s->grp_t0.size();
 }
 
+// Types with at least one pair between occupied points of `mask`, with
+// their pair counts, ordered by physical length on the lattice (square:
+// dx^2 + dy^2; triangular, basis (1,0), (1/2, sqrt3/2): dx^2 + dx dy + dy^2),
+// ties by angle in [0, pi) (the lattice map preserves orientation, so the
+// lattice cross product orders the angles).
+std::vector<std::pair<TypeVec, long>> masked_types(int L, const std::vector<int32_t> &mask, int lattice) {
+    std::vector<std::pair<TypeVec, long>> t;
+    for (int dy = 0; dy < L; ++dy)
+        for (int dx = -(L - 1); dx < L; ++dx) {
+            if (!(dy > 0 || dx > 0)) continue;
+            long n = 0;
+            for (int y = std::max(0, -dy); y < std::min(L, L - dy); ++y)
+                for (int x = std::max(0, -dx); x < std::min(L, L - dx); ++x)
+                    n += mask[y * L + x] && mask[(y + dy) * L + x + dx];
+            if (n > 0) t.push_back({{dx, dy}, n});
+        }
+    auto len2 = [lattice](const TypeVec &d) {
+        return lattice ? (long)d.dx * d.dx + (long)d.dx * d.dy + (long)d.dy * d.dy
+                       : (long)d.dx * d.dx + (long)d.dy * d.dy;
+    };
+    std::stable_sort(t.begin(), t.end(), [&](const std::pair<TypeVec, long> &a, const std::pair<TypeVec, long> &b) {
+        const long la = len2(a.first), lb = len2(b.first);
+        if (la != lb) return la < lb;
+        return (long)a.first.dx * b.first.dy - (long)a.first.dy * b.first.dx > 0;
+    });
+    return t;
+}
+
+// Start-point tree of a masked selection: breadth-first over the pairs of the
+// (1,0) and (0,1) types from the first occupied point.  False when these
+// types do not connect every occupied point.
+bool fill_tree(gc_sel *s) {
+    const int L = s->L, N = L * L;
+    int ax = -1, ay = -1;
+    for (int k = 0; k < s->n_ubl; ++k) {
+        if (s->types[2 * k] == 1 && s->types[2 * k + 1] == 0) ax = k;
+        if (s->types[2 * k] == 0 && s->types[2 * k + 1] == 1) ay = k;
+    }
+    if (ax < 0 || ay < 0 || s->nbr.empty()) return false;
+    s->tree_ant.clear();
+    s->tree_pair.clear();
+    s->tree_sign.clear();
+    std::vector<char> seen(N, 0);
+    int root = 0;
+    while (root < N && !s->mask[root]) ++root;
+    if (root == N) return false;
+    seen[root] = 1;
+    s->tree_ant.push_back(root);
+    s->tree_pair.push_back(-1);
+    s->tree_sign.push_back(0);
+    for (size_t h = 0; h < s->tree_ant.size(); ++h) {
+        const int a = s->tree_ant[h];
+        for (int k : {ax, ay}) {
+            for (int role = 0; role < 2; ++role) {
+                // role 0: a is the first member, the partner the second; role 1: the reverse
+                const int q = s->nbr[(size_t)(role * s->n_ubl + k) * N + a];
+                if (q < 0) continue;
+                const int b = role == 0 ? s->pair_j[q] : s->pair_i[q];
+                if (seen[b]) continue;
+                seen[b] = 1;
+                s->tree_ant.push_back(b);
+                s->tree_pair.push_back(q);
+                s->tree_sign.push_back(role == 0 ? -1 : 1);   // b second member: -1; first: +1
+            }
+        }
+    }
+    return (int)s->tree_ant.size() == s->n_occ;
+}
+
 }  // namespace
 
 void gc_sel_release_device(gc_sel *s) {
@@ -150,11 +220,12 @@ gc_status gc_sel_upload(gc_ctx *ctx, gc_sel *s) {
     if (s->d_base && s->device == ctx->device) return GC_OK;
     gc_sel_release_device(s);
     // one allocation: types, type_ptr, pair_i, pair_j, pair_type, win_t0, win_t1, grp_* arrays
-    const std::vector<int32_t> *parts[] = {&s->types,   &s->type_ptr, &s->pair_i,    &s->pair_j,
-                                           &s->pair_type, &s->win_t0, &s->win_t1,   &s->grp_types,
-                                           &s->grp_off, &s->grp_t0,   &s->grp_t1,   &s->grp_first,
-                                           &s->grp_win,   &s->nbr,      &s->grp_dymax};
-    constexpr int kParts = 15;
+    const std::vector<int32_t> *parts[] = {&s->types,    &s->type_ptr,  &s->pair_i,    &s->pair_j,
+                                           &s->pair_type, &s->win_t0,   &s->win_t1,    &s->grp_types,
+                                           &s->grp_off,  &s->grp_t0,    &s->grp_t1,    &s->grp_first,
+                                           &s->grp_win,  &s->nbr,       &s->grp_dymax, &s->mask,
+                                           &s->tree_ant, &s->tree_pair, &s->tree_sign};
+    constexpr int kParts = 19;
     size_t total = 0;
     size_t offs[kParts];
     for (int i = 0; i < kParts; ++i) {
@@ -176,12 +247,13 @@ gc_status gc_sel_upload(gc_ctx *ctx, gc_sel *s) {
             return gc_cuda_fail(ctx, e, "upload selection");
         }
     }
-    int32_t **dst[] = {&s->d_types,   &s->d_type_ptr, &s->d_pair_i,   &s->d_pair_j,
-                       &s->d_pair_type, &s->d_win_t0, &s->d_win_t1,   &s->d_grp_types,
-                       &s->d_grp_off, &s->d_grp_t0,   &s->d_grp_t1,   &s->d_grp_first,
-                       &s->d_grp_win,   &s->d_nbr,      &s->d_grp_dymax};
-    for (int i = 0; i < kParts; ++i) *dst[i] = reinterpret_cast<int32_t *>(static_cast<char *>(base) + offs[i]);
-    if (s->nbr.empty()) s->d_nbr = nullptr;
+    int32_t **dst[] = {&s->d_types,    &s->d_type_ptr,  &s->d_pair_i,    &s->d_pair_j,
+                       &s->d_pair_type, &s->d_win_t0,   &s->d_win_t1,    &s->d_grp_types,
+                       &s->d_grp_off,  &s->d_grp_t0,    &s->d_grp_t1,    &s->d_grp_first,
+                       &s->d_grp_win,  &s->d_nbr,       &s->d_grp_dymax, &s->d_mask,
+                       &s->d_tree_ant, &s->d_tree_pair, &s->d_tree_sign};
+    for (int i = 0; i < kParts; ++i)
+        *dst[i] = parts[i]->empty() ? nullptr : reinterpret_cast<int32_t *>(static_cast<char *>(base) + offs[i]);
     s->d_base = base;
     s->device = ctx->device;
     return GC_OK;
@@ -218,6 +290,7 @@ gc_status gc_selection_subset(int L, int T, double p, double log_base, gc_sel **
     s->scheme = 0;
     s->L = L;
     s->T = T;
+    s->n_occ = L * L;
     s->n_ubl = k;
     s->n_cycle = 1;
     s->t_int = T;
@@ -261,6 +334,7 @@ gc_status gc_selection_lowcad(int L, int T, double p, double log_base, gc_sel **
     s->scheme = 1;
     s->L = L;
     s->T = T;
+    s->n_occ = L * L;
     s->n_ubl = (int)ord.size();
     s->n_cycle = n_cycle;
     s->t_int = t_int;
@@ -274,6 +348,76 @@ gc_status gc_selection_lowcad(int L, int T, double p, double log_base, gc_sel **
     }
     fill_pairs(s);
     fill_groups(s);
+    *out = s;
+    return GC_OK;
+}
+
+gc_status gc_selection_subset_masked(int L, int T, double p, double log_base, const uint8_t *mask, int lattice,
+                                     gc_sel **out) {
+    if (!out) return GC_EINVAL;
+    *out = nullptr;
+    if (!mask || L < 3 || L > 256 || T < 1 || !(p > 0.0) || log_base < 0.0 || log_base == 1.0 ||
+        (lattice != GC_LATTICE_SQUARE && lattice != GC_LATTICE_TRIANGULAR))
+        return GC_EINVAL;
+    std::vector<int32_t> m((size_t)L * L);
+    int n_occ = 0;
+    for (int i = 0; i < L * L; ++i) n_occ += (m[i] = mask[i] ? 1 : 0);
+    if (n_occ < 3) return GC_EINVAL;
+    const auto ord = masked_types(L, m, lattice);
+    const double target = pair_budget(n_occ, p, log_base);
+    long cum = 0;
+    int best_k = 1;
+    double best_err = -1.0;
+    for (size_t k = 0; k < ord.size(); ++k) {
+        cum += ord[k].second;
+        const double err = std::fabs((double)cum - target);
+        if (best_err < 0.0 || err < best_err) {
+            best_err = err;
+            best_k = (int)k + 1;
+        }
+    }
+    // degeneracy criterion (Sec. 5.2) by rule: both axis types, and a type
+    // that breaks the checkerboard amplitude pattern -- dx + dy even on the
+    // square lattice, (-1, 1) on the triangular one (the third unit direction)
+    auto criterion = [&](int k) {
+        bool x = false, y = false, odd_cycle = false;
+        for (int q = 0; q < k; ++q) {
+            const TypeVec &d = ord[q].first;
+            if (d.dx == 1 && d.dy == 0) x = true;
+            if (d.dx == 0 && d.dy == 1) y = true;
+            if (lattice == GC_LATTICE_SQUARE ? ((d.dx + d.dy) & 1) == 0 : (d.dx == -1 && d.dy == 1)) odd_cycle = true;
+        }
+        return x && y && odd_cycle;
+    };
+    int k = best_k;
+    while (k < (int)ord.size() && !criterion(k)) ++k;
+    if (!criterion(k)) return GC_EDEGEN;
+    gc_sel *s = new (std::nothrow) gc_sel();
+    if (!s) return GC_ENOMEM;
+    s->scheme = 0;
+    s->L = L;
+    s->T = T;
+    s->n_ubl = k;
+    s->n_cycle = 1;
+    s->t_int = T;
+    s->null_dim = 4;
+    s->target = target;
+    s->lattice = lattice;
+    s->masked = 1;
+    s->n_occ = n_occ;
+    s->mask = m;
+    for (int q = 0; q < k; ++q) {
+        s->types.push_back(ord[q].first.dx);
+        s->types.push_back(ord[q].first.dy);
+        s->win_t0.push_back(0);
+        s->win_t1.push_back(T);
+    }
+    fill_pairs(s);
+    fill_groups(s);
+    if (!fill_tree(s)) {   // the axis types must connect the array
+        delete s;
+        return GC_EDEGEN;
+    }
     *out = s;
     return GC_OK;
 }
@@ -294,6 +438,9 @@ gc_status gc_sel_info(const gc_sel *s, int32_t *info) {
     info[5] = s->t_int;
     info[6] = s->null_dim;
     info[7] = s->scheme;
+    info[8] = s->masked;
+    info[9] = s->lattice;
+    info[10] = s->n_occ;
     return GC_OK;
 }
 

@@ -20,6 +20,7 @@ GC_OK, GC_EINVAL, GC_ENOMEM, GC_ECUDA, GC_ENOCONV, GC_ETIMEOUT, GC_EDEGEN, GC_EU
 STATUS_NAMES = ["GC_OK", "GC_EINVAL", "GC_ENOMEM", "GC_ECUDA", "GC_ENOCONV", "GC_ETIMEOUT",
                 "GC_EDEGEN", "GC_EUNSUPPORTED"]
 GC_C64, GC_I4C, GC_C32H = 0, 1, 2
+LATTICES = {"square": 0, "triangular": 1}
 
 
 class GridcorrError(RuntimeError):
@@ -56,6 +57,8 @@ _lib.gc_correlate.restype = _i
 _lib.gc_selection_subset.argtypes = [_i, _i, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp)]
 _lib.gc_selection_subset.restype = _i
 _lib.gc_selection_lowcad.argtypes = [_i, _i, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp)]
+_lib.gc_selection_subset_masked.argtypes = [_i, _i, ctypes.c_double, ctypes.c_double, _vp, _i, ctypes.POINTER(_vp)]
+_lib.gc_selection_subset_masked.restype = _i
 _lib.gc_selection_lowcad.restype = _i
 _lib.gc_sel_free.argtypes = [_vp]
 _lib.gc_sel_free.restype = None
@@ -389,20 +392,38 @@ class Selection:
 
     Attributes (numpy int32 copies): types [n_ubl, 2], type_ptr [n_ubl+1],
     pair_i, pair_j [P], win_t0, win_t1 [n_ubl]; scalars L, T, P, n_ubl,
-    n_cycle, t_int, null_dim, scheme ('subset' or 'lowcad')."""
+    n_cycle, t_int, null_dim, scheme ('subset' or 'lowcad'), masked,
+    lattice ('square' or 'triangular'), n_ant (occupied points).
 
-    def __init__(self, scheme: str, L: int, T: int, p: float = 1.0, log_base: float = 2.0):
+    mask: for an array on a partly occupied lattice (e.g. hex_mask(s)), the
+    L*L occupancy of the bounding grid (subset scheme only).
+    """
+
+    def __init__(self, scheme: str, L: int, T: int, p: float = 1.0, log_base: float = 2.0,
+                 mask=None, lattice: str = "square"):
         import numpy as np
         h = _vp()
-        fn = {"subset": _lib.gc_selection_subset, "lowcad": _lib.gc_selection_lowcad}[scheme]
-        st = fn(L, T, p, log_base, ctypes.byref(h))
+        if mask is not None:
+            if scheme != "subset":
+                raise ValueError("masked arrays support the subset scheme")
+            m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
+            if m.size != L * L:
+                raise ValueError("mask must have L*L entries")
+            self.mask = m
+            st = _lib.gc_selection_subset_masked(L, T, p, log_base, m.ctypes.data_as(_vp),
+                                                 LATTICES[lattice], ctypes.byref(h))
+        else:
+            self.mask = None
+            fn = {"subset": _lib.gc_selection_subset, "lowcad": _lib.gc_selection_lowcad}[scheme]
+            st = fn(L, T, p, log_base, ctypes.byref(h))
         if st != GC_OK:
-            raise GridcorrError(st, f"gc_selection_{scheme}(L={L}, T={T}, p={p})")
+            raise GridcorrError(st, f"gc_selection_{scheme}(L={L}, T={T}, p={p}, masked={mask is not None})")
         self._h = h
-        info = (ctypes.c_int32 * 8)()
+        info = (ctypes.c_int32 * 11)()
         _lib.gc_sel_info(h, info)
         (self.L, self.T, self.P, self.n_ubl, self.n_cycle, self.t_int, self.null_dim,
-         sch) = list(info)
+         sch, self.masked, lat, self.n_ant) = list(info)
+        self.lattice = "triangular" if lat == 1 else "square"
         self.scheme = "subset" if sch == 0 else "lowcad"
         ptrs = [ctypes.POINTER(ctypes.c_int32)() for _ in range(6)]
         _lib.gc_sel_arrays(h, *[ctypes.byref(q) for q in ptrs])

@@ -72,6 +72,30 @@ def grid_positions(L: int, device="cpu") -> torch.Tensor:
     return torch.stack([x.reshape(-1), y.reshape(-1)], dim=1).to(torch.float64)
 
 
+def lattice_positions(L: int, lattice: str = "square", device="cpu") -> torch.Tensor:
+    """[N, 2] float64 physical positions of the L x L lattice points
+    (i = y*L + x): the grid itself for "square", x (1, 0) + y (1/2, sqrt3/2)
+    for "triangular" (the lattice of hexagonal arrays)."""
+    p = grid_positions(L, device)
+    if lattice == "triangular":
+        p = torch.stack([p[:, 0] + 0.5 * p[:, 1], p[:, 1] * (math.sqrt(3.0) / 2.0)], dim=1)
+    elif lattice != "square":
+        raise ValueError(lattice)
+    return p
+
+
+def hex_mask(s: int):
+    """Layout of a hexagonal array of side s (3 s (s - 1) + 1 antennas) on
+    the triangular lattice: axial coordinates (a, b) with |a|, |b|, |a + b|
+    <= s - 1 at grid point x = a + s - 1, y = b + s - 1 of the (2 s - 1)^2
+    bounding grid.  Returns (L, mask) with mask a uint8 numpy array [L * L]."""
+    import numpy as np
+    L = 2 * s - 1
+    y, x = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    m = ((x + y >= s - 1) & (x + y <= 3 * s - 3)).astype(np.uint8)
+    return L, m.reshape(-1)
+
+
 def _cnormal(n_shape, var, g, device):
     """Complex normal with E|z|^2 = var (var broadcastable)."""
     re = torch.randn(*n_shape, generator=g, device=device, dtype=torch.float32)
@@ -82,19 +106,21 @@ def _cnormal(n_shape, var, g, device):
 
 def make_voltages(seed: int, L: int, C: int, T: int, n_src: int, snr: float = 10.0,
                   device="cpu", gains: torch.Tensor | None = None, noise: bool = True,
-                  out: torch.Tensor | None = None, channel0: int = 0):
+                  out: torch.Tensor | None = None, channel0: int = 0, lattice: str = "square"):
     """Voltages [C, T, N] complex64 (row-major grid index), and the true gains.
 
     Returns (volt, gains, sky).  `out` may be a preallocated [C, T, N]
     complex64 tensor.  `channel0` offsets the channel index of the draws, so
     that channels c0..c0+C-1 of a large workload can be generated chunk by
     chunk (same sky for every chunk; pass that chunk's gains).
+    lattice: "triangular" places point i = y*L + x at x (1, 0) + y (1/2,
+    sqrt3/2) (hexagonal arrays); the voltages keep the grid layout.
     """
     N = L * L
     sky = make_sky(seed, n_src, device)
     if gains is None:
         gains = make_gains(seed, channel0 + C, N, device)[channel0:]
-    pos = grid_positions(L, device)
+    pos = lattice_positions(L, lattice, device)
     # steering phases e^{2 pi i r_i . l_k}: [K, N] complex64 (draw-time geometry)
     steer = torch.polar(torch.ones((), dtype=torch.float64, device=device),
                         _TWO_PI * (sky.l @ pos.T)).to(torch.complex64)

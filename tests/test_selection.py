@@ -55,3 +55,41 @@ def test_selection_errors(gcmod):
         gcmod.Selection("subset", 1, 10)
     with pytest.raises(gcmod.GridcorrError):
         gcmod.Selection("lowcad", 8, 0)
+
+
+@pytest.mark.parametrize("s", [3, 4, 6, 8, 11])
+def test_hex_subset_matches_oracle(gcmod, s):
+    """Masked-lattice subset selection of a hexagonal array equals the oracle's
+    (types, order, pairs), and both hexagon layouts agree."""
+    from paper_2005_03060_gb300 import synth
+    L, m = osel.hex_mask(s)
+    L2, m2 = synth.hex_mask(s)
+    assert L2 == L and np.array_equal(m, m2)
+    ref = osel.subset_layout(L, m, "triangular", 512)
+    sel = gcmod.Selection("subset", L, 512, mask=m, lattice="triangular")
+    assert sel.masked == 1 and sel.lattice == "triangular" and sel.n_ant == int(m.sum())
+    assert [tuple(t) for t in sel.types.tolist()] == ref.types
+    assert np.array_equal(sel.type_ptr, ref.type_ptr)
+    assert np.array_equal(sel.pair_i, ref.pair_i) and np.array_equal(sel.pair_j, ref.pair_j)
+    assert sel.null_dim == 4
+
+
+def test_full_mask_equals_unmasked(gcmod):
+    L = 8
+    a = gcmod.Selection("subset", L, 256)
+    b = gcmod.Selection("subset", L, 256, mask=np.ones(L * L, np.uint8))
+    assert np.array_equal(a.types, b.types) and np.array_equal(a.pair_i, b.pair_i)
+    assert np.array_equal(a.pair_j, b.pair_j)
+
+
+def test_masked_selection_errors(gcmod):
+    L = 6
+    m = np.zeros(L * L, np.uint8)
+    m[:2] = 1                                  # two antennas
+    with pytest.raises(gcmod.GridcorrError):
+        gcmod.Selection("subset", L, 64, mask=m)
+    m = np.zeros(L * L, np.uint8)
+    m[0::2] = 1                                # columns 0, 2, 4: the (1,0) type has no pair
+    with pytest.raises(gcmod.GridcorrError) as e:
+        gcmod.Selection("subset", L, 64, mask=m)
+    assert e.value.status == gcmod.GC_EDEGEN
