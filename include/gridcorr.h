@@ -162,6 +162,18 @@ GC_API gc_status gc_selection_subset(int L, int T, double p, double log_base, gc
 GC_API gc_status gc_selection_lowcad(int L, int T, double p, double log_base, gc_sel **out);
 
 /*
+ * The FFT-correlator for an array on a partly occupied lattice (layout as
+ * gc_selection_subset_masked; the paper's hexagonal arrays, Sec. 3): as
+ * gc_correlate on the L x L grid of lattice points, with the points where
+ * mask[i] == 0 (host, L*L bytes) contributing nothing (their gains are not
+ * read), and V^unique(d) = R(d) / (T N_d) with N_d the number of pairs of
+ * occupied points at lattice separation d (computed on the host per call,
+ * O(antennas^2)); lags without a pair are 0.  Uses the context workspace.
+ */
+GC_API gc_status gc_correlate_masked(gc_ctx *ctx, const void *volt, int vfmt, int L, int C, int T,
+                                     const uint8_t *mask, const float *gains, float *vunique, void *stream);
+
+/*
  * Subset selection for an array on a partly occupied lattice -- the paper's
  * own arrays are hexagonal (Sec. 3; Fig. 13's 331 antennas).  The array is
  * held as the L x L bounding grid of lattice points (point i = y L + x) with

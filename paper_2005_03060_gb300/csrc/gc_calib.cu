@@ -53,6 +53,10 @@ struct CalParams {
     const int32_t *nbr;          // [2][n_ubl][N] neighbour table or null
     int ax, ay;                  // indices of types (1,0) and (0,1)
     int stencil;                 // matrix-free operator by per-antenna gather (<= kStencilTypes types)
+    // partly occupied lattice (null / L*L otherwise): occupancy [N], the
+    // breadth-first start-point tree over the axis types, antennas
+    const int32_t *mask, *tree_ant, *tree_pair, *tree_sign;
+    int n_occ;
     int t_autos;                 // samples summed in autos
     float2 *gains;               // [C][N] (in: warm start when warm != 0)
     float2 *vmodel;              // [C][n_ubl]
@@ -134,20 +138,35 @@ __device__ void block_sum(R (&v)[NV], R *red /* smem [32][NV] */) {
 template <class R>
 __device__ void start_point(const CalParams &p, int c, R *xg, R *xv, R *red, R *phi /* N reals of scratch */) {
     const int L = p.L, N = p.N;
-    if (threadIdx.x == 0) {
-        phi[0] = 0;
-        for (int x = 1; x < L; ++x) {
-            const float2 v = vobs(p, c, pair_index(p, p.ax, x - 1, 0));
-            phi[x] = phi[x - 1] + (R)atan2f(v.y, v.x);
+    if (p.tree_ant) {
+        // partly occupied lattice: walk the breadth-first tree, phi_i - phi_j
+        // = arg V_p along each linking pair p = (i, j); empty points get 0
+        for (int i = threadIdx.x; i < N; i += blockDim.x) phi[i] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int h = 1; h < p.n_occ; ++h) {
+                const int a = p.tree_ant[h], q = p.tree_pair[h];
+                const float2 v = vobs(p, c, q);
+                const R arg = (R)atan2f(v.y, v.x);
+                phi[a] = p.tree_sign[h] > 0 ? phi[p.pair_j[q]] + arg : phi[p.pair_i[q]] - arg;
+            }
         }
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < L; x += blockDim.x) {
-        R acc = phi[x];
-        for (int y = 1; y < L; ++y) {
-            const float2 v = vobs(p, c, pair_index(p, p.ay, x, y - 1));
-            acc += (R)atan2f(v.y, v.x);
-            phi[y * L + x] = acc;
+    } else {
+        if (threadIdx.x == 0) {
+            phi[0] = 0;
+            for (int x = 1; x < L; ++x) {
+                const float2 v = vobs(p, c, pair_index(p, p.ax, x - 1, 0));
+                phi[x] = phi[x - 1] + (R)atan2f(v.y, v.x);
+            }
+        }
+        __syncthreads();
+        for (int x = threadIdx.x; x < L; x += blockDim.x) {
+            R acc = phi[x];
+            for (int y = 1; y < L; ++y) {
+                const float2 v = vobs(p, c, pair_index(p, p.ay, x, y - 1));
+                acc += (R)atan2f(v.y, v.x);
+                phi[y * L + x] = acc;
+            }
         }
     }
     __syncthreads();
@@ -164,8 +183,9 @@ __device__ void start_point(const CalParams &p, int c, R *xg, R *xv, R *red, R *
             s = (R)sf;
             co = (R)cf;
         }
-        xg[2 * i] = co;
-        xg[2 * i + 1] = s;
+        const bool occ = !p.mask || p.mask[i];   // empty points hold g = 0
+        xg[2 * i] = occ ? co : (R)0;
+        xg[2 * i + 1] = occ ? s : (R)0;
     }
     __syncthreads();
     // V_alpha: one warp per type
@@ -675,9 +695,10 @@ __device__ void gn_project(const CalParams &p, GnWork<R> &w, R *red) {
 // arg V_(0,1) = 0, arg g_0 = 0.  Works on float2 gains in place.
 __device__ void output_convention(const CalParams &p, float2 *g, float2 *V, double *red) {
     double s[1] = {0.0};
-    for (int i = threadIdx.x; i < p.N; i += blockDim.x) s[0] += log(hypot((double)g[i].x, (double)g[i].y));
+    for (int i = threadIdx.x; i < p.N; i += blockDim.x)
+        if (!p.mask || p.mask[i]) s[0] += log(hypot((double)g[i].x, (double)g[i].y));
     block_sum<double, 1>(s, red);
-    const double sc = exp(s[0] / p.N);
+    const double sc = exp(s[0] / p.n_occ);
     const double kx = atan2((double)V[p.ax].y, (double)V[p.ax].x);
     const double ky = atan2((double)V[p.ay].y, (double)V[p.ay].x);
     __syncthreads();
@@ -688,8 +709,10 @@ __device__ void output_convention(const CalParams &p, float2 *g, float2 *V, doub
         const double vx = V[k].x * sc * sc, vy = V[k].y * sc * sc;
         V[k] = make_float2((float)(vx * cs - vy * sn), (float)(vx * sn + vy * cs));
     }
-    // phase of g_0 after the slope change (x = y = 0 for antenna 0)
-    const double psi = atan2((double)g[0].y, (double)g[0].x);
+    // phase of the first antenna after the slope change (antenna 0 of a full
+    // grid, at x = y = 0; the first occupied point of a partly occupied one)
+    const int r0 = p.tree_ant ? p.tree_ant[0] : 0;
+    const double psi = atan2((double)g[r0].y, (double)g[r0].x) + kx * (r0 % p.L) + ky * (r0 / p.L);
     __syncthreads();
     for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
         const double ph = kx * (i % p.L) + ky * (i / p.L) - psi;
@@ -730,7 +753,7 @@ __device__ void finish_channel(const CalParams &p, int c, const R *xg, const R *
     if (threadIdx.x == 0) {
         gc_calstats s;
         s.chi2 = acc[0];
-        s.dof = p.P - p.N - p.n_ubl + 2;
+        s.dof = p.P - p.n_occ - p.n_ubl + 2;
         s.chi2r = p.autos && s.dof > 0 ? acc[1] / s.dof : -1.0;
         s.iters = iters;
         s.status = st;
@@ -1741,7 +1764,7 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
     const uint64_t t_start = gc_globaltimer();
     if (p.warm) {
         for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
-            const float2 g = p.gains[(size_t)c * p.N + i];
+            const float2 g = (!p.mask || p.mask[i]) ? p.gains[(size_t)c * p.N + i] : make_float2(0.f, 0.f);
             w.xg[2 * i] = g.x;
             w.xg[2 * i + 1] = g.y;
         }
@@ -2382,6 +2405,8 @@ static gc_status fill_params(gc_ctx *ctx, gc_sel *sel, int C, const void *vreduc
         return gc_fail(ctx, GC_EINVAL, "gc_calibrate: null argument");
     if (vfmt != GC_C64 && vfmt != GC_I4C) return gc_fail(ctx, GC_EINVAL, "gc_calibrate: unknown format");
     if (sel->null_dim != 4) return gc_fail(ctx, GC_EDEGEN, "gc_calibrate: selection has extra degeneracies");
+    if (sel->masked && o.solver != GC_LINCAL_CG)
+        return gc_fail(ctx, GC_EUNSUPPORTED, "gc_calibrate: partly occupied lattices are built for GC_LINCAL_CG");
     if (o.solver != GC_LINCAL && o.solver != GC_OMNICAL && o.solver != GC_LINCAL_CG)
         return gc_fail(ctx, GC_EINVAL, "gc_calibrate: solver");
     if (o.precision != GC_FP64 && o.precision != GC_FP32) return gc_fail(ctx, GC_EINVAL, "gc_calibrate: precision");
@@ -2414,8 +2439,14 @@ static gc_status fill_params(gc_ctx *ctx, gc_sel *sel, int C, const void *vreduc
     p.nbr = sel->d_nbr;
     p.ax = ax;
     p.ay = ay;
-    // both selection builders take baseline-types whole, in pair_index order
-    p.stencil = ctx->tune[GC_TUNE_CAL_OP] == 0 && sel->n_ubl <= kStencilTypes ? 1 : 0;
+    // both full-grid selection builders take baseline-types whole, in
+    // pair_index order; a partly occupied lattice takes the pair-list form
+    p.stencil = ctx->tune[GC_TUNE_CAL_OP] == 0 && sel->n_ubl <= kStencilTypes && !sel->masked ? 1 : 0;
+    p.mask = sel->masked ? sel->d_mask : nullptr;
+    p.tree_ant = sel->masked ? sel->d_tree_ant : nullptr;
+    p.tree_pair = sel->masked ? sel->d_tree_pair : nullptr;
+    p.tree_sign = sel->masked ? sel->d_tree_sign : nullptr;
+    p.n_occ = sel->masked ? sel->n_occ : sel->L * sel->L;
     p.t_autos = sel->n_cycle * sel->t_int;
     p.gains = reinterpret_cast<float2 *>(gains);
     p.vmodel = reinterpret_cast<float2 *>(vmodel);

@@ -30,6 +30,7 @@ struct Chi2Params {
     float2 *dg, *dV;         // [C][N], [C][n_ubl]
     float2 *resid_out;       // [C][P] residuals stored by the forward pass, or null
     const float2 *resid_in;  // [C][P] residuals the backward pass reads, or null (recompute)
+    const int32_t *pair_of2; // partly occupied lattice: pair index of (r_j + d_k, r_j) by [k][j], or null
 };
 
 __device__ __forceinline__ float2 obs(const Chi2Params &p, int c, int q) {
@@ -62,6 +63,7 @@ __device__ __forceinline__ int pidx(const Chi2Params &p, int k, int xj, int yj) 
     const int dx = p.types[2 * k], dy = p.types[2 * k + 1], L = p.L;
     const int xi = xj + dx, yi = yj + dy;
     if (xj < 0 || xj >= L || yj < 0 || yj >= L || xi < 0 || xi >= L || yi < 0 || yi >= L) return -1;
+    if (p.pair_of2) return p.pair_of2[(size_t)k * p.N + yj * L + xj];
     return p.type_ptr[k] + (yj - max(0, -dy)) * (L - abs(dx)) + (xj - max(0, -dx));
 }
 
@@ -178,6 +180,11 @@ gc_status chi2_setup(gc_ctx *ctx, const void *vred, int vfmt, const gc_sel *csel
     p.dg = p.dV = nullptr;
     p.resid_out = nullptr;
     p.resid_in = nullptr;
+    p.pair_of2 = nullptr;
+    if (sel->masked) {
+        if (!sel->d_nbr) return gc_fail(ctx, GC_EUNSUPPORTED, "gc_chi2: masked selection without pair table");
+        p.pair_of2 = sel->d_nbr + (size_t)sel->n_ubl * p.N;
+    }
     return GC_OK;
 }
 

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <vector>
 
 #include "gc_internal.h"
 
@@ -179,6 +180,7 @@ struct Params {
     int chunk_len;           // multiple of G*NT
     int n_chunks;
     int n_items;             // C * R * n_chunks
+    const unsigned char *mask = nullptr;   // [L*L] occupied lattice points, or null (all)
 };
 
 // Copy the G*NT samples starting at t into stage (plain-load fallback for
@@ -309,7 +311,7 @@ fftcorr_accumulate(const __grid_constant__ CUtensorMap tmap, const Params p) {
         for (int i = tid; i < K::LMAX * K::CROW; i += K::NTHREADS) {
             const int x = i % K::CROW, y = i / K::CROW;
             float2 cc = make_float2(0.f, 0.f);
-            if (x < L && y < L) {
+            if (x < L && y < L && (!p.mask || p.mask[y * L + x])) {
                 const float2 gg = p.gains[(size_t)c * L * L + y * L + x];
                 const float d = gg.x * gg.x + gg.y * gg.y;
                 cc = make_float2(gg.x / d, -gg.y / d);
@@ -496,7 +498,8 @@ fftcorr_accumulate(const __grid_constant__ CUtensorMap tmap, const Params p) {
 // ----------------------------------------------------------------- finalize
 template <int M>
 __global__ void __launch_bounds__(256)
-fftcorr_finalize(const float *__restrict__ ppart, int n_parts, float2 *__restrict__ vunique, int L, int T) {
+fftcorr_finalize(const float *__restrict__ ppart, int n_parts, float2 *__restrict__ vunique, int L, int T,
+                 const float *__restrict__ ndtab) {
     extern __shared__ __align__(128) unsigned char smem[];
     float *P = reinterpret_cast<float *>(smem);                 // [M][M]
     float2 *Q = reinterpret_cast<float2 *>(smem + M * M * 4);   // [M][W]
@@ -538,8 +541,9 @@ fftcorr_finalize(const float *__restrict__ ppart, int n_parts, float2 *__restric
             re = fmaf(qv.x, w.x, fmaf(qv.y, w.y, re));
             im = fmaf(qv.y, w.x, fmaf(-qv.x, w.y, im));
         }
-        const int nd = (L - (dx < 0 ? -dx : dx)) * (L - (dy < 0 ? -dy : dy));
-        const float s = (float)(1.0 / ((double)M * M * (double)T * nd));
+        // N_d: pairs per lag (a partly occupied lattice passes its table)
+        const double nd = ndtab ? (double)ndtab[idx] : (double)((L - (dx < 0 ? -dx : dx)) * (L - (dy < 0 ? -dy : dy)));
+        const float s = nd > 0.0 ? (float)(1.0 / ((double)M * M * (double)T * nd)) : 0.f;
         vunique[(size_t)c * W * W + idx] = make_float2(re * s, im * s);
     }
 }
@@ -585,7 +589,8 @@ fftcorr_finalize_rows(const float *__restrict__ ppart, int n_parts, float2 *__re
 
 template <int M>
 __global__ void __launch_bounds__(256)
-fftcorr_finalize_cols(const float2 *__restrict__ Q, float2 *__restrict__ vunique, int L, int T) {
+fftcorr_finalize_cols(const float2 *__restrict__ Q, float2 *__restrict__ vunique, int L, int T,
+                      const float *__restrict__ ndtab) {
     __shared__ float2 Qs[M][kFinCols];
     __shared__ float2 tws[M];
     const int c = blockIdx.x, dx0 = blockIdx.y * kFinCols, W = 2 * L - 1;
@@ -609,8 +614,9 @@ fftcorr_finalize_cols(const float2 *__restrict__ Q, float2 *__restrict__ vunique
             re = fmaf(qv.x, w.x, fmaf(qv.y, w.y, re));
             im = fmaf(qv.y, w.x, fmaf(-qv.x, w.y, im));
         }
-        const int nd = (L - (dx < 0 ? -dx : dx)) * (L - (dy < 0 ? -dy : dy));
-        const float s = (float)(1.0 / ((double)M * M * (double)T * nd));
+        const double nd = ndtab ? (double)ndtab[(size_t)dyi * W + dxi]
+                                : (double)((L - (dx < 0 ? -dx : dx)) * (L - (dy < 0 ? -dy : dy)));
+        const float s = nd > 0.0 ? (float)(1.0 / ((double)M * M * (double)T * nd)) : 0.f;
         vunique[(size_t)c * W * W + (size_t)dyi * W + dxi] = make_float2(re * s, im * s);
     }
 }
@@ -624,8 +630,10 @@ CUtensorMapDataType tma_dtype() {
 
 template <class K>
 struct Launcher {
+    // h_mask (host, L*L, or null): a partly occupied lattice -- zero
+    // coefficients at the empty points and N_d from the mask's pairs
     static gc_status run(gc_ctx *ctx, const void *volt, int L, int C, int T, const float *gains,
-                         float *vunique, cudaStream_t stream) {
+                         float *vunique, cudaStream_t stream, const unsigned char *h_mask = nullptr) {
         const int N = L * L;
         const bool tma = gc_aligned(volt, 16) && ((size_t)L * K::ESZ) % 16 == 0;
         auto kern = tma ? fftcorr_accumulate<K, true> : fftcorr_accumulate<K, false>;
@@ -670,9 +678,33 @@ struct Launcher {
         p.n_items = C * K::R * best_n;
         const size_t part_bytes = ((size_t)C * best_n * K::M * K::M * sizeof(float) + 255) / 256 * 256;
         const size_t q_bytes = K::M > 128 ? (size_t)C * K::M * (2 * L - 1) * sizeof(float2) : 0;
-        gc_status st = gc_scratch_reserve(ctx, part_bytes + q_bytes);
+        const int Wd = 2 * L - 1;
+        const size_t nd_bytes = h_mask ? ((size_t)Wd * Wd * sizeof(float) + 255) / 256 * 256 : 0;
+        const size_t mask_bytes = h_mask ? ((size_t)N + 255) / 256 * 256 : 0;
+        const size_t qb = (q_bytes + 255) / 256 * 256;
+        gc_status st = gc_scratch_reserve(ctx, part_bytes + qb + nd_bytes + mask_bytes);
         if (st != GC_OK) return st;
         p.ppart = reinterpret_cast<float *>(ctx->scratch);
+        const float *ndtab = nullptr;
+        if (h_mask) {
+            // N_d = number of occupied pairs per lag (host, once per call)
+            std::vector<float> nd((size_t)Wd * Wd, 0.f);
+            std::vector<int> occ;
+            for (int i = 0; i < N; ++i)
+                if (h_mask[i]) occ.push_back(i);
+            for (int a : occ)
+                for (int b : occ) nd[(size_t)(a / L - b / L + L - 1) * Wd + (a % L - b % L + L - 1)] += 1.f;
+            char *aux = static_cast<char *>(ctx->scratch) + part_bytes + qb;
+            std::vector<unsigned char> m01(N);
+            for (int i = 0; i < N; ++i) m01[i] = h_mask[i] ? 1 : 0;
+            // pageable sources: the calls return once the data is staged
+            e = cudaMemcpyAsync(aux, nd.data(), (size_t)Wd * Wd * sizeof(float), cudaMemcpyHostToDevice, stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(aux + nd_bytes, m01.data(), (size_t)N, cudaMemcpyHostToDevice, stream);
+            if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "upload lattice mask");
+            ndtab = reinterpret_cast<const float *>(aux);
+            p.mask = reinterpret_cast<const unsigned char *>(aux + nd_bytes);
+        }
 
         CUtensorMap tmap;
         memset(&tmap, 0, sizeof tmap);
@@ -697,7 +729,7 @@ struct Launcher {
             rec = gc_prof_begin(ctx, stream, "fftcorr_finalize");
             fftcorr_finalize_rows<K::M><<<dim3(C, K::M / kFinRows), 256, 0, stream>>>(p.ppart, best_n, Q, L);
             fftcorr_finalize_cols<K::M><<<dim3(C, (W + kFinCols - 1) / kFinCols), 256, 0, stream>>>(
-                Q, reinterpret_cast<float2 *>(vunique), L, T);
+                Q, reinterpret_cast<float2 *>(vunique), L, T, ndtab);
             gc_prof_end(ctx, stream, rec);
         } else {
             const size_t fsmem = (size_t)K::M * K::M * 4 + (size_t)K::M * W * 8 + K::M * 8;
@@ -705,7 +737,7 @@ struct Launcher {
             e = cudaFuncSetAttribute(fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
             if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(fftcorr_finalize)");
             rec = gc_prof_begin(ctx, stream, "fftcorr_finalize");
-            fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n, reinterpret_cast<float2 *>(vunique), L, T);
+            fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n, reinterpret_cast<float2 *>(vunique), L, T, ndtab);
             gc_prof_end(ctx, stream, rec);
         }
         e = cudaGetLastError();
@@ -735,8 +767,8 @@ using CfgH128 = Cfg<128, 4, 32, 32, 1, 2, GC_C32H>;
 
 }  // namespace
 
-extern "C" gc_status gc_correlate(gc_ctx *ctx, const void *volt, int vfmt, int L, int C, int T,
-                                  const float *gains, float *vunique, void *stream) {
+static gc_status correlate_impl(gc_ctx *ctx, const void *volt, int vfmt, int L, int C, int T, const float *gains,
+                                float *vunique, void *stream, const unsigned char *h_mask) {
     if (!ctx) return GC_EINVAL;
     ctx->last_error.clear();
     if (!volt || !gains || !vunique) return gc_fail(ctx, GC_EINVAL, "gc_correlate: null buffer");
@@ -755,28 +787,39 @@ extern "C" gc_status gc_correlate(gc_ctx *ctx, const void *volt, int vfmt, int L
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (vfmt == GC_C64) {
         switch (M) {
-            case 16: return Launcher<CfgC16>::run(ctx, volt, L, C, T, gains, vunique, s);
-            case 32: return Launcher<CfgC32>::run(ctx, volt, L, C, T, gains, vunique, s);
-            case 64: return Launcher<CfgC64>::run(ctx, volt, L, C, T, gains, vunique, s);
-            case 128: return Launcher<CfgC128>::run(ctx, volt, L, C, T, gains, vunique, s);
+            case 16: return Launcher<CfgC16>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
+            case 32: return Launcher<CfgC32>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
+            case 64: return Launcher<CfgC64>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
+            case 128: return Launcher<CfgC128>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
         }
     } else if (vfmt == GC_C32H) {
         switch (M) {
-            case 16: return Launcher<CfgH16>::run(ctx, volt, L, C, T, gains, vunique, s);
-            case 32: return Launcher<CfgH32>::run(ctx, volt, L, C, T, gains, vunique, s);
-            case 64: return Launcher<CfgH64>::run(ctx, volt, L, C, T, gains, vunique, s);
-            case 128: return Launcher<CfgH128>::run(ctx, volt, L, C, T, gains, vunique, s);
+            case 16: return Launcher<CfgH16>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
+            case 32: return Launcher<CfgH32>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
+            case 64: return Launcher<CfgH64>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
+            case 128: return Launcher<CfgH128>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
         }
     } else {
         switch (M) {
-            case 16: return Launcher<CfgI16>::run(ctx, volt, L, C, T, gains, vunique, s);
-            case 32: return Launcher<CfgI32>::run(ctx, volt, L, C, T, gains, vunique, s);
-            case 64: return Launcher<CfgI64>::run(ctx, volt, L, C, T, gains, vunique, s);
-            case 128: return Launcher<CfgI128>::run(ctx, volt, L, C, T, gains, vunique, s);
-            case 256: return Launcher<CfgI256>::run(ctx, volt, L, C, T, gains, vunique, s);
+            case 16: return Launcher<CfgI16>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
+            case 32: return Launcher<CfgI32>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
+            case 64: return Launcher<CfgI64>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
+            case 128: return Launcher<CfgI128>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
+            case 256: return Launcher<CfgI256>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
         }
     }
     return gc_fail(ctx, GC_EUNSUPPORTED, "gc_correlate: no kernel for this grid size");
+}
+
+extern "C" gc_status gc_correlate(gc_ctx *ctx, const void *volt, int vfmt, int L, int C, int T,
+                                  const float *gains, float *vunique, void *stream) {
+    return correlate_impl(ctx, volt, vfmt, L, C, T, gains, vunique, stream, nullptr);
+}
+
+extern "C" gc_status gc_correlate_masked(gc_ctx *ctx, const void *volt, int vfmt, int L, int C, int T,
+                                         const uint8_t *mask, const float *gains, float *vunique, void *stream) {
+    if (ctx && !mask) return gc_fail(ctx, GC_EINVAL, "gc_correlate_masked: null mask");
+    return correlate_impl(ctx, volt, vfmt, L, C, T, gains, vunique, stream, mask);
 }
 
 // ============================================================================
@@ -906,7 +949,7 @@ gc_status noalloc_run(const NoallocDev &d, const void *volt, int L, int C, int T
     auto fin = fftcorr_finalize<K::M>;
     if (cudaFuncSetAttribute(fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem) != cudaSuccess)
         return GC_ECUDA;
-    fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n, reinterpret_cast<float2 *>(vunique), L, T);
+    fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n, reinterpret_cast<float2 *>(vunique), L, T, nullptr);
     if (cudaGetLastError() != cudaSuccess) return GC_ECUDA;
     return GC_OK;
 }

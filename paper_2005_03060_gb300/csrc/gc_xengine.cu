@@ -45,6 +45,10 @@ struct XParams {
     int rows_stage;           // 1: stage only the block's rows plus the dy halo
     size_t stage_stride;      // bytes per stage buffer (ns staged samples)
     int conv_recs;            // 4+4-bit: expanded antenna records (staged antennas + a zero record)
+    // partly occupied lattice: pair index of (r_j + d_k, r_j) by [type][j],
+    // -1 where either point is empty (null: every pair of the grid is in
+    // the selection, at its arithmetic index)
+    const int32_t *pair_of;
 };
 
 template <int VF>
@@ -62,7 +66,7 @@ template <int VF, int NTY, int NP>
 __global__ void __launch_bounds__(kXThreads, 2) xeng_accumulate(const XParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[2];
-    __shared__ int s_dx[GC_XENG_NTY], s_dy[GC_XENG_NTY], s_base[GC_XENG_NTY];
+    __shared__ int s_dx[GC_XENG_NTY], s_dy[GC_XENG_NTY], s_base[GC_XENG_NTY], s_type[GC_XENG_NTY];
     __shared__ int s_err;
     constexpr bool kI4 = VF == GC_I4C;
     const int tid = threadIdx.x;
@@ -103,6 +107,7 @@ __global__ void __launch_bounds__(kXThreads, 2) xeng_accumulate(const XParams p)
             s_dx[tid] = p.types[2 * k];
             s_dy[tid] = p.types[2 * k + 1];
             s_base[tid] = p.type_ptr[k];
+            s_type[tid] = k;
         }
         const int j = rb * kXThreads + tid;
         const int x = j % L, y = j / L;
@@ -298,9 +303,12 @@ __global__ void __launch_bounds__(kXThreads, 2) xeng_accumulate(const XParams p)
                     const int xlo = max(0, -dx), ylo = max(0, -dy);
                     const int xi = x + dx, yi = y + dy;
                     if (xi >= 0 && xi < L && yi >= 0 && yi < L) {
-                        const size_t o = s_base[k] + (y - ylo) * (L - abs(dx)) + (x - xlo);
-                        if constexpr (kI4) reinterpret_cast<int2 *>(out)[o] = make_int2(ire[k], iim[k]);
-                        else out[o] = acc[k];
+                        long o = s_base[k] + (y - ylo) * (L - abs(dx)) + (x - xlo);
+                        if (p.pair_of) o = p.pair_of[(size_t)s_type[k] * p.N + j];
+                        if (o >= 0) {
+                            if constexpr (kI4) reinterpret_cast<int2 *>(out)[o] = make_int2(ire[k], iim[k]);
+                            else out[o] = acc[k];
+                        }
                     }
                 }
             }
@@ -475,6 +483,11 @@ extern "C" gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, i
     p.rows_stage = rows_stage;
     p.stage_stride = stage_stride;
     p.conv_recs = conv_recs;
+    p.pair_of = nullptr;
+    if (sel->masked) {
+        if (!sel->d_nbr) return gc_fail(ctx, GC_EUNSUPPORTED, "gc_reduce: masked selection without pair table");
+        p.pair_of = sel->d_nbr + (size_t)sel->n_ubl * N;   // antenna as the second member
+    }
     const int grid = (int)std::min<long>(p.n_items, slots);
     int rec = gc_prof_begin(ctx, s, "xeng_accumulate");
     void *args[] = {&p};

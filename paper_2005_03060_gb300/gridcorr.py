@@ -54,6 +54,8 @@ _lib.gc_profile_read.argtypes = [_vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_d
 _lib.gc_profile_read.restype = _i
 _lib.gc_correlate.argtypes = [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp]
 _lib.gc_correlate.restype = _i
+_lib.gc_correlate_masked.argtypes = [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp]
+_lib.gc_correlate_masked.restype = _i
 _lib.gc_selection_subset.argtypes = [_i, _i, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp)]
 _lib.gc_selection_subset.restype = _i
 _lib.gc_selection_lowcad.argtypes = [_i, _i, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp)]
@@ -178,10 +180,11 @@ class Context:
 
     # ------------------------------------------------------------------ correlate
     def correlate(self, volt: torch.Tensor, gains: torch.Tensor, L: int | None = None,
-                  out: torch.Tensor | None = None) -> torch.Tensor:
+                  out: torch.Tensor | None = None, mask=None) -> torch.Tensor:
         """V^unique [C, 2L-1, 2L-1] complex64 from voltages [C, T, L*L]
         (complex64; binary16 pairs as complex32 [C, T, L*L] or float16
-        [C, T, L*L, 2]; or uint8/int8 4+4-bit) and gains [C, L*L] complex64."""
+        [C, T, L*L, 2]; or uint8/int8 4+4-bit) and gains [C, L*L] complex64.
+        mask: L*L occupancy of a partly occupied lattice (gc_correlate_masked)."""
         vfmt, (C, T, N) = _volt_format(volt)
         L = L or int(round(N ** 0.5))
         if L * L != N:
@@ -194,9 +197,18 @@ class Context:
         W = 2 * L - 1
         if out is None:
             out = torch.empty(C, W, W, dtype=torch.complex64, device=volt.device)
-        self.check(_lib.gc_correlate(self._h, _vp(volt.data_ptr()), vfmt, L, C, T,
-                                     _vp(gains.data_ptr()), _vp(out.data_ptr()),
-                                     _vp(_stream_ptr(volt.device))))
+        if mask is None:
+            self.check(_lib.gc_correlate(self._h, _vp(volt.data_ptr()), vfmt, L, C, T,
+                                         _vp(gains.data_ptr()), _vp(out.data_ptr()),
+                                         _vp(_stream_ptr(volt.device))))
+        else:
+            import numpy as np
+            m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
+            if m.size != N:
+                raise ValueError("mask must have L*L entries")
+            self.check(_lib.gc_correlate_masked(self._h, _vp(volt.data_ptr()), vfmt, L, C, T,
+                                                m.ctypes.data_as(_vp), _vp(gains.data_ptr()),
+                                                _vp(out.data_ptr()), _vp(_stream_ptr(volt.device))))
         return out
 
     # ------------------------------------------------------------------ reduce
