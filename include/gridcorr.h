@@ -188,10 +188,16 @@ GC_API gc_status gc_correlate_masked(gc_ctx *ctx, const void *volt, int vfmt, in
  * (-1, 1) (triangular).  GC_EDEGEN when no prefix satisfies it or the axis
  * types do not connect the array; GC_EINVAL for a NULL mask, fewer than 3
  * antennas or the size limits of gc_selection_subset.  Works with
- * gc_reduce, gc_calibrate (GC_LINCAL_CG) and gc_correlate_masked.
+ * gc_reduce, gc_calibrate (GC_LINCAL_CG), gc_chi2 and gc_correlate_masked.
  */
 typedef enum gc_lattice { GC_LATTICE_SQUARE = 0, GC_LATTICE_TRIANGULAR = 1 } gc_lattice;
 GC_API gc_status gc_selection_subset_masked(int L, int T, double p, double log_base, const uint8_t *mask,
+                                            int lattice, gc_sel **out);
+/* Low-cadence selection (Sec. 4) on a partly occupied lattice: every type
+ * with a pair between occupied points, packed as gc_selection_lowcad with
+ * N the occupied points.  GC_EDEGEN when the axis types do not connect the
+ * array; other errors as gc_selection_lowcad. */
+GC_API gc_status gc_selection_lowcad_masked(int L, int T, double p, double log_base, const uint8_t *mask,
                                             int lattice, gc_sel **out);
 GC_API void gc_sel_free(gc_sel *sel);
 /* info[11] = {L, T, P (pairs), n_ubl (types), n_cycle, t_int, null_dim,

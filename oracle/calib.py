@@ -383,17 +383,39 @@ def logcal_matrices(L, types, pi, pj, alpha):
     return A, B
 
 
-def gain_variance_prediction(L, types, pi, pj, alpha):
+def logcal_normal_matrices(N, types, pi, pj, alpha):
+    """A^T A and B^T B of Eq. logcal for N antennas, summed pair by pair
+    (the outer products of the rows e_i + e_j + e_alpha and e_i - e_j +
+    e_alpha): the same integers as A.T @ A and B.T @ B without forming the
+    P x (N + n_ubl) design matrices, for arrays with many pairs."""
+    nu = len(types)
+    pi, pj = np.asarray(pi, np.int64), np.asarray(pj, np.int64)
+    ka = N + np.asarray(alpha, np.int64)
+    AtA = np.zeros((N + nu, N + nu))
+    BtB = np.zeros((N + nu, N + nu))
+    idx = [pi, pj, ka]
+    sa = [1.0, 1.0, 1.0]
+    sb = [1.0, -1.0, 1.0]
+    for u in range(3):
+        for v in range(3):
+            np.add.at(AtA, (idx[u], idx[v]), sa[u] * sa[v])
+            np.add.at(BtB, (idx[u], idx[v]), sb[u] * sb[v])
+    return AtA, BtB
+
+
+def gain_variance_prediction(L, types, pi, pj, alpha, N=None):
     """diag[(A^T A)^+]_{N x N} of Eq. gaincov, amplitude + phase parts.
 
     The pseudo-inverse leaves out the degenerate directions, which the
-    paper's comparison fixes against the true gains.
+    paper's comparison fixes against the true gains.  N: antennas when the
+    pair indices are not those of an L x L grid (e.g. a hexagonal array in
+    its occupied-point numbering); default L * L.
     """
-    N = L * L
-    A, B = logcal_matrices(L, types, pi, pj, alpha)
+    N = L * L if N is None else N
+    AtA, BtB = logcal_normal_matrices(N, types, pi, pj, alpha)
     # the exact degeneracies (Sec. 5.2) are singular values at rounding level;
     # a relative cut-off of 1e-9 leaves them out (the smallest physical
     # singular values of these normal matrices are ~1e-4 of the largest)
-    ca = np.linalg.pinv(A.T @ A, rcond=1e-9, hermitian=True)
-    cb = np.linalg.pinv(B.T @ B, rcond=1e-9, hermitian=True)
+    ca = np.linalg.pinv(AtA, rcond=1e-9, hermitian=True)
+    cb = np.linalg.pinv(BtB, rcond=1e-9, hermitian=True)
     return np.diag(ca)[:N], np.diag(cb)[:N]

@@ -331,3 +331,38 @@ def compact(sel: Selection, mask):
     col[occ] = np.arange(len(occ))
     pos = np.stack([occ % sel.L, occ // sel.L], 1).astype(float)
     return col[sel.pair_i], col[sel.pair_j], pos
+
+
+def lowcad_layout(L: int, mask, lattice: str, T: int, p: float = 1.0, log_base: float = 2.0) -> Selection:
+    """Low-cadence calibration (Sec. 4) on a masked lattice: every type with
+    an occupied pair, first-fit into cycles of floor(p N log N) pairs (N the
+    occupied points), t_int = floor(T / N_cycle)."""
+    mask = np.asarray(mask, np.uint8)
+    N = int(mask.sum())
+    ordered, counts = layout_types(L, mask, lattice)
+    cap = int(math.floor(budget(N, p, log_base)))
+    remaining, cycle_of = [], []
+    for n in counts:
+        if n > cap:
+            raise ValueError("a redundant group exceeds the per-cycle capacity")
+        for c, r in enumerate(remaining):
+            if r >= n:
+                remaining[c] -= n
+                cycle_of.append(c)
+                break
+        else:
+            remaining.append(cap - n)
+            cycle_of.append(len(remaining) - 1)
+    n_cycle = len(remaining)
+    t_int = T // n_cycle
+    ptr, pi, pj = [0], [], []
+    for d in ordered:
+        prs = masked_type_pairs(L, mask, d)
+        pi += [a for a, _ in prs]
+        pj += [b for _, b in prs]
+        ptr.append(len(pi))
+    t0 = [c * t_int for c in cycle_of]
+    t1 = [(c + 1) * t_int for c in cycle_of]
+    return Selection(L, ordered, np.asarray(ptr, np.int32), np.asarray(pi, np.int32), np.asarray(pj, np.int32),
+                     np.asarray(t0, np.int32), np.asarray(t1, np.int32), n_cycle=n_cycle, t_int=t_int,
+                     null_dim=4, extra=dict(cap=cap, cycle_of=cycle_of, mask=mask, lattice=lattice, N=N))

@@ -422,6 +422,67 @@ gc_status gc_selection_subset_masked(int L, int T, double p, double log_base, co
     return GC_OK;
 }
 
+gc_status gc_selection_lowcad_masked(int L, int T, double p, double log_base, const uint8_t *mask, int lattice,
+                                     gc_sel **out) {
+    if (!out) return GC_EINVAL;
+    *out = nullptr;
+    if (!mask || L < 3 || L > 256 || T < 1 || !(p > 0.0) || log_base < 0.0 || log_base == 1.0 ||
+        (lattice != GC_LATTICE_SQUARE && lattice != GC_LATTICE_TRIANGULAR))
+        return GC_EINVAL;
+    std::vector<int32_t> m((size_t)L * L);
+    int n_occ = 0;
+    for (int i = 0; i < L * L; ++i) n_occ += (m[i] = mask[i] ? 1 : 0);
+    if (n_occ < 3) return GC_EINVAL;
+    const auto ord = masked_types(L, m, lattice);
+    const double target = pair_budget(n_occ, p, log_base);
+    const long cap = (long)std::floor(target);
+    std::vector<long> room;
+    std::vector<int> cycle(ord.size());
+    for (size_t k = 0; k < ord.size(); ++k) {   // first-fit of whole types, shortest first
+        const long n = ord[k].second;
+        if (n > cap) return GC_EINVAL;
+        size_t c = 0;
+        while (c < room.size() && room[c] < n) ++c;
+        if (c == room.size()) room.push_back(cap);
+        room[c] -= n;
+        cycle[k] = (int)c;
+    }
+    const int n_cycle = (int)room.size();
+    const int t_int = T / n_cycle;
+    if (t_int < 1) return GC_EINVAL;
+    gc_sel *s = new (std::nothrow) gc_sel();
+    if (!s) return GC_ENOMEM;
+    s->scheme = 1;
+    s->L = L;
+    s->T = T;
+    s->n_ubl = (int)ord.size();
+    s->n_cycle = n_cycle;
+    s->t_int = t_int;
+    s->null_dim = 4;   // every type is in: the criterion holds when the array is connected (checked below)
+    s->target = target;
+    s->lattice = lattice;
+    s->masked = 1;
+    s->n_occ = n_occ;
+    s->mask = m;
+    bool x = false, y = false;
+    for (size_t k = 0; k < ord.size(); ++k) {
+        s->types.push_back(ord[k].first.dx);
+        s->types.push_back(ord[k].first.dy);
+        s->win_t0.push_back(cycle[k] * t_int);
+        s->win_t1.push_back((cycle[k] + 1) * t_int);
+        x = x || (ord[k].first.dx == 1 && ord[k].first.dy == 0);
+        y = y || (ord[k].first.dx == 0 && ord[k].first.dy == 1);
+    }
+    fill_pairs(s);
+    fill_groups(s);
+    if (!x || !y || !fill_tree(s)) {
+        delete s;
+        return GC_EDEGEN;
+    }
+    *out = s;
+    return GC_OK;
+}
+
 void gc_sel_free(gc_sel *sel) {
     if (!sel) return;
     gc_sel_release_device(sel);

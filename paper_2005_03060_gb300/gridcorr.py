@@ -61,6 +61,8 @@ _lib.gc_selection_subset.restype = _i
 _lib.gc_selection_lowcad.argtypes = [_i, _i, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp)]
 _lib.gc_selection_subset_masked.argtypes = [_i, _i, ctypes.c_double, ctypes.c_double, _vp, _i, ctypes.POINTER(_vp)]
 _lib.gc_selection_subset_masked.restype = _i
+_lib.gc_selection_lowcad_masked.argtypes = [_i, _i, ctypes.c_double, ctypes.c_double, _vp, _i, ctypes.POINTER(_vp)]
+_lib.gc_selection_lowcad_masked.restype = _i
 _lib.gc_selection_lowcad.restype = _i
 _lib.gc_sel_free.argtypes = [_vp]
 _lib.gc_sel_free.restype = None
@@ -408,7 +410,7 @@ class Selection:
     lattice ('square' or 'triangular'), n_ant (occupied points).
 
     mask: for an array on a partly occupied lattice (e.g. hex_mask(s)), the
-    L*L occupancy of the bounding grid (subset scheme only).
+    L*L occupancy of the bounding grid.
     """
 
     def __init__(self, scheme: str, L: int, T: int, p: float = 1.0, log_base: float = 2.0,
@@ -416,14 +418,12 @@ class Selection:
         import numpy as np
         h = _vp()
         if mask is not None:
-            if scheme != "subset":
-                raise ValueError("masked arrays support the subset scheme")
             m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
             if m.size != L * L:
                 raise ValueError("mask must have L*L entries")
             self.mask = m
-            st = _lib.gc_selection_subset_masked(L, T, p, log_base, m.ctypes.data_as(_vp),
-                                                 LATTICES[lattice], ctypes.byref(h))
+            fn = {"subset": _lib.gc_selection_subset_masked, "lowcad": _lib.gc_selection_lowcad_masked}[scheme]
+            st = fn(L, T, p, log_base, m.ctypes.data_as(_vp), LATTICES[lattice], ctypes.byref(h))
         else:
             self.mask = None
             fn = {"subset": _lib.gc_selection_subset, "lowcad": _lib.gc_selection_lowcad}[scheme]

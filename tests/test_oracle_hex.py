@@ -100,3 +100,26 @@ def test_hex_subset_331():
     k = int(np.argmin(np.abs(cums - 331 * np.log2(331)))) + 1
     assert sel.n_ubl == k and sel.P == cums[k - 1]
     assert sel.types == ts[:k]
+
+
+def test_normal_matrices_equal_design_products():
+    """Eq. logcal's normal matrices summed pair by pair equal A^T A, B^T B."""
+    L = 6
+    sel = osel.subset(L, 64)
+    A, B = oc.logcal_matrices(L, sel.types, sel.pair_i, sel.pair_j, sel.pair_type())
+    AtA, BtB = oc.logcal_normal_matrices(L * L, sel.types, sel.pair_i, sel.pair_j, sel.pair_type())
+    assert np.array_equal(AtA, A.T @ A) and np.array_equal(BtB, B.T @ B)
+
+
+def test_hex_gain_variance_prediction_is_finite_and_positive():
+    L, m = osel.hex_mask(4)
+    for sel in (osel.subset_layout(L, m, "triangular", 256), osel.lowcad_layout(L, m, "triangular", 256)):
+        pi, pj, pos = osel.compact(sel, m)
+        pa, pp = oc.gain_variance_prediction(None, sel.types, pi, pj, sel.pair_type(), N=len(pos))
+        assert np.all(pa > 0) and np.all(pp > 0) and np.all(np.isfinite(pa + pp))
+    # at equal visibility noise, more pairs per antenna (low-cadence: all of them) predict less variance
+    sub = osel.subset_layout(L, m, "triangular", 256)
+    low = osel.lowcad_layout(L, m, "triangular", 256)
+    a = [oc.gain_variance_prediction(None, s.types, *osel.compact(s, m)[:2], s.pair_type(), N=int(m.sum()))
+         for s in (sub, low)]
+    assert np.mean(a[1][0] + a[1][1]) < np.mean(a[0][0] + a[0][1])

@@ -93,3 +93,17 @@ def test_masked_selection_errors(gcmod):
     with pytest.raises(gcmod.GridcorrError) as e:
         gcmod.Selection("subset", L, 64, mask=m)
     assert e.value.status == gcmod.GC_EDEGEN
+
+
+@pytest.mark.parametrize("s,T", [(4, 256), (8, 1024), (11, 4096)])
+def test_hex_lowcad_matches_oracle(gcmod, s, T):
+    L, m = osel.hex_mask(s)
+    ref = osel.lowcad_layout(L, m, "triangular", T)
+    sel = gcmod.Selection("lowcad", L, T, mask=m, lattice="triangular")
+    assert [tuple(t) for t in sel.types.tolist()] == ref.types
+    assert np.array_equal(sel.type_ptr, ref.type_ptr)
+    assert np.array_equal(sel.pair_i, ref.pair_i) and np.array_equal(sel.pair_j, ref.pair_j)
+    assert np.array_equal(sel.win_t0, ref.win_t0) and np.array_equal(sel.win_t1, ref.win_t1)
+    assert sel.n_cycle == ref.n_cycle and sel.t_int == ref.t_int
+    n = int(m.sum())
+    assert sel.P == n * (n - 1) // 2            # every pair exactly once
