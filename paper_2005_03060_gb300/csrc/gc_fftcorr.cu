@@ -86,6 +86,21 @@ constexpr Tw256 make_tw256() {
 __constant__ Tw256 c_tw = make_tw256();
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+
+// Packed two-lane FP32 add / subtract (one instruction for both parts of a
+// complex number; each lane rounds as the scalar operation does).
+__device__ __forceinline__ unsigned long long pk2(float2 a) { return *reinterpret_cast<unsigned long long *>(&a); }
+__device__ __forceinline__ float2 up2(unsigned long long a) { return *reinterpret_cast<float2 *>(&a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return up2(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return up2(d);
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 w) {
     return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
 }
@@ -117,8 +132,8 @@ __device__ __forceinline__ void fft_reg(float2 (&a)[F]) {
 #pragma unroll
             for (int j = 0; j < len / 2; ++j) {
                 const float2 u = a[blk + j], v = a[blk + j + len / 2];
-                a[blk + j] = cadd(u, v);
-                a[blk + j + len / 2] = tw_apply(make_float2(u.x - v.x, u.y - v.y), j * (256 / len));
+                a[blk + j] = add2(u, v);
+                a[blk + j + len / 2] = tw_apply(sub2(u, v), j * (256 / len));
             }
         }
     }
@@ -254,9 +269,14 @@ template <class K, int S2V>
 __device__ __forceinline__ void col_fold2(float2 (&b)[K::F2], const float2 *icol, const float2 *tws) {
 #pragma unroll
     for (int yp = 0; yp < K::F2; ++yp) {
-        const float2 a0 = icol[yp * K::IROW];
-        const float2 r = rot_mi<S2V>(icol[(yp + K::F2) * K::IROW]);
-        const float2 t = make_float2(a0.x + r.x, a0.y + r.y);
+        const float2 a0 = icol[yp * K::IROW], a1 = icol[(yp + K::F2) * K::IROW];
+        float2 t;
+        if constexpr (S2V == 0) t = add2(a0, a1);
+        else if constexpr (S2V == 2) t = sub2(a0, a1);
+        else {
+            const float2 r = rot_mi<S2V>(a1);
+            t = make_float2(a0.x + r.x, a0.y + r.y);
+        }
         b[yp] = S2V == 0 ? t : cmul(t, tws[(S2V * yp) & (K::M - 1)]);
     }
 }
