@@ -323,6 +323,23 @@ GC_API gc_status gc_calibrate_batched(gc_ctx *ctx, int n_arrays, const gc_batch_
                                       const gc_calopts *opts, void *stream);
 
 /*
+ * Predicted calibration variances of a selection (Eq. gaincov, the
+ * uniform-noise form of Eq. noisecov): for every unknown u -- antennas
+ * u < L*L, then model visibilities u = L*L + k -- the diagonal entry of the
+ * pseudo-inverse of Eq. logcal's normal matrices, amplitude [(A^T A)^+]_uu
+ * into var_amp[u] and phase [(B^T B)^+]_uu into var_phase[u] (device float
+ * arrays of L*L + n_ubl; the four degeneracies of Sec. 5.2 are left out,
+ * empty points of a partly occupied lattice get 0).  With per-visibility
+ * noise variance sigma^2 the gain variance is sigma^2 (var_amp + var_phase)
+ * / 2 per unit gain (|V| = 1); sum over antennas for the array mean, or
+ * leave out edge antennas as the paper's Sec. 5.4 does.  One
+ * Jacobi-preconditioned conjugate-gradient solve per unknown (relative
+ * residual 1e-6) on the GPU.  Uses the context workspace.
+ */
+GC_API gc_status gc_gain_variance(gc_ctx *ctx, const gc_sel *sel, float *var_amp, float *var_phase,
+                                  void *stream);
+
+/*
  * Tuning knobs of a context (0 = automatic), set by the autotuner:
  *   "fft.chunk_len"    time samples per FFT-correlator work item
  *   "xeng.tsplit"      time slices per X-engine window

@@ -56,6 +56,8 @@ _lib.gc_correlate.argtypes = [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp]
 _lib.gc_correlate.restype = _i
 _lib.gc_correlate_masked.argtypes = [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _vp]
 _lib.gc_correlate_masked.restype = _i
+_lib.gc_gain_variance.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.gc_gain_variance.restype = _i
 _lib.gc_selection_subset.argtypes = [_i, _i, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp)]
 _lib.gc_selection_subset.restype = _i
 _lib.gc_selection_lowcad.argtypes = [_i, _i, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp)]
@@ -212,6 +214,19 @@ class Context:
                                                 m.ctypes.data_as(_vp), _vp(gains.data_ptr()),
                                                 _vp(out.data_ptr()), _vp(_stream_ptr(volt.device))))
         return out
+
+    # ------------------------------------------------------------------ covariance
+    def gain_variance(self, sel: Selection):
+        """Eq. gaincov predicted variances (gc_gain_variance): (var_amp,
+        var_phase), float32 CUDA tensors of L*L + n_ubl (antennas, then model
+        visibilities), for unit visibility noise."""
+        dev = self.device
+        n = sel.L * sel.L + sel.n_ubl
+        va = torch.empty(n, dtype=torch.float32, device=dev)
+        vp = torch.empty(n, dtype=torch.float32, device=dev)
+        self.check(_lib.gc_gain_variance(self._h, sel.handle, _vp(va.data_ptr()), _vp(vp.data_ptr()),
+                                         _vp(_stream_ptr(dev))))
+        return va, vp
 
     # ------------------------------------------------------------------ reduce
     def reduce(self, volt: torch.Tensor, sel: Selection, autos: bool = True, out=None, out_autos=None):
