@@ -413,7 +413,7 @@ GC_API gc_status gc_chi2_backward_ckpt(gc_ctx *ctx, const float *residuals, cons
  *   vreduced, autos  device outputs as gc_reduce (autos may be NULL)
  *   opts      calibration options (NULL: defaults); gains_out [C][L*L],
  *             vmodel [C][n_ubl], stats [C]: device outputs as gc_calibrate
- * The context allocates two device staging buffers of chunk * T * L*L
+ * The context allocates three device staging buffers of chunk * T * L*L
  * voltage elements on first need (cudaMalloc, which synchronises the
  * device) and keeps them.  Everything is enqueued; the call returns when
  * the work is queued.  The staging buffers and h_volt must not be modified

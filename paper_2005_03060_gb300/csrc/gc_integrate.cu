@@ -2,7 +2,9 @@
 // paper's Fig. 1 (FFT-correlator, reduced X-engine, calibration), streamed
 // channel chunk by channel chunk: the host->device copy of chunk i+1 (on the
 // context's copy stream) overlaps the correlator and X-engine kernels of
-// chunk i (on the caller's stream).  The first chunk is a quarter of the
+// chunk i (on the caller's stream); with three staging buffers a copy can
+// run two chunks ahead, so a host link about as fast as the kernels still
+// stays hidden.  The first chunk is a quarter of the
 // others, so that little copy time is exposed before the first kernel; the
 // calibration is one launch over all channels at the end (the kernels share
 // one stream, so splitting it would only leave partial waves of CTAs).
@@ -21,7 +23,7 @@ gc_status ensure_streaming(gc_ctx *ctx, size_t stage_bytes) {
     if (!ctx->copy_stream) {
         e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaStreamCreate(copy)");
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < GC_NSTAGE; ++b) {
             if ((e = cudaEventCreateWithFlags(&ctx->ev_copied[b], cudaEventDisableTiming)) != cudaSuccess ||
                 (e = cudaEventCreateWithFlags(&ctx->ev_free[b], cudaEventDisableTiming)) != cudaSuccess)
                 return gc_cuda_fail(ctx, e, "cudaEventCreate");
@@ -31,12 +33,12 @@ gc_status ensure_streaming(gc_ctx *ctx, size_t stage_bytes) {
         // the old buffers may still be read by queued kernels
         e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaDeviceSynchronize before staging growth");
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < GC_NSTAGE; ++b) {
             if (ctx->stage[b]) cudaFree(ctx->stage[b]);
             ctx->stage[b] = nullptr;
         }
         ctx->stage_bytes = 0;
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < GC_NSTAGE; ++b) {
             e = cudaMalloc(&ctx->stage[b], stage_bytes);
             if (e != cudaSuccess) {
                 cudaGetLastError();
@@ -81,7 +83,7 @@ extern "C" gc_status gc_integrate_host(gc_ctx *ctx, const void *h_volt, int vfmt
     const int n_chunks = (int)bounds.size() - 1;
     const char *h = static_cast<const char *>(h_volt);
     for (int i = 0; i < n_chunks; ++i) {
-        const int b = i & 1;
+        const int b = i % GC_NSTAGE;
         const int c0 = bounds[i], cc = bounds[i + 1] - c0;
         // a staging buffer is refilled once the last kernel that read it --
         // of this call, or of the previous call for the first two chunks --

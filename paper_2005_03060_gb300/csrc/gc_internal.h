@@ -34,6 +34,10 @@ enum {
     GC_TUNE_N = 5
 };
 
+// staging buffers of the streamed integration: with three, a chunk's copy
+// may run two chunks ahead of the kernels
+constexpr int GC_NSTAGE = 3;
+
 struct gc_ctx {
     int device = 0;
     int tune[GC_TUNE_N] = {0, 0, 0, 0, 0};
@@ -49,9 +53,9 @@ struct gc_ctx {
     std::vector<cudaEvent_t> event_pool;
     // gc_integrate_host: copy stream, two device staging buffers, events
     cudaStream_t copy_stream = nullptr;
-    void *stage[2] = {nullptr, nullptr};
+    void *stage[GC_NSTAGE] = {nullptr, nullptr, nullptr};   // gc_integrate_host staging buffers
     size_t stage_bytes = 0;
-    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copied[GC_NSTAGE] = {nullptr, nullptr, nullptr}, ev_free[GC_NSTAGE] = {nullptr, nullptr, nullptr};
 };
 
 // launch timing helpers: no-ops unless profiling is enabled

@@ -134,7 +134,7 @@ void gc_destroy(gc_ctx *ctx) {
     cudaDeviceSynchronize();
     prof_clear(ctx);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < GC_NSTAGE; ++b) {
         if (ctx->stage[b]) cudaFree(ctx->stage[b]);
         if (ctx->ev_copied[b]) cudaEventDestroy(ctx->ev_copied[b]);
         if (ctx->ev_free[b]) cudaEventDestroy(ctx->ev_free[b]);
