@@ -530,11 +530,21 @@ def run_ours(args, rank, world, local_rank):
 
     for _ in range(2):
         e2e_step()
+    # this box's pinned host-to-device rate (one plain copy of the voltages):
+    # the streamed step cannot beat bytes / rate however well it overlaps
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    w.volt.copy_(h_volt, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    link_gbs = h_volt.numel() * h_volt.element_size() / (e0.elapsed_time(e1) * 1e6)
     e2e_ms = _timed(e2e_step, e2e_steps, stream, barrier) / e2e_steps
     e2e_ms = shard.max_over_ranks(e2e_ms, dev)
     e2e = {"value": shard.job_rate(w.units, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
            "h2d_bytes_per_step": h_volt.numel() * h_volt.element_size() + h_gains.numel() * 8,
            "d2h_bytes_per_step": h_vu.numel() * 8 + h_g.numel() * 8,
+           "h2d_link_gbs": link_gbs,
            "path": ("gc_integrate_host: pinned host voltages streamed in channel chunks, each copy "
                     "overlapping the previous chunk's kernels; gains H2D, V^unique and gains D2H")}
     del h_volt
