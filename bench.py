@@ -545,8 +545,9 @@ def run_ours(args, rank, world, local_rank):
            "h2d_bytes_per_step": h_volt.numel() * h_volt.element_size() + h_gains.numel() * 8,
            "d2h_bytes_per_step": h_vu.numel() * 8 + h_g.numel() * 8,
            "h2d_link_gbs": link_gbs,
-           "path": ("gc_integrate_host: pinned host voltages streamed in channel chunks, each copy "
-                    "overlapping the previous chunk's kernels; gains H2D, V^unique and gains D2H")}
+           "path": ("gc_integrate_host: pinned host voltages streamed in channel chunks through three "
+                    "staging buffers, copies up to two chunks ahead of the kernels; gains H2D, V^unique "
+                    "and gains D2H")}
     del h_volt
 
     peaks = load_peaks() or {}
