@@ -86,6 +86,43 @@ def test_quantiser_rules(orc):
     assert _round_half_away32(h).tolist() == [3.0, -3.0, 1.0, -1.0]
 
 
+def test_quantiser_code_distribution_closed_form(orc):
+    """For Gaussian voltages the codes follow a closed form that the quantiser's
+    stated rule fixes (RMS of 3 levels per component, round to nearest, clip to
+    +-7): with x ~ N(0, 3^2), P(q = k) = Phi((k + 1/2)/3) - Phi((k - 1/2)/3) for
+    |k| <= 6 and P(q = +-7) = 1 - Phi(6.5/3).  A wrong scale (per complex value
+    instead of per component: a factor sqrt 2), truncation instead of rounding,
+    a clip at 8 or swapped nibbles fail the chi-square bound."""
+    from scipy.stats import norm, chi2
+    rng = np.random.default_rng(20050306)
+    T, N = 4096, 64
+    # Re and Im with different spreads: the scale comes from their pooled RMS
+    sr, si = 1.25, 0.65
+    v = (sr * rng.standard_normal((T, N)) + 1j * si * rng.standard_normal((T, N))).astype(np.complex64)
+    b, s = orc.quantize(v)
+    q = orc.unpack_i4c(b)
+    pooled = math.sqrt((sr * sr + si * si) / 2.0)
+    for comp, sig in ((q.real, 3.0 * sr / pooled), (q.imag, 3.0 * si / pooled)):
+        k = np.arange(-7, 8)
+        p = norm.cdf((k + 0.5) / sig) - norm.cdf((k - 0.5) / sig)
+        p[0] = norm.cdf(-6.5 / sig)
+        p[-1] = 1.0 - norm.cdf(6.5 / sig)
+        assert abs(p.sum() - 1.0) < 1e-12
+        counts = np.array([(comp == kk).sum() for kk in k], dtype=np.float64)
+        assert counts.sum() == comp.size            # nothing outside [-7, 7]
+        e = p * comp.size
+        keep = e > 5.0
+        stat = float((((counts - e) ** 2) / e)[keep].sum())
+        assert stat < chi2.ppf(1.0 - 1e-6, int(keep.sum()) - 1), (sig, stat)
+        # second moment of the clipped, rounded Gaussian
+        assert np.mean(comp ** 2) == pytest.approx(float((p * k * k).sum()), rel=0.01)
+    # byte layout: two's-complement Re in the high nibble, Im in the low
+    w = np.ones((1000, 4), np.complex64)           # unit rows keep the scale near 3
+    w[0] = [40 - 40j, -40 + 40j, 0, 1e-3 - 1e-3j]  # clipped, clipped, zero, rounds to zero
+    bb, _ = orc.quantize(w)
+    assert bb[0].tolist() == [0x79, 0x97, 0x00, 0x00]
+
+
 def test_canonical_types_cover_all_pairs():
     for L in (2, 3, 5):
         N = L * L
