@@ -195,8 +195,15 @@ def initial_solution(vobs, pi, pj, alpha, types, L, sparse=False):
                     phi[b] = phi[a] + dphi
                     queue.append(b)
         assert seen.all(), "the axis types do not connect the array"
-    # wrapped residual phase logcal: dphi_i - dphi_j + theta_a = wrap(arg V - phi_i + phi_j)
+    # wrapped residual phase logcal: dphi_i - dphi_j + theta_a = wrap(arg V - phi_i + phi_j).
+    # Eq. logcal's phase equation holds modulo 2 pi; the branch is taken per
+    # redundant group around the group's circular mean, so that a group whose
+    # residual phase sits near +-pi does not split across the cut
     res = np.angle(vobs * np.exp(-1j * (phi[pi] - phi[pj])))
+    mu = np.zeros(nu, np.complex128)
+    np.add.at(mu, alpha, np.exp(1j * res))
+    mu = np.angle(mu)
+    res = mu[alpha] + np.angle(np.exp(1j * (res - mu[alpha])))
     idx = [(int(pi[p]), int(pj[p]), N + int(alpha[p])) for p in range(len(vobs))]
     sol = _lstsq_rows(N + nu, idx, [(1.0, -1.0, 1.0)] * len(vobs), res, sparse)
     phi = phi + sol[:N]

@@ -101,16 +101,73 @@ def test_gain_variance_follows_eq_gaincov():
     alpha = sel.pair_type()
     pa, pp = oc.gain_variance_prediction(L, sel.types, sel.pair_i, sel.pair_j, alpha)
     pred = 0.5 * sigma ** 2 * (pa + pp)
-    errs = []
+    errs, e_amp, e_ph = [], [], []
     for s in range(nsim):
         _, _, g, V, vobs = _problem(L, 1000 + s, sigma=sigma, unit_amp=True, sel=sel)
         ge, Ve, it, ok = oc.calibrate(vobs, sel.pair_i, sel.pair_j, alpha, sel.types, L, "lincal")
         assert ok
         gf = oc.fit_degeneracies(ge, g, L)
         errs.append(np.abs(gf / g - 1.0) ** 2)
+        e_amp.append(np.log(np.abs(gf / g)) ** 2)
+        e_ph.append(np.angle(gf / g) ** 2)
     meas = np.mean(errs, axis=0)
     ratio = np.mean(meas) / np.mean(pred)
     assert 0.85 < ratio < 1.15, ratio
+    # the parts separately: ln|g| follows the amplitude system (A, one null
+    # direction), arg g the phase system (B, three); on this array the two
+    # predictions differ by ~1.5x, so exchanging them fails
+    r_amp = np.mean(e_amp) / np.mean(0.5 * sigma ** 2 * pa)
+    r_ph = np.mean(e_ph) / np.mean(0.5 * sigma ** 2 * pp)
+    assert 0.9 < r_amp < 1.1 and 0.9 < r_ph < 1.1, (r_amp, r_ph)
+
+
+def test_dof_is_the_expected_residual():
+    """Eq. dof from the statistics of least squares rather than from its
+    formula: at high SNR the fit is linear, and the residual chi^2 of complex
+    noise of variance sigma^2 has expectation sigma^2 (N_obs - N - N_ubl + 2)
+    -- 2 N_obs real observations less 2 (N + N_ubl) - 4 effective real
+    parameters (four degeneracies, Sec. 5.2), halved per real component.  A
+    3 x 3 array keeps DoF small so that 800 draws resolve a unit error."""
+    L, sigma, nsim = 3, 1e-3, 800
+    sel = osel.subset(L, 100)
+    alpha = sel.pair_type()
+    vals = []
+    for s in range(nsim):
+        _, _, g, V, vobs = _problem(L, 90000 + s, sigma=sigma, sel=sel)
+        ge, Ve, it, ok = oc.calibrate(vobs, sel.pair_i, sel.pair_j, alpha, sel.types, L, "lincal")
+        assert ok
+        vals.append(oc.chi2(vobs, ge, Ve, sel.pair_i, sel.pair_j, alpha) / sigma ** 2)
+    d = oc.dof(sel.P, L * L, sel.n_ubl)
+    # std of the mean: sqrt(DoF / nsim) (chi^2 / sigma^2 is half a chi-square of 2 DoF)
+    assert abs(np.mean(vals) - d) < 4.0 * np.sqrt(d / nsim), (np.mean(vals), d)
+
+
+def test_start_point_is_exact_without_noise():
+    """The logcal start (Eq. logcal: ln|V_p| = eta_i + eta_j + a_alpha and
+    arg V_p = phi_i - phi_j + theta_alpha) is exact on noise-free data: its
+    model reproduces every visibility before any lincal or omnical step."""
+    for L, seed in ((3, 4), (5, 8)):
+        sel, alpha, g, V, vobs = _problem(L, seed)
+        g0, V0 = oc.initial_solution(vobs, sel.pair_i, sel.pair_j, alpha, sel.types, L)
+        m0 = oc.model(g0, V0, sel.pair_i, sel.pair_j, alpha)
+        assert np.max(np.abs(m0 - vobs)) < 1e-10 * np.max(np.abs(vobs))
+    # with noise the start is the logcal estimate itself, which is where Eq.
+    # gaincov comes from: at high SNR and |g| = |V| = 1 its ln|g| and arg g
+    # errors have the variances 0.5 sigma^2 diag[(A^T A)^+] and diag[(B^T B)^+]
+    L, sigma, nsim = 4, 0.02, 300
+    sel = osel.subset(L, 100)
+    alpha = sel.pair_type()
+    pa, pp = oc.gain_variance_prediction(L, sel.types, sel.pair_i, sel.pair_j, alpha)
+    e_amp, e_ph = [], []
+    for s in range(nsim):
+        _, _, g, V, vobs = _problem(L, 7000 + s, sigma=sigma, unit_amp=True, sel=sel)
+        g0, _ = oc.initial_solution(vobs, sel.pair_i, sel.pair_j, alpha, sel.types, L)
+        q = oc.fit_degeneracies(g0, g, L) / g
+        e_amp.append(np.log(np.abs(q)) ** 2)
+        e_ph.append(np.angle(q) ** 2)
+    r_amp = np.mean(e_amp) / np.mean(0.5 * sigma ** 2 * pa)
+    r_ph = np.mean(e_ph) / np.mean(0.5 * sigma ** 2 * pp)
+    assert 0.9 < r_amp < 1.1 and 0.9 < r_ph < 1.1, (r_amp, r_ph)
 
 
 def test_reduced_chi2_is_one():
