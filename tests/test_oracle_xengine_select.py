@@ -55,6 +55,24 @@ def test_xengine_matches_fx_full_matrix(orc):
     assert np.allclose(s, T * vf[pi, pj], atol=1e-12)
 
 
+def test_autos_are_windowed_self_pairs(orc):
+    """A_i over [t0, t1) equals the X-engine's sum of the pair (i, i) over the
+    same window (real, |v_i|^2 summed) and T V^full_ii of the FX oracle for
+    the full window; a window that starts late drops the early samples."""
+    rng = np.random.default_rng(5)
+    L, T = 3, 10
+    N = L * L
+    v = rng.standard_normal((T, N)) + 1j * rng.standard_normal((T, N))
+    ii = np.arange(N)
+    for t0, t1 in ((0, T), (3, 8), (4, 4)):
+        a = orc.autos(v, t0, t1)
+        s = orc.xengine_c64(v, ii, ii, [t0] * N, [t1] * N)
+        assert np.allclose(a, s.real, atol=1e-12) and np.all(s.imag == 0)
+    _, vf = orc.fx(v, None, L, full=True)
+    assert np.allclose(orc.autos(v), T * np.diag(vf).real, atol=1e-12)
+    assert np.allclose(orc.autos(v, 3, 8), np.sum(np.abs(v[3:8]) ** 2, axis=0), atol=1e-12)
+
+
 def _round_half_away32(x):
     a = np.abs(x).astype(np.float32)
     f = np.floor(a)
