@@ -55,6 +55,17 @@ def test_xengine_matches_fx_full_matrix(orc):
     assert np.allclose(s, T * vf[pi, pj], atol=1e-12)
 
 
+def test_subset_tie_goes_to_the_shorter_prefix():
+    """Sec. 6.1 takes the whole number of groups closest to p N log N and
+    leaves ties open; the reading here is the shorter prefix.  On a 4 x 4
+    grid the prefixes hold 12, 24, 33, 42 pairs; p = 0.5859375 puts the
+    budget at 37.5, exactly between 33 and 42."""
+    sel = osel.subset(4, 64, p=0.5859375)
+    assert sel.extra["target"] == 37.5
+    assert sel.P == 33 and sel.types == [(1, 0), (0, 1), (1, 1)]
+    assert osel.subset(4, 64, p=0.5859375 + 1e-6).P == 42
+
+
 def test_autos_are_windowed_self_pairs(orc):
     """A_i over [t0, t1) equals the X-engine's sum of the pair (i, i) over the
     same window (real, |v_i|^2 summed) and T V^full_ii of the FX oracle for

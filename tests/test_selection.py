@@ -25,7 +25,8 @@ def _same(a, b):
 
 
 @pytest.mark.parametrize("L,T,p", [(3, 10, 1.0), (4, 64, 1.0), (5, 100, 0.5), (6, 33, 0.05),
-                                   (8, 256, 1.0), (12, 2048, 1.0), (16, 100, 2.0), (32, 4096, 1.0)])
+                                   (8, 256, 1.0), (12, 2048, 1.0), (16, 100, 2.0), (32, 4096, 1.0),
+                                   (4, 64, 0.5859375)])   # budget 37.5: a tie between 33 and 42 pairs
 def test_subset_matches_oracle(gcmod, L, T, p):
     _same(gcmod.Selection("subset", L, T, p), osel.subset(L, T, p))
 
