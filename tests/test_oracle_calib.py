@@ -170,6 +170,24 @@ def test_start_point_is_exact_without_noise():
     assert 0.9 < r_amp < 1.1 and 0.9 < r_ph < 1.1, (r_amp, r_ph)
 
 
+def test_full_redcal_variance_scales_as_one_over_n():
+    """Eq. gainvar_redcal: with the full visibility matrix every antenna sits
+    in N - 1 equations and the diagonal of (A^T A)^+ approaches 1/N for the
+    amplitude and for the phase part alike; N times the mean predicted
+    variance falls towards 1 as the grid grows (every pair, unit noise)."""
+    prev = None
+    for L in (4, 6, 8, 12):
+        sel = osel.lowcad(L, 10 ** 6)            # every baseline-type, i.e. every pair
+        assert sel.P == L * L * (L * L - 1) // 2
+        pa, pp = oc.gain_variance_prediction(L, sel.types, sel.pair_i, sel.pair_j, sel.pair_type())
+        na, npp = L * L * pa.mean(), L * L * pp.mean()
+        assert na > 1.0 and npp > 0.95
+        if prev is not None:
+            assert na < prev
+        prev = na
+    assert na == pytest.approx(1.0, abs=0.05) and npp == pytest.approx(1.0, abs=0.05)
+
+
 def test_reduced_chi2_is_one():
     """Eq. redchi / Eq. dof: with the true noise variance chi^2_r ~ 1."""
     L, sigma, nsim = 4, 0.05, 200
