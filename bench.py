@@ -157,13 +157,21 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle arm
-def _oracle_pipeline(wl: dict, Ts: int):
-    """The oracle's per-channel pipeline on one channel x Ts samples of the
-    workload, as two timed parts: corr() = (4+4-bit: the quantiser, then the
-    integer voltages) FX correlator + Eq. modelvis and the X-engine over the
-    subset selection; cal() = lincal of that channel's V^reduced (dense
-    normal equations up to 32 x 32, the sparse form of the same equations
-    beyond)."""
+def _host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_pipeline(wl: dict, Ts: int, n_ch: int):
+    """The oracle's pipeline on n_ch channels x Ts samples of the workload,
+    as two timed parts: corr() = (4+4-bit: the quantiser, then the integer
+    voltages) FX correlator + Eq. modelvis over the channels (the oracle's
+    OpenMP loop over channels) and the X-engine over the subset selection;
+    cal() = lincal of the first channel's V^reduced (dense normal equations
+    up to 32 x 32, the sparse form of the same equations beyond).  corr()
+    returns the threads the FX correlator ran on."""
     import numpy as np
 
     import oracle
@@ -172,47 +180,54 @@ def _oracle_pipeline(wl: dict, Ts: int):
     from paper_2005_03060_gb300 import synth
 
     L = wl["L"]
-    volt, gains, _ = synth.make_voltages(wl["seed"], L, 1, Ts, n_src=wl["n_src"], snr=wl["snr"])
-    v = volt.numpy()[0]
-    g = gains.numpy()[0]
+    volt, gains, _ = synth.make_voltages(wl["seed"], L, n_ch, Ts, n_src=wl["n_src"], snr=wl["snr"])
+    v = volt.numpy()
+    g = gains.numpy()
     sel = osel.subset(L, Ts)
     pt = sel.pair_type()
+    t0s, t1s = sel.win_t0[pt], sel.win_t1[pt]
     i4c = wl["vfmt"] == "i4c"
     state = {}
 
     def corr():
         if i4c:
-            q, _ = oracle.quantize(v)
-            vc = oracle.unpack_i4c(q)
-            oracle.fx(vc, g, L)
-            s = oracle.xengine_i4c(q, sel.pair_i, sel.pair_j, sel.win_t0[pt], sel.win_t1[pt])
-            state["S"] = s[:, 0] + 1j * s[:, 1]
+            vc = np.empty(v.shape, np.complex128)
+            S = []
+            for c in range(n_ch):
+                q, _ = oracle.quantize(v[c])
+                vc[c] = oracle.unpack_i4c(q)
+                s = oracle.xengine_i4c(q, sel.pair_i, sel.pair_j, t0s, t1s)
+                S.append(s[:, 0] + 1j * s[:, 1])
         else:
             vc = v.astype(np.complex128)
-            oracle.fx(vc, g, L)
-            state["S"] = oracle.xengine_c64(vc, sel.pair_i, sel.pair_j, sel.win_t0[pt], sel.win_t1[pt])
+            S = [oracle.xengine_c64(vc[c], sel.pair_i, sel.pair_j, t0s, t1s) for c in range(n_ch)]
+        _, threads = oracle.fx_multi(vc, g, L)
+        state["S"] = S
+        return threads
 
     def cal():
         # subset selection: every pair's window is the whole integration
-        oc.calibrate(state["S"] / Ts, sel.pair_i, sel.pair_j, pt, sel.types, L, "lincal", sparse=L > 32)
+        oc.calibrate(state["S"][0] / Ts, sel.pair_i, sel.pair_j, pt, sel.types, L, "lincal", sparse=L > 32)
 
     return corr, cal
 
 
-def _oracle_desc(wl, Ts, with_cal, why=""):
+def _oracle_desc(wl, Ts, n_ch, threads, with_cal, why=""):
     L = wl["L"]
     quant = "4+4-bit quantiser, " if wl["vfmt"] == "i4c" else ""
     form = "sparse" if L > 32 else "dense"
-    return (f"1 channel x {Ts} samples of the {L * L}-antenna workload through the FP64 oracle: "
-            f"{quant}FX correlator (all N^2 pairs, Eq. modelvis), X-engine over the subset selection"
-            + (f", lincal to 1e-10 ({form} normal equations, numpy/scipy)" if with_cal else
-               f"; lincal omitted{why}"))
+    return (f"{n_ch} channels x {Ts} samples of the {L * L}-antenna workload through the FP64 oracle: "
+            f"{quant}FX correlator (all N^2 pairs, Eq. modelvis; OpenMP over the channels, {threads} threads), "
+            f"X-engine over the subset selection"
+            + (f", lincal to 1e-10 ({form} normal equations, numpy/scipy) timed on one channel and "
+               f"counted once per channel" if with_cal else f"; lincal omitted{why}"))
 
 
-def _oracle_corr_samples(wl, budget_s: float) -> int:
-    """Samples whose correlator part takes about budget_s (the cost grows a
-    little faster than T, hence the margin)."""
-    corr, _ = _oracle_pipeline(wl, 16)
+def _oracle_corr_samples(wl, n_ch: int, budget_s: float) -> int:
+    """Samples whose correlator part over n_ch channels takes about budget_s
+    (the cost grows faster than T once a channel's voltages leave the
+    caches, hence the margin)."""
+    corr, _ = _oracle_pipeline(wl, 16, n_ch)
     t0 = time.perf_counter()
     corr()
     t16 = max(time.perf_counter() - t0, 1e-3)
@@ -221,24 +236,28 @@ def _oracle_corr_samples(wl, budget_s: float) -> int:
 
 def cpu_baseline(wl):
     """A bounded sample of the workload through the oracle pipeline on the
-    host cores: the correlator part on about 10 s worth of samples, plus the
-    calibration of that channel for the small arrays (for 4096 antennas one
-    sparse FP64 solve of a short, noisy integration runs for minutes, so it
-    is left out of the bounded sample and said so)."""
-    Ts = _oracle_corr_samples(wl, 10.0)
-    corr, cal = _oracle_pipeline(wl, Ts)
+    host cores (one channel per core): the correlator part on about 10 s
+    worth of samples, plus the calibration of one channel for the small
+    arrays (for 4096 antennas one sparse FP64 solve of a short, noisy
+    integration runs for minutes, so it is left out of the bounded sample
+    and said so)."""
+    n_ch = _host_cores()
+    Ts = _oracle_corr_samples(wl, n_ch, 10.0)
+    corr, cal = _oracle_pipeline(wl, Ts, n_ch)
     with_cal = wl["L"] <= 32
     t0 = time.perf_counter()
-    corr()
+    threads = corr()
     t1 = time.perf_counter()
     if with_cal:
         cal()
     t2 = time.perf_counter()
     L = wl["L"]
+    secs = (t1 - t0) + n_ch * (t2 - t1)
     why = " (one sparse FP64 solve of this 4096-antenna sample runs for minutes on these cores)"
-    return {"value": L * L * Ts / (t2 - t0), "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
-            "sample": _oracle_desc(wl, Ts, with_cal, why), "seconds": round(t2 - t0, 2),
-            "seconds_correlator_xengine": round(t1 - t0, 2), "seconds_calibration": round(t2 - t1, 2)}
+    return {"value": n_ch * L * L * Ts / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": _oracle_desc(wl, Ts, n_ch, threads, with_cal, why), "seconds": round(secs, 2),
+            "seconds_correlator_xengine": round(t1 - t0, 2),
+            "seconds_calibration": round(n_ch * (t2 - t1), 2)}
 
 
 def run_reference(args, rank):
@@ -246,13 +265,14 @@ def run_reference(args, rank):
         return
     wl = WORKLOADS[args.workload]
     L = wl["L"]
+    n_ch = _host_cores()
     budget = 150.0 / (args.steps + args.warmup)     # seconds per step
-    Ts = _oracle_corr_samples(wl, 0.5 * budget)
-    corr, cal = _oracle_pipeline(wl, Ts)
+    Ts = _oracle_corr_samples(wl, n_ch, 0.5 * budget)
+    corr, cal = _oracle_pipeline(wl, Ts, n_ch)
     with_cal = False
     why = " (one sparse FP64 solve of this 4096-antenna sample runs for minutes on these cores)"
+    threads = corr()
     if L <= 32:
-        corr()
         t0 = time.perf_counter()
         cal()
         t_cal = time.perf_counter() - t0
@@ -260,25 +280,25 @@ def run_reference(args, rank):
         why = f" (one channel's solve takes {t_cal:.1f} s, over half the {budget:.1f} s per-step budget)"
 
     def run():
+        t0 = time.perf_counter()
         corr()
+        t1 = time.perf_counter()
         if with_cal:
             cal()
+        # the calibration is timed on one channel and counted once per channel
+        return (t1 - t0) + n_ch * (time.perf_counter() - t1)
 
-    desc = _oracle_desc(wl, Ts, with_cal, why) + " per step"
+    desc = _oracle_desc(wl, Ts, n_ch, threads, with_cal, why) + " per step"
     for _ in range(args.warmup):
         run()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        run()
-    dt = (time.perf_counter() - t0) / args.steps
-    value = L * L * Ts / dt
-    cores = os.cpu_count() or 1
+    dt = sum(run() for _ in range(args.steps)) / args.steps
+    value = n_ch * L * L * Ts / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl["name"], "sample": desc},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
