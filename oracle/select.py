@@ -206,22 +206,6 @@ def lowcad(L: int, T: int, p: float = 1.0, log_base: float = 2.0) -> Selection:
                      null_dim=4, extra=dict(cap=cap, cycle_of=cycle_of))
 
 
-def n_bl_per_ant(sel: Selection) -> float:
-    """Eq. subredcal_n_bl: N_obs / N."""
-    return sel.P / (sel.L * sel.L)
-
-
-def n_ubl_per_ant(sel: Selection) -> float:
-    """Eq. subredcal_n_ubl: (1/N) sum_alpha (antennas taking part in alpha)."""
-    N = sel.L * sel.L
-    tot = 0
-    for k in range(sel.n_ubl):
-        a = set(sel.pair_i[sel.type_ptr[k]:sel.type_ptr[k + 1]].tolist())
-        a |= set(sel.pair_j[sel.type_ptr[k]:sel.type_ptr[k + 1]].tolist())
-        tot += len(a)
-    return tot / N
-
-
 # --------------------------------------------------------------------------- lattice layouts
 # Arrays on a lattice that is not fully occupied -- the paper's own arrays
 # are hexagonal (Sec. 3) -- are held as an L x L bounding grid of lattice
