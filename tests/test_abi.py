@@ -36,6 +36,22 @@ def test_library_exports_every_declared_symbol(libso):
     assert not missing, missing
 
 
+def test_every_exported_entry_point_is_declared(libso):
+    """The reverse direction: no gc_* symbol leaves the library undocumented
+    (the dynamic symbol table as nm lists it)."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    from paper_2005_03060_gb300 import _build
+    out = subprocess.run([nm, "-D", "--defined-only", _build.build()], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.split() and ln.split()[-1].startswith("gc_")}
+    assert exported, "no gc_* symbols exported"
+    assert sorted(exported - set(declared_symbols())) == []
+
+
 def test_fft_size(libso):
     libso.gc_fft_size.argtypes = [ctypes.c_int]
     expect = {1: 2, 2: 4, 3: 8, 8: 16, 9: 32, 16: 32, 17: 64, 32: 64, 33: 128, 64: 128, 128: 256}
