@@ -251,10 +251,14 @@ GC_API gc_status gc_quantize(gc_ctx *ctx, const float *volt, int C, int T, int N
  *              of each step; up to 64 baseline-types (subset selections).
  *   GC_OMNICAL damped simultaneous least-squares fixed point (damping 0.3
  *              by default, Sec. 3), FP32; any selection (low-cadence).
- *   GC_LINCAL_CG Gauss-Newton with the step from Jacobi-preconditioned
- *              conjugate gradients on J^T J, matrix-free (J v per pair, J^T u
- *              by gather), FP32 products with FP64 reductions (CG stops at
- *              relative residual 1e-4); any selection.
+ *   GC_LINCAL_CG Gauss-Newton with the step from conjugate gradients on
+ *              J^T J, preconditioned by Jacobi plus a patch-level coarse
+ *              space, matrix-free (per-antenna gather over the grid, or a
+ *              scatter over the pair list: "cal.operator"), FP32 products
+ *              with FP64 reductions; inexact-Newton CG tolerance from 0.1 down
+ *              to 1e-4 relative residual as the gradient falls, at most 500
+ *              CG iterations per step; any selection, and the only solver
+ *              for partly occupied lattices.
  * Start point (unless warm_start): spanning-tree phases over the (1,0) and
  * (0,1) types, unit amplitudes, group-mean model visibilities.  Warm start
  * reads gains and vmodel as given.
@@ -332,9 +336,13 @@ GC_API gc_status gc_calibrate_batched(gc_ctx *ctx, int n_arrays, const gc_batch_
  * empty points of a partly occupied lattice get 0).  With per-visibility
  * noise variance sigma^2 the gain variance is sigma^2 (var_amp + var_phase)
  * / 2 per unit gain (|V| = 1); sum over antennas for the array mean, or
- * leave out edge antennas as the paper's Sec. 5.4 does.  One
- * Jacobi-preconditioned conjugate-gradient solve per unknown (relative
- * residual 1e-6) on the GPU.  Uses the context workspace.
+ * leave out edge antennas as the paper's Sec. 5.4 does.  One FP64
+ * Jacobi-preconditioned conjugate-gradient solve per unknown on the GPU
+ * (relative residual 1e-8, at most 4000 iterations; an unknown whose solve
+ * does not get there reads NaN).  The cost grows as unknowns x iterations x
+ * pairs: meant for arrays of hundreds of antennas.  GC_EDEGEN for a
+ * selection with more than the four degeneracies.  Uses the context
+ * workspace.
  */
 GC_API gc_status gc_gain_variance(gc_ctx *ctx, const gc_sel *sel, float *var_amp, float *var_phase,
                                   void *stream);
