@@ -14,8 +14,10 @@ every workload of this library:
 * n_i(t) ~ CN(0, sigma_n^2) with sigma_n^2 = sum_k S_k / snr (power ratio);
 * g_i = (1 + N(0, 0.05)) * exp(i U(-pi, pi)), independent per channel.
 
-The paper's own simulations (Sec. 3) used ~10 % gain scatter, mean gain
-amplitude 1 and SNR 10; those values are the defaults here.
+The paper's own simulations (Sec. 3) used gains of mean amplitude 1 with a
+scatter at the ~10 % level and an SNR of 10; the defaults here keep the mean
+and the SNR and draw the amplitude scatter with a standard deviation of 0.05,
+the figure the benchmark workloads are specified with.
 
 Every draw comes from a torch.Generator seeded from (seed, channel, stream),
 so a channel's data does not depend on how many channels are generated or in
