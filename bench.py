@@ -486,6 +486,177 @@ def calibration_variants(w: Workload, Cs: int, reps_fast: int):
     return out
 
 
+# ----------------------------------------------------------------------------- batching and differentiation forms
+BATCH_GRIDS = (8, 12, 16, 24, 32, 40, 48, 64, 80, 96, 112, 128)
+BATCH_T = 2048
+DIFF_L, DIFF_C, DIFF_T = 128, 512, 4096
+
+
+def _batch_channels():
+    """Channels per array of the batching form, drawn U{64..512} (seeded)."""
+    import numpy as np
+    return [int(c) for c in np.random.default_rng(2048).integers(64, 513, size=len(BATCH_GRIDS))]
+
+
+def _forms_timed(fn, stream, reps):
+    """Mean CUDA-event time of fn on `stream` after one untimed call."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_batching(ctx, dev, stream):
+    """Batching form: twelve square arrays of 8x8 .. 128x128 with U{64..512}
+    channels each (T = 2048, subset selections), calibrated by the
+    matrix-free lincal in one persistent gc_calibrate_batched launch, against
+    one gc_calibrate launch per array.  V^reduced comes from the paper's own
+    visibility-level simulation (Sec. 3) at SNR 10 per sample."""
+    import numpy as np
+    import torch
+
+    from paper_2005_03060_gb300 import gridcorr, synth
+
+    chans = _batch_channels()
+    arrays, per = [], []
+    for k, (L, C) in enumerate(zip(BATCH_GRIDS, chans)):
+        sel = gridcorr.Selection("subset", L, BATCH_T)
+        pt = sel.pair_type()
+        tp = (sel.win_t1 - sel.win_t0)[pt]
+        sums, _, _ = synth.make_visibilities(300 + k, L, C, sel.pair_i, sel.pair_j, pt, sel.n_ubl, tp,
+                                             snr=10.0, device=dev)
+        arrays.append({"vred": sums.contiguous(), "sel": sel})
+        per.append((torch.empty(C, L * L, dtype=torch.complex64, device=dev),
+                    torch.empty(C, sel.n_ubl, dtype=torch.complex64, device=dev),
+                    torch.empty(C, 32, dtype=torch.uint8, device=dev)))
+
+    def one_launch_per_array():
+        for a, (g, v, st) in zip(arrays, per):
+            ctx.calibrate(a["vred"], a["sel"], solver="lincal_cg", precision="fp32", gains=g, vmodel=v, stats=st)
+
+    ms_per = _forms_timed(one_launch_per_array, stream, 3)
+    for a, (g, v, st) in zip(arrays, ctx.calibrate_batched(arrays)):
+        a["gains"], a["vmodel"], a["stats"] = g, v, st
+    ms_b = _forms_timed(lambda: ctx.calibrate_batched(arrays), stream, 3)
+    ctx.device_status()
+    ok = all(bool(np.all(gridcorr.decode_stats(a["stats"])["status"] == 0)) for a in arrays)
+    diff = max(((a["gains"] - g).abs() / g.abs()).max().item() for a, (g, _, _) in zip(arrays, per))
+    total = sum(chans)
+    return {"arrays": [[L, C] for L, C in zip(BATCH_GRIDS, chans)], "channels": total,
+            "antennas": sum(L * L for L in BATCH_GRIDS), "T": BATCH_T,
+            "batched_ms": ms_b, "batched_chans_per_s": total / (ms_b * 1e-3),
+            "per_array_ms": ms_per, "per_array_chans_per_s": total / (ms_per * 1e-3),
+            "all_converged": ok, "max_gain_diff_batched_vs_per_array": diff,
+            "input": "V^reduced from the paper's visibility-level simulation (Sec. 3), SNR 10 per sample; "
+                     "subset selections (p = 1, log2); eager launches (the batched launch is also "
+                     "graph-capturable)"}
+
+
+def measure_differentiation(ctx, dev, stream, hbm_peak):
+    """Differentiation form: the chi^2 of the redundant model (numerator of
+    Eq. redchi) and its adjoint on the 128x128 array (16 384 antennas, 512
+    channels, T = 4096, subset selection), residuals recomputed in the
+    backward pass or checkpointed by the forward pass.  Exact int32 pair sums
+    (the visibility-level simulation rounded to integers) stand where the
+    X-engine output of 4+4-bit voltages would; the evaluation point is the
+    true gains and visibilities.  chi^2 is bandwidth-bound: algorithmic bytes
+    are 8 per pair per pass over V^reduced or the residuals, plus the gains
+    and model visibilities once."""
+    import torch
+
+    from paper_2005_03060_gb300 import gridcorr, synth
+
+    L, C, T = DIFF_L, DIFF_C, DIFF_T
+    sel = gridcorr.Selection("subset", L, T)
+    pt = sel.pair_type()
+    tp = (sel.win_t1 - sel.win_t0)[pt]
+    sums, g, v = synth.make_visibilities(500, L, C, sel.pair_i, sel.pair_j, pt, sel.n_ubl, tp,
+                                         snr=10.0, device=dev)
+    vr = torch.stack([sums.real.round(), sums.imag.round()], dim=-1).to(torch.int32).contiguous()
+    del sums
+    g, v = g.contiguous(), v.contiguous()
+    res = torch.empty(C, sel.P, dtype=torch.complex64, device=dev)
+    out = torch.empty(C, dtype=torch.float64, device=dev)
+    ms = {"chi2_fwd": _forms_timed(lambda: ctx.chi2(vr, sel, g, v, out=out), stream, 5),
+          "chi2_bwd": _forms_timed(lambda: ctx.chi2_backward(vr, sel, g, v), stream, 5),
+          "chi2_fwd_ckpt": _forms_timed(lambda: ctx.chi2(vr, sel, g, v, out=out, residuals=res), stream, 5),
+          "chi2_bwd_ckpt": _forms_timed(lambda: ctx.chi2_backward_ckpt(res, sel, g, v), stream, 5)}
+    ctx.device_status()
+    pairs = C * sel.P * 8
+    par = C * (L * L + sel.n_ubl) * 8
+    algo = {"chi2_fwd": pairs + par, "chi2_bwd": pairs + 2 * par,
+            "chi2_fwd_ckpt": 2 * pairs + par, "chi2_bwd_ckpt": pairs + 2 * par}
+    kern = {}
+    for k, t in ms.items():
+        gbs = algo[k] / (t * 1e6)
+        kern[k] = {"ms": t, "algorithmic_bytes": algo[k], "gb_s": gbs, "hbm_frac": gbs / hbm_peak}
+    return {"L": L, "antennas": L * L, "channels": C, "pairs": sel.P, "kernels": kern,
+            "fwd_bwd_chans_per_s": C / ((ms["chi2_fwd"] + ms["chi2_bwd"]) * 1e-3),
+            "hbm_peak_gbs": hbm_peak,
+            "input": "int32 pair sums rounded from the paper's visibility-level simulation (Sec. 3), SNR 10 "
+                     "per sample; evaluation at the true gains and visibilities"}
+
+
+def measure_forms(ctx, dev, stream, hbm_peak):
+    """Both forms; a failure is recorded in the result instead of ending the run."""
+    import torch
+    out = {}
+    for name, fn in (("batching", lambda: measure_batching(ctx, dev, stream)),
+                     ("differentiation", lambda: measure_differentiation(ctx, dev, stream, hbm_peak))):
+        try:
+            out[name] = fn()
+        except Exception as e:                      # noqa: BLE001 -- reported, not hidden
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:400]}
+        torch.cuda.empty_cache()
+    return out
+
+
+def cpu_forms_baseline():
+    """The oracle on one channel of each form (context only): the chi^2 and
+    its gradient at 16 384 antennas, and one FP64 lincal of a 16x16 array of
+    the batching form."""
+    import numpy as np
+
+    from oracle import calib as oc
+    from oracle import select as osel
+    from paper_2005_03060_gb300 import synth
+
+    out = {}
+    sel = osel.subset(DIFF_L, DIFF_T)
+    pt = sel.pair_type()
+    tp = (sel.win_t1 - sel.win_t0)[pt]
+    sums, g, v = synth.make_visibilities(500, DIFF_L, 1, sel.pair_i, sel.pair_j, pt, sel.n_ubl, tp, snr=10.0)
+    vobs = sums[0].numpy().astype(np.complex128) / tp
+    gg, vv = g[0].numpy().astype(np.complex128), v[0].numpy().astype(np.complex128)
+    t0 = time.perf_counter()
+    oc.chi2(vobs, gg, vv, sel.pair_i, sel.pair_j, pt)
+    oc.chi2_grad(vobs, gg, vv, sel.pair_i, sel.pair_j, pt)
+    dt = time.perf_counter() - t0
+    out["differentiation"] = {"value": 1.0 / dt, "unit": "channels/s", "cores": 1, "kind": "oracle",
+                              "sample": f"chi^2 and its gradient (numpy, FP64) of one channel of the "
+                                        f"{DIFF_L}x{DIFF_L} array ({sel.P} pairs)"}
+    L = 16
+    sel = osel.subset(L, BATCH_T)
+    pt = sel.pair_type()
+    tp = (sel.win_t1 - sel.win_t0)[pt]
+    sums, _, _ = synth.make_visibilities(302, L, 1, sel.pair_i, sel.pair_j, pt, sel.n_ubl, tp, snr=10.0)
+    vobs = sums[0].numpy().astype(np.complex128) / tp
+    t0 = time.perf_counter()
+    oc.calibrate(vobs, sel.pair_i, sel.pair_j, pt, sel.types, L, "lincal")
+    dt = time.perf_counter() - t0
+    out["batching"] = {"value": 1.0 / dt, "unit": "channels/s", "cores": _host_cores(), "kind": "oracle",
+                       "sample": f"one FP64 lincal (dense normal equations, numpy; its BLAS may use every "
+                                 f"core) of one channel of the {L}x{L} array of the batching form"}
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -606,6 +777,9 @@ def run_ours(args, rank, world, local_rank):
                      "ms_per_step": ms2, "steps": steps2, "calibrated_chans_per_s": w2.C / (ms2 * 1e-3),
                      "kernels": {k: {"ms_per_step": v[0] / steps2, "launches": v[1]} for k, v in kern2.items()},
                      "rooflines": rl2}
+    forms = None
+    if not args.no_forms and world == 1 and args.channels is None:
+        forms = measure_forms(ctx, dev, stream, peaks.get("hbm_gbs", 6800.0))
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -631,8 +805,15 @@ def run_ours(args, rank, world, local_rank):
             "e2e": e2e, "clocks": clocks}
     if secondary:
         line["secondary"] = secondary
+    if forms:
+        line["forms"] = forms
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
+        if forms:
+            try:
+                line["cpu_baseline"]["forms"] = cpu_forms_baseline()
+            except Exception as e:                  # noqa: BLE001 -- reported, not hidden
+                line["cpu_baseline"]["forms"] = {"error": f"{type(e).__name__}: {e}"[:400]}
     print(json.dumps(line), flush=True)
 
 
@@ -645,6 +826,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="precision64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batching and differentiation forms (timed after the cycle)")
     ap.add_argument("--channels", type=int, default=None,
                     help="channels per GPU (default: the workload's); smaller values are for "
                          "profiling captures only")
