@@ -155,7 +155,11 @@ GC_API gc_status gc_correlate(gc_ctx *ctx, const void *volt, int vfmt, int L, in
  * gc_selection_lowcad  (Sec. 4, Eq. lowcadcal_inttime): every type; types
  *   are packed first-fit, shortest first, into cycles of floor(p N log N)
  *   pairs; N_cycle cycles of t_int = floor(T / N_cycle) samples; the types of
- *   cycle c are integrated over [c t_int, (c + 1) t_int).
+ *   cycle c are integrated over [c t_int, (c + 1) t_int).  Holding every
+ *   pair, it is refused with GC_EUNSUPPORTED past 2^28 pairs
+ *   (N (N - 1) / 2 > 2^28: about 23 000 antennas, L > 152).
+ * Every builder returns GC_ENOMEM when host memory runs out; no C++
+ * exception leaves the library.
  */
 typedef struct gc_sel gc_sel;
 GC_API gc_status gc_selection_subset(int L, int T, double p, double log_base, gc_sel **out);
@@ -196,7 +200,7 @@ GC_API gc_status gc_selection_subset_masked(int L, int T, double p, double log_b
 /* Low-cadence selection (Sec. 4) on a partly occupied lattice: every type
  * with a pair between occupied points, packed as gc_selection_lowcad with
  * N the occupied points.  GC_EDEGEN when the axis types do not connect the
- * array; other errors as gc_selection_lowcad. */
+ * array; other errors (and the 2^28-pair limit) as gc_selection_lowcad. */
 GC_API gc_status gc_selection_lowcad_masked(int L, int T, double p, double log_base, const uint8_t *mask,
                                             int lattice, gc_sel **out);
 GC_API void gc_sel_free(gc_sel *sel);

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -203,6 +204,23 @@ bool fill_tree(gc_sel *s) {
     return (int)s->tree_ant.size() == s->n_occ;
 }
 
+// Largest selection the builders hold: 2^28 pairs (3.2 GB of host pair
+// arrays, as much again on the device).  Low-cadence selections take every
+// pair, N (N - 1) / 2, so they stop at about 23 000 antennas.
+constexpr long kMaxPairs = 1L << 28;
+
+// No C++ exception leaves the C ABI: allocation failure reads GC_ENOMEM.
+template <class F>
+gc_status no_throw(F &&f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        return GC_ENOMEM;
+    } catch (...) {
+        return GC_EINVAL;
+    }
+}
+
 }  // namespace
 
 void gc_sel_release_device(gc_sel *s) {
@@ -261,7 +279,7 @@ gc_status gc_sel_upload(gc_ctx *ctx, gc_sel *s) {
 
 extern "C" {
 
-gc_status gc_selection_subset(int L, int T, double p, double log_base, gc_sel **out) {
+static gc_status gc_selection_subset_impl(int L, int T, double p, double log_base, gc_sel **out) {
     if (!out) return GC_EINVAL;
     *out = nullptr;
     if (L == 2) return GC_EDEGEN;   // 6 visibilities for 8 unknowns: never four degeneracies
@@ -285,7 +303,7 @@ gc_status gc_selection_subset(int L, int T, double p, double log_base, gc_sel **
     std::vector<TypeVec> chosen(ord.begin(), ord.begin() + k);
     const int nd = null_dim_of(L, chosen);
     if (nd != 4) return GC_EDEGEN;
-    gc_sel *s = new (std::nothrow) gc_sel();
+    std::unique_ptr<gc_sel> s(new (std::nothrow) gc_sel());
     if (!s) return GC_ENOMEM;
     s->scheme = 0;
     s->L = L;
@@ -302,13 +320,13 @@ gc_status gc_selection_subset(int L, int T, double p, double log_base, gc_sel **
         s->win_t0.push_back(0);
         s->win_t1.push_back(T);
     }
-    fill_pairs(s);
-    fill_groups(s);
-    *out = s;
+    fill_pairs(s.get());
+    fill_groups(s.get());
+    *out = s.release();
     return GC_OK;
 }
 
-gc_status gc_selection_lowcad(int L, int T, double p, double log_base, gc_sel **out) {
+static gc_status gc_selection_lowcad_impl(int L, int T, double p, double log_base, gc_sel **out) {
     if (!out) return GC_EINVAL;
     *out = nullptr;
     if (L < 3 || L > 256 || T < 1 || !(p > 0.0) || log_base < 0.0 || log_base == 1.0) return GC_EINVAL;
@@ -329,7 +347,8 @@ gc_status gc_selection_lowcad(int L, int T, double p, double log_base, gc_sel **
     const int n_cycle = (int)room.size();
     const int t_int = T / n_cycle;
     if (t_int < 1) return GC_EINVAL;     // integration too short for the cycle count
-    gc_sel *s = new (std::nothrow) gc_sel();
+    if ((long)L * L * ((long)L * L - 1) / 2 > kMaxPairs) return GC_EUNSUPPORTED;
+    std::unique_ptr<gc_sel> s(new (std::nothrow) gc_sel());
     if (!s) return GC_ENOMEM;
     s->scheme = 1;
     s->L = L;
@@ -346,13 +365,13 @@ gc_status gc_selection_lowcad(int L, int T, double p, double log_base, gc_sel **
         s->win_t0.push_back(cycle[k] * t_int);
         s->win_t1.push_back((cycle[k] + 1) * t_int);
     }
-    fill_pairs(s);
-    fill_groups(s);
-    *out = s;
+    fill_pairs(s.get());
+    fill_groups(s.get());
+    *out = s.release();
     return GC_OK;
 }
 
-gc_status gc_selection_subset_masked(int L, int T, double p, double log_base, const uint8_t *mask, int lattice,
+static gc_status gc_selection_subset_masked_impl(int L, int T, double p, double log_base, const uint8_t *mask, int lattice,
                                      gc_sel **out) {
     if (!out) return GC_EINVAL;
     *out = nullptr;
@@ -392,7 +411,7 @@ gc_status gc_selection_subset_masked(int L, int T, double p, double log_base, co
     int k = best_k;
     while (k < (int)ord.size() && !criterion(k)) ++k;
     if (!criterion(k)) return GC_EDEGEN;
-    gc_sel *s = new (std::nothrow) gc_sel();
+    std::unique_ptr<gc_sel> s(new (std::nothrow) gc_sel());
     if (!s) return GC_ENOMEM;
     s->scheme = 0;
     s->L = L;
@@ -412,17 +431,16 @@ gc_status gc_selection_subset_masked(int L, int T, double p, double log_base, co
         s->win_t0.push_back(0);
         s->win_t1.push_back(T);
     }
-    fill_pairs(s);
-    fill_groups(s);
-    if (!fill_tree(s)) {   // the axis types must connect the array
-        delete s;
+    fill_pairs(s.get());
+    fill_groups(s.get());
+    if (!fill_tree(s.get())) {   // the axis types must connect the array
         return GC_EDEGEN;
     }
-    *out = s;
+    *out = s.release();
     return GC_OK;
 }
 
-gc_status gc_selection_lowcad_masked(int L, int T, double p, double log_base, const uint8_t *mask, int lattice,
+static gc_status gc_selection_lowcad_masked_impl(int L, int T, double p, double log_base, const uint8_t *mask, int lattice,
                                      gc_sel **out) {
     if (!out) return GC_EINVAL;
     *out = nullptr;
@@ -450,7 +468,8 @@ gc_status gc_selection_lowcad_masked(int L, int T, double p, double log_base, co
     const int n_cycle = (int)room.size();
     const int t_int = T / n_cycle;
     if (t_int < 1) return GC_EINVAL;
-    gc_sel *s = new (std::nothrow) gc_sel();
+    if ((long)n_occ * (n_occ - 1) / 2 > kMaxPairs) return GC_EUNSUPPORTED;
+    std::unique_ptr<gc_sel> s(new (std::nothrow) gc_sel());
     if (!s) return GC_ENOMEM;
     s->scheme = 1;
     s->L = L;
@@ -473,14 +492,35 @@ gc_status gc_selection_lowcad_masked(int L, int T, double p, double log_base, co
         x = x || (ord[k].first.dx == 1 && ord[k].first.dy == 0);
         y = y || (ord[k].first.dx == 0 && ord[k].first.dy == 1);
     }
-    fill_pairs(s);
-    fill_groups(s);
-    if (!x || !y || !fill_tree(s)) {
-        delete s;
+    fill_pairs(s.get());
+    fill_groups(s.get());
+    if (!x || !y || !fill_tree(s.get())) {
         return GC_EDEGEN;
     }
-    *out = s;
+    *out = s.release();
     return GC_OK;
+}
+
+gc_status gc_selection_subset(int L, int T, double p, double log_base, gc_sel **out) {
+    if (out) *out = nullptr;
+    return no_throw([&] { return gc_selection_subset_impl(L, T, p, log_base, out); });
+}
+
+gc_status gc_selection_lowcad(int L, int T, double p, double log_base, gc_sel **out) {
+    if (out) *out = nullptr;
+    return no_throw([&] { return gc_selection_lowcad_impl(L, T, p, log_base, out); });
+}
+
+gc_status gc_selection_subset_masked(int L, int T, double p, double log_base, const uint8_t *mask, int lattice,
+                                     gc_sel **out) {
+    if (out) *out = nullptr;
+    return no_throw([&] { return gc_selection_subset_masked_impl(L, T, p, log_base, mask, lattice, out); });
+}
+
+gc_status gc_selection_lowcad_masked(int L, int T, double p, double log_base, const uint8_t *mask, int lattice,
+                                     gc_sel **out) {
+    if (out) *out = nullptr;
+    return no_throw([&] { return gc_selection_lowcad_masked_impl(L, T, p, log_base, mask, lattice, out); });
 }
 
 void gc_sel_free(gc_sel *sel) {

@@ -58,6 +58,20 @@ def test_selection_errors(gcmod):
         gcmod.Selection("lowcad", 8, 0)
 
 
+def test_lowcad_beyond_the_pair_cap_is_refused(gcmod):
+    """A low-cadence selection takes every pair, N (N - 1) / 2; past 2^28 pairs
+    (about 23 000 antennas) the builder refuses with GC_EUNSUPPORTED before
+    allocating them, instead of running out of host memory."""
+    import time
+    t0 = time.perf_counter()
+    with pytest.raises(gcmod.GridcorrError) as e:
+        gcmod.Selection("lowcad", 256, 1 << 20)
+    assert e.value.status == gcmod.GC_EUNSUPPORTED
+    assert time.perf_counter() - t0 < 60.0
+    sel = gcmod.Selection("lowcad", 24, 4096)        # well inside the cap: every pair
+    assert sel.P == 576 * 575 // 2
+
+
 @pytest.mark.parametrize("s", [3, 4, 6, 8, 11])
 def test_hex_subset_matches_oracle(gcmod, s):
     """Masked-lattice subset selection of a hexagonal array equals the oracle's
