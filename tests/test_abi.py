@@ -70,6 +70,41 @@ def test_null_context_is_rejected(libso):
     assert libso.gc_last_error(None) == b"null context"
 
 
+def test_host_entry_points_validate_arguments(libso):
+    """The host-only calls reject what the header says they reject, without a
+    GPU: NULL outputs, sizes out of range, p <= 0, log base 1, a NULL mask or
+    an unknown lattice (GC_EINVAL = 1), and L = 2 (GC_EDEGEN = 6)."""
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    out = vp()
+    ref = ctypes.byref(out)
+    sub, low = libso.gc_selection_subset, libso.gc_selection_lowcad
+    subm, lowm = libso.gc_selection_subset_masked, libso.gc_selection_lowcad_masked
+    for f in (sub, low):
+        f.argtypes = [i, i, d, d, vp]
+    for f in (subm, lowm):
+        f.argtypes = [i, i, d, d, vp, i, vp]
+    assert sub(8, 64, 1.0, 2.0, None) == 1
+    for args in ((1, 64, 1.0, 2.0), (257, 64, 1.0, 2.0), (8, 0, 1.0, 2.0), (8, 64, 0.0, 2.0),
+                 (8, 64, 1.0, 1.0), (8, 64, -1.0, 2.0)):
+        assert sub(*args, ref) == 1, args
+        assert out.value is None
+        assert low(*args, ref) == 1, args
+    assert sub(2, 64, 1.0, 2.0, ref) == 6
+    mask = (ctypes.c_uint8 * 64)(*([1] * 64))
+    assert subm(8, 64, 1.0, 2.0, None, 0, ref) == 1
+    assert lowm(8, 64, 1.0, 2.0, None, 0, ref) == 1
+    assert subm(8, 64, 1.0, 2.0, ctypes.cast(mask, vp), 7, ref) == 1
+    assert subm(8, 64, 1.0, 2.0, ctypes.cast(mask, vp), 0, ref) == 0 and out.value
+    libso.gc_sel_free.argtypes = [vp]
+    libso.gc_sel_info.argtypes = [vp, vp]
+    info = (ctypes.c_int32 * 11)()
+    assert libso.gc_sel_info(out, ctypes.cast(info, vp)) == 0 and info[0] == 8 and info[10] == 64
+    assert libso.gc_sel_info(None, ctypes.cast(info, vp)) == 1
+    assert libso.gc_sel_info(out, None) == 1
+    libso.gc_sel_free(out)
+    libso.gc_sel_free(None)
+
+
 def test_binding_refuses_without_library(tmp_path, monkeypatch):
     """The binding raises when the compiled library is absent (no fallback)."""
     import importlib.util
