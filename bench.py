@@ -419,6 +419,28 @@ def rooflines(w: Workload, kern: dict, st_last, peaks: dict, probes: dict):
             rl["xeng_accumulate"] = {
                 "bound": "hbm", **hbm, "traffic": traffic, "algorithmic_bytes": by, "useful_flops": ops,
                 "per_unit": "8 B per antenna-sample", "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    if "xeng_tc_accumulate" in kern:
+        ms, n = kern["xeng_tc_accumulate"]
+        dur = ms / n * 1e-3
+        by = float(esz) * N * C * T
+        ops = 8.0 * sel.P * C * T          # useful: 8 integer ops per pair-sample
+        # executed: per 32-sample stage of each 128-antenna block, four dense
+        # e4m3 MMAs of 128 x 256 x 32 (D1 = RE.RE + IM.IM, D2 = IM.RE - RE.IM)
+        stages = C * (N // 128) * math.ceil(T / 32)
+        mma = stages * 4 * 2.0 * 128 * 256 * 32
+        rl["xeng_tc_accumulate"] = {
+            "bound": "tensor", "achieved": mma / dur / 1e12, "peak": probes["tc_f8"],
+            "unit": "TFLOP/s (e4m3 MMA executed)", "frac": mma / dur / 1e12 / probes["tc_f8"],
+            "traffic": recorded_traffic("xeng_tc_accumulate" + key,
+                                        source_hash("paper_2005_03060_gb300/csrc/gc_xengine_tc.cu")),
+            "executed_flops": mma, "useful_ops": ops, "useful_fraction": ops / mma,
+            "useful_tops": ops / dur / 1e12, "algorithmic_bytes": by,
+            "per_unit": (f"1 B and {8.0 * sel.P / N:.1f} useful integer ops per antenna-sample; "
+                         f"{4 * 2.0 * 128 * 256 * 32 / (128 * 32):.0f} executed MMA flops per antenna-sample "
+                         "(128 own antennas x 256-antenna halo per 32-sample stage)"),
+            "peak_source": "measured: gc_peak_probe dense e4m3 tcgen05 MMA on this GPU",
+            "hbm": {"achieved": by / dur / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": by / dur / 1e9 / hbm_peak}}
     if "lincal_cg" in kern:
         ms, n = kern["lincal_cg"]
         dur = ms / n * 1e-3
@@ -744,7 +766,7 @@ def run_ours(args, rank, world, local_rank):
     del h_volt
 
     peaks = load_peaks() or {}
-    probes = {k: ctx.peak_probe(k) for k in ("fp32", "fp64", "dp4a")}
+    probes = {k: ctx.peak_probe(k) for k in ("fp32", "fp64", "dp4a", "tc_f8")}
     rl = rooflines(w, kern, st_last, peaks, probes)
     if "lincal_fp64" in variants:
         v64 = variants["lincal_fp64"]
@@ -802,7 +824,7 @@ def run_ours(args, rank, world, local_rank):
             "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches": v[1]} for k, v in kern.items()},
             "calibration_variants": variants,
             "measured_peaks": {"fp32_tflops": probes["fp32"], "fp64_tflops": probes["fp64"],
-                               "dp4a_tops": probes["dp4a"]},
+                               "dp4a_tops": probes["dp4a"], "tc_f8_tflops": probes["tc_f8"]},
             "gpu_launches": launches,
             "e2e": e2e, "clocks": clocks}
     if secondary:

@@ -94,10 +94,13 @@ GC_API int gc_profile_read(gc_ctx *ctx, char *names, double *total_ms, int *laun
 
 /* Arithmetic throughput probe (not part of the paper's method; used for
  * roofline denominators).  kind 0: FP32 FMA, kind 1: FP64 FMA, kind 2: 4-way
- * signed 8-bit dot product with int32 accumulate (dp4a).  Launches a kernel
- * of independent chains on the context's device (legacy default stream),
+ * signed 8-bit dot product with int32 accumulate (dp4a), kind 3: dense FP8
+ * tensor-core MMA (tcgen05 kind::f8f6f4, e4m3 x e4m3 -> FP32, M = 128,
+ * N = 256, K = 32, one CTA per SM, operands resident in shared memory),
+ * kind 4: warp-level int8 MMA (mma.sync m16n8k32 s8 x s8 -> s32).
+ * Launches a kernel on the context's device (legacy default stream),
  * synchronises, and writes the achieved tera-operations per second (FMA = 2
- * flops; dp4a = 8 integer ops).  GC_EINVAL for another kind. */
+ * flops; dp4a = 8 integer ops; MMA = 2 M N K).  GC_EINVAL for another kind. */
 GC_API gc_status gc_peak_probe(gc_ctx *ctx, int kind, double *tflops);
 
 /* Smallest FFT side M for an L x L grid: the smallest power of two >= 2L - 1,

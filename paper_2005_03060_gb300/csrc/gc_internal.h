@@ -31,7 +31,9 @@ enum {
     GC_TUNE_CAL_CTAS = 2,
     GC_TUNE_CAL_ORDER = 3,
     GC_TUNE_CAL_OP = 4,
-    GC_TUNE_N = 5
+    GC_TUNE_XENG_PATH = 5,
+    GC_TUNE_XENG_TC_SHAPE = 6,
+    GC_TUNE_N = 7
 };
 
 // staging buffers of the streamed integration: with three, a chunk's copy
@@ -40,7 +42,7 @@ constexpr int GC_NSTAGE = 3;
 
 struct gc_ctx {
     int device = 0;
-    int tune[GC_TUNE_N] = {0, 0, 0, 0, 0};
+    int tune[GC_TUNE_N] = {0, 0, 0, 0, 0, 0, 0};
     int sm_count = 0;
     unsigned int *status_dev = nullptr;   // device error word
     void *scratch = nullptr;              // grow-only workspace

@@ -45,3 +45,9 @@ struct gc_sel {
 
 gc_status gc_sel_upload(gc_ctx *ctx, gc_sel *s);
 void gc_sel_release_device(gc_sel *s);
+
+// tensor-core X-engine (gc_xengine_tc.cu)
+bool gc_xeng_tc_eligible(const gc_sel *sel, int vfmt, const void *volt, int L);
+int gc_xeng_tc_slices(const gc_ctx *ctx, const gc_sel *sel, int L, int C);
+gc_status gc_xeng_tc_launch(gc_ctx *ctx, const void *volt, int L, int C, int T, const gc_sel *sel, void *part,
+                            void *apart, int n_tsplit, cudaStream_t s);

@@ -1,0 +1,120 @@
+// Inline-PTX helpers for the fifth-generation tensor cores (tcgen05): tensor
+// memory allocation, shared-memory matrix descriptors, the MMA itself, its
+// completion tracking and tensor-memory loads.  Shared by the tensor-core
+// X-engine and the throughput probe.
+#pragma once
+
+#include "gc_internal.h"
+
+#ifdef __CUDACC__
+
+// Instruction descriptor of tcgen05.mma kind::f8f6f4 / kind::f16 (dense):
+// FP32 accumulator (bit 4), A and B formats 0 (e4m3 / f16, bits 7-9 and
+// 10-12), MN-major A / B when the flags are set (bits 15 / 16), N / 8 at
+// bits 17-22, M / 16 at bits 24-28.  Bit 13 negates A.
+__host__ __device__ constexpr uint32_t gc_tc_idesc(int M, int N, bool a_mn, bool b_mn) {
+    return (1u << 4) | (a_mn ? (1u << 15) : 0u) | (b_mn ? (1u << 16) : 0u) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+constexpr uint32_t GC_TC_NEGATE_A = 1u << 13;
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading
+// dimension byte offset (stride between core matrices along K) and stride
+// dimension byte offset (stride between core matrices along M / N), all in
+// 16-byte units; bit 46 is the fixed descriptor version of this family.
+// A core matrix is 128 contiguous bytes: 8 rows of 16 bytes (K-major: 8 M/N
+// rows x 16 K bytes; MN-major: 8 K rows x 16 M/N bytes).
+__device__ __forceinline__ uint64_t gc_tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Whole-warp tensor-memory allocation of `ncols` columns (power of two >= 32);
+// the base address is written to shared memory at `slot`.
+__device__ __forceinline__ void gc_tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gc_smem_addr(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void gc_tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void gc_tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void gc_tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// D[tmem] (+)= A * B^T, kind::f8f6f4 (e4m3 x e4m3 -> f32), issued by one thread.
+__device__ __forceinline__ void gc_tc_mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive once on `bar` when every tcgen05.mma issued so far by this thread
+// has completed.
+__device__ __forceinline__ void gc_tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     gc_smem_addr(bar))
+                 : "memory");
+}
+
+// 32 consecutive 32-bit columns of this warp's 32 tensor-memory lanes
+// (thread t receives lane base + t), then wait for the load.
+__device__ __forceinline__ void gc_tmem_ld32(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void gc_mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(gc_smem_addr(bar)) : "memory");
+}
+
+// Bounded parity wait that also gives up when another role has raised
+// `*abort`; true when the phase completed.
+__device__ __forceinline__ bool gc_mbar_wait_abort(uint64_t *bar, uint32_t parity, volatile int *abort,
+                                                   uint64_t limit_ns) {
+    const uint32_t a = gc_smem_addr(bar);
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63u) == 0u) {
+            if (*abort) return false;
+            const uint64_t now = gc_globaltimer();
+            if (it == 0u) t0 = now;
+            else if (now - t0 > limit_ns) return false;
+        }
+    }
+}
+
+// 2-D tiled TMA load into shared memory, completing on `bar`.
+__device__ __forceinline__ void gc_tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(gc_smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(gc_smem_addr(bar))
+        : "memory");
+}
+
+#endif  // __CUDACC__

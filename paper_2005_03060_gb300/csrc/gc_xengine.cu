@@ -394,6 +394,35 @@ extern "C" gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, i
     gc_status st = gc_sel_upload(ctx, sel);
     if (st != GC_OK) return st;
     const int N = L * L;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // tensor cores for 4+4-bit subset selections ("xeng.path": 0 automatic,
+    // 1 integer SIMT path, 2 tensor cores only)
+    const int path = ctx->tune[GC_TUNE_XENG_PATH];
+    const bool tc_ok = gc_xeng_tc_eligible(sel, vfmt, volt, L);
+    if (path == 2 && !tc_ok)
+        return gc_fail(ctx, GC_EUNSUPPORTED, "gc_reduce: the tensor-core X-engine does not cover this call");
+    if (tc_ok && path != 1) {
+        int n_tsplit = gc_xeng_tc_slices(ctx, sel, L, C);
+        if (ctx->tune[GC_TUNE_XENG_TSPLIT] > 0) n_tsplit = std::max(n_tsplit, std::min(ctx->tune[GC_TUNE_XENG_TSPLIT], 64));
+        const size_t part_bytes = (size_t)n_tsplit * C * sel->P * sizeof(int2);
+        const size_t apart_bytes = autos ? (size_t)n_tsplit * C * N * sizeof(int) : 0;
+        st = gc_scratch_reserve(ctx, part_bytes + apart_bytes + 512);
+        if (st != GC_OK) return st;
+        char *scr = static_cast<char *>(ctx->scratch);
+        void *part = scr;
+        int *apart = autos ? reinterpret_cast<int *>(scr + ((part_bytes + 255) / 256) * 256) : nullptr;
+        st = gc_xeng_tc_launch(ctx, volt, L, C, T, sel, part, apart, n_tsplit, s);
+        if (st != GC_OK) return st;
+        const size_t work = (size_t)C * sel->P + (autos ? (size_t)C * N : 0);
+        const int rgrid = (int)std::min<size_t>((work + 255) / 256, (size_t)ctx->sm_count * 8);
+        int rec = gc_prof_begin(ctx, s, "xeng_reduce");
+        xeng_reduce<<<rgrid, 256, 0, s>>>(static_cast<const float2 *>(part), n_tsplit, C, sel->P, vfmt, vreduced,
+                                          reinterpret_cast<const float *>(apart), n_tsplit, N, autos);
+        gc_prof_end(ctx, s, rec);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch xeng_reduce");
+        return GC_OK;
+    }
     const int esz = vfmt == GC_C64 ? 8 : (vfmt == GC_C32H ? 4 : 1);
     const size_t sample_bytes = (size_t)N * esz;
     const bool tma = gc_aligned(volt, 16) && sample_bytes % 16 == 0;
@@ -452,7 +481,6 @@ extern "C" gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, i
     char *scr = static_cast<char *>(ctx->scratch);
     float2 *part = reinterpret_cast<float2 *>(scr);
     float *apart = autos ? reinterpret_cast<float *>(scr + ((part_bytes + 255) / 256) * 256) : nullptr;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
     XParams p;
     p.volt = volt;

@@ -177,9 +177,10 @@ class Context:
 
     def peak_probe(self, kind: str) -> float:
         """Measured throughput in tera-ops/s: 'fp32' / 'fp64' FMA (2 flops),
-        'dp4a' (8 integer ops)."""
+        'dp4a' (8 integer ops), 'tc_f8' (dense e4m3 tensor-core MMA, 2 M N K),
+        'mma_s8' (warp-level int8 MMA, 2 M N K)."""
         v = ctypes.c_double()
-        self.check(_lib.gc_peak_probe(self._h, {"fp32": 0, "fp64": 1, "dp4a": 2}[kind], ctypes.byref(v)))
+        self.check(_lib.gc_peak_probe(self._h, {"fp32": 0, "fp64": 1, "dp4a": 2, "tc_f8": 3, "mma_s8": 4}[kind], ctypes.byref(v)))
         return v.value
 
     # ------------------------------------------------------------------ correlate
