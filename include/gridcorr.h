@@ -61,7 +61,7 @@ typedef enum gc_vfmt {
                              (two's-complement Re in the high nibble, Im in the low) */
     GC_C32H = 2           /* binary16 pair (Re, Im): 4 bytes per antenna-sample; the
                              FP16-storage variant -- arithmetic stays FP32.
-                             Accepted by gc_correlate only. */
+                             Accepted by the correlators and gc_reduce. */
 } gc_vfmt;
 
 typedef struct gc_ctx gc_ctx;
@@ -78,7 +78,9 @@ GC_API void gc_destroy(gc_ctx *ctx);
 GC_API const char *gc_last_error(const gc_ctx *ctx);
 
 /* Synchronise `stream`, read and clear the device-side error word.  Returns
- * GC_ETIMEOUT if a kernel gave up a bounded wait since the last check. */
+ * GC_ETIMEOUT if a kernel gave up a bounded wait since the last check, and
+ * GC_EINVAL if a kernel met a zero or non-finite gain, or voltages whose
+ * sums were not finite (NaN or infinity in the input). */
 GC_API gc_status gc_device_status(gc_ctx *ctx, void *stream);
 
 /* Launch timing (not part of the paper's method; used by benchmarks).
@@ -122,7 +124,9 @@ GC_API int gc_fft_size(int L);
  *
  *   volt     [C][T][L*L] c64 (8-byte aligned), c32h (4-byte aligned) or
  *            i4c (device)
- *   gains    [C][L*L]    c64 (device); a zero gain gives inf/NaN output
+ *   gains    [C][L*L]    c64 (device); a zero or non-finite gain leaves
+ *            that antenna out of the sums and makes gc_device_status return
+ *            GC_EINVAL, as do voltages whose spectra are not finite
  *   vunique  [C][2L-1][2L-1] c64 (device), index [dy + L - 1][dx + L - 1]
  *   1 <= L <= 128, C >= 1, T >= 1 (GC_EINVAL otherwise); L > 64 (M = 256)
  *   is built for i4c only (GC_EUNSUPPORTED for c64 / c32h).
@@ -223,9 +227,16 @@ GC_API gc_status gc_sel_arrays(const gc_sel *sel, const int32_t **types, const i
  *   S_p = sum_{t in [t0_p, t1_p)} v_{i_p}(t) v_{j_p}(t)^*     (raw sums)
  *   A_i = sum_{t in [0, N_cycle t_int)} |v_i(t)|^2            (autos)
  *
- *   volt      [C][T][L*L] c64 or i4c (device), T >= the selection's T
- *   vreduced  c64: [C][P] c64 (FP32 sums); i4c: [C][P][2] int32, exact
- *   autos     c64: [C][L*L] float; i4c: [C][L*L] int32; may be NULL
+ *   volt      [C][T][L*L] c64, c32h or i4c (device), T >= the selection's T
+ *   vreduced  c64 / c32h: [C][P] c64 (FP32 sums); i4c: [C][P][2] int32, exact
+ *   autos     c64 / c32h: [C][L*L] float; i4c: [C][L*L] int32; may be NULL
+ * Non-finite complex64 / binary16 sums make gc_device_status return
+ * GC_EINVAL.
+ * 4+4-bit voltages of a subset selection (one window, at most 16 types) on
+ * an L = 16, 32 or 64 grid whose halo 128 + dy_max L is at most 256 antennas
+ * run on the tensor cores (tcgen05 FP8 MMAs on exact integer codes, equal bit
+ * for bit to the SIMT path); the tuning knob "xeng.path" forces the SIMT
+ * path (1) or the tensor cores (2; GC_EUNSUPPORTED where they do not apply).
  * Uses the context workspace (time-slice partial sums).  Two kernels.
  */
 GC_API gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, int C, int T,
@@ -280,7 +291,8 @@ GC_API gc_status gc_quantize(gc_ctx *ctx, const float *volt, int C, int T, int N
  *             chi2r = sum |r|^2 / sigma_p^2 / DoF with the radiometer
  *             sigma_p^2 = (A_i/T_a)(A_j/T_a)/t_p, DoF = P - N - n_ubl + 2,
  *             iters, status (GC_OK, GC_ENOCONV at max_iter, GC_ETIMEOUT past
- *             time_limit_ms, GC_EDEGEN on a non-positive pivot).
+ *             time_limit_ms, GC_EDEGEN on a non-positive pivot, GC_EINVAL
+ *             when the channel's V^reduced or its solution is not finite).
  * Zero-valued option fields select the defaults: max_iter 50 (lincal) /
  * 20000 (omnical), tol 1e-10 (lincal FP64) / 1e-6 (otherwise), damping
  * 0.3, time_limit_ms 10000 per channel.  Uses the context workspace.
@@ -363,6 +375,10 @@ GC_API gc_status gc_gain_variance(gc_ctx *ctx, const gc_sel *sel, float *var_amp
  *   "cal.operator"     GC_LINCAL_CG operator: 0 per-antenna gather over the
  *                      grid (selections of <= 16 baseline-types; others
  *                      fall back to 1), 1 scatter over the pair list
+ *   "xeng.path"        gc_reduce for 4+4-bit voltages: 0 tensor cores where
+ *                      they apply, 1 integer SIMT (dp4a), 2 tensor cores only
+ *   "xeng.tc_shape"    tensor-core X-engine launch shape (0 default; 1-4:
+ *                      converter warps and ring depths)
  * GC_EINVAL for an unknown name or a negative value.
  */
 GC_API gc_status gc_set_tuning(gc_ctx *ctx, const char *name, int value);
@@ -457,18 +473,21 @@ GC_API gc_status gc_integrate_host(gc_ctx *ctx, const void *h_volt, int vfmt, in
  * (M = max(16, gc_fft_size(L)));
  * e.g. L = 32, T = 4096 allows up to 512 channels per call.
  *
- * The first call on a device (the current device) looks up the device
- * address of that array (cudaGetSymbolAddress) and the tensor-map encoder;
- * make that first call before any stream capture.  Later calls only enqueue
- * two kernels on `stream`.
+ * Every call looks up the device address of that array on the current
+ * device (cudaGetSymbolAddress, which enqueues nothing; the first call on a
+ * device also loads the library's device code and the tensor-map encoder, so
+ * make that first call before any stream capture).  Apart from the lookup a
+ * call only enqueues two kernels on `stream`.
  *
  * `status` (optional, device, caller-zeroed) receives the device-side error
  * bits of the call (non-zero = a bounded wait ran out and the output is
- * incomplete); NULL sends them to a word of the library that is not
- * reported.  All calls on a device share the one scratch array, and each
- * call overwrites every element it later reads, so nothing has to be
- * cleared between calls; calls that overlap on the GPU (different streams
- * without ordering between them) race on the array and give wrong results.
+ * incomplete, or a gain or voltage was zero or not finite); NULL sends them to
+ * a word of the library that is not reported, so with NULL such a call still
+ * returns GC_OK and its output can hold spectra an earlier call left in the
+ * shared array.  All calls on a device share the one scratch array, and each
+ * call overwrites every element it later reads, so nothing has to be cleared
+ * between calls; calls that overlap on the GPU (different streams without
+ * ordering between them) race on the array and give wrong results.
  *
  * Returns GC_EINVAL for bad arguments or sizes beyond the fixed scratch,
  * GC_ECUDA when a CUDA call fails, GC_EUNSUPPORTED for an unbuilt size.

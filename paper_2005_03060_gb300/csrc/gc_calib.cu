@@ -756,7 +756,8 @@ __device__ void finish_channel(const CalParams &p, int c, const R *xg, const R *
         s.dof = p.P - p.n_occ - p.n_ubl + 2;
         s.chi2r = p.autos && s.dof > 0 ? acc[1] / s.dof : -1.0;
         s.iters = iters;
-        s.status = st;
+        // observations or solution not finite: the channel has no result
+        s.status = isfinite(acc[0]) ? st : GC_EINVAL;
         s.inner = inner;
         p.stats[c] = s;
     }

@@ -334,7 +334,12 @@ fftcorr_accumulate(const __grid_constant__ CUtensorMap tmap, const Params p) {
             if (x < L && y < L && (!p.mask || p.mask[y * L + x])) {
                 const float2 gg = p.gains[(size_t)c * L * L + y * L + x];
                 const float d = gg.x * gg.x + gg.y * gg.y;
-                cc = make_float2(gg.x / d, -gg.y / d);
+                if (d > 0.f && isfinite(d)) {
+                    cc = make_float2(gg.x / d, -gg.y / d);
+                } else {
+                    // w = v / g is undefined: report it and leave the antenna out
+                    atomicOr(p.status, GC_DEV_BADINPUT);
+                }
                 // one row residue (k = q for the whole item): the row twiddle
                 // omega_M^{k x} rides on the coefficient
                 if (K::S1 == 1) cc = cmul(cc, tws[(q * x) & (K::M - 1)]);
@@ -519,7 +524,7 @@ fftcorr_accumulate(const __grid_constant__ CUtensorMap tmap, const Params p) {
 template <int M>
 __global__ void __launch_bounds__(256)
 fftcorr_finalize(const float *__restrict__ ppart, int n_parts, float2 *__restrict__ vunique, int L, int T,
-                 const float *__restrict__ ndtab) {
+                 const float *__restrict__ ndtab, unsigned int *status) {
     extern __shared__ __align__(128) unsigned char smem[];
     float *P = reinterpret_cast<float *>(smem);                 // [M][M]
     float2 *Q = reinterpret_cast<float2 *>(smem + M * M * 4);   // [M][W]
@@ -533,6 +538,7 @@ fftcorr_finalize(const float *__restrict__ ppart, int n_parts, float2 *__restric
     for (int k = threadIdx.x; k < M * M; k += blockDim.x) {
         double s = 0.0;
         for (int pp = 0; pp < n_parts; ++pp) s += (double)src[(size_t)pp * M * M + k];
+        if (!isfinite(s)) atomicOr(status, GC_DEV_BADINPUT);   // non-finite voltages
         P[k] = (float)s;
     }
     __syncthreads();
@@ -579,7 +585,8 @@ constexpr int kFinCols = 16;
 
 template <int M>
 __global__ void __launch_bounds__(256)
-fftcorr_finalize_rows(const float *__restrict__ ppart, int n_parts, float2 *__restrict__ Q, int L) {
+fftcorr_finalize_rows(const float *__restrict__ ppart, int n_parts, float2 *__restrict__ Q, int L,
+                      unsigned int *status) {
     __shared__ float P[kFinRows][M];
     __shared__ float2 tws[M];
     const int c = blockIdx.x, ky0 = blockIdx.y * kFinRows, W = 2 * L - 1;
@@ -591,6 +598,7 @@ fftcorr_finalize_rows(const float *__restrict__ ppart, int n_parts, float2 *__re
     for (int k = threadIdx.x; k < kFinRows * M; k += blockDim.x) {
         double s = 0.0;
         for (int pp = 0; pp < n_parts; ++pp) s += (double)src[(size_t)pp * M * M + k];
+        if (!isfinite(s)) atomicOr(status, GC_DEV_BADINPUT);
         P[k / M][k % M] = (float)s;
     }
     __syncthreads();
@@ -747,7 +755,8 @@ struct Launcher {
         if constexpr (K::M > 128) {
             float2 *Q = reinterpret_cast<float2 *>(static_cast<char *>(ctx->scratch) + part_bytes);
             rec = gc_prof_begin(ctx, stream, "fftcorr_finalize");
-            fftcorr_finalize_rows<K::M><<<dim3(C, K::M / kFinRows), 256, 0, stream>>>(p.ppart, best_n, Q, L);
+            fftcorr_finalize_rows<K::M><<<dim3(C, K::M / kFinRows), 256, 0, stream>>>(p.ppart, best_n, Q, L,
+                                                                                       p.status);
             fftcorr_finalize_cols<K::M><<<dim3(C, (W + kFinCols - 1) / kFinCols), 256, 0, stream>>>(
                 Q, reinterpret_cast<float2 *>(vunique), L, T, ndtab);
             gc_prof_end(ctx, stream, rec);
@@ -757,7 +766,7 @@ struct Launcher {
             e = cudaFuncSetAttribute(fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
             if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaFuncSetAttribute(fftcorr_finalize)");
             rec = gc_prof_begin(ctx, stream, "fftcorr_finalize");
-            fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n, reinterpret_cast<float2 *>(vunique), L, T, ndtab);
+            fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n, reinterpret_cast<float2 *>(vunique), L, T, ndtab, p.status);
             gc_prof_end(ctx, stream, rec);
         }
         e = cudaGetLastError();
@@ -856,35 +865,29 @@ static __device__ __align__(256) float g_noalloc_scratch[kNoallocScratchBytes / 
 static __device__ unsigned int g_noalloc_status;       // timeout flags when the caller passes none
 
 struct NoallocDev {
-    bool ready = false;
     float *scratch = nullptr;
     unsigned int *status = nullptr;
 };
-constexpr int kMaxDevices = 64;
-NoallocDev g_noalloc_dev[kMaxDevices];
 std::mutex g_noalloc_mu;
 void *g_noalloc_encode = nullptr;
 
-// Once per device, with that device current: resolve the device addresses of
-// the file-scope arrays (host code only sees a host-side stand-in symbol).
-gc_status noalloc_setup(int dev, NoallocDev **out) {
-    if (dev < 0 || dev >= kMaxDevices) return GC_EUNSUPPORTED;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    NoallocDev &d = g_noalloc_dev[dev];
-    if (!d.ready) {
-        void *p = nullptr, *q = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
-            cudaGetLastError();
-            return GC_ECUDA;
-        }
-        if (cudaGetSymbolAddress(&q, g_noalloc_status) != cudaSuccess) {
-            cudaGetLastError();
-            return GC_ECUDA;
-        }
-        d.scratch = static_cast<float *>(p);
-        d.status = static_cast<unsigned int *>(q);
-        d.ready = true;
+// On every call, with the caller's device current: resolve the device
+// addresses of the file-scope arrays (host code only sees a host-side
+// stand-in symbol).  The lookup enqueues nothing; doing it per call keeps the
+// addresses right after a device or context reset reloads the module.
+gc_status noalloc_setup(NoallocDev *d) {
+    void *p = nullptr, *q = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+        cudaGetLastError();
+        return GC_ECUDA;
     }
+    if (cudaGetSymbolAddress(&q, g_noalloc_status) != cudaSuccess) {
+        cudaGetLastError();
+        return GC_ECUDA;
+    }
+    d->scratch = static_cast<float *>(p);
+    d->status = static_cast<unsigned int *>(q);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_encode) {
         cudaDriverEntryPointQueryResult qr;
         void *fn = nullptr;
@@ -893,7 +896,6 @@ gc_status noalloc_setup(int dev, NoallocDev **out) {
             qr == cudaDriverEntryPointSuccess)
             g_noalloc_encode = fn;
     }
-    *out = &d;
     return GC_OK;
 }
 
@@ -969,7 +971,8 @@ gc_status noalloc_run(const NoallocDev &d, const void *volt, int L, int C, int T
     auto fin = fftcorr_finalize<K::M>;
     if (cudaFuncSetAttribute(fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem) != cudaSuccess)
         return GC_ECUDA;
-    fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n, reinterpret_cast<float2 *>(vunique), L, T, nullptr);
+    fin<<<C, 256, fsmem, stream>>>(p.ppart, best_n, reinterpret_cast<float2 *>(vunique), L, T, nullptr,
+                                   p.status);
     if (cudaGetLastError() != cudaSuccess) return GC_ECUDA;
     return GC_OK;
 }
@@ -984,11 +987,10 @@ extern "C" gc_status gc_correlate_noalloc(const void *volt, int vfmt, int L, int
     if (!gc_aligned(gains, 8) || !gc_aligned(vunique, 8) || (vfmt == GC_C64 && !gc_aligned(volt, 8)) ||
         (vfmt == GC_C32H && !gc_aligned(volt, 4)) || (status && !gc_aligned(status, 4)))
         return GC_EINVAL;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return GC_ECUDA;
-    NoallocDev *d = nullptr;
-    gc_status st = noalloc_setup(dev, &d);
+    NoallocDev dd;
+    gc_status st = noalloc_setup(&dd);
     if (st != GC_OK) return st;
+    const NoallocDev *d = &dd;
     const int M = std::max(16, gc_fft_size(L));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (vfmt == GC_C64) {

@@ -15,6 +15,7 @@
 #define GC_DEV_TIMEOUT_XENG  0x2u
 #define GC_DEV_TIMEOUT_CAL   0x4u
 #define GC_DEV_BADINDEX      0x8u
+#define GC_DEV_BADINPUT      0x10u   // zero or non-finite gain, non-finite sums
 
 // bounded waits: give up after this many nanoseconds of %globaltimer
 #define GC_WAIT_LIMIT_NS     1000000000ull

@@ -163,6 +163,8 @@ gc_status gc_device_status(gc_ctx *ctx, void *stream) {
         return gc_fail(ctx, GC_ETIMEOUT, buf);
     }
     if (h & GC_DEV_BADINDEX) return gc_fail(ctx, GC_EINVAL, "device saw an out-of-range index");
+    if (h & GC_DEV_BADINPUT)
+        return gc_fail(ctx, GC_EINVAL, "a gain was zero or not finite, or the voltages gave non-finite sums");
     return GC_OK;
 }
 

@@ -331,7 +331,8 @@ __global__ void __launch_bounds__(kXThreads, 2) xeng_accumulate(const XParams p)
 
 // Sum the time slices: V^reduced (c64: float2, i4c: exact int32 pairs) and autos.
 __global__ void xeng_reduce(const float2 *__restrict__ part, int n_tsplit, int C, int P, int vfmt, void *vred,
-                            const float *__restrict__ apart, int n_aslots, int N, void *autos) {
+                            const float *__restrict__ apart, int n_aslots, int N, void *autos,
+                            unsigned int *status) {
     const size_t total = (size_t)C * P;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total + (size_t)C * N;
          idx += (size_t)gridDim.x * blockDim.x) {
@@ -343,6 +344,7 @@ __global__ void xeng_reduce(const float2 *__restrict__ part, int n_tsplit, int C
                     re += v.x;
                     im += v.y;
                 }
+                if (!isfinite(re) || !isfinite(im)) atomicOr(status, GC_DEV_BADINPUT);   // non-finite voltages
                 reinterpret_cast<float2 *>(vred)[idx] = make_float2((float)re, (float)im);
             } else {
                 int re = 0, im = 0;
@@ -417,7 +419,8 @@ extern "C" gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, i
         const int rgrid = (int)std::min<size_t>((work + 255) / 256, (size_t)ctx->sm_count * 8);
         int rec = gc_prof_begin(ctx, s, "xeng_reduce");
         xeng_reduce<<<rgrid, 256, 0, s>>>(static_cast<const float2 *>(part), n_tsplit, C, sel->P, vfmt, vreduced,
-                                          reinterpret_cast<const float *>(apart), n_tsplit, N, autos);
+                                          reinterpret_cast<const float *>(apart), n_tsplit, N, autos,
+                                          ctx->status_dev);
         gc_prof_end(ctx, s, rec);
         e = cudaGetLastError();
         if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch xeng_reduce");
@@ -528,7 +531,7 @@ extern "C" gc_status gc_reduce(gc_ctx *ctx, const void *volt, int vfmt, int L, i
     const int rgrid = (int)std::min<size_t>((work + 255) / 256, (size_t)ctx->sm_count * 8);
     rec = gc_prof_begin(ctx, s, "xeng_reduce");
     xeng_reduce<<<rgrid, 256, 0, s>>>(part, n_tsplit, C, sel->P, vfmt, vreduced, apart,
-                                      sel->n_windows * n_tsplit, N, autos);
+                                      sel->n_windows * n_tsplit, N, autos, ctx->status_dev);
     gc_prof_end(ctx, s, rec);
     e = cudaGetLastError();
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch xeng_reduce");
