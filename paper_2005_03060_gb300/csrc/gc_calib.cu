@@ -2026,10 +2026,21 @@ __device__ void cg_solve_channel_rel(const CalParams &p, int c, CgWork &w, doubl
         if (!coarse) return ry;
         for (int t2 = threadIdx.x; t2 < 2 * nc; t2 += blockDim.x) {
             const int m = t2 / nc, row = t2 - m * nc;
-            const float *Am = m ? w.Cp : w.Ca;
+            const float *arow = (m ? w.Cp : w.Ca) + (size_t)row * nc;
             const float *rr = w.rc + m * nc;
-            float a = 0.f;
-            for (int cc = 0; cc < nc; ++cc) a = fmaf(Am[row * nc + cc], rr[cc], a);
+            // four partial sums, so that the row's loads (global memory when
+            // the coarse operators do not fit beside the vectors) overlap
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            int cc = 0;
+#pragma unroll 4
+            for (; cc + 4 <= nc; cc += 4) {
+                a0 = fmaf(arow[cc], rr[cc], a0);
+                a1 = fmaf(arow[cc + 1], rr[cc + 1], a1);
+                a2 = fmaf(arow[cc + 2], rr[cc + 2], a2);
+                a3 = fmaf(arow[cc + 3], rr[cc + 3], a3);
+            }
+            for (; cc < nc; ++cc) a0 = fmaf(arow[cc], rr[cc], a0);
+            const float a = (a0 + a1) + (a2 + a3);
             w.yc[t2] = a;
             ry = fmaf(a, w.rc[t2], ry);
         }
@@ -2039,8 +2050,19 @@ __device__ void cg_solve_channel_rel(const CalParams &p, int c, CgWork &w, doubl
     // anything, NaN patterns included, before the first update); rc is
     // cleared for the next restriction
     auto update_q = [&](float beta, bool first) {
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-            float2 z = zs[e];
+        constexpr int U = 4;   // elements whose z loads are in flight together
+        for (int e0 = threadIdx.x; e0 < ne; e0 += U * blockDim.x) {
+            float2 zu[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * blockDim.x;
+                zu[u] = e < ne ? zs[e] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e >= ne) break;
+            float2 z = zu[u];
             if (coarse) {
                 const unsigned ci = w.cid[e];
                 if (ci != 0xffffu) {
@@ -2053,6 +2075,7 @@ __device__ void cg_solve_channel_rel(const CalParams &p, int c, CgWork &w, doubl
             } else {
                 const float2 pq = q[e];
                 q[e] = make_float2(z.x + beta * pq.x, z.y + beta * pq.y);
+            }
             }
         }
         for (int t2 = threadIdx.x; t2 < 2 * nc; t2 += blockDim.x) w.rc[t2] = 0.f;
@@ -2097,17 +2120,34 @@ __device__ void cg_solve_channel_rel(const CalParams &p, int c, CgWork &w, doubl
             if (!(v1[0] > 0.f)) break;
             const float alpha = rz / v1[0];
             float v3[3] = {0.f, 0.f, 0.f};
-            for (int e0 = threadIdx.x - lane0; e0 < ne; e0 += blockDim.x) {
-                const int e = e0 + lane0;
-                float2 rn = make_float2(0.f, 0.f);
-                if (e < ne) {
-                    const float2 pq = q[e], a = acc[e], x = xs[e], r = rs[e];
-                    const float mg = mu * w.G[e];
-                    xs[e] = make_float2(x.x + alpha * pq.x, x.y + alpha * pq.y);
-                    rn = make_float2(r.x - alpha * (a.x + mg * pq.x), r.y - alpha * (a.y + mg * pq.y));
-                    rs[e] = rn;
+            // the same elements per thread as before, four at a time so that
+            // their global loads (acc, x, r) are in flight together
+            constexpr int U = 4;
+            for (int e0 = threadIdx.x - lane0; e0 < ne; e0 += U * blockDim.x) {   // warp-uniform trip count
+                float2 au[U], xu[U], ru[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = e0 + lane0 + u * blockDim.x;
+                    if (e < ne) {
+                        au[u] = acc[e];
+                        xu[u] = xs[e];
+                        ru[u] = rs[e];
+                    }
                 }
-                jacobi(e, rn, mu, v3[0], v3[1]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (e0 + u * blockDim.x >= ne) break;   // warp-uniform
+                    const int e = e0 + lane0 + u * blockDim.x;
+                    float2 rn = make_float2(0.f, 0.f);
+                    if (e < ne) {
+                        const float2 pq = q[e], a = au[u], x = xu[u], r = ru[u];
+                        const float mg = mu * w.G[e];
+                        xs[e] = make_float2(x.x + alpha * pq.x, x.y + alpha * pq.y);
+                        rn = make_float2(r.x - alpha * (a.x + mg * pq.x), r.y - alpha * (a.y + mg * pq.y));
+                        rs[e] = rn;
+                    }
+                    jacobi(e, rn, mu, v3[0], v3[1]);
+                }
             }
             __syncthreads();
             v3[2] = coarse_solve();

@@ -245,6 +245,17 @@ __device__ __forceinline__ float2 i4c_to_f2(unsigned int byte) {
     return make_float2(re, im);
 }
 
+// Byte e of words of n + 8 codes (Re, Im) -> floats: the byte placed under
+// the exponent of 2^23 is the float 2^23 + n + 8 (one byte permute), and
+// subtracting 2^23 + 8 leaves n -- the values of i4c_to_f2, with the nibble
+// extraction shared by the four bytes of a word.
+__device__ __forceinline__ float2 i4c_bytes_to_f2(unsigned int ure, unsigned int uim, int e) {
+    const unsigned int sel = 0x7440u | (unsigned int)e;
+    const float re = __uint_as_float(__byte_perm(ure, 0x4B000000u, sel)) - 8388616.0f;
+    const float im = __uint_as_float(__byte_perm(uim, 0x4B000000u, sel)) - 8388616.0f;
+    return make_float2(re, im);
+}
+
 // One row input into the fold: b += v c omega_M^{k x}.  With one row residue
 // per item (S1 == 1) the coefficient already carries the twiddle.
 template <class K>
@@ -426,11 +437,19 @@ fftcorr_accumulate(const __grid_constant__ CUtensorMap tmap, const Params p) {
                             if (x0 < K::LMAX) {
                                 const uint4 raw = *reinterpret_cast<const uint4 *>(srow + x0);
                                 const unsigned int words[4] = {raw.x, raw.y, raw.z, raw.w};
+                                // n + 8 of the four Re and the four Im nibbles of a word,
+                                // one byte each (two and one instructions)
+                                unsigned int ure[4], uim[4];
+#pragma unroll
+                                for (int w = 0; w < 4; ++w) {
+                                    ure[w] = ((words[w] >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
+                                    uim[w] = (words[w] & 0x0F0F0F0Fu) ^ 0x08080808u;
+                                }
 #pragma unroll
                                 for (int e = 0; e < 16 && xp + e < K::F1; ++e) {
                                     const int x = x0 + e;
                                     if (x < K::LMAX) {
-                                        const float2 v = i4c_to_f2(words[e >> 2] >> (8 * (e & 3)));
+                                        const float2 v = i4c_bytes_to_f2(ure[e >> 2], uim[e >> 2], e & 3);
                                         row_in<K>(b[xp + e], v, crow[x], tws, k, x);
                                     }
                                 }

@@ -79,35 +79,6 @@ __device__ __forceinline__ void gc_tmem_ld32(uint32_t taddr, uint32_t *r) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void gc_mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(gc_smem_addr(bar)) : "memory");
-}
-
-// Bounded parity wait that also gives up when another role has raised
-// `*abort`; true when the phase completed.
-__device__ __forceinline__ bool gc_mbar_wait_abort(uint64_t *bar, uint32_t parity, volatile int *abort,
-                                                   uint64_t limit_ns) {
-    const uint32_t a = gc_smem_addr(bar);
-    uint64_t t0 = 0;
-    for (uint32_t it = 0;; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if ((it & 63u) == 0u) {
-            if (*abort) return false;
-            const uint64_t now = gc_globaltimer();
-            if (it == 0u) t0 = now;
-            else if (now - t0 > limit_ns) return false;
-        }
-    }
-}
-
 // 2-D tiled TMA load into shared memory, completing on `bar`.
 __device__ __forceinline__ void gc_tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1) {
     asm volatile(

@@ -197,3 +197,40 @@ def test_correlate_paper_scale_sampled(gc, orc):
             assert e < TOL, (c, dx, dy, e)
     del volt
     torch.cuda.empty_cache()
+
+
+
+@pytest.mark.parametrize("L,C,T", [(64, 2, 300), (33, 3, 77), (48, 1, 1031), (64, 5, 4)])
+def test_correlate_i4c_m128_ragged(gc, orc, L, C, T):
+    """M = 128 (L = 33..64) with 4+4-bit voltages over ragged sample counts
+    (odd T, T below one stage copy) and rows L < 64 that stay zero."""
+    volt, gains, _ = synth.make_voltages(700 + L + T, L, C, T, n_src=20)
+    q = _quantised(volt)
+    out = gc.correlate(torch.from_numpy(q).cuda(), gains.cuda())
+    gc.device_status()
+    got = out.cpu().numpy()
+    for c in range(C):
+        ref = orc.fx(orc.unpack_i4c(q[c]), gains[c].numpy(), L)
+        assert lag_err(got[c], ref, L) < TOL, (L, c)
+
+
+def test_correlate_i4c_m128_chunk_sizes_agree(gc):
+    """Work items of 2..512 samples (the "fft.chunk_len" knob) over many
+    channels give the same V^unique to FP32 rounding on the 64x64 grid."""
+    L, C, T = 64, 12, 2048
+    g = torch.Generator(device="cuda").manual_seed(3)
+    q = torch.randint(0, 256, (C, T, L * L), dtype=torch.uint8, device="cuda", generator=g)
+    _, gains, _ = synth.make_voltages(5, L, C, 1, n_src=1)
+    gains = gains.cuda()
+    outs = {}
+    try:
+        for chunk in (0, 2, 130, 512):
+            gc.set_tuning("fft.chunk_len", chunk)
+            outs[chunk] = gc.correlate(q, gains).cpu().numpy()
+            gc.device_status()
+    finally:
+        gc.set_tuning("fft.chunk_len", 0)
+    ref = outs[0]
+    for key, got in outs.items():
+        for c in range(C):
+            assert lag_err(got[c], ref[c], L) < TOL, key
