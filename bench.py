@@ -465,6 +465,16 @@ def rooflines(w: Workload, kern: dict, st_last, peaks: dict, probes: dict):
     return rl
 
 
+def tune_workload(ctx, w) -> dict:
+    """Run the project's autotuner (paper_2005_03060_gb300/autotune.py) over
+    the correlator and X-engine knobs of workload w; returns the choices and
+    the timings behind them."""
+    from paper_2005_03060_gb300 import autotune
+    out = {"correlator": autotune.tune_correlator(ctx, w.volt, w.gains, w.L, reps=1)}
+    out["xengine"] = autotune.tune_xengine(ctx, w.volt, w.sel, reps=1)
+    return out
+
+
 def calibration_variants(w: Workload, Cs: int, reps_fast: int):
     """The other solvers on the first Cs channels of the same V^reduced,
     compared with the banded FP64 solve (gain difference after the output
@@ -477,22 +487,26 @@ def calibration_variants(w: Workload, Cs: int, reps_fast: int):
     vr, au = w.vr[:Cs].contiguous(), w.au[:Cs].contiguous()
     out, g64 = {}, None
     # op: the matrix-free operator ("cal.operator": 0 gather over the grid, 1 pair-list scatter)
-    for name, solver, prec, allc, op in [("lincal_fp64", "lincal", "fp64", False, 0),
-                                         ("lincal_fp32", "lincal", "fp32", False, 0),
-                                         ("omnical_fp32", "omnical", "fp32", False, 0),
-                                         ("lincal_cg_mixed", "lincal_cg", "fp32", True, 0),
-                                         ("lincal_cg_mixed_pair_scatter", "lincal_cg", "fp32", True, 1)]:
+    # lincal_cg_plain_fp32: the same matrix-free solver with every reduction
+    # in FP32 (the like-for-like plain-FP32 form of the mixed one)
+    for name, solver, prec, allc, op, r32 in [("lincal_fp64", "lincal", "fp64", False, 0, False),
+                                              ("lincal_fp32", "lincal", "fp32", False, 0, False),
+                                              ("omnical_fp32", "omnical", "fp32", False, 0, False),
+                                              ("lincal_cg_mixed", "lincal_cg", "fp32", True, 0, False),
+                                              ("lincal_cg_plain_fp32", "lincal_cg", "fp32", True, 0, True),
+                                              ("lincal_cg_mixed_pair_scatter", "lincal_cg", "fp32", True, 1, False)]:
         ctx.set_tuning("cal.operator", op)
         v_in, a_in = (w.vr, w.au) if allc else (vr, au)
         Cn = w.C if allc else Cs
         reps = reps_fast if allc else 1
-        g, V, st = ctx.calibrate(v_in, sel, a_in, solver=solver, precision=prec)
+        g, V, st = ctx.calibrate(v_in, sel, a_in, solver=solver, precision=prec, fp32_reductions=r32)
         torch.cuda.synchronize(w.dev)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(reps):
-            ctx.calibrate(v_in, sel, a_in, solver=solver, precision=prec, gains=g, vmodel=V, stats=st)
+            ctx.calibrate(v_in, sel, a_in, solver=solver, precision=prec, gains=g, vmodel=V, stats=st,
+                          fp32_reductions=r32)
         b.record()
         torch.cuda.synchronize(w.dev)
         ms = a.elapsed_time(b) / reps
@@ -563,10 +577,31 @@ def measure_batching(ctx, dev, stream):
         for a, (g, v, st) in zip(arrays, per):
             ctx.calibrate(a["vred"], a["sel"], solver="lincal_cg", precision="fp32", gains=g, vmodel=v, stats=st)
 
+    from paper_2005_03060_gb300 import autotune
+    tuned = autotune.tune_calibration(ctx, arrays, reps=1)   # "cal.order", "cal.ctas_per_sm"
     ms_per = _forms_timed(one_launch_per_array, stream, 3)
     for a, (g, v, st) in zip(arrays, ctx.calibrate_batched(arrays)):
         a["gains"], a["vmodel"], a["stats"] = g, v, st
     ms_b = _forms_timed(lambda: ctx.calibrate_batched(arrays), stream, 3)
+    ctx.device_status()
+    # the same persistent launch captured once into a CUDA graph and replayed
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream(device=stream.device)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        ctx.calibrate_batched(arrays)
+    graph.replay()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps_g = 3
+    # replay() launches on the current stream: time it there
+    e0.record(stream)
+    for _ in range(reps_g):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_g = e0.elapsed_time(e1) / reps_g
     ctx.device_status()
     ok = all(bool(np.all(gridcorr.decode_stats(a["stats"])["status"] == 0)) for a in arrays)
     diff = max(((a["gains"] - g).abs() / g.abs()).max().item() for a, (g, _, _) in zip(arrays, per))
@@ -575,14 +610,16 @@ def measure_batching(ctx, dev, stream):
             "antennas": sum(L * L for L in BATCH_GRIDS), "T": BATCH_T,
             "batched_ms": ms_b, "batched_chans_per_s": total / (ms_b * 1e-3),
             "per_array_ms": ms_per, "per_array_chans_per_s": total / (ms_per * 1e-3),
+            "graph_ms": ms_g, "graph_chans_per_s": total / (ms_g * 1e-3),
+            "autotuned": {k: {"knob": v["knob"], "best": v["best"], "ms": v["ms"]} for k, v in tuned.items()},
             "all_converged": ok, "max_gain_diff_batched_vs_per_array": diff,
             "l2": f"V^reduced of all arrays {sum(a['vred'].numel() * 8 for a in arrays) / 1e9:.2f} GB, larger than L2",
             "input": "V^reduced from the paper's visibility-level simulation (Sec. 3), SNR 10 per sample; "
-                     "subset selections (p = 1, log2); eager launches (the batched launch is also "
-                     "graph-capturable)"}
+                     "subset selections (p = 1, log2); batched_ms: eager launch, graph_ms: the same "
+                     "launch captured in a CUDA graph and replayed; knobs from the autotuner"}
 
 
-def measure_differentiation(ctx, dev, stream, hbm_peak):
+def measure_differentiation(ctx, dev, stream, hbm_peak, channels=None):
     """Differentiation form: the chi^2 of the redundant model (numerator of
     Eq. redchi) and its adjoint on the 128x128 array (16 384 antennas, 512
     channels, T = 4096, subset selection), residuals recomputed in the
@@ -596,7 +633,7 @@ def measure_differentiation(ctx, dev, stream, hbm_peak):
 
     from paper_2005_03060_gb300 import gridcorr, synth
 
-    L, C, T = DIFF_L, DIFF_C, DIFF_T
+    L, C, T = DIFF_L, channels or DIFF_C, DIFF_T
     sel = gridcorr.Selection("subset", L, T)
     pt = sel.pair_type()
     tp = (sel.win_t1 - sel.win_t0)[pt]
@@ -628,12 +665,13 @@ def measure_differentiation(ctx, dev, stream, hbm_peak):
                      "per sample; evaluation at the true gains and visibilities"}
 
 
-def measure_forms(ctx, dev, stream, hbm_peak):
+def measure_forms(ctx, dev, stream, hbm_peak, diff_channels=None):
     """Both forms; a failure is recorded in the result instead of ending the run."""
     import torch
     out = {}
     for name, fn in (("batching", lambda: measure_batching(ctx, dev, stream)),
-                     ("differentiation", lambda: measure_differentiation(ctx, dev, stream, hbm_peak))):
+                     ("differentiation", lambda: measure_differentiation(ctx, dev, stream, hbm_peak,
+                                                                         diff_channels))):
         try:
             out[name] = fn()
         except Exception as e:                      # noqa: BLE001 -- reported, not hidden
@@ -700,6 +738,9 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    # launch shapes from the autotuner, on this workload's own data (knobs
+    # only change how the work is split, never the arithmetic's definition)
+    autotuned = None if args.no_autotune else tune_workload(ctx, w)
     for _ in range(args.warmup):
         w.step()
     ctx.device_status()
@@ -766,7 +807,7 @@ def run_ours(args, rank, world, local_rank):
     del h_volt
 
     peaks = load_peaks() or {}
-    probes = {k: ctx.peak_probe(k) for k in ("fp32", "fp64", "dp4a", "tc_f8")}
+    probes = {k: ctx.peak_probe(k) for k in ("fp32", "fp64", "dp4a", "tc_f8", "mma_s8")}
     rl = rooflines(w, kern, st_last, peaks, probes)
     if "lincal_fp64" in variants:
         v64 = variants["lincal_fp64"]
@@ -786,6 +827,7 @@ def run_ours(args, rank, world, local_rank):
         del w
         torch.cuda.empty_cache()
         w2 = Workload(WORKLOADS["paper32"], WORKLOADS["paper32"]["C"], dev, ctx, rank)
+        tuned2 = tune_workload(ctx, w2)
         for _ in range(3):
             w2.step()
         ctx.profile(True)
@@ -800,7 +842,7 @@ def run_ours(args, rank, world, local_rank):
         secondary = {"workload": WORKLOADS["paper32"]["name"], "value": w2.units / (ms2 * 1e-3), "unit": UNIT,
                      "ms_per_step": ms2, "steps": steps2, "calibrated_chans_per_s": w2.C / (ms2 * 1e-3),
                      "kernels": {k: {"ms_per_step": v[0] / steps2, "launches": v[1]} for k, v in kern2.items()},
-                     "rooflines": rl2}
+                     "rooflines": rl2, "autotuned": tuned2}
     forms = None
     if not args.no_forms and world == 1 and args.channels is None:
         forms = measure_forms(ctx, dev, stream, peaks.get("hbm_gbs", 6800.0))
@@ -823,8 +865,10 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roofline, "rooflines": rl,
             "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches": v[1]} for k, v in kern.items()},
             "calibration_variants": variants,
+            "autotuned": autotuned,
             "measured_peaks": {"fp32_tflops": probes["fp32"], "fp64_tflops": probes["fp64"],
-                               "dp4a_tops": probes["dp4a"], "tc_f8_tflops": probes["tc_f8"]},
+                               "dp4a_tops": probes["dp4a"], "tc_f8_tflops": probes["tc_f8"],
+                               "mma_sync_s8_tops": probes["mma_s8"]},
             "gpu_launches": launches,
             "e2e": e2e, "clocks": clocks}
     if secondary:
@@ -855,11 +899,26 @@ def main():
     ap.add_argument("--channels", type=int, default=None,
                     help="channels per GPU (default: the workload's); smaller values are for "
                          "profiling captures only")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes (for profiling captures of them)")
+    ap.add_argument("--only-forms", action="store_true",
+                    help="time only the batching and differentiation forms (the differentiation form "
+                         "with --channels channels when given); for profiling captures")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.only_forms:
+        import torch
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        from paper_2005_03060_gb300 import gridcorr
+        ctx = gridcorr.Context(local_rank)
+        peaks = load_peaks() or {}
+        print(json.dumps(measure_forms(ctx, dev, torch.cuda.current_stream(dev), peaks.get("hbm_gbs", 6800.0),
+                                       args.channels)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, rank)
         return

@@ -307,7 +307,9 @@ typedef struct gc_calopts {
     double tol;        /* relative step / change */
     double damping;    /* omnical */
     int time_limit_ms; /* per channel, device-side */
-    int reserved;
+    int fp32_reductions; /* GC_LINCAL_CG with the grid-gather operator: 1 = every
+                            reduction in FP32 too (the plain-FP32 form), 0 = the
+                            chi^2 and step norms in FP64 (default) */
 } gc_calopts;
 typedef struct gc_calstats {
     double chi2;
@@ -379,6 +381,9 @@ GC_API gc_status gc_gain_variance(gc_ctx *ctx, const gc_sel *sel, float *var_amp
  *                      they apply, 1 integer SIMT (dp4a), 2 tensor cores only
  *   "xeng.tc_shape"    tensor-core X-engine launch shape (0 default; 1-4:
  *                      converter warps and ring depths)
+ *   "fft.shape"        FFT-correlator launch shape: 0 default, 1 the
+ *                      alternative sample grouping built for the 64x64
+ *                      4+4-bit and 32x32 complex64 grids (others ignore it)
  * GC_EINVAL for an unknown name or a negative value.
  */
 GC_API gc_status gc_set_tuning(gc_ctx *ctx, const char *name, int value);
@@ -396,7 +401,11 @@ GC_API gc_status gc_get_tuning(const gc_ctx *ctx, const char *name, int *value);
  *   grad_gains[c][k]  = dchi2/dRe g_k + i dchi2/dIm g_k
  *                     = -2 [sum_{i_p=k} w r g_j conj(V) + sum_{j_p=k} w conj(r) g_i V]
  *   grad_vmodel[c][a] = -2 sum_{p in a} w r conj(g_i) g_j
- * recomputing the residuals from (gains, vmodel).  FP32 products, FP64 sums.
+ * recomputing the residuals from (gains, vmodel).  FP32 products; sums of at
+ * most 32 terms in FP32, longer sums in FP64.  Selections of at most 16
+ * baseline-types on a full grid split each channel's antennas over several
+ * CTAs and keep their partial sums in the context workspace (a second small
+ * kernel adds them in a fixed order, so results do not vary between runs).
  */
 GC_API gc_status gc_chi2(gc_ctx *ctx, const void *vreduced, int vfmt, const gc_sel *sel, int C,
                          const float *gains, const float *vmodel, const float *weights, double *chi2,

@@ -36,17 +36,27 @@ def _sweep(ctx, knob: str, values, fn, reps: int) -> dict:
 
 
 def tune_correlator(ctx, volt, gains, L=None, reps: int = 3) -> dict:
-    out = torch.empty(volt.shape[0], 2 * (L or int(round(volt.shape[2] ** 0.5))) - 1,
-                      2 * (L or int(round(volt.shape[2] ** 0.5))) - 1, dtype=torch.complex64,
-                      device=volt.device)
-    return _sweep(ctx, "fft.chunk_len", [0, 128, 256, 512, 1024],
-                  lambda: ctx.correlate(volt, gains, L, out=out), reps)
+    """FFT-correlator: the launch shape ("fft.shape": sample grouping of the
+    CTA), then the time-chunk length of a work item ("fft.chunk_len")."""
+    L = L or int(round(volt.shape[2] ** 0.5))
+    out = torch.empty(volt.shape[0], 2 * L - 1, 2 * L - 1, dtype=torch.complex64, device=volt.device)
+    fn = lambda: ctx.correlate(volt, gains, L, out=out)   # noqa: E731
+    shape = _sweep(ctx, "fft.shape", [0, 1], fn, reps)
+    chunk = _sweep(ctx, "fft.chunk_len", [0, 128, 256, 512, 1024], fn, reps)
+    return {"knob": "fft.shape, fft.chunk_len", "best": [shape["best"], chunk["best"]],
+            "ms": {"fft.shape": shape["ms"], "fft.chunk_len": chunk["ms"]}}
 
 
 def tune_xengine(ctx, volt, sel, reps: int = 3) -> dict:
+    """Reduced X-engine: the tensor-core launch shape ("xeng.tc_shape",
+    converter warps and ring depths; ignored by the SIMT path), then the time
+    slices of a window ("xeng.tsplit")."""
     vr, au = ctx.reduce(volt, sel)
-    return _sweep(ctx, "xeng.tsplit", [0, 1, 2, 4, 8],
-                  lambda: ctx.reduce(volt, sel, out=vr, out_autos=au), reps)
+    fn = lambda: ctx.reduce(volt, sel, out=vr, out_autos=au)   # noqa: E731
+    shape = _sweep(ctx, "xeng.tc_shape", [0, 1, 2, 4], fn, reps)
+    ts = _sweep(ctx, "xeng.tsplit", [0, 1, 2, 4, 8], fn, reps)
+    return {"knob": "xeng.tc_shape, xeng.tsplit", "best": [shape["best"], ts["best"]],
+            "ms": {"xeng.tc_shape": shape["ms"], "xeng.tsplit": ts["ms"]}}
 
 
 def tune_calibration(ctx, arrays, reps: int = 2) -> dict:

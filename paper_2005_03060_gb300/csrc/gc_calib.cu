@@ -68,6 +68,7 @@ struct CalParams {
     size_t work_per_cta;
     unsigned int *status;
     unsigned long long deadline_ns;   // per-channel time budget
+    int red32;                   // matrix-free solver: every reduction in FP32 (the plain-FP32 form)
 };
 
 __device__ __forceinline__ float2 vobs(const CalParams &p, int c, int pidx) {
@@ -1293,7 +1294,13 @@ __device__ double rel_resid_pass(const CalParams &p, int c, const CgWork &w, dou
     for (int k = threadIdx.x; k < nu; k += blockDim.x) w.dv[k] = w.G[N + k] > 0.f ? w.D[N + k] / w.G[N + k] : 0.f;
     for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
     double s[1] = {(double)chi};
-    block_sum<double, 1>(s, red);
+    if (p.red32) {   // the plain-FP32 form: the chi^2 sum in FP32 as well
+        float sf[1] = {(float)chi};
+        block_sum<float, 1>(sf, reinterpret_cast<float *>(red));
+        s[0] = (double)sf[0];
+    } else {
+        block_sum<double, 1>(s, red);
+    }
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)dm;
     __syncthreads();
     double mx = 0.0;
@@ -2214,10 +2221,22 @@ __device__ void cg_solve_channel_rel(const CalParams &p, int c, CgWork &w, doubl
                                     : reinterpret_cast<const float2 *>(w.xv)[e - N];
             const float2 dp = make_float2(sv.x * d.x - sv.y * d.y, sv.x * d.y + sv.y * d.x);
             zs[e] = dp;
-            nr[0] += (double)sv.x * sv.x + (double)sv.y * sv.y;
-            nr[1] += (double)dp.x * dp.x + (double)dp.y * dp.y;
+            if (p.red32) {
+                nr[0] = (double)((float)nr[0] + (sv.x * sv.x + sv.y * sv.y));
+                nr[1] = (double)((float)nr[1] + (dp.x * dp.x + dp.y * dp.y));
+            } else {
+                nr[0] += (double)sv.x * sv.x + (double)sv.y * sv.y;
+                nr[1] += (double)dp.x * dp.x + (double)dp.y * dp.y;
+            }
         }
-        block_sum<double, 2>(nr, red);
+        if (p.red32) {
+            float nf[2] = {(float)nr[0], (float)nr[1]};
+            block_sum<float, 2>(nf, redf);
+            nr[0] = nf[0];
+            nr[1] = nf[1];
+        } else {
+            block_sum<double, 2>(nr, red);
+        }
         // halving line search on chi^2; each trial point is staged in the
         // q area (free once the CG loop is done) for the pair gathers
         float step = 1.f;
@@ -2502,6 +2521,7 @@ static gc_status fill_params(gc_ctx *ctx, gc_sel *sel, int C, const void *vreduc
     p.tol = o.tol > 0.0 ? o.tol : (fp64_ne ? 1e-10 : 1e-6);
     p.max_iter = o.max_iter > 0 ? o.max_iter : (o.solver == GC_OMNICAL ? 20000 : 50);
     p.mu_rel = fp64_ne ? 1e-12 : 1e-7;
+    p.red32 = o.solver == GC_LINCAL_CG && o.fp32_reductions ? 1 : 0;
     p.work = nullptr;
     p.work_per_cta = 0;
     return GC_OK;
@@ -2517,7 +2537,7 @@ static gc_calopts default_opts(const gc_calopts *opts) {
     o.damping = 0.3;
     o.warm_start = 0;
     o.time_limit_ms = 0;
-    o.reserved = 0;
+    o.fp32_reductions = 0;
     return o;
 }
 

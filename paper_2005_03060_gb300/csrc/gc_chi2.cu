@@ -9,8 +9,16 @@
 //   dchi2/dV_alpha = -2 sum_{p in alpha} w r conj(g_i) g_j
 // The backward pass recomputes the residuals from (g, V) -- nothing but the
 // inputs is kept between forward and backward -- or, in the checkpointed
-// form, reads the residuals the forward pass stored.  FP32 products, FP64
-// sums.
+// form, reads the residuals the forward pass stored.  FP32 products; sums of
+// a few terms (one antenna's pairs, a run of 32 pairs) in FP32, every longer
+// sum in FP64.
+//
+// Selections of at most 16 types on a full grid take the stencil form: the
+// thread owning antenna m finds its pairs by grid arithmetic (pair index
+// from the type's row-major enumeration), so no pair lists are read; the
+// forward pass visits each pair once (m as first member), the adjoint visits
+// each pair from both members and accumulates the model-visibility gradient
+// per type in registers (one pass over V^reduced instead of two).
 #include <algorithm>
 
 #include "gc_sel.h"
@@ -71,12 +79,20 @@ __global__ void __launch_bounds__(kKThreads) chi2_fwd(const Chi2Params p) {
     __shared__ double red[kKThreads / 32];
     for (int c = blockIdx.x; c < p.C; c += gridDim.x) {
         double s = 0.0;
+        float sf = 0.f;
+        int run = 0;
         for (int q = threadIdx.x; q < p.P; q += blockDim.x) {
             const float2 r = resid(p, c, q, p.pair_i[q], p.pair_j[q], p.pair_type[q]);
             if (p.resid_out) p.resid_out[(size_t)c * p.P + q] = r;
             const float wq = p.w ? p.w[(size_t)c * p.P + q] : 1.0f;
-            s += (double)wq * ((double)r.x * r.x + (double)r.y * r.y);
+            sf = fmaf(wq, fmaf(r.x, r.x, r.y * r.y), sf);
+            if (++run == 32) {   // runs of 32 pairs in FP32, the rest in FP64
+                s += (double)sf;
+                sf = 0.f;
+                run = 0;
+            }
         }
+        s += (double)sf;
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
         __syncthreads();
@@ -147,6 +163,230 @@ __global__ void __launch_bounds__(kKThreads) chi2_bwd(const Chi2Params p) {
     }
 }
 
+
+// ----------------------------------------------------------------- stencil form
+constexpr int kStTypes = 16;
+
+struct StTypes {
+    int dx[kStTypes], dy[kStTypes], off[kStTypes], base[kStTypes];
+    float inv[kStTypes];
+};
+
+__device__ __forceinline__ void load_types(const Chi2Params &p, StTypes &t) {
+    if (threadIdx.x < p.n_ubl) {
+        const int k = threadIdx.x;
+        t.dx[k] = p.types[2 * k];
+        t.dy[k] = p.types[2 * k + 1];
+        t.off[k] = t.dy[k] * p.L + t.dx[k];
+        t.base[k] = p.type_ptr[k];
+        t.inv[k] = 1.0f / (float)(p.win_t1[k] - p.win_t0[k]);
+    }
+}
+
+// residual of the pair with observation index q from its gains and model
+// (the same arithmetic as resid(), so stored and recomputed residuals agree)
+__device__ __forceinline__ float2 st_resid(const Chi2Params &p, int c, int q, float inv, float2 gi, float2 gj,
+                                           float2 V) {
+    float2 o;
+    if (p.vfmt == GC_C64) {
+        const float2 v = reinterpret_cast<const float2 *>(p.vred)[(size_t)c * p.P + q];
+        o = make_float2(v.x * inv, v.y * inv);
+    } else {
+        const int2 v = reinterpret_cast<const int2 *>(p.vred)[(size_t)c * p.P + q];
+        o = make_float2((float)v.x * inv, (float)v.y * inv);
+    }
+    const float ex = gi.x * gj.x + gi.y * gj.y, ey = gi.y * gj.x - gi.x * gj.y;
+    return make_float2(o.x - (ex * V.x - ey * V.y), o.y - (ex * V.y + ey * V.x));
+}
+
+// The stencil kernels split each channel's antennas into ranges of
+// kStJ x kKThreads antennas, one CTA each; a thread holds kStJ antennas and the
+// type loop is outermost, so every type step issues the loads of all its
+// antennas together (many independent requests per thread, few registers).
+// Each CTA writes FP64 partial sums that chi2_st_reduce adds in a fixed
+// order, so the results do not depend on scheduling.
+constexpr int kStJ = 8;
+struct StSplit {
+    int parts;         // antenna ranges per channel
+    double *partial;   // fwd: [C][parts]; bwd: [C][parts][n_ubl][2]
+};
+
+__global__ void __launch_bounds__(kKThreads) chi2_fwd_st(const Chi2Params p, const StSplit sp) {
+    __shared__ StTypes t;
+    __shared__ float2 sV[kStTypes];
+    __shared__ double red[kKThreads / 32];
+    load_types(p, t);
+    const int L = p.L, nu = p.n_ubl;
+    const int c = blockIdx.x / sp.parts, part = blockIdx.x % sp.parts;
+    const int m0 = part * kStJ * kKThreads;
+    if (threadIdx.x < nu) sV[threadIdx.x] = p.V[(size_t)c * nu + threadIdx.x];
+    __syncthreads();
+    const float2 *g = p.g + (size_t)c * p.N;
+    float2 gm[kStJ];
+#pragma unroll
+    for (int j = 0; j < kStJ; ++j) {
+        const int m = m0 + threadIdx.x + j * kKThreads;
+        gm[j] = m < p.N ? g[m] : make_float2(0.f, 0.f);
+    }
+    double s = 0.0;
+    for (int k = 0; k < nu; ++k) {
+        const int dx = t.dx[k], dy = t.dy[k], off = t.off[k], base = t.base[k];
+        const float inv = t.inv[k];
+        const float2 V = sV[k];
+        float sf = 0.f;   // kStJ terms of one type in FP32
+#pragma unroll
+        for (int j = 0; j < kStJ; ++j) {
+            const int m = m0 + threadIdx.x + j * kKThreads;
+            const int x = m % L, y = m / L;
+            const int xj = x - dx, yj = y - dy;
+            if (m >= p.N || xj < 0 || xj >= L || yj < 0 || yj >= L) continue;
+            const int q = base + (yj - max(0, -dy)) * (L - abs(dx)) + (xj - max(0, -dx));
+            const float2 r = st_resid(p, c, q, inv, gm[j], g[m - off], V);
+            if (p.resid_out) p.resid_out[(size_t)c * p.P + q] = r;
+            const float wq = p.w ? p.w[(size_t)c * p.P + q] : 1.0f;
+            sf = fmaf(wq, fmaf(r.x, r.x, r.y * r.y), sf);
+        }
+        s += (double)sf;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tt = 0.0;
+        for (int u = 0; u < kKThreads / 32; ++u) tt += red[u];
+        sp.partial[blockIdx.x] = tt;
+    }
+}
+
+__global__ void __launch_bounds__(kKThreads) chi2_bwd_st(const Chi2Params p, const StSplit sp) {
+    __shared__ StTypes t;
+    __shared__ float2 sV[kStTypes];
+    __shared__ double red[2 * kStTypes * (kKThreads / 32)];
+    load_types(p, t);
+    const int L = p.L, nu = p.n_ubl;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int c = blockIdx.x / sp.parts, part = blockIdx.x % sp.parts;
+    const int m0 = part * kStJ * kKThreads;
+    if (threadIdx.x < nu) sV[threadIdx.x] = p.V[(size_t)c * nu + threadIdx.x];
+    __syncthreads();
+    const double go = p.gout ? p.gout[c] : 1.0;
+    const float2 *g = p.g + (size_t)c * p.N;
+    float2 gm[kStJ], acc[kStJ];   // each antenna's gain and gradient (at most 2 x 16 terms)
+#pragma unroll
+    for (int j = 0; j < kStJ; ++j) {
+        const int m = m0 + threadIdx.x + j * kKThreads;
+        gm[j] = m < p.N ? g[m] : make_float2(0.f, 0.f);
+        acc[j] = make_float2(0.f, 0.f);
+    }
+    for (int k = 0; k < nu; ++k) {
+        const int dx = t.dx[k], dy = t.dy[k], off = t.off[k], base = t.base[k];
+        const float inv = t.inv[k];
+        const float2 V = sV[k];
+        float vx = 0.f, vy = 0.f;   // this thread's part of dV_k (kStJ terms)
+#pragma unroll
+        for (int j = 0; j < kStJ; ++j) {
+            const int m = m0 + threadIdx.x + j * kKThreads;
+            if (m >= p.N) continue;
+            const int x = m % L, y = m / L;
+            // m = i_p of the pair (m, m - d): w r g_j conj(V) to dg_m, w r conj(g_m) g_j to dV_k
+            const int xj = x - dx, yj = y - dy;
+            if (xj >= 0 && xj < L && yj >= 0 && yj < L) {
+                const int q = base + (yj - max(0, -dy)) * (L - abs(dx)) + (xj - max(0, -dx));
+                const float2 gj = g[m - off];
+                const float2 r = p.resid_in ? p.resid_in[(size_t)c * p.P + q] : st_resid(p, c, q, inv, gm[j], gj, V);
+                const float wq = p.w ? p.w[(size_t)c * p.P + q] : 1.0f;
+                const float rx = wq * r.x, ry = wq * r.y;
+                const float tx = gj.x * V.x + gj.y * V.y, ty = gj.y * V.x - gj.x * V.y;   // g_j conj(V)
+                acc[j].x = fmaf(rx, tx, fmaf(-ry, ty, acc[j].x));
+                acc[j].y = fmaf(rx, ty, fmaf(ry, tx, acc[j].y));
+                const float ux = gm[j].x * gj.x + gm[j].y * gj.y, uy = gm[j].x * gj.y - gm[j].y * gj.x;   // conj(g_m) g_j
+                vx = fmaf(rx, ux, fmaf(-ry, uy, vx));
+                vy = fmaf(rx, uy, fmaf(ry, ux, vy));
+            }
+            // m = j_p of the pair (m + d, m): w conj(r) g_i V to dg_m
+            const int xi = x + dx, yi = y + dy;
+            if (xi >= 0 && xi < L && yi >= 0 && yi < L) {
+                const int q = base + (y - max(0, -dy)) * (L - abs(dx)) + (x - max(0, -dx));
+                const float2 gp = g[m + off];
+                const float2 r = p.resid_in ? p.resid_in[(size_t)c * p.P + q] : st_resid(p, c, q, inv, gp, gm[j], V);
+                const float wq = p.w ? p.w[(size_t)c * p.P + q] : 1.0f;
+                const float rx = wq * r.x, ry = wq * r.y;
+                const float tx = gp.x * V.x - gp.y * V.y, ty = gp.x * V.y + gp.y * V.x;   // g_i V
+                acc[j].x = fmaf(rx, tx, fmaf(ry, ty, acc[j].x));
+                acc[j].y = fmaf(rx, ty, fmaf(-ry, tx, acc[j].y));
+            }
+        }
+        // warp sums of dV_k, kept per warp for the block sum below
+        double sx = vx, sy = vy;
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        }
+        if (lane == 0) {
+            red[(2 * k) * (kKThreads / 32) + wp] = sx;
+            red[(2 * k + 1) * (kKThreads / 32) + wp] = sy;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kStJ; ++j) {
+        const int m = m0 + threadIdx.x + j * kKThreads;
+        if (m < p.N) p.dg[(size_t)c * p.N + m] = make_float2((float)(-2.0 * go * acc[j].x), (float)(-2.0 * go * acc[j].y));
+    }
+    __syncthreads();
+    if (threadIdx.x < nu) {
+        const int k = threadIdx.x;
+        double sx = 0.0, sy = 0.0;
+        for (int u = 0; u < kKThreads / 32; ++u) {
+            sx += red[(2 * k) * (kKThreads / 32) + u];
+            sy += red[(2 * k + 1) * (kKThreads / 32) + u];
+        }
+        sp.partial[((size_t)blockIdx.x * nu + k) * 2] = sx;
+        sp.partial[((size_t)blockIdx.x * nu + k) * 2 + 1] = sy;
+    }
+}
+
+// chi^2 (fwd) or dV (bwd) from the ranges' partial sums, in range order
+__global__ void chi2_st_reduce(const Chi2Params p, const StSplit sp, int bwd) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (!bwd) {
+        if (idx >= p.C) return;
+        double s = 0.0;
+        for (int u = 0; u < sp.parts; ++u) s += sp.partial[(size_t)idx * sp.parts + u];
+        p.chi2[idx] = s;
+        return;
+    }
+    if (idx >= p.C * p.n_ubl) return;
+    const int c = idx / p.n_ubl, k = idx % p.n_ubl;
+    double sx = 0.0, sy = 0.0;
+    for (int u = 0; u < sp.parts; ++u) {
+        const size_t b = (((size_t)c * sp.parts + u) * p.n_ubl + k) * 2;
+        sx += sp.partial[b];
+        sy += sp.partial[b + 1];
+    }
+    const double go = p.gout ? p.gout[c] : 1.0;
+    p.dV[(size_t)c * p.n_ubl + k] = make_float2((float)(-2.0 * go * sx), (float)(-2.0 * go * sy));
+}
+
+bool use_stencil(const gc_sel *sel) { return !sel->masked && sel->n_ubl <= kStTypes; }
+
+// kStJ x kKThreads antennas per CTA
+gc_status st_launch(gc_ctx *ctx, const Chi2Params &p, bool bwd, cudaStream_t s) {
+    StSplit sp;
+    sp.parts = (p.N + kStJ * kKThreads - 1) / (kStJ * kKThreads);
+    const size_t n = (size_t)p.C * sp.parts * (bwd ? 2 * p.n_ubl : 1);
+    gc_status st = gc_scratch_reserve(ctx, n * sizeof(double));
+    if (st != GC_OK) return st;
+    sp.partial = static_cast<double *>(ctx->scratch);
+    const unsigned grid = (unsigned)(p.C * sp.parts);
+    if (bwd) chi2_bwd_st<<<grid, kKThreads, 0, s>>>(p, sp);
+    else chi2_fwd_st<<<grid, kKThreads, 0, s>>>(p, sp);
+    const int nr = bwd ? p.C * p.n_ubl : p.C;
+    chi2_st_reduce<<<(nr + 255) / 256, 256, 0, s>>>(p, sp, bwd ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return gc_cuda_fail(ctx, e, bwd ? "launch chi2_bwd" : "launch chi2_fwd");
+    return GC_OK;
+}
+
 gc_status chi2_setup(gc_ctx *ctx, const void *vred, int vfmt, const gc_sel *csel, int C, const float *gains,
                      const float *vmodel, const float *weights, Chi2Params &p) {
     if (!ctx) return GC_EINVAL;
@@ -201,7 +441,12 @@ extern "C" gc_status gc_chi2(gc_ctx *ctx, const void *vreduced, int vfmt, const 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int grid = std::min(C, ctx->sm_count * 8);
     int rec = gc_prof_begin(ctx, s, "chi2_fwd");
-    chi2_fwd<<<grid, kKThreads, 0, s>>>(p);
+    if (use_stencil(sel)) {
+        st = st_launch(ctx, p, false, s);
+        if (st != GC_OK) return st;
+    } else {
+        chi2_fwd<<<grid, kKThreads, 0, s>>>(p);
+    }
     gc_prof_end(ctx, s, rec);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch chi2_fwd");
@@ -222,7 +467,12 @@ extern "C" gc_status gc_chi2_backward(gc_ctx *ctx, const void *vreduced, int vfm
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int grid = std::min(C, ctx->sm_count * 8);
     int rec = gc_prof_begin(ctx, s, "chi2_bwd");
-    chi2_bwd<<<grid, kKThreads, 0, s>>>(p);
+    if (use_stencil(sel)) {
+        st = st_launch(ctx, p, true, s);
+        if (st != GC_OK) return st;
+    } else {
+        chi2_bwd<<<grid, kKThreads, 0, s>>>(p);
+    }
     gc_prof_end(ctx, s, rec);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch chi2_bwd");
@@ -242,7 +492,12 @@ extern "C" gc_status gc_chi2_ckpt(gc_ctx *ctx, const void *vreduced, int vfmt, c
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int grid = std::min(C, ctx->sm_count * 8);
     int rec = gc_prof_begin(ctx, s, "chi2_fwd");
-    chi2_fwd<<<grid, kKThreads, 0, s>>>(p);
+    if (use_stencil(sel)) {
+        st = st_launch(ctx, p, false, s);
+        if (st != GC_OK) return st;
+    } else {
+        chi2_fwd<<<grid, kKThreads, 0, s>>>(p);
+    }
     gc_prof_end(ctx, s, rec);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch chi2_fwd");
@@ -266,7 +521,12 @@ extern "C" gc_status gc_chi2_backward_ckpt(gc_ctx *ctx, const float *residuals, 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int grid = std::min(C, ctx->sm_count * 8);
     int rec = gc_prof_begin(ctx, s, "chi2_bwd");
-    chi2_bwd<<<grid, kKThreads, 0, s>>>(p);
+    if (use_stencil(sel)) {
+        st = st_launch(ctx, p, true, s);
+        if (st != GC_OK) return st;
+    } else {
+        chi2_bwd<<<grid, kKThreads, 0, s>>>(p);
+    }
     gc_prof_end(ctx, s, rec);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "launch chi2_bwd");

@@ -803,6 +803,11 @@ using CfgI16 = Cfg<16, 1, 16, 16, 2, 8, GC_I4C>;
 using CfgI32 = Cfg<32, 1, 32, 32, 2, 4, GC_I4C>;
 using CfgI64 = Cfg<64, 1, 32, 32, 2, 1, GC_I4C>;
 using CfgI128 = Cfg<128, 4, 32, 32, 1, 2, GC_I4C, 2>;   // two groups share the coefficients; 16 warps/SM
+// alternative launch shapes ("fft.shape" = 1): one sample group of two
+// samples per thread (no idle threads in the row pass, 8 warps/SM) for the
+// 64x64 4+4-bit grid; two groups of one sample for the 32x32 complex64 grid
+using CfgI128b = Cfg<128, 4, 32, 32, 2, 1, GC_I4C, 2>;
+using CfgC64b = Cfg<64, 1, 32, 32, 1, 2, GC_C64>;
 // M = 256 (L = 65..128): 4+4-bit only -- one complex64 or binary16 grid sample
 // (128 rows of 1 KB / 512 B) does not fit a double-buffered stage beside the
 // 133 KB coefficient table.  Eight k_x residues, one sample per iteration,
@@ -837,7 +842,9 @@ static gc_status correlate_impl(gc_ctx *ctx, const void *volt, int vfmt, int L, 
         switch (M) {
             case 16: return Launcher<CfgC16>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
             case 32: return Launcher<CfgC32>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
-            case 64: return Launcher<CfgC64>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
+            case 64:
+                if (ctx->tune[GC_TUNE_FFT_SHAPE] == 1) return Launcher<CfgC64b>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
+                return Launcher<CfgC64>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
             case 128: return Launcher<CfgC128>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
         }
     } else if (vfmt == GC_C32H) {
@@ -852,7 +859,9 @@ static gc_status correlate_impl(gc_ctx *ctx, const void *volt, int vfmt, int L, 
             case 16: return Launcher<CfgI16>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
             case 32: return Launcher<CfgI32>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
             case 64: return Launcher<CfgI64>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
-            case 128: return Launcher<CfgI128>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
+            case 128:
+                if (ctx->tune[GC_TUNE_FFT_SHAPE] == 1) return Launcher<CfgI128b>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
+                return Launcher<CfgI128>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
             case 256: return Launcher<CfgI256>::run(ctx, volt, L, C, T, gains, vunique, s, h_mask);
         }
     }

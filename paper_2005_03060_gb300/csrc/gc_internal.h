@@ -34,7 +34,8 @@ enum {
     GC_TUNE_CAL_OP = 4,
     GC_TUNE_XENG_PATH = 5,
     GC_TUNE_XENG_TC_SHAPE = 6,
-    GC_TUNE_N = 7
+    GC_TUNE_FFT_SHAPE = 7,
+    GC_TUNE_N = 8
 };
 
 // staging buffers of the streamed integration: with three, a chunk's copy
@@ -43,7 +44,7 @@ constexpr int GC_NSTAGE = 3;
 
 struct gc_ctx {
     int device = 0;
-    int tune[GC_TUNE_N] = {0, 0, 0, 0, 0, 0, 0};
+    int tune[GC_TUNE_N] = {0, 0, 0, 0, 0, 0, 0, 0};
     int sm_count = 0;
     unsigned int *status_dev = nullptr;   // device error word
     void *scratch = nullptr;              // grow-only workspace

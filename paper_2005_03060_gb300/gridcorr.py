@@ -254,8 +254,11 @@ class Context:
                   solver: str = "lincal", precision: str = "fp64", max_iter: int = 0,
                   tol: float = 0.0, damping: float = 0.0, time_limit_ms: int = 0,
                   gains: torch.Tensor | None = None, vmodel: torch.Tensor | None = None,
-                  warm_start: bool = False, stats: torch.Tensor | None = None):
+                  warm_start: bool = False, stats: torch.Tensor | None = None,
+                  fp32_reductions: bool = False):
         """Per-channel redundant calibration of V^reduced (gc_reduce output).
+        fp32_reductions: the matrix-free solver's plain-FP32 form (chi^2 and
+        step norms summed in FP32 instead of FP64).
         Returns (gains [C, N] complex64, vmodel [C, n_ubl] complex64, stats
         as a uint8 device tensor [C, 32]; decode with `decode_stats`)."""
         vfmt = GC_C64 if vred.dtype == torch.complex64 else GC_I4C
@@ -267,7 +270,7 @@ class Context:
         stats = stats if stats is not None else torch.empty(C, 32, dtype=torch.uint8, device=dev)
         o = CalOpts({"lincal": GC_LINCAL, "omnical": GC_OMNICAL, "lincal_cg": GC_LINCAL_CG}[solver],
                     GC_FP64 if precision == "fp64" else GC_FP32, max_iter, 1 if warm_start else 0,
-                    tol, damping, time_limit_ms, 0)
+                    tol, damping, time_limit_ms, 1 if fp32_reductions else 0)
         self.check(_lib.gc_calibrate(self._h, _vp(vred.data_ptr()), vfmt, sel.handle, C,
                                      _vp(autos.data_ptr() if autos is not None else None),
                                      ctypes.byref(o), _vp(gains.data_ptr()), _vp(vmodel.data_ptr()),
