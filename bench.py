@@ -260,6 +260,30 @@ def cpu_baseline(wl):
             "seconds_calibration": round(n_ch * (t2 - t1), 2)}
 
 
+def oracle_calibration_time(w) -> dict:
+    """One channel of w's V^reduced through the FP64 oracle's Gauss-Newton
+    lincal (oracle/calib.py; sparse normal equations for large arrays),
+    timed once: the CPU counterpart of the GPU's calibrated channels/s."""
+    import numpy as np
+
+    from oracle import calib as oc
+    from oracle import select as osel
+    sel = w.sel
+    osl = osel.subset(w.L, w.T)
+    pt = osl.pair_type()
+    tp = (osl.win_t1 - osl.win_t0)[pt].astype(np.float64)
+    vr = w.vr[0].cpu().numpy()
+    S = vr[..., 0].astype(np.float64) + 1j * vr[..., 1].astype(np.float64) if vr.ndim == 2 else vr.astype(np.complex128)
+    t0 = time.perf_counter()
+    g, _, _, ok = oc.calibrate(S / tp, osl.pair_i, osl.pair_j, pt, osl.types, w.L, "lincal", sparse=w.N > 1024)
+    dt = time.perf_counter() - t0
+    gg = w.gbuf[w.k % 2][0].cpu().numpy().astype(np.complex128)   # the GPU's gains of this channel
+    return {"chans_per_s": 1.0 / dt, "seconds_one_channel": dt, "converged": bool(ok),
+            "max_rel_gain_diff_gpu_vs_oracle": float(np.max(np.abs(gg - g) / np.abs(g))),
+            "sample": (f"channel 0 of the workload's V^reduced ({sel.P} pairs, {w.N} antennas): FP64 "
+                       "Gauss-Newton lincal of the oracle (scipy sparse normal equations), tolerance 1e-10")}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -764,6 +788,15 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- calibration variants on the same V^reduced (equal-error comparison)
     variants = calibration_variants(w, min(C, 16 if wl["L"] > 32 else C), max(1, min(5, args.steps // 4)))
+    # the oracle's calibration of one channel of this workload's own
+    # V^reduced (the full integration the GPU calibrates), timed once for
+    # the CPU baseline
+    cal_cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            cal_cpu = oracle_calibration_time(w)
+        except Exception as e:                          # noqa: BLE001 -- reported, not hidden
+            cal_cpu = {"error": f"{type(e).__name__}: {e}"[:400]}
 
     # ---- end to end through the public API with host buffers (pinned): the
     # voltages stream from host memory chunk by chunk (gc_integrate_host),
@@ -777,9 +810,10 @@ def run_ours(args, rank, world, local_rank):
     e2e_steps = max(3, min(args.steps, 5))
 
     def e2e_step():
-        g_in, g_out = w.gbuf[w.k % 2], w.gbuf[(w.k + 1) % 2]
-        g_in.copy_(h_gains, non_blocking=True)
-        ctx.integrate_host(h_volt, w.sel, g_in, w.vu, w.vr, w.au, g_out, w.vmod, w.stats)
+        # the gains go in from pinned host memory: the library copies them on
+        # its copy stream ahead of the voltage chunks
+        g_out = w.gbuf[(w.k + 1) % 2]
+        ctx.integrate_host(h_volt, w.sel, h_gains, w.vu, w.vr, w.au, g_out, w.vmod, w.stats)
         w.k += 1
         h_vu.copy_(w.vu, non_blocking=True)
         h_g.copy_(g_out, non_blocking=True)
@@ -795,15 +829,24 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     link_gbs = h_volt.numel() * h_volt.element_size() / (e0.elapsed_time(e1) * 1e6)
+    ctx.profile(True)
+    ctx.profile_read()
     e2e_ms = _timed(e2e_step, e2e_steps, stream, barrier) / e2e_steps
+    e2e_kern = ctx.profile_read()
+    ctx.profile(False)
     e2e_ms = shard.max_over_ranks(e2e_ms, dev)
+    chunk_copy = e2e_kern.get("h2d_chunk", (0.0, 0))
     e2e = {"value": shard.job_rate(w.units, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
            "h2d_bytes_per_step": h_volt.numel() * h_volt.element_size() + h_gains.numel() * 8,
            "d2h_bytes_per_step": h_vu.numel() * 8 + h_g.numel() * 8,
            "h2d_link_gbs": link_gbs,
+           "link_floor_ms": h_volt.numel() * h_volt.element_size() / (link_gbs * 1e6),
+           "h2d_chunk_copies": {"count_per_step": chunk_copy[1] / e2e_steps,
+                                "ms_per_step": chunk_copy[0] / e2e_steps,
+                                "note": "sum of the chunk copies' own durations (events on the copy stream)"},
            "path": ("gc_integrate_host: pinned host voltages streamed in channel chunks through three "
-                    "staging buffers, copies up to two chunks ahead of the kernels; gains H2D, V^unique "
-                    "and gains D2H")}
+                    "staging buffers, copies up to two chunks ahead of the kernels; pinned host gains "
+                    "copied by the library on its copy stream; V^unique and gains D2H")}
     del h_volt
 
     peaks = load_peaks() or {}
@@ -877,6 +920,7 @@ def run_ours(args, rank, world, local_rank):
         line["forms"] = forms
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
+        line["cpu_baseline"]["calibration"] = cal_cpu
         if forms:
             try:
                 line["cpu_baseline"]["forms"] = cpu_forms_baseline()

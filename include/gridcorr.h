@@ -448,7 +448,10 @@ GC_API gc_status gc_chi2_backward_ckpt(gc_ctx *ctx, const float *residuals, cons
  *   h_volt    [C][T][L*L] host memory, c64 / c32h / i4c as gc_correlate;
  *             page-locked memory lets the copies overlap (pageable memory
  *             works, with synchronous copies)
- *   gains_in  [C][L*L] c64 device: the gains the correlator applies
+ *   gains_in  [C][L*L] c64: the gains the correlator applies, in device
+ *             memory or in HOST memory (page-locked for an asynchronous
+ *             copy); host gains are copied on the copy stream ahead of the
+ *             first chunk into a context buffer (allocated on first need)
  *   vunique   [C][2L-1][2L-1] c64 device (output)
  *   vreduced, autos  device outputs as gc_reduce (autos may be NULL)
  *   opts      calibration options (NULL: defaults); gains_out [C][L*L],
@@ -458,6 +461,8 @@ GC_API gc_status gc_chi2_backward_ckpt(gc_ctx *ctx, const float *residuals, cons
  * device) and keeps them.  Everything is enqueued; the call returns when
  * the work is queued.  The staging buffers and h_volt must not be modified
  * until `stream` has completed the call's work.  Errors as the three calls.
+ * With gc_profile_enable, each chunk's host->device copy is recorded as
+ * "h2d_chunk" (events on the copy stream).
  */
 GC_API gc_status gc_integrate_host(gc_ctx *ctx, const void *h_volt, int vfmt, int L, int C, int T,
                                    const gc_sel *sel, const float *gains_in, float *vunique, void *vreduced,

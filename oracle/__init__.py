@@ -52,6 +52,8 @@ def lib():
             L.orc_fx.argtypes = [i, i, dp, dp, dp, dp]
             L.orc_fx_multi.argtypes = [i, i, i, dp, dp, dp]
             L.orc_fx_multi.restype = ctypes.c_int
+            L.orc_fx_par.argtypes = [i, i, dp, dp, dp]
+            L.orc_fx_par.restype = ctypes.c_int
             L.orc_dft.argtypes = [i, i, i, dp, dp, dp, dp]
             L.orc_lag.argtypes = [i, i, dp, dp, i, i, dp]
             L.orc_xeng_c64.argtypes = [i, i, dp, i, ip, ip, ip, ip, dp]
@@ -90,6 +92,19 @@ def fx(volt, gains=None, L=None, full=False):
     lib().orc_fx(L, T, _dp(v), _dp(g) if g is not None else None, _dp(out),
                  _dp(vf) if full else None)
     return (out, vf) if full else out
+
+
+def fx_par(volt, gains, L=None):
+    """V^unique of one channel by the FX definition (orc_fx's sums, the pair
+    loop over OpenMP threads); volt [T, N] complex.  Returns (V^unique, threads)."""
+    v = _c128(volt)
+    T, N = v.shape
+    L = L or int(round(N ** 0.5))
+    W = 2 * L - 1
+    out = np.zeros((W, W), np.complex128)
+    g = None if gains is None else _c128(gains)
+    n = lib().orc_fx_par(L, T, _dp(v), _dp(g) if g is not None else None, _dp(out))
+    return out, n
 
 
 def fx_multi(volt, gains, L):

@@ -72,6 +72,63 @@ void orc_fx(int L, int T, const double *volt, const double *gains,
     free(w);
 }
 
+/* orc_fx's V^unique with its pair loop split over threads, for one large
+ * channel: the calibrated voltages are copied antenna-major so that each
+ * pair's time sum walks contiguous memory (the same sum over t as orc_fx),
+ * every thread adds its first antennas' pairs into its own lag array, and
+ * the arrays are added in thread order before the division by N_alpha
+ * (Eq. modelvis).  Returns the number of threads. */
+int orc_fx_par(int L, int T, const double *volt, const double *gains, double *vunique) {
+    const int N = L * L, W = 2 * L - 1;
+    double *w = (double *)malloc(sizeof(double) * 2 * (size_t)N * T);
+    for (int t = 0; t < T; ++t)
+        for (int i = 0; i < N; ++i)
+            calibrated(volt + 2 * ((size_t)t * N + i), gains ? gains + 2 * i : NULL,
+                       w + 2 * ((size_t)i * T + t));
+    int nthreads = 1;
+#ifdef _OPENMP
+    nthreads = omp_get_max_threads();
+#endif
+    double *acc = (double *)calloc((size_t)nthreads * 2 * W * W, sizeof(double));
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *a = acc + (size_t)tid * 2 * W * W;
+#pragma omp for schedule(static)
+        for (int i = 0; i < N; ++i) {
+            const double *wi = w + 2 * (size_t)i * T;
+            for (int j = 0; j < N; ++j) {
+                const double *wj = w + 2 * (size_t)j * T;
+                double re = 0.0, im = 0.0;
+                for (int t = 0; t < T; ++t) {
+                    re += wi[2 * t] * wj[2 * t] + wi[2 * t + 1] * wj[2 * t + 1];
+                    im += wi[2 * t + 1] * wj[2 * t] - wi[2 * t] * wj[2 * t + 1];
+                }
+                const int dx = (i % L) - (j % L), dy = (i / L) - (j / L);
+                const int o = (dy + L - 1) * W + (dx + L - 1);
+                a[2 * o] += re / T;
+                a[2 * o + 1] += im / T;
+            }
+        }
+    }
+    memset(vunique, 0, sizeof(double) * 2 * W * W);
+    for (int u = 0; u < nthreads; ++u)
+        for (int o = 0; o < 2 * W * W; ++o) vunique[o] += acc[(size_t)u * 2 * W * W + o];
+    for (int dy = -(L - 1); dy <= L - 1; ++dy)
+        for (int dx = -(L - 1); dx <= L - 1; ++dx) {
+            const int o = (dy + L - 1) * W + (dx + L - 1);
+            const double n = (double)n_redundant(L, dx, dy);
+            vunique[2 * o] /= n;
+            vunique[2 * o + 1] /= n;
+        }
+    free(acc);
+    free(w);
+    return nthreads;
+}
+
 int orc_fx_multi(int C, int L, int T, const double *volt, const double *gains,
                  double *vunique) {
     const int N = L * L, W = 2 * L - 1;

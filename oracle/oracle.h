@@ -37,6 +37,9 @@ void orc_fx(int L, int T, const double *volt, const double *gains,
  * vunique [C][(2L-1)^2]. Returns the number of threads used. */
 int orc_fx_multi(int C, int L, int T, const double *volt, const double *gains,
                  double *vunique);
+/* orc_fx's V^unique for one channel with the pair loop over OpenMP threads
+ * (fixed-order reduction); returns the thread count. */
+int orc_fx_par(int L, int T, const double *volt, const double *gains, double *vunique);
 
 /* FFT-correlator written as direct DFTs (Fig. 1b, Sec. 1): per sample
  * X(k) = sum_r w(r) e^{-2 pi i k.r / M} on an M x M zero-padded grid,

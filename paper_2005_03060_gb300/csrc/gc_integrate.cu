@@ -8,7 +8,10 @@
 // others, so that little copy time is exposed before the first kernel; the
 // calibration is one launch over all channels at the end (the kernels share
 // one stream, so splitting it would only leave partial waves of CTAs).
-// Host code only: every step is one of the library's own kernels.
+// Gains in host memory are copied on the copy stream too, ahead of the
+// first chunk, so that no voltage copy ever waits behind a copy queued on
+// the caller's stream.  Host code only: every step is one of the library's
+// own kernels.
 #include <algorithm>
 #include <vector>
 
@@ -28,6 +31,9 @@ gc_status ensure_streaming(gc_ctx *ctx, size_t stage_bytes) {
                 (e = cudaEventCreateWithFlags(&ctx->ev_free[b], cudaEventDisableTiming)) != cudaSuccess)
                 return gc_cuda_fail(ctx, e, "cudaEventCreate");
         }
+        if ((e = cudaEventCreateWithFlags(&ctx->ev_gains_copied, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ctx->ev_gains_free, cudaEventDisableTiming)) != cudaSuccess)
+            return gc_cuda_fail(ctx, e, "cudaEventCreate");
     }
     if (stage_bytes > ctx->stage_bytes) {
         // the old buffers may still be read by queued kernels
@@ -48,6 +54,16 @@ gc_status ensure_streaming(gc_ctx *ctx, size_t stage_bytes) {
         ctx->stage_bytes = stage_bytes;
     }
     return GC_OK;
+}
+
+// Whether p is host memory (page-locked or pageable) rather than device memory.
+bool is_host_pointer(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;   // not known to the runtime: ordinary pageable memory
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
 }
 
 }  // namespace
@@ -82,6 +98,31 @@ extern "C" gc_status gc_integrate_host(gc_ctx *ctx, const void *h_volt, int vfmt
     while (bounds.back() < C) bounds.push_back(std::min(C, bounds.back() + chunk));
     const int n_chunks = (int)bounds.size() - 1;
     const char *h = static_cast<const char *>(h_volt);
+    // host-resident gains: copied on the copy stream ahead of the first
+    // chunk, into a context buffer that the previous call's correlator
+    // kernels have finished with; the correlator waits for the copy
+    const float *gains_d = gains_in;
+    if (is_host_pointer(gains_in)) {
+        const size_t gb = (size_t)C * N * 2 * sizeof(float);
+        if (gb > ctx->gains_bytes) {
+            if ((e = cudaDeviceSynchronize()) != cudaSuccess) return gc_cuda_fail(ctx, e, "synchronize before growth");
+            if (ctx->gains_dev) cudaFree(ctx->gains_dev);
+            ctx->gains_dev = nullptr;
+            ctx->gains_bytes = 0;
+            if ((e = cudaMalloc(&ctx->gains_dev, gb)) != cudaSuccess) {
+                cudaGetLastError();
+                return gc_cuda_fail(ctx, e, "cudaMalloc(gains)");
+            }
+            ctx->gains_bytes = gb;
+        }
+        if ((e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_gains_free, 0)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(ctx->gains_dev, gains_in, gb, cudaMemcpyHostToDevice, ctx->copy_stream)) !=
+                cudaSuccess ||
+            (e = cudaEventRecord(ctx->ev_gains_copied, ctx->copy_stream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, ctx->ev_gains_copied, 0)) != cudaSuccess)
+            return gc_cuda_fail(ctx, e, "copy the gains");
+        gains_d = static_cast<const float *>(ctx->gains_dev);
+    }
     for (int i = 0; i < n_chunks; ++i) {
         const int b = i % GC_NSTAGE;
         const int c0 = bounds[i], cc = bounds[i + 1] - c0;
@@ -91,13 +132,15 @@ extern "C" gc_status gc_integrate_host(gc_ctx *ctx, const void *h_volt, int vfmt
         // calibration (an event never recorded makes the wait a no-op)
         if ((e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[b], 0)) != cudaSuccess)
             return gc_cuda_fail(ctx, e, "wait for a free staging buffer");
+        const int rec = gc_prof_begin(ctx, ctx->copy_stream, "h2d_chunk");
         e = cudaMemcpyAsync(ctx->stage[b], h + (size_t)c0 * per_ch, (size_t)cc * per_ch, cudaMemcpyHostToDevice,
                             ctx->copy_stream);
+        gc_prof_end(ctx, ctx->copy_stream, rec);
         if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "cudaMemcpyAsync(voltages)");
         if ((e = cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(s, ctx->ev_copied[b], 0)) != cudaSuccess)
             return gc_cuda_fail(ctx, e, "order the chunk copy");
-        st = gc_correlate(ctx, ctx->stage[b], vfmt, L, cc, T, gains_in + (size_t)c0 * N * 2,
+        st = gc_correlate(ctx, ctx->stage[b], vfmt, L, cc, T, gains_d + (size_t)c0 * N * 2,
                           vunique + (size_t)c0 * W * W * 2, stream);
         if (st != GC_OK) return st;
         st = gc_reduce(ctx, ctx->stage[b], vfmt, L, cc, T, sel,
@@ -107,6 +150,8 @@ extern "C" gc_status gc_integrate_host(gc_ctx *ctx, const void *h_volt, int vfmt
         if ((e = cudaEventRecord(ctx->ev_free[b], s)) != cudaSuccess)
             return gc_cuda_fail(ctx, e, "record staging release");
     }
+    if (gains_d != gains_in && (e = cudaEventRecord(ctx->ev_gains_free, s)) != cudaSuccess)
+        return gc_cuda_fail(ctx, e, "record gains release");
     const int cfmt = vfmt == GC_I4C ? GC_I4C : GC_C64;   // X-engine output format
     return gc_calibrate(ctx, vreduced, cfmt, sel, C, autos, opts, gains_out, vmodel, stats, stream);
 }

@@ -60,6 +60,11 @@ struct gc_ctx {
     void *stage[GC_NSTAGE] = {nullptr, nullptr, nullptr};   // gc_integrate_host staging buffers
     size_t stage_bytes = 0;
     cudaEvent_t ev_copied[GC_NSTAGE] = {nullptr, nullptr, nullptr}, ev_free[GC_NSTAGE] = {nullptr, nullptr, nullptr};
+    // gc_integrate_host with host-resident gains: their device copy and the
+    // events that order it against the kernels reading it
+    void *gains_dev = nullptr;
+    size_t gains_bytes = 0;
+    cudaEvent_t ev_gains_copied = nullptr, ev_gains_free = nullptr;
 };
 
 // launch timing helpers: no-ops unless profiling is enabled

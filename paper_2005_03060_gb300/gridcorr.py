@@ -284,14 +284,18 @@ class Context:
         """One integration of host-resident voltages (pinned CPU tensor of
         any gc_vfmt layout) through correlate -> reduce -> calibrate,
         streamed in channel chunks (gc_integrate_host); outputs are the
-        device tensors passed in, on the current stream."""
+        device tensors passed in, on the current stream.  gains_in may be a
+        CUDA tensor or a (pinned) host tensor, which the library copies on
+        its own copy stream."""
         if h_volt.is_cuda or not h_volt.is_contiguous():
             raise ValueError("h_volt must be a contiguous host tensor")
         vfmt, (C, T, N) = _volt_format(h_volt)
-        dev = gains_in.device
-        for t in (gains_in, vunique, vreduced, gains_out, vmodel, stats) + ((autos,) if autos is not None else ()):
+        dev = vunique.device
+        if gains_in.dtype != torch.complex64 or not gains_in.is_contiguous() or tuple(gains_in.shape) != (C, N):
+            raise ValueError("gains_in must be a contiguous complex64 [C, L*L] tensor")
+        for t in (vunique, vreduced, gains_out, vmodel, stats) + ((autos,) if autos is not None else ()):
             if not t.is_cuda or not t.is_contiguous():
-                raise ValueError("outputs and gains must be contiguous CUDA tensors")
+                raise ValueError("outputs must be contiguous CUDA tensors")
         o = CalOpts({"lincal": GC_LINCAL, "omnical": GC_OMNICAL, "lincal_cg": GC_LINCAL_CG}[solver],
                     GC_FP64 if precision == "fp64" else GC_FP32, 0, 0, 0.0, 0.0, 0, 0)
         self.check(_lib.gc_integrate_host(self._h, _vp(h_volt.data_ptr()), vfmt, sel.L, C, T, sel.handle,

@@ -67,3 +67,38 @@ def test_streamed_cycle_rejects_device_voltages(gc, ctx):
     e = torch.empty(1, device="cuda")
     with pytest.raises(ValueError):
         ctx.integrate_host(volt, sel, gains, e, e, None, e, e, e)
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_streamed_cycle_with_host_gains(gc, ctx, pinned):
+    """Gains handed over in host memory (page-locked or pageable) are copied
+    by the library on its copy stream; two integrations in a row with
+    different gains give what device-resident gains give (the gains buffer is
+    not overwritten while the previous call's correlator still reads it)."""
+    L, C, T = 16, 24, 256
+    N, W = L * L, 2 * L - 1
+    volt, _, _ = synth.make_voltages(71, L, C, T, n_src=20, device="cuda")
+    volt = ctx.quantize(volt)[0]
+    sel = gc.Selection("subset", L, T)
+    h = torch.empty(volt.shape, dtype=volt.dtype, pin_memory=True)
+    h.copy_(volt)
+    outs = []
+    for seed in (1, 2):
+        _, gains, _ = synth.make_voltages(seed, L, C, 1, n_src=1)
+        hg = torch.empty(gains.shape, dtype=gains.dtype, pin_memory=pinned)
+        hg.copy_(gains)
+        vu = torch.empty(C, W, W, dtype=torch.complex64, device="cuda")
+        vr, au = ctx.reduce(volt, sel)
+        g = torch.empty(C, N, dtype=torch.complex64, device="cuda")
+        V = torch.empty(C, sel.n_ubl, dtype=torch.complex64, device="cuda")
+        st = torch.empty(C, 32, dtype=torch.uint8, device="cuda")
+        ctx.integrate_host(h, sel, hg, vu, vr, au, g, V, st, chunk=8)
+        outs.append((vu, gains.cuda()))
+    ctx.device_status()
+    r = np.arange(-(L - 1), L)
+    nd = (L - np.abs(r))[:, None] * (L - np.abs(r))[None, :]
+    for vu, gd in outs:
+        ref = ctx.correlate(volt, gd).cpu().numpy()
+        a = vu.cpu().numpy()
+        for c in range(C):
+            assert np.max(np.abs(a[c] - ref[c]) * nd) / (N * abs(ref[c, L - 1, L - 1])) < 1e-5

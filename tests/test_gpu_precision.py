@@ -105,3 +105,27 @@ def test_calibration_matches_oracle(run, orc, oracle_bytes):
         assert ok, c
         e = float(np.max(np.abs(run["ch"][c]["g"] - gr) / np.abs(gr)))
         assert e < 1e-3, (c, e)
+
+
+def test_vunique_all_lags_one_channel(run, orc, oracle_bytes):
+    """Every one of the (2L-1)^2 = 16 129 lags of channel 0 at full size
+    (4096 antennas x 8192 samples) against the FX definition (orc_fx_par,
+    Eq. modelvis).  Bound: the lag-sum form, max_d |dV(d)| N_d / (N |V(0)|)
+    <= 1e-5.  Also reported (printed): max_d |dV(d)| / |V(0)| and the relative
+    L2 error over all lags; at the longest lags N_d is 1, so the FP32 FFT's
+    rounding, spread evenly over the lag sums R(d) = T N_d V(d), shows there
+    up to N / N_d times larger relative to V(0)."""
+    c = CHANNELS[0]
+    v = orc.unpack_i4c(oracle_bytes[c])
+    ref, threads = orc.fx_par(v, run["ch"][c]["gains"], L)
+    got = run["ch"][c]["vu"].astype(np.complex128)
+    r = np.arange(-(L - 1), L)
+    nd = (L - np.abs(r))[:, None] * (L - np.abs(r))[None, :]
+    v0 = abs(ref[L - 1, L - 1])
+    d = np.abs(got - ref)
+    lag_sum = float(np.max(d * nd) / (N * v0))
+    inf_rel = float(np.max(d) / v0)
+    l2_rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    print(f"\nV^unique, channel {c}, all {ref.size} lags (oracle on {threads} threads): lag-sum "
+          f"{lag_sum:.3e}, max|dV|/|V(0)| {inf_rel:.3e}, relative L2 {l2_rel:.3e}")
+    assert lag_sum < 1e-5, lag_sum

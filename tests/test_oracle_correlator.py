@@ -126,3 +126,19 @@ def test_fx_multi_matches_single(orc):
     assert nt >= 1
     for c in range(C):
         assert np.allclose(out[c], orc.fx(v[c], g[c], L), atol=1e-13)
+
+
+@pytest.mark.parametrize("L,T", [(3, 17), (8, 50), (11, 23)])
+def test_fx_par_equals_fx(orc, L, T):
+    """The threaded FX oracle (pair loop split over threads, antenna-major
+    copy of the calibrated voltages) computes the same Eq. modelvis sums as
+    the plain FX loop; a planted change in either would show here and in the
+    pins above."""
+    rng = np.random.default_rng(L * T)
+    N = L * L
+    v = rng.standard_normal((T, N)) + 1j * rng.standard_normal((T, N))
+    g = (1 + 0.1 * rng.standard_normal(N)) * np.exp(1j * rng.uniform(-np.pi, np.pi, N))
+    ref = orc.fx(v, g, L)
+    got, n = orc.fx_par(v, g, L)
+    assert n >= 1
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
