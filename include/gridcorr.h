@@ -214,6 +214,10 @@ GC_API void gc_sel_free(gc_sel *sel);
 /* info[11] = {L, T, P (pairs), n_ubl (types), n_cycle, t_int, null_dim,
  *             scheme (0 subset, 1 low-cadence), masked, lattice, antennas} */
 GC_API gc_status gc_sel_info(const gc_sel *sel, int32_t *info);
+/* Edge antennas of the selection's array (Sec. 5.4): edge[i] = 1 for an
+ * occupied point with an unoccupied or outside nearest neighbour (4 on the
+ * square lattice, 6 on the triangular one), else 0.  edge: host [L*L]. */
+GC_API gc_status gc_sel_edge(const gc_sel *sel, uint8_t *edge);
 /* Host arrays owned by the selection (valid until gc_sel_free): types [n_ubl][2],
  * type_ptr [n_ubl + 1] (pairs of type k are [type_ptr[k], type_ptr[k+1])),
  * pair_i, pair_j [P], win_t0, win_t1 [n_ubl].  Any output may be NULL. */
@@ -367,6 +371,69 @@ GC_API gc_status gc_calibrate_batched(gc_ctx *ctx, int n_arrays, const gc_batch_
  */
 GC_API gc_status gc_gain_variance(gc_ctx *ctx, const gc_sel *sel, float *var_amp, float *var_phase,
                                   void *stream);
+
+/*
+ * Gain covariance rows (Eq. gaincov; covariance rows and matrices of
+ * Sec. 5.3, Figs. 7-8), in the units of gc_gain_variance (per unit noise;
+ * multiply by sigma^2 / 2 for the covariance of the log-amplitude and phase
+ * errors).
+ *   fixed = 0: rows[r] is an unknown (antenna < L*L, then types); row r of
+ *              the pseudo-inverses, cov_amp[r][u] = [(A^T A)^+]_{rows[r],u}
+ *              and cov_phase[r][u] = [(B^T B)^+]_{rows[r],u},
+ *              u < L*L + n_ubl;
+ *   fixed = 1: rows[r] is an antenna; the antenna covariance after the
+ *              four degeneracies are fixed against the true gains by least
+ *              squares over the antennas (how the paper's simulations
+ *              compare gains, Sec. 3): P (A^T A)^+ P and P (B^T B)^+ P
+ *              restricted to the antennas, P the projector off the
+ *              antenna-space degeneracy directions (amplitude: constant;
+ *              phase: constant, x, y), u < L*L.
+ * rows: host [n_rows], read before the call returns.  cov_amp, cov_phase:
+ * device float [n_rows][row length].  Empty points of a partly occupied
+ * lattice read 0; a row whose solve does not converge reads NaN (same
+ * solver and limits as gc_gain_variance, one solve per row).  The amplitude
+ * plus phase sum of a row is the quantity Figs. 7-8 plot.  GC_EINVAL for a
+ * row out of range, GC_EDEGEN as gc_gain_variance.  Uses the context
+ * workspace.
+ */
+GC_API gc_status gc_gain_covariance(gc_ctx *ctx, const gc_sel *sel, int fixed, int n_rows,
+                                    const int32_t *rows, float *cov_amp, float *cov_phase, void *stream);
+
+/*
+ * Variance of calibrated redundant visibilities (Sec. 6.2): for every lag
+ * alpha = (dx, dy) of the full array (plane [(2L-1)^2], index
+ * (dy + L - 1)(2L - 1) + dx + L - 1), the relative variance SNR^-2 of
+ * V^unique_alpha, the redundant average of the N_alpha full-array pairs
+ * (i, j = i + alpha) calibrated with gains from this selection's
+ * calibrator.  Gains and visibilities of unit amplitude (the paper's own
+ * simplification before Eq. visvar); each full-array visibility has
+ * SNR^-2 = snr_full_inv2; the calibrator's visibilities have noise
+ * variance sigma_cal2 (relative), independent of the former, so that the
+ * log-gain errors a = eta + i phi have covariance (sigma_cal2 / 2) C_a and
+ * (sigma_cal2 / 2) C_p, with C the fixed-degeneracy antenna covariance of
+ * gc_gain_covariance (fixed = 1).
+ *   var_pair[alpha]  = (1 / N_a^2) sum_{(i,j) in alpha} [snr_full_inv2
+ *                      + s_i + s_j + 2 rho_ij], the per-pair form before
+ *                      Eq. visvar, s_i = E|a_i|^2 and rho_ij =
+ *                      Re E[a_i a_j] = Cov(eta_i, eta_j) - Cov(phi_i, phi_j)
+ *                      (the covariance term of a calibrated visibility
+ *                      V_ij / (g_i conj(g_j)));
+ *   var_exact[alpha] = (1 / N_a^2) [N_a snr_full_inv2 + (sigma_cal2 / 2)
+ *                      (u^T C_a u + w^T C_p w)], u = sum (e_i + e_j),
+ *                      w = sum (e_i - e_j) over the lag's pairs: the full
+ *                      linearised variance, with the covariance between
+ *                      different pairs that the paper's form leaves out
+ *                      (NULL to skip);
+ *   n_pairs[alpha]   = N_alpha (NULL to skip).
+ * Outputs are device arrays; lag 0 and lags without pairs read NaN (n 0).
+ * Cost: L*L covariance solves, then (2L-1)^2 x (L*L)^2 multiply-adds; meant
+ * for arrays up to about a thousand antennas.  Workspace: 8 (L*L)^2 bytes
+ * plus the solver's.  GC_EINVAL for negative or NaN variances, GC_EDEGEN as
+ * gc_gain_variance.
+ */
+GC_API gc_status gc_visibility_variance(gc_ctx *ctx, const gc_sel *sel, double snr_full_inv2,
+                                        double sigma_cal2, double *var_pair, double *var_exact,
+                                        int32_t *n_pairs, void *stream);
 
 /*
  * Tuning knobs of a context (0 = automatic), set by the autotuner:

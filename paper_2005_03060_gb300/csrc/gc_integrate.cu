@@ -9,9 +9,10 @@
 // calibration is one launch over all channels at the end (the kernels share
 // one stream, so splitting it would only leave partial waves of CTAs).
 // Gains in host memory are copied on the copy stream too, ahead of the
-// first chunk, so that no voltage copy ever waits behind a copy queued on
-// the caller's stream.  Host code only: every step is one of the library's
-// own kernels.
+// first chunk, into one of two device buffers used by alternate calls, so
+// that no voltage copy ever waits behind a copy queued on the caller's
+// stream or behind the previous call's last kernels.  Host code only:
+// every step is one of the library's own kernels.
 #include <algorithm>
 #include <vector>
 
@@ -32,7 +33,8 @@ gc_status ensure_streaming(gc_ctx *ctx, size_t stage_bytes) {
                 return gc_cuda_fail(ctx, e, "cudaEventCreate");
         }
         if ((e = cudaEventCreateWithFlags(&ctx->ev_gains_copied, cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&ctx->ev_gains_free, cudaEventDisableTiming)) != cudaSuccess)
+            (e = cudaEventCreateWithFlags(&ctx->ev_gains_free[0], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ctx->ev_gains_free[1], cudaEventDisableTiming)) != cudaSuccess)
             return gc_cuda_fail(ctx, e, "cudaEventCreate");
     }
     if (stage_bytes > ctx->stage_bytes) {
@@ -99,29 +101,37 @@ extern "C" gc_status gc_integrate_host(gc_ctx *ctx, const void *h_volt, int vfmt
     const int n_chunks = (int)bounds.size() - 1;
     const char *h = static_cast<const char *>(h_volt);
     // host-resident gains: copied on the copy stream ahead of the first
-    // chunk, into a context buffer that the previous call's correlator
-    // kernels have finished with; the correlator waits for the copy
+    // chunk, into one of two context buffers (alternate calls), so that the
+    // copy waits only for the correlator kernels of the call before the
+    // previous one -- never for this call's predecessor, whose last chunks
+    // may still be running; the correlator waits for the copy
     const float *gains_d = gains_in;
+    int gslot = -1;
     if (is_host_pointer(gains_in)) {
         const size_t gb = (size_t)C * N * 2 * sizeof(float);
         if (gb > ctx->gains_bytes) {
             if ((e = cudaDeviceSynchronize()) != cudaSuccess) return gc_cuda_fail(ctx, e, "synchronize before growth");
-            if (ctx->gains_dev) cudaFree(ctx->gains_dev);
-            ctx->gains_dev = nullptr;
-            ctx->gains_bytes = 0;
-            if ((e = cudaMalloc(&ctx->gains_dev, gb)) != cudaSuccess) {
-                cudaGetLastError();
-                return gc_cuda_fail(ctx, e, "cudaMalloc(gains)");
+            for (int b = 0; b < 2; ++b) {
+                if (ctx->gains_dev[b]) cudaFree(ctx->gains_dev[b]);
+                ctx->gains_dev[b] = nullptr;
             }
+            ctx->gains_bytes = 0;
+            for (int b = 0; b < 2; ++b)
+                if ((e = cudaMalloc(&ctx->gains_dev[b], gb)) != cudaSuccess) {
+                    cudaGetLastError();
+                    return gc_cuda_fail(ctx, e, "cudaMalloc(gains)");
+                }
             ctx->gains_bytes = gb;
         }
-        if ((e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_gains_free, 0)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(ctx->gains_dev, gains_in, gb, cudaMemcpyHostToDevice, ctx->copy_stream)) !=
+        gslot = ctx->gains_slot;
+        ctx->gains_slot ^= 1;
+        if ((e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_gains_free[gslot], 0)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(ctx->gains_dev[gslot], gains_in, gb, cudaMemcpyHostToDevice, ctx->copy_stream)) !=
                 cudaSuccess ||
             (e = cudaEventRecord(ctx->ev_gains_copied, ctx->copy_stream)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(s, ctx->ev_gains_copied, 0)) != cudaSuccess)
             return gc_cuda_fail(ctx, e, "copy the gains");
-        gains_d = static_cast<const float *>(ctx->gains_dev);
+        gains_d = static_cast<const float *>(ctx->gains_dev[gslot]);
     }
     for (int i = 0; i < n_chunks; ++i) {
         const int b = i % GC_NSTAGE;
@@ -150,7 +160,7 @@ extern "C" gc_status gc_integrate_host(gc_ctx *ctx, const void *h_volt, int vfmt
         if ((e = cudaEventRecord(ctx->ev_free[b], s)) != cudaSuccess)
             return gc_cuda_fail(ctx, e, "record staging release");
     }
-    if (gains_d != gains_in && (e = cudaEventRecord(ctx->ev_gains_free, s)) != cudaSuccess)
+    if (gslot >= 0 && (e = cudaEventRecord(ctx->ev_gains_free[gslot], s)) != cudaSuccess)
         return gc_cuda_fail(ctx, e, "record gains release");
     const int cfmt = vfmt == GC_I4C ? GC_I4C : GC_C64;   // X-engine output format
     return gc_calibrate(ctx, vreduced, cfmt, sel, C, autos, opts, gains_out, vmodel, stats, stream);

@@ -62,9 +62,10 @@ struct gc_ctx {
     cudaEvent_t ev_copied[GC_NSTAGE] = {nullptr, nullptr, nullptr}, ev_free[GC_NSTAGE] = {nullptr, nullptr, nullptr};
     // gc_integrate_host with host-resident gains: their device copy and the
     // events that order it against the kernels reading it
-    void *gains_dev = nullptr;
+    void *gains_dev[2] = {nullptr, nullptr};   // host gains staged on the device, alternate calls
     size_t gains_bytes = 0;
-    cudaEvent_t ev_gains_copied = nullptr, ev_gains_free = nullptr;
+    int gains_slot = 0;
+    cudaEvent_t ev_gains_copied = nullptr, ev_gains_free[2] = {nullptr, nullptr};
 };
 
 // launch timing helpers: no-ops unless profiling is enabled

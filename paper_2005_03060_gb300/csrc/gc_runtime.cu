@@ -139,9 +139,11 @@ void gc_destroy(gc_ctx *ctx) {
         if (ctx->ev_copied[b]) cudaEventDestroy(ctx->ev_copied[b]);
         if (ctx->ev_free[b]) cudaEventDestroy(ctx->ev_free[b]);
     }
-    if (ctx->gains_dev) cudaFree(ctx->gains_dev);
+    for (int b = 0; b < 2; ++b) {
+        if (ctx->gains_dev[b]) cudaFree(ctx->gains_dev[b]);
+        if (ctx->ev_gains_free[b]) cudaEventDestroy(ctx->ev_gains_free[b]);
+    }
     if (ctx->ev_gains_copied) cudaEventDestroy(ctx->ev_gains_copied);
-    if (ctx->ev_gains_free) cudaEventDestroy(ctx->ev_gains_free);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->status_dev) cudaFree(ctx->status_dev);

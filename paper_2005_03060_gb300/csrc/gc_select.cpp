@@ -557,4 +557,25 @@ gc_status gc_sel_arrays(const gc_sel *s, const int32_t **types, const int32_t **
     return GC_OK;
 }
 
+gc_status gc_sel_edge(const gc_sel *s, uint8_t *edge) {
+    if (!s || !edge) return GC_EINVAL;
+    // nearest-neighbour steps: 4 on the square lattice; the triangular
+    // lattice is stored sheared, its other two neighbours at (1, -1), (-1, 1)
+    static const int kStep[6][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, -1}, {-1, 1}};
+    const int n_step = s->lattice == 1 ? 6 : 4;
+    const int L = s->L;
+    auto occ = [&](int x, int y) {
+        return x >= 0 && x < L && y >= 0 && y < L && (!s->masked || s->mask[(size_t)y * L + x] != 0);
+    };
+    for (int y = 0; y < L; ++y)
+        for (int x = 0; x < L; ++x) {
+            uint8_t e = 0;
+            if (occ(x, y))
+                for (int k = 0; k < n_step; ++k)
+                    if (!occ(x + kStep[k][0], y + kStep[k][1])) e = 1;
+            edge[(size_t)y * L + x] = e;
+        }
+    return GC_OK;
+}
+
 }  // extern "C"

@@ -58,6 +58,12 @@ _lib.gc_correlate_masked.argtypes = [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _v
 _lib.gc_correlate_masked.restype = _i
 _lib.gc_gain_variance.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.gc_gain_variance.restype = _i
+_lib.gc_gain_covariance.argtypes = [_vp, _vp, _i, _i, _vp, _vp, _vp, _vp]
+_lib.gc_gain_covariance.restype = _i
+_lib.gc_visibility_variance.argtypes = [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp, _vp]
+_lib.gc_visibility_variance.restype = _i
+_lib.gc_sel_edge.argtypes = [_vp, _vp]
+_lib.gc_sel_edge.restype = _i
 _lib.gc_selection_subset.argtypes = [_i, _i, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp)]
 _lib.gc_selection_subset.restype = _i
 _lib.gc_selection_lowcad.argtypes = [_i, _i, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_vp)]
@@ -228,6 +234,36 @@ class Context:
         self.check(_lib.gc_gain_variance(self._h, sel.handle, _vp(va.data_ptr()), _vp(vp.data_ptr()),
                                          _vp(_stream_ptr(dev))))
         return va, vp
+
+    def gain_covariance(self, sel: Selection, rows, fixed: bool = False):
+        """Gain covariance rows (gc_gain_covariance): (cov_amp, cov_phase),
+        float32 CUDA tensors [len(rows), row length] -- rows of the
+        pseudo-inverses over all L*L + n_ubl unknowns, or (fixed) the antenna
+        covariance with the degeneracies fixed against the truth, [.., L*L]."""
+        import numpy as np
+        r = np.ascontiguousarray(np.asarray(rows, dtype=np.int32).reshape(-1))
+        dev = self.device
+        n = sel.L * sel.L + (0 if fixed else sel.n_ubl)
+        ca = torch.empty(r.size, n, dtype=torch.float32, device=dev)
+        cp = torch.empty(r.size, n, dtype=torch.float32, device=dev)
+        self.check(_lib.gc_gain_covariance(self._h, sel.handle, int(bool(fixed)), int(r.size),
+                                           r.ctypes.data_as(_vp), _vp(ca.data_ptr()), _vp(cp.data_ptr()),
+                                           _vp(_stream_ptr(dev))))
+        return ca, cp
+
+    def visibility_variance(self, sel: Selection, snr_full_inv2: float, sigma_cal2: float):
+        """Relative variance of every V^unique lag calibrated with this
+        selection's gains (gc_visibility_variance): (var_pair, var_exact,
+        n_pairs), CUDA tensors [2L-1, 2L-1] indexed [dy + L - 1, dx + L - 1]."""
+        dev = self.device
+        n = 2 * sel.L - 1
+        vp = torch.empty(n, n, dtype=torch.float64, device=dev)
+        ve = torch.empty(n, n, dtype=torch.float64, device=dev)
+        npr = torch.empty(n, n, dtype=torch.int32, device=dev)
+        self.check(_lib.gc_visibility_variance(self._h, sel.handle, float(snr_full_inv2), float(sigma_cal2),
+                                               _vp(vp.data_ptr()), _vp(ve.data_ptr()), _vp(npr.data_ptr()),
+                                               _vp(_stream_ptr(dev))))
+        return vp, ve, npr
 
     # ------------------------------------------------------------------ reduce
     def reduce(self, volt: torch.Tensor, sel: Selection, autos: bool = True, out=None, out_autos=None):
@@ -475,6 +511,16 @@ class Selection:
     def pair_type(self):
         import numpy as np
         return np.repeat(np.arange(self.n_ubl, dtype=np.int32), np.diff(self.type_ptr))
+
+    def edge_mask(self):
+        """Edge antennas (gc_sel_edge): uint8 numpy [L*L], 1 on occupied
+        points with a missing nearest neighbour."""
+        import numpy as np
+        e = np.zeros(self.L * self.L, dtype=np.uint8)
+        st = _lib.gc_sel_edge(self._h, e.ctypes.data_as(_vp))
+        if st != GC_OK:
+            raise GridcorrError(st, "gc_sel_edge")
+        return e
 
     def close(self):
         if getattr(self, "_h", None):

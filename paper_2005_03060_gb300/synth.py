@@ -145,7 +145,8 @@ def complex_to_interleaved(z: torch.Tensor) -> torch.Tensor:
 
 
 def make_visibilities(seed: int, L: int, C: int, pair_i, pair_j, pair_type, n_ubl: int, t_pair,
-                      snr: float = 10.0, amp_sigma: float = 0.05, device="cpu", unit_amp: bool = False):
+                      snr: float = 10.0, amp_sigma: float = 0.05, device="cpu", unit_amp: bool = False,
+                      shared_truth: bool = False):
     """Visibility-level draw in the manner of the paper's own simulations
     (Sec. 3): true visibilities of random amplitude, uncorrelated between
     baseline-types and constant in time; gains with ~5 % amplitude scatter and
@@ -156,6 +157,9 @@ def make_visibilities(seed: int, L: int, C: int, pair_i, pair_j, pair_type, n_ub
     so that the sums stand where the X-engine output would.  unit_amp: every
     baseline-type has |V| = 1 (the same SNR for all types, the setting of the
     paper's gain-variance curves); otherwise |V| ~ U(0.5, 1.5).
+    shared_truth: every channel has channel 0's gains and visibilities and
+    only the noise differs (the repeated-simulation setting of the paper's
+    bias study, Sec. 6.3).
     """
     N = L * L
     pi = torch.as_tensor(pair_i, dtype=torch.long, device=device)
@@ -164,10 +168,12 @@ def make_visibilities(seed: int, L: int, C: int, pair_i, pair_j, pair_type, n_ub
     tp = torch.as_tensor(t_pair, dtype=torch.float64, device=device)
     P = pi.numel()
     gains = make_gains(seed, C, N, device, amp_sigma)
+    if shared_truth:
+        gains = gains[:1].expand(C, N).contiguous()
     out = torch.empty(C, P, dtype=torch.complex64, device=device)
     vt = torch.empty(C, n_ubl, dtype=torch.complex64, device=device)
     for c in range(C):
-        g = _gen(device, seed, c, 4)
+        g = _gen(device, seed, 0 if shared_truth else c, 4)
         amp = 0.5 + torch.rand(n_ubl, generator=g, device=device, dtype=torch.float64)
         if unit_amp:
             amp = torch.ones_like(amp)
@@ -176,6 +182,8 @@ def make_visibilities(seed: int, L: int, C: int, pair_i, pair_j, pair_type, n_ub
         gc = gains[c].to(torch.complex128)
         m = gc[pi] * gc[pj].conj() * V[pt]
         sig = amp[pt] / snr / torch.sqrt(tp)
+        if shared_truth:
+            g = _gen(device, seed, c, 5)
         nre = torch.randn(P, generator=g, device=device, dtype=torch.float64)
         nim = torch.randn(P, generator=g, device=device, dtype=torch.float64)
         noise = torch.complex(nre, nim) * (sig / math.sqrt(2.0))

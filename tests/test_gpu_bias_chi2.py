@@ -1,0 +1,174 @@
+"""The paper's Monte-Carlo studies through the library (Sec. 6.3, Fig. 11;
+Sec. 6.4, Fig. 12), channels standing in for independent simulations:
+
+  * bias against N_sim: gains and visibilities shared by every channel,
+    only the noise differs (synth.make_visibilities(shared_truth=True)).
+    The GPU gains, fixed against the truth, averaged over n channels,
+    deviate from the truth by (1 / n) of the variance that Eq. gaincov
+    (the oracle's fixed-degeneracy covariance) predicts -- the trend of an
+    unbiased estimate -- for n = 1 .. 256, both schemes;
+  * chi^2_r against N: voltages of the point-source sky through the whole
+    library path -- gc_reduce -> gc_calibrate (chi^2_r of the fit to
+    V^reduced, the paper's hollow points) -> gc_correlate with the
+    estimated gains (V^unique) -> gc_reduce with every baseline-type of the
+    array (V^full) -> gc_chi2 (chi^2_r of gains and V^unique against
+    V^full, the solid points).  At the small sizes the oracle runs the
+    same chain (its X-engine, lincal, FX correlator, chi^2_r) on the same
+    voltages and the two agree per channel; the table over N is printed
+    (run with -s).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from oracle import calib as oc
+from oracle import select as osel
+from oracle import visvar as ov
+from paper_2005_03060_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gc():
+    from paper_2005_03060_gb300 import gridcorr
+    return gridcorr
+
+
+@pytest.fixture(scope="module")
+def ctx(gc):
+    return gc.Context(0)
+
+
+NSIM = [1, 2, 4, 8, 16, 32, 64, 128, 256]
+
+
+@pytest.mark.parametrize("scheme", ["subset", "lowcad"])
+def test_gain_bias_averages_down(gc, ctx, scheme):
+    L, C, T, SNR = 16, 256, 4096, 10.0
+    sel = gc.Selection(scheme, L, T)
+    pt = sel.pair_type()
+    tp = (sel.win_t1 - sel.win_t0)[pt]
+    S, g_true, _ = synth.make_visibilities(1100 + L, L, C, sel.pair_i, sel.pair_j, pt, sel.n_ubl, tp, snr=SNR,
+                                           device="cuda", unit_amp=True, shared_truth=True)
+    g, V, st = ctx.calibrate(S.contiguous(), sel, solver="lincal_cg", precision="fp32")
+    ctx.device_status()
+    assert np.all(gc.decode_stats(st)["status"] == gc.GC_OK)
+    gt = g_true[0].cpu().numpy().astype(np.complex128)
+    ge = g.cpu().numpy().astype(np.complex128)
+    a = np.stack([ov.fixed_log_errors(ge[c], gt, L) for c in range(C)])
+    # Eq. gaincov with the degeneracies fixed against the truth, per antenna
+    osl = osel.subset(L, T) if scheme == "subset" else osel.lowcad(L, T)
+    ca, cb = ov.gain_covariance(L, [tuple(t) for t in osl.types], np.asarray(osl.pair_i), np.asarray(osl.pair_j),
+                                osl.pair_type())
+    fa, fp = ov.fixed_gain_covariance(ca, cb, L)
+    t = float(np.mean(osl.win_t1 - osl.win_t0))
+    var = (np.diag(fa) + np.diag(fp)) / (2.0 * SNR ** 2 * t)
+    rows = []
+    for n in NSIM:
+        dev = np.mean(np.abs(a[:n].mean(axis=0)) ** 2 / var)
+        rows.append((n, dev, dev * n))
+    print(f"\n{scheme}: deviation of gains averaged over n simulations / Eq. gaincov variance")
+    print("    n      deviation   n x deviation")
+    for n, d, dn in rows:
+        print(f"{n:5d}   {d:.4e}   {dn:8.3f}")
+    # the 1 / n trend of an unbiased estimate (dashed line of Fig. 11)
+    for n, d, dn in rows:
+        assert 0.7 < dn < 1.4, (scheme, n, dn)
+    slope = np.polyfit(np.log([r[0] for r in rows]), np.log([r[1] for r in rows]), 1)[0]
+    assert -1.12 < slope < -0.88, slope
+
+
+def _full_sel(gc, L, T):
+    # p large enough for every baseline-type of the array
+    return gc.Selection("subset", L, T, p=1e6)
+
+
+def _chain_gpu(gc, ctx, volt, sel, sel_full, L):
+    """(chi^2_r against V^reduced, chi^2_r against V^full) per channel."""
+    C, T, N = volt.shape
+    vr, au = ctx.reduce(volt, sel)
+    g, V, st = ctx.calibrate(vr, sel, au, solver="lincal_cg", precision="fp32")
+    s = gc.decode_stats(st)
+    assert np.all(s["status"] == gc.GC_OK)
+    vu = ctx.correlate(volt, g, L)
+    vf, af = ctx.reduce(volt, sel_full)
+    ty = torch.as_tensor(sel_full.types, device=volt.device).long()
+    vmod = vu[:, ty[:, 1] + L - 1, ty[:, 0] + L - 1].contiguous()
+    pi = torch.as_tensor(sel_full.pair_i, device=volt.device).long()
+    pj = torch.as_tensor(sel_full.pair_j, device=volt.device).long()
+    a = af.double() / T
+    sigma2 = a[:, pi] * a[:, pj] / T
+    w = (1.0 / sigma2).float().contiguous()
+    chi2 = ctx.chi2(vf, sel_full, g, vmod, weights=w)
+    ctx.device_status()
+    dof = oc.dof(sel_full.P, N, sel_full.n_ubl)
+    return s["chi2r"].copy(), (chi2.cpu().numpy() / dof), g.cpu().numpy().astype(np.complex128)
+
+
+def _chain_oracle(volt_c, osl, ofull, L):
+    """The same two chi^2_r of one channel through the oracle."""
+    T, N = volt_c.shape
+    types = [tuple(t) for t in osl.types]
+    pt = osl.pair_type()
+    t0 = np.asarray(osl.win_t0)[pt]
+    t1 = np.asarray(osl.win_t1)[pt]
+    vr = orc.xengine_c64(volt_c, osl.pair_i, osl.pair_j, t0, t1) / (t1 - t0)
+    g, V, _, ok = oc.calibrate(vr, np.asarray(osl.pair_i), np.asarray(osl.pair_j), pt, types, L)
+    assert ok
+    ta = int(osl.n_cycle * osl.t_int)
+    au = orc.autos(volt_c, 0, ta) / ta
+    pi, pj = np.asarray(osl.pair_i), np.asarray(osl.pair_j)
+    chi_red = oc.chi2_r(vr, g, V, pi, pj, pt, au[pi] * au[pj] / (t1 - t0))
+    vu = orc.fx(volt_c, g, L)
+    fpt = ofull.pair_type()
+    fi, fj = np.asarray(ofull.pair_i), np.asarray(ofull.pair_j)
+    vf = orc.xengine_c64(volt_c, fi, fj, np.zeros(len(fi), np.int32), np.full(len(fi), T, np.int32)) / T
+    af = orc.autos(volt_c) / T
+    vmod = np.array([vu[dy + L - 1, dx + L - 1] for dx, dy in ofull.types])
+    chi_full = oc.chi2_r(vf, g, vmod, fi, fj, fpt, af[fi] * af[fj] / T)
+    return chi_red, chi_full
+
+
+SIZES = [6, 8, 12, 16, 24, 32]
+ORACLE_SIZES = (6, 8)
+
+
+def test_chi2r_against_array_size(gc, ctx):
+    C, T = 8, 4096
+    rows = []
+    for scheme in ("subset", "lowcad"):
+        for L in SIZES:
+            sel = gc.Selection(scheme, L, T)
+            sel_full = _full_sel(gc, L, T)
+            assert sel_full.P == L * L * (L * L - 1) // 2
+            # per-antenna SNR 0.1: thermal noise dominates each voltage, so
+            # the sky's own sampling noise (common to redundant pairs, and
+            # absorbed by the fit) stays a small part of each visibility's
+            # variance and the radiometer sigma_p^2 of chi^2_r holds
+            volt, _, _ = synth.make_voltages(1200 + L, L, C, T, n_src=20, snr=0.1, device="cuda")
+            red, full, _ = _chain_gpu(gc, ctx, volt, sel, sel_full, L)
+            if L in ORACLE_SIZES:
+                osl = osel.subset(L, T) if scheme == "subset" else osel.lowcad(L, T)
+                ofull = osel.subset(L, T, p=1e6)
+                vc = volt.cpu().numpy()
+                for c in range(C):
+                    o_red, o_full = _chain_oracle(vc[c], osl, ofull, L)
+                    assert red[c] == pytest.approx(o_red, rel=2e-3), (scheme, L, c)
+                    assert full[c] == pytest.approx(o_full, rel=2e-3), (scheme, L, c)
+            dof_red = oc.dof(sel.P, L * L, sel.n_ubl)
+            rows.append((scheme, L, sel.P, sel.n_ubl, dof_red, red, full))
+            # hollow points: the calibrator's own fit, chi^2_r = 1 within
+            # the chi^2 scatter of its DoF
+            assert abs(np.mean(red) - 1.0) < 6.0 * np.sqrt(2.0 / (dof_red * C)) + 0.02, (scheme, L, red)
+            # solid points: gains that were fitted to V^reduced describe the
+            # full matrix less well than the calibrator's own fit, but still
+            # reasonably (the subset scheme's larger gain variance shows as
+            # the larger excess, as in the paper's figure)
+            assert np.mean(red) - 0.05 < np.mean(full) < 3.0, (scheme, L, red, full)
+    print("\nper-antenna SNR 0.1, T = 4096, 8 channels per size")
+    print("scheme   L     N      P  n_ubl   chi2_r(V^reduced) mean [min, max]   chi2_r(V^full) mean [min, max]")
+    for scheme, L, P, nu, dof, red, full in rows:
+        print(f"{scheme:7s}{L:3d} {L * L:5d} {P:6d} {nu:5d}   {np.mean(red):.4f} [{red.min():.4f}, {red.max():.4f}]"
+              f"            {np.mean(full):.4f} [{full.min():.4f}, {full.max():.4f}]")

@@ -122,3 +122,17 @@ def test_hex_lowcad_matches_oracle(gcmod, s, T):
     assert sel.n_cycle == ref.n_cycle and sel.t_int == ref.t_int
     n = int(m.sum())
     assert sel.P == n * (n - 1) // 2            # every pair exactly once
+
+
+@pytest.mark.parametrize("L,s", [(3, None), (8, None), (5, 3), (9, 5)])
+def test_edge_mask_matches_oracle(gcmod, L, s):
+    """gc_sel_edge (host) against the oracle's edge antennas (Sec. 5.4):
+    square grids, and hexagonal arrays of side s on the triangular lattice."""
+    from oracle import visvar as ov
+    if s is None:
+        sel, m, lat = gcmod.Selection("subset", L, 64), None, "square"
+    else:
+        L2, m = osel.hex_mask(s)
+        assert L2 == L
+        sel, lat = gcmod.Selection("subset", L, 64, mask=m, lattice="triangular"), "triangular"
+    assert np.array_equal(sel.edge_mask().astype(bool), ov.edge_antennas(L, m, lat))
