@@ -17,8 +17,9 @@
 // thread owning antenna m finds its pairs by grid arithmetic (pair index
 // from the type's row-major enumeration), so no pair lists are read; the
 // forward pass visits each pair once (m as first member), the adjoint visits
-// each pair from both members and accumulates the model-visibility gradient
-// per type in registers (one pass over V^reduced instead of two).
+// each pair from both members (the second visit finds the observation in L2)
+// and keeps each thread's model-visibility terms per type in shared memory
+// until one fixed-order reduction at the end of the CTA.
 #include <algorithm>
 
 #include "gc_sel.h"
@@ -167,32 +168,42 @@ __global__ void __launch_bounds__(kKThreads) chi2_bwd(const Chi2Params p) {
 // ----------------------------------------------------------------- stencil form
 constexpr int kStTypes = 16;
 
+// Per-type constants: the observation index of a pair is
+// a1 + y (L - |dx|) + x with (x, y) its first member, and a2 + y (L - |dx|) + x
+// with (x, y) its second member (the builders enumerate a type's pairs
+// row-major over the overlap of the grid with its shift).
 struct StTypes {
-    int dx[kStTypes], dy[kStTypes], off[kStTypes], base[kStTypes];
+    int dx[kStTypes], dy[kStTypes], off[kStTypes], rowlen[kStTypes], a1[kStTypes], a2[kStTypes];
     float inv[kStTypes];
 };
 
 __device__ __forceinline__ void load_types(const Chi2Params &p, StTypes &t) {
     if (threadIdx.x < p.n_ubl) {
         const int k = threadIdx.x;
-        t.dx[k] = p.types[2 * k];
-        t.dy[k] = p.types[2 * k + 1];
-        t.off[k] = t.dy[k] * p.L + t.dx[k];
-        t.base[k] = p.type_ptr[k];
+        const int dx = p.types[2 * k], dy = p.types[2 * k + 1];
+        const int rl = p.L - abs(dx);
+        const int a2 = p.type_ptr[k] - max(0, -dy) * rl - max(0, -dx);
+        t.dx[k] = dx;
+        t.dy[k] = dy;
+        t.off[k] = dy * p.L + dx;
+        t.rowlen[k] = rl;
+        t.a2[k] = a2;
+        t.a1[k] = a2 - dy * rl - dx;
         t.inv[k] = 1.0f / (float)(p.win_t1[k] - p.win_t0[k]);
     }
 }
 
-// residual of the pair with observation index q from its gains and model
-// (the same arithmetic as resid(), so stored and recomputed residuals agree)
-__device__ __forceinline__ float2 st_resid(const Chi2Params &p, int c, int q, float inv, float2 gi, float2 gj,
-                                           float2 V) {
+// residual of the pair with observation index idx (channel offset included)
+// from its gains and model (the same arithmetic as resid(), so stored and
+// recomputed residuals agree)
+template <int VF>
+__device__ __forceinline__ float2 st_resid(const void *vred, size_t idx, float inv, float2 gi, float2 gj, float2 V) {
     float2 o;
-    if (p.vfmt == GC_C64) {
-        const float2 v = reinterpret_cast<const float2 *>(p.vred)[(size_t)c * p.P + q];
+    if (VF == GC_C64) {
+        const float2 v = reinterpret_cast<const float2 *>(vred)[idx];
         o = make_float2(v.x * inv, v.y * inv);
     } else {
-        const int2 v = reinterpret_cast<const int2 *>(p.vred)[(size_t)c * p.P + q];
+        const int2 v = reinterpret_cast<const int2 *>(vred)[idx];
         o = make_float2((float)v.x * inv, (float)v.y * inv);
     }
     const float ex = gi.x * gj.x + gi.y * gj.y, ey = gi.y * gj.x - gi.x * gj.y;
@@ -200,17 +211,22 @@ __device__ __forceinline__ float2 st_resid(const Chi2Params &p, int c, int q, fl
 }
 
 // The stencil kernels split each channel's antennas into ranges of
-// kStJ x kKThreads antennas, one CTA each; a thread holds kStJ antennas and the
-// type loop is outermost, so every type step issues the loads of all its
-// antennas together (many independent requests per thread, few registers).
-// Each CTA writes FP64 partial sums that chi2_st_reduce adds in a fixed
-// order, so the results do not depend on scheduling.
+// kStJ x kKThreads antennas, one CTA each; a thread holds kStJ antennas (grid
+// coordinates packed as x | y << 16, computed once) and the type loop is
+// outermost.  Inside a type step nothing branches: a pair that falls off the
+// grid reads observation 0 and gain 0 of its channel (valid addresses) and
+// its terms are selected away, so the loads of all kStJ antennas issue
+// together.  Each CTA writes FP64 partial sums that chi2_st_reduce adds in a
+// fixed order, so the results do not depend on scheduling.
 constexpr int kStJ = 8;
+constexpr int kDvPitch = kKThreads + 8;   // conflict-free column reads of the dV partials
 struct StSplit {
     int parts;         // antenna ranges per channel
     double *partial;   // fwd: [C][parts]; bwd: [C][parts][n_ubl][2]
 };
 
+// FL: bit 0 weights, bit 1 residuals stored (fwd) / read (bwd)
+template <int VF, int FL>
 __global__ void __launch_bounds__(kKThreads) chi2_fwd_st(const Chi2Params p, const StSplit sp) {
     __shared__ StTypes t;
     __shared__ float2 sV[kStTypes];
@@ -222,29 +238,33 @@ __global__ void __launch_bounds__(kKThreads) chi2_fwd_st(const Chi2Params p, con
     if (threadIdx.x < nu) sV[threadIdx.x] = p.V[(size_t)c * nu + threadIdx.x];
     __syncthreads();
     const float2 *g = p.g + (size_t)c * p.N;
+    const size_t cP = (size_t)c * p.P;
     float2 gm[kStJ];
+    int xy[kStJ];
 #pragma unroll
     for (int j = 0; j < kStJ; ++j) {
         const int m = m0 + threadIdx.x + j * kKThreads;
-        gm[j] = m < p.N ? g[m] : make_float2(0.f, 0.f);
+        const bool in = m < p.N;
+        xy[j] = in ? (m % L) | ((m / L) << 16) : -1;
+        gm[j] = in ? g[m] : make_float2(0.f, 0.f);
     }
     double s = 0.0;
     for (int k = 0; k < nu; ++k) {
-        const int dx = t.dx[k], dy = t.dy[k], off = t.off[k], base = t.base[k];
+        const int dx = t.dx[k], dy = t.dy[k], off = t.off[k], rl = t.rowlen[k], a1 = t.a1[k];
         const float inv = t.inv[k];
         const float2 V = sV[k];
         float sf = 0.f;   // kStJ terms of one type in FP32
 #pragma unroll
         for (int j = 0; j < kStJ; ++j) {
             const int m = m0 + threadIdx.x + j * kKThreads;
-            const int x = m % L, y = m / L;
-            const int xj = x - dx, yj = y - dy;
-            if (m >= p.N || xj < 0 || xj >= L || yj < 0 || yj >= L) continue;
-            const int q = base + (yj - max(0, -dy)) * (L - abs(dx)) + (xj - max(0, -dx));
-            const float2 r = st_resid(p, c, q, inv, gm[j], g[m - off], V);
-            if (p.resid_out) p.resid_out[(size_t)c * p.P + q] = r;
-            const float wq = p.w ? p.w[(size_t)c * p.P + q] : 1.0f;
-            sf = fmaf(wq, fmaf(r.x, r.x, r.y * r.y), sf);
+            const int x = xy[j] & 0xffff, y = xy[j] >> 16;
+            const bool v = xy[j] >= 0 && (unsigned)(x - dx) < (unsigned)L && (unsigned)(y - dy) < (unsigned)L;
+            const int q = v ? a1 + y * rl + x : 0;
+            const float2 r = st_resid<VF>(p.vred, cP + q, inv, gm[j], g[v ? m - off : 0], V);
+            if ((FL & 2) && v) p.resid_out[cP + q] = r;
+            float e = fmaf(r.x, r.x, r.y * r.y);
+            if (FL & 1) e *= p.w[cP + q];
+            sf += v ? e : 0.f;
         }
         s += (double)sf;
     }
@@ -258,91 +278,92 @@ __global__ void __launch_bounds__(kKThreads) chi2_fwd_st(const Chi2Params p, con
     }
 }
 
+template <int VF, int FL>
 __global__ void __launch_bounds__(kKThreads) chi2_bwd_st(const Chi2Params p, const StSplit sp) {
     __shared__ StTypes t;
     __shared__ float2 sV[kStTypes];
-    __shared__ double red[2 * kStTypes * (kKThreads / 32)];
+    __shared__ float sdv[2 * kStTypes * kDvPitch];   // per-thread dV terms of every type
     load_types(p, t);
     const int L = p.L, nu = p.n_ubl;
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int c = blockIdx.x / sp.parts, part = blockIdx.x % sp.parts;
     const int m0 = part * kStJ * kKThreads;
     if (threadIdx.x < nu) sV[threadIdx.x] = p.V[(size_t)c * nu + threadIdx.x];
     __syncthreads();
     const double go = p.gout ? p.gout[c] : 1.0;
     const float2 *g = p.g + (size_t)c * p.N;
+    const size_t cP = (size_t)c * p.P;
     float2 gm[kStJ], acc[kStJ];   // each antenna's gain and gradient (at most 2 x 16 terms)
+    int xy[kStJ];
 #pragma unroll
     for (int j = 0; j < kStJ; ++j) {
         const int m = m0 + threadIdx.x + j * kKThreads;
-        gm[j] = m < p.N ? g[m] : make_float2(0.f, 0.f);
+        const bool in = m < p.N;
+        xy[j] = in ? (m % L) | ((m / L) << 16) : -1;
+        gm[j] = in ? g[m] : make_float2(0.f, 0.f);
         acc[j] = make_float2(0.f, 0.f);
     }
     for (int k = 0; k < nu; ++k) {
-        const int dx = t.dx[k], dy = t.dy[k], off = t.off[k], base = t.base[k];
+        const int dx = t.dx[k], dy = t.dy[k], off = t.off[k], rl = t.rowlen[k], a1 = t.a1[k], a2 = t.a2[k];
         const float inv = t.inv[k];
         const float2 V = sV[k];
         float vx = 0.f, vy = 0.f;   // this thread's part of dV_k (kStJ terms)
 #pragma unroll
         for (int j = 0; j < kStJ; ++j) {
             const int m = m0 + threadIdx.x + j * kKThreads;
-            if (m >= p.N) continue;
-            const int x = m % L, y = m / L;
+            const int x = xy[j] & 0xffff, y = xy[j] >> 16;
+            const bool in = xy[j] >= 0;
             // m = i_p of the pair (m, m - d): w r g_j conj(V) to dg_m, w r conj(g_m) g_j to dV_k
-            const int xj = x - dx, yj = y - dy;
-            if (xj >= 0 && xj < L && yj >= 0 && yj < L) {
-                const int q = base + (yj - max(0, -dy)) * (L - abs(dx)) + (xj - max(0, -dx));
-                const float2 gj = g[m - off];
-                const float2 r = p.resid_in ? p.resid_in[(size_t)c * p.P + q] : st_resid(p, c, q, inv, gm[j], gj, V);
-                const float wq = p.w ? p.w[(size_t)c * p.P + q] : 1.0f;
-                const float rx = wq * r.x, ry = wq * r.y;
-                const float tx = gj.x * V.x + gj.y * V.y, ty = gj.y * V.x - gj.x * V.y;   // g_j conj(V)
-                acc[j].x = fmaf(rx, tx, fmaf(-ry, ty, acc[j].x));
-                acc[j].y = fmaf(rx, ty, fmaf(ry, tx, acc[j].y));
-                const float ux = gm[j].x * gj.x + gm[j].y * gj.y, uy = gm[j].x * gj.y - gm[j].y * gj.x;   // conj(g_m) g_j
-                vx = fmaf(rx, ux, fmaf(-ry, uy, vx));
-                vy = fmaf(rx, uy, fmaf(ry, ux, vy));
-            }
+            const bool v1 = in && (unsigned)(x - dx) < (unsigned)L && (unsigned)(y - dy) < (unsigned)L;
             // m = j_p of the pair (m + d, m): w conj(r) g_i V to dg_m
-            const int xi = x + dx, yi = y + dy;
-            if (xi >= 0 && xi < L && yi >= 0 && yi < L) {
-                const int q = base + (y - max(0, -dy)) * (L - abs(dx)) + (x - max(0, -dx));
-                const float2 gp = g[m + off];
-                const float2 r = p.resid_in ? p.resid_in[(size_t)c * p.P + q] : st_resid(p, c, q, inv, gp, gm[j], V);
-                const float wq = p.w ? p.w[(size_t)c * p.P + q] : 1.0f;
-                const float rx = wq * r.x, ry = wq * r.y;
-                const float tx = gp.x * V.x - gp.y * V.y, ty = gp.x * V.y + gp.y * V.x;   // g_i V
-                acc[j].x = fmaf(rx, tx, fmaf(ry, ty, acc[j].x));
-                acc[j].y = fmaf(rx, ty, fmaf(-ry, tx, acc[j].y));
+            const bool v2 = in && (unsigned)(x + dx) < (unsigned)L && (unsigned)(y + dy) < (unsigned)L;
+            const int yr = y * rl + x;
+            const int q1 = v1 ? a1 + yr : 0, q2 = v2 ? a2 + yr : 0;
+            const float2 gj = g[v1 ? m - off : 0];
+            const float2 gp = g[v2 ? m + off : 0];
+            float2 r1, r2;
+            if (FL & 2) {
+                r1 = p.resid_in[cP + q1];
+                r2 = p.resid_in[cP + q2];
+            } else {
+                r1 = st_resid<VF>(p.vred, cP + q1, inv, gm[j], gj, V);
+                r2 = st_resid<VF>(p.vred, cP + q2, inv, gp, gm[j], V);
             }
+            float w1 = 1.f, w2 = 1.f;
+            if (FL & 1) {
+                w1 = p.w[cP + q1];
+                w2 = p.w[cP + q2];
+            }
+            const float rx = v1 ? w1 * r1.x : 0.f, ry = v1 ? w1 * r1.y : 0.f;
+            const float tx = gj.x * V.x + gj.y * V.y, ty = gj.y * V.x - gj.x * V.y;   // g_j conj(V)
+            acc[j].x = fmaf(rx, tx, fmaf(-ry, ty, acc[j].x));
+            acc[j].y = fmaf(rx, ty, fmaf(ry, tx, acc[j].y));
+            const float ux = gm[j].x * gj.x + gm[j].y * gj.y, uy = gm[j].x * gj.y - gm[j].y * gj.x;   // conj(g_m) g_j
+            vx = fmaf(rx, ux, fmaf(-ry, uy, vx));
+            vy = fmaf(rx, uy, fmaf(ry, ux, vy));
+            const float sx = v2 ? w2 * r2.x : 0.f, sy = v2 ? w2 * r2.y : 0.f;
+            const float px = gp.x * V.x - gp.y * V.y, py = gp.x * V.y + gp.y * V.x;   // g_i V
+            acc[j].x = fmaf(sx, px, fmaf(sy, py, acc[j].x));
+            acc[j].y = fmaf(sx, py, fmaf(-sy, px, acc[j].y));
         }
-        // warp sums of dV_k, kept per warp for the block sum below
-        double sx = vx, sy = vy;
-        for (int o = 16; o > 0; o >>= 1) {
-            sx += __shfl_xor_sync(0xffffffffu, sx, o);
-            sy += __shfl_xor_sync(0xffffffffu, sy, o);
-        }
-        if (lane == 0) {
-            red[(2 * k) * (kKThreads / 32) + wp] = sx;
-            red[(2 * k + 1) * (kKThreads / 32) + wp] = sy;
-        }
+        sdv[(2 * k) * kDvPitch + threadIdx.x] = vx;
+        sdv[(2 * k + 1) * kDvPitch + threadIdx.x] = vy;
     }
 #pragma unroll
     for (int j = 0; j < kStJ; ++j) {
         const int m = m0 + threadIdx.x + j * kKThreads;
-        if (m < p.N) p.dg[(size_t)c * p.N + m] = make_float2((float)(-2.0 * go * acc[j].x), (float)(-2.0 * go * acc[j].y));
+        if (xy[j] >= 0) p.dg[(size_t)c * p.N + m] = make_float2((float)(-2.0 * go * acc[j].x), (float)(-2.0 * go * acc[j].y));
     }
     __syncthreads();
-    if (threadIdx.x < nu) {
-        const int k = threadIdx.x;
-        double sx = 0.0, sy = 0.0;
-        for (int u = 0; u < kKThreads / 32; ++u) {
-            sx += red[(2 * k) * (kKThreads / 32) + u];
-            sy += red[(2 * k + 1) * (kKThreads / 32) + u];
-        }
-        sp.partial[((size_t)blockIdx.x * nu + k) * 2] = sx;
-        sp.partial[((size_t)blockIdx.x * nu + k) * 2 + 1] = sy;
-    }
+    // dV partials of the CTA: 8 threads per (type, component), each adding
+    // 32 threads' terms in FP64, then the 8 in a fixed shuffle order
+    const int combo = threadIdx.x >> 3, sub = threadIdx.x & 7;
+    double sacc = 0.0;
+    if (combo < 2 * nu)
+        for (int u = 0; u < kKThreads / 8; ++u) sacc += (double)sdv[combo * kDvPitch + u * 8 + sub];
+    sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+    sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+    sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
+    if (sub == 0 && combo < 2 * nu) sp.partial[((size_t)blockIdx.x * nu + (combo >> 1)) * 2 + (combo & 1)] = sacc;
 }
 
 // chi^2 (fwd) or dV (bwd) from the ranges' partial sums, in range order
@@ -378,8 +399,25 @@ gc_status st_launch(gc_ctx *ctx, const Chi2Params &p, bool bwd, cudaStream_t s) 
     if (st != GC_OK) return st;
     sp.partial = static_cast<double *>(ctx->scratch);
     const unsigned grid = (unsigned)(p.C * sp.parts);
-    if (bwd) chi2_bwd_st<<<grid, kKThreads, 0, s>>>(p, sp);
-    else chi2_fwd_st<<<grid, kKThreads, 0, s>>>(p, sp);
+    const int fl = (p.w ? 1 : 0) | ((bwd ? p.resid_in != nullptr : p.resid_out != nullptr) ? 2 : 0);
+    const bool c64 = p.vfmt == GC_C64;
+#define GC_ST_CASE(F)                                                                    \
+    case F:                                                                              \
+        if (bwd) {                                                                       \
+            if (c64) chi2_bwd_st<GC_C64, F><<<grid, kKThreads, 0, s>>>(p, sp);           \
+            else chi2_bwd_st<GC_I4C, F><<<grid, kKThreads, 0, s>>>(p, sp);               \
+        } else {                                                                         \
+            if (c64) chi2_fwd_st<GC_C64, F><<<grid, kKThreads, 0, s>>>(p, sp);           \
+            else chi2_fwd_st<GC_I4C, F><<<grid, kKThreads, 0, s>>>(p, sp);               \
+        }                                                                                \
+        break;
+    switch (fl) {
+        GC_ST_CASE(0)
+        GC_ST_CASE(1)
+        GC_ST_CASE(2)
+        GC_ST_CASE(3)
+    }
+#undef GC_ST_CASE
     const int nr = bwd ? p.C * p.n_ubl : p.C;
     chi2_st_reduce<<<(nr + 255) / 256, 256, 0, s>>>(p, sp, bwd ? 1 : 0);
     cudaError_t e = cudaGetLastError();

@@ -159,15 +159,29 @@ def test_chi2r_against_array_size(gc, ctx):
                     assert full[c] == pytest.approx(o_full, rel=2e-3), (scheme, L, c)
             dof_red = oc.dof(sel.P, L * L, sel.n_ubl)
             rows.append((scheme, L, sel.P, sel.n_ubl, dof_red, red, full))
-            # hollow points: the calibrator's own fit, chi^2_r = 1 within
-            # the chi^2 scatter of its DoF
-            assert abs(np.mean(red) - 1.0) < 6.0 * np.sqrt(2.0 / (dof_red * C)) + 0.02, (scheme, L, red)
+            # hollow points: the calibrator's own fit.  The radiometer
+            # sigma_p^2 treats every pair's noise as independent; at voltage
+            # level the terms n_i conj(s_j) of one antenna's noise with the
+            # sky are shared by all pairs of that antenna, and the gain fit
+            # absorbs part of them, so chi^2_r falls a few per cent below 1
+            # as the pairs per antenna grow (the oracle shows the same on
+            # the same voltages, and it goes away at lower per-antenna SNR,
+            # below); the paper's visibility-level draws have no such terms
+            assert 0.85 < np.mean(red) < 1.0 + 6.0 * np.sqrt(2.0 / (dof_red * C)) + 0.02, (scheme, L, red)
             # solid points: gains that were fitted to V^reduced describe the
             # full matrix less well than the calibrator's own fit, but still
             # reasonably (the subset scheme's larger gain variance shows as
             # the larger excess, as in the paper's figure)
             assert np.mean(red) - 0.05 < np.mean(full) < 3.0, (scheme, L, red, full)
-    print("\nper-antenna SNR 0.1, T = 4096, 8 channels per size")
+    # the shared-noise deficit is a matter of SNR: at per-antenna SNR 0.03
+    # the 24 x 24 subset calibration's own chi^2_r is 1 within its scatter
+    sel = gc.Selection("subset", 24, T)
+    volt, _, _ = synth.make_voltages(1224, 24, C, T, n_src=20, snr=0.03, device="cuda")
+    red_lo, _, _ = _chain_gpu(gc, ctx, volt, sel, _full_sel(gc, 24, T), 24)
+    dof_lo = oc.dof(sel.P, 24 * 24, sel.n_ubl)
+    assert abs(np.mean(red_lo) - 1.0) < 6.0 * np.sqrt(2.0 / (dof_lo * C)) + 0.02, red_lo
+    print(f"\nsubset 24 x 24 at per-antenna SNR 0.03: chi2_r(V^reduced) {np.mean(red_lo):.4f}")
+    print("per-antenna SNR 0.1, T = 4096, 8 channels per size")
     print("scheme   L     N      P  n_ubl   chi2_r(V^reduced) mean [min, max]   chi2_r(V^full) mean [min, max]")
     for scheme, L, P, nu, dof, red, full in rows:
         print(f"{scheme:7s}{L:3d} {L * L:5d} {P:6d} {nu:5d}   {np.mean(red):.4f} [{red.min():.4f}, {red.max():.4f}]"
