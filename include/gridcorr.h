@@ -133,6 +133,13 @@ GC_API int gc_fft_size(int L);
  * Voltages are staged by TMA when the buffer is 16-byte aligned and a grid
  * row is a multiple of 16 bytes (c64: L even; c32h: L % 4 == 0; i4c:
  * L % 16 == 0), by plain loads otherwise.
+ * 4+4-bit voltages on grids of L = 40, 48, 56 or 64 (M = 128, 16-byte
+ * aligned, unmasked) take the row stage of the FFT on the tensor cores
+ * (tcgen05 kind::f16 products of binary16 hi/lo splits of the DFT matrix and
+ * of w, FP32 accumulation; the column stage and |X|^2 on the CUDA cores);
+ * the knob "fft.path" = 1 keeps them on the CUDA-core kernel.  Both meet the
+ * same accuracy (lag sums within 1e-5 of the zero-lag power, FP64
+ * reference).
  *
  * Uses the context's scratch workspace for per-time-chunk power spectra
  * (C * chunks * M^2 * 4 bytes, plus C * M * (2L-1) * 8 bytes for M = 256;
@@ -451,6 +458,9 @@ GC_API gc_status gc_visibility_variance(gc_ctx *ctx, const gc_sel *sel, double s
  *   "fft.shape"        FFT-correlator launch shape: 0 default, 1 the
  *                      alternative sample grouping built for the 64x64
  *                      4+4-bit and 32x32 complex64 grids (others ignore it)
+ *   "fft.path"         FFT-correlator for 4+4-bit voltages with M = 128: 0
+ *                      row stage on the tensor cores where it applies, 1
+ *                      CUDA cores only
  * GC_EINVAL for an unknown name or a negative value.
  */
 GC_API gc_status gc_set_tuning(gc_ctx *ctx, const char *name, int value);

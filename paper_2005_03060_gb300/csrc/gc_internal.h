@@ -35,7 +35,8 @@ enum {
     GC_TUNE_XENG_PATH = 5,
     GC_TUNE_XENG_TC_SHAPE = 6,
     GC_TUNE_FFT_SHAPE = 7,
-    GC_TUNE_N = 8
+    GC_TUNE_FFT_PATH = 8,
+    GC_TUNE_N = 9
 };
 
 // staging buffers of the streamed integration: with three, a chunk's copy
@@ -44,7 +45,7 @@ constexpr int GC_NSTAGE = 3;
 
 struct gc_ctx {
     int device = 0;
-    int tune[GC_TUNE_N] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int tune[GC_TUNE_N] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     int sm_count = 0;
     unsigned int *status_dev = nullptr;   // device error word
     void *scratch = nullptr;              // grow-only workspace
@@ -77,6 +78,11 @@ gc_status gc_fail(gc_ctx *ctx, gc_status st, const std::string &msg);
 gc_status gc_cuda_fail(gc_ctx *ctx, cudaError_t e, const char *what);
 gc_status gc_scratch_reserve(gc_ctx *ctx, size_t bytes);
 bool gc_aligned(const void *p, size_t a);
+
+// FFT-correlator with the row stage on the tensor cores (gc_fftcorr_tc.cu)
+bool gc_fft_tc_eligible(const gc_ctx *ctx, int vfmt, int L, const void *volt, bool masked);
+gc_status gc_fft_tc_run(gc_ctx *ctx, const void *volt, int L, int C, int T, const float *gains, float **ppart,
+                        int *n_chunks, cudaStream_t stream);
 
 // tensor-map encode through the driver entry point (no libcuda link)
 gc_status gc_encode_tiled(gc_ctx *ctx, CUtensorMap *map, CUtensorMapDataType dt, int rank,

@@ -216,7 +216,7 @@ static int tune_index(const char *name) {
     if (!name) return -1;
     static const char *names[GC_TUNE_N] = {"fft.chunk_len", "xeng.tsplit", "cal.ctas_per_sm", "cal.order",
                                                  "cal.operator", "xeng.path",
-                                                 "xeng.tc_shape", "fft.shape"};
+                                                 "xeng.tc_shape", "fft.shape", "fft.path"};
     for (int k = 0; k < GC_TUNE_N; ++k)
         if (strcmp(name, names[k]) == 0) return k;
     return -1;

@@ -57,6 +57,19 @@ __device__ __forceinline__ void gc_tc_mma_f8(uint32_t d_tmem, uint64_t adesc, ui
         : "memory");
 }
 
+// D[tmem] (+)= A[tmem] * B^T, kind::f16 (f16 x f16 -> f32) with the A operand
+// in tensor memory (lane = row of A, two 16-bit elements of K per 32-bit
+// column, the lower K index in the low half) and B from a shared-memory
+// descriptor; issued by one thread.
+__device__ __forceinline__ void gc_tc_mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                                 uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive once on `bar` when every tcgen05.mma issued so far by this thread
 // has completed.
 __device__ __forceinline__ void gc_tc_commit(uint64_t *bar) {
@@ -78,6 +91,31 @@ __device__ __forceinline__ void gc_tmem_ld32(uint32_t taddr, uint32_t *r) {
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+
+// 8 consecutive 32-bit columns of this warp's 32 lanes, without the wait
+// (issue several, then gc_tmem_wait_ld once).
+__device__ __forceinline__ void gc_tmem_ld8_nowait(uint32_t taddr, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void gc_tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Store 16 / 32 consecutive 32-bit columns of this warp's 32 lanes (thread t
+// writes lane base + t); gc_tmem_wait_st before the columns are read again.
+__device__ __forceinline__ void gc_tmem_st16(uint32_t taddr, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void gc_tmem_st32(uint32_t taddr, const uint32_t *r) {
+    gc_tmem_st16(taddr, r);
+    gc_tmem_st16(taddr + 16, r + 16);
+}
+__device__ __forceinline__ void gc_tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // 2-D tiled TMA load into shared memory, completing on `bar`.
 __device__ __forceinline__ void gc_tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1) {
