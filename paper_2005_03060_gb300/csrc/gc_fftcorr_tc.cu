@@ -94,40 +94,58 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
+// 4 columns (y .. y + 3 of Re and Im, and of Re and Im 32 rows further) of
+// this lane's D buffer into r[0..15], without the wait
+__device__ __forceinline__ void d_chunk_load(uint32_t dre, uint32_t dim, int y, uint32_t *r) {
+    gc_tmem_ld4_nowait(dre + y, r);
+    gc_tmem_ld4_nowait(dre + 32 + y, r + 4);
+    gc_tmem_ld4_nowait(dim + y, r + 8);
+    gc_tmem_ld4_nowait(dim + 32 + y, r + 12);
+}
+
+template <int S2V>
+__device__ __forceinline__ void fold_chunk(float2 (&b)[32], const uint32_t *r, int c) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int yp = 4 * c + j;
+        const float2 a0 = make_float2(__uint_as_float(r[j]), __uint_as_float(r[8 + j]));
+        const float2 a1 = make_float2(__uint_as_float(r[4 + j]), __uint_as_float(r[12 + j]));
+        float2 t;
+        if constexpr (S2V == 0) t = add2(a0, a1);
+        else if constexpr (S2V == 2) t = sub2(a0, a1);
+        else {
+            const float2 q = rot_mi_tc<S2V>(a1);
+            t = make_float2(a0.x + q.x, a0.y + q.y);
+        }
+        // omega_128^(s2 y) = omega_256^(2 s2 y)
+        b[yp] = S2V == 0 ? t : tw_apply(t, (2 * S2V * yp) & 255);
+    }
+}
+
 // One column residue S2V of the current sample: fold the 64 values of this
-// lane's D columns, 32-point FFT, |X|^2 into the residue's power columns.
+// lane's D columns (the loads of the next 4 rows in flight while a chunk
+// folds), 32-point FFT, |X|^2 into the residue's power columns.
 template <int S2V>
 __device__ __forceinline__ void column_residue(uint32_t dre, uint32_t dim, uint32_t pcol, bool first) {
     float2 b[32];
+    uint32_t r0[16], r1[16];
+    d_chunk_load(dre, dim, 0, r0);
+    gc_tmem_wait_ld16_regs(r0);
 #pragma unroll
-    for (int c4 = 0; c4 < 4; ++c4) {
-        uint32_t ra[8], rb[8], ia[8], ib[8];
-        gc_tmem_ld8_nowait(dre + 8 * c4, ra);
-        gc_tmem_ld8_nowait(dre + 32 + 8 * c4, rb);
-        gc_tmem_ld8_nowait(dim + 8 * c4, ia);
-        gc_tmem_ld8_nowait(dim + 32 + 8 * c4, ib);
-        gc_tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int yp = 8 * c4 + j;
-            const float2 a0 = make_float2(__uint_as_float(ra[j]), __uint_as_float(ia[j]));
-            const float2 a1 = make_float2(__uint_as_float(rb[j]), __uint_as_float(ib[j]));
-            float2 t;
-            if constexpr (S2V == 0) t = add2(a0, a1);
-            else if constexpr (S2V == 2) t = sub2(a0, a1);
-            else {
-                const float2 r = rot_mi_tc<S2V>(a1);
-                t = make_float2(a0.x + r.x, a0.y + r.y);
-            }
-            // omega_128^(s2 y) = omega_256^(2 s2 y)
-            b[yp] = S2V == 0 ? t : tw_apply(t, (2 * S2V * yp) & 255);
-        }
+    for (int c = 0; c < 8; c += 2) {
+        d_chunk_load(dre, dim, 4 * (c + 1), r1);
+        fold_chunk<S2V>(b, r0, c);
+        gc_tmem_wait_ld16_regs(r1);
+        if (c + 2 < 8) d_chunk_load(dre, dim, 4 * (c + 2), r0);
+        fold_chunk<S2V>(b, r1, c + 1);
+        if (c + 2 < 8) gc_tmem_wait_ld16_regs(r0);
     }
     fft_reg<32>(b);
     uint32_t pv[32];
     if (!first) {
         gc_tmem_wait_st();
-        gc_tmem_ld32(pcol, pv);
+        gc_tmem_ld32_nowait(pcol, pv);
+        gc_tmem_wait_ld_regs(pv);
     }
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
@@ -437,7 +455,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
             for (int r = 0; r < 2; ++r) {
                 const int s2 = 2 * half + r;
                 uint32_t pv[32];
-                gc_tmem_ld32(lb + kColP + 32 * s2, pv);
+                gc_tmem_ld32_nowait(lb + kColP + 32 * s2, pv);
+                gc_tmem_wait_ld_regs(pv);
 #pragma unroll
                 for (int i = 0; i < 32; ++i) out[(s2 + 4 * bitrev<32>(i)) * kTM + kx] = __uint_as_float(pv[i]);
             }
