@@ -1336,23 +1336,23 @@ __device__ float rel_op_pass(const CalParams &p, const CgWork &w, float mu) {
             const float2 wk = q[N + k];
             const float GU = Gm * G[N + k];
             const int off = dy * L + dx;
+            // without branches: a pair off the grid reads antenna m itself
+            // and gets weight 0 (fmaf(0, a, s) = s, so the sums are those of
+            // the pairs that exist)
+            const bool v1 = (unsigned)(x - dx) < (unsigned)L && (unsigned)(y - dy) < (unsigned)L;
+            const bool v2 = (unsigned)(x + dx) < (unsigned)L && (unsigned)(y + dy) < (unsigned)L;
+            const int j = v1 ? m - off : m, i = v2 ? m + off : m;
+            const float2 qj = q[j], qi = q[i];
+            const float W1 = v1 ? GU * G[j] : 0.f, W2 = v2 ? GU * G[i] : 0.f;
             // m first: s = q_m + conj(q_j) + w_k
-            if (x - dx >= 0 && x - dx < L && y - dy >= 0 && y - dy < L) {
-                const float2 qj = q[m - off];
-                const float Wp = GU * G[m - off];
-                const float ax = qm.x + wk.x + qj.x, ay = qm.y + wk.y - qj.y;
-                sx = fmaf(Wp, ax, sx);
-                sy = fmaf(Wp, ay, sy);
-                tvx[k] = fmaf(Wp, ax, tvx[k]);
-                tvy[k] = fmaf(Wp, ay, tvy[k]);
-            }
+            const float ax = qm.x + wk.x + qj.x, ay = qm.y + wk.y - qj.y;
+            sx = fmaf(W1, ax, sx);
+            sy = fmaf(W1, ay, sy);
+            tvx[k] = fmaf(W1, ax, tvx[k]);
+            tvy[k] = fmaf(W1, ay, tvy[k]);
             // m second: conj(s) = conj(q_i) + q_m + conj(w_k)
-            if (x + dx >= 0 && x + dx < L && y + dy >= 0 && y + dy < L) {
-                const float2 qi = q[m + off];
-                const float Wp = GU * G[m + off];
-                sx = fmaf(Wp, qi.x + qm.x + wk.x, sx);
-                sy = fmaf(Wp, qm.y - qi.y - wk.y, sy);
-            }
+            sx = fmaf(W2, qi.x + qm.x + wk.x, sx);
+            sy = fmaf(W2, qm.y - qi.y - wk.y, sy);
         }
         w.acc[2 * m] = sx;
         w.acc[2 * m + 1] = sy;

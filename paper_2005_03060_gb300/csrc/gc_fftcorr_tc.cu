@@ -29,12 +29,13 @@
 // spectra [C][chunks][128][128] that fftcorr_finalize inverts.
 //
 // Warp roles (one CTA per SM, persistent over (channel, time chunk) items):
-//   warps 0-7   column stage (warps w and w + 4 share tensor-memory lanes
-//               32 (w % 4) .. +31; warp w < 4 takes residues 0, 1, the other 2, 3);
-//   warps 8-9   converters: raw 4+4-bit samples -> w = v / g -> hi / lo
+//   warps 0-15  column stage: warp w takes tensor-memory lanes 32 (w % 4) ..
+//               +31 and the column residue s2 = w / 4;
+//   warps 16-19 converters: raw 4+4-bit samples -> w = v / g -> hi / lo
 //               binary16 B operands in shared memory (K-major, no swizzle);
-//   warp 10     bulk copies of raw samples (two per stage) into a ring;
-//   warp 11     MMA issue (one thread), completion committed to the rings.
+//   warp 20     bulk copies of raw samples (two per stage) into a ring;
+//   warp 21     MMA issue (one thread), completion committed to the rings;
+//   warps 22-23 idle (their warpgroup gives its registers to the others).
 // Tensor memory (512 columns): D (two buffers of Re 64 + Im 64 columns),
 // A_hi, A_lo (64 columns each: two binary16 of K per column), the power
 // spectrum (128 columns: 4 residues x 32 bins).  Every wait is bounded; a
@@ -51,8 +52,14 @@ namespace {
 
 constexpr int kTM = 128;                 // FFT side
 constexpr int kTL = 64;                  // largest grid side (rows y and inputs x of the row stage)
-constexpr int kThreadsTC = 384;
-constexpr int kWarpConv0 = 8, kConvWarps = 2, kWarpTma = 10, kWarpMma = 11;
+// 24 warps: column stage 0-15 (one residue s2 = warp / 4 each), converters
+// 16-19, bulk copies 20, MMA issue 21, 22-23 idle.  Launched at 80 registers
+// a thread (768 x 80 = 61 440); each warpgroup then resizes with setmaxnreg
+// at the top of its branch: column stage 96, converters 56, the last
+// warpgroup 40 (512 x 96 + 128 x 56 + 128 x 40 = 61 440, the launch total).
+constexpr int kThreadsTC = 768;
+constexpr int kEpiWarps = 16;
+constexpr int kWarpConv0 = 16, kConvWarps = 4, kWarpTma = 20, kWarpMma = 21;
 constexpr int kConvThreads = 32 * kConvWarps;
 constexpr int kTasks = kTL * 8 / kConvThreads;   // (row, group of 8 inputs) tasks per converter thread
 constexpr int kBStages = 3;
@@ -123,36 +130,39 @@ __device__ __forceinline__ void fold_chunk(float2 (&b)[32], const uint32_t *r, i
 }
 
 // One column residue S2V of the current sample: fold the 64 values of this
-// lane's D columns (the loads of the next 4 rows in flight while a chunk
-// folds), 32-point FFT, |X|^2 into the residue's power columns.
+// lane's D columns (four rows at a time; the other column-stage warps of the
+// SM hide the load latency), 32-point FFT, |X|^2 into the residue's power
+// columns (16 at a time).
 template <int S2V>
 __device__ __forceinline__ void column_residue(uint32_t dre, uint32_t dim, uint32_t pcol, bool first) {
     float2 b[32];
-    uint32_t r0[16], r1[16];
-    d_chunk_load(dre, dim, 0, r0);
-    gc_tmem_wait_ld16_regs(r0);
 #pragma unroll
-    for (int c = 0; c < 8; c += 2) {
-        d_chunk_load(dre, dim, 4 * (c + 1), r1);
-        fold_chunk<S2V>(b, r0, c);
-        gc_tmem_wait_ld16_regs(r1);
-        if (c + 2 < 8) d_chunk_load(dre, dim, 4 * (c + 2), r0);
-        fold_chunk<S2V>(b, r1, c + 1);
-        if (c + 2 < 8) gc_tmem_wait_ld16_regs(r0);
+    for (int c = 0; c < 8; ++c) {
+        uint32_t r[16];
+        d_chunk_load(dre, dim, 4 * c, r);
+        gc_tmem_wait_ld16_regs(r);
+        fold_chunk<S2V>(b, r, c);
     }
     fft_reg<32>(b);
-    uint32_t pv[32];
-    if (!first) {
-        gc_tmem_wait_st();
-        gc_tmem_ld32_nowait(pcol, pv);
-        gc_tmem_wait_ld_regs(pv);
-    }
+    if (!first) gc_tmem_wait_st();
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        const float p0 = first ? 0.f : __uint_as_float(pv[i]);
-        pv[i] = __float_as_uint(fmaf(b[i].x, b[i].x, fmaf(b[i].y, b[i].y, p0)));
+    for (int h = 0; h < 2; ++h) {
+        uint32_t pv[16];
+        if (!first) {
+            gc_tmem_ld4_nowait(pcol + 16 * h, pv);
+            gc_tmem_ld4_nowait(pcol + 16 * h + 4, pv + 4);
+            gc_tmem_ld4_nowait(pcol + 16 * h + 8, pv + 8);
+            gc_tmem_ld4_nowait(pcol + 16 * h + 12, pv + 12);
+            gc_tmem_wait_ld16_regs(pv);
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const float2 v = b[16 * h + i];
+            const float p0 = first ? 0.f : __uint_as_float(pv[i]);
+            pv[i] = __float_as_uint(fmaf(v.x, v.x, fmaf(v.y, v.y, p0)));
+        }
+        gc_tmem_st16(pcol + 16 * h, pv);
     }
-    gc_tmem_st32(pcol, pv);
 }
 
 struct ItemTC {
@@ -194,7 +204,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
         }
         for (int i = 0; i < 2; ++i) {
             gc_mbar_init(&full_d[i], 1);
-            gc_mbar_init(&empty_d[i], 8);
+            gc_mbar_init(&empty_d[i], kEpiWarps);
         }
         gc_mbar_init(&mma_done, 1);
         gc_fence_mbar_init();
@@ -233,8 +243,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
     __syncthreads();
     gc_tc_fence_after();
     bool ok = true;
+    const int wg = warp >> 2;
 
-    if (warp == kWarpTma) {
+    if (wg == kWarpTma / 4) {
+      asm volatile("setmaxnreg.dec.sync.aligned.u32 40;");
+      if (warp == kWarpTma) {
         // ---------------------------------------------------------------- bulk copies of raw samples
         if (lane == 0) {
             uint32_t rs = 0, rph = 0;
@@ -271,7 +284,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
                     gc_mbar_wait(&full_raw[i], (uint32_t)(last_round[i] & 1), GC_WAIT_LIMIT_NS / 10);
         }
         __syncwarp();
-    } else if (warp == kWarpMma) {
+      } else if (warp == kWarpMma) {
         // ---------------------------------------------------------------- MMA issue
         if (lane == 0) {
             const uint32_t idesc = gc_tc_idesc(128, kTL, false, false);
@@ -327,7 +340,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
             gc_mbar_wait(&mma_done, 0, GC_WAIT_LIMIT_NS / 10);
         }
         __syncwarp();
-    } else if (warp >= kWarpConv0) {
+      }
+    } else if (wg == kWarpConv0 / 4) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 56;");
         // ---------------------------------------------------------------- converters
         // task (row y, group of 8 inputs kg): y = (ct >> 3) + (kConvThreads / 8) i, kg = ct & 7
         const int ct = tid - 32 * kWarpConv0;
@@ -416,8 +431,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
             if (lane == 0) atomicOr(p.status, GC_DEV_TIMEOUT_FFT);
         }
     } else {
-        // ---------------------------------------------------------------- column stage (warps 0-7)
-        const int lq = warp & 3, half = warp >> 2;
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 96;");
+        // ---------------------------------------------------------------- column stage (warps 0-15)
+        const int lq = warp & 3, s2w = warp >> 2;
         const int kx = 32 * lq + lane;
         const uint32_t lb = tmem + ((uint32_t)(32 * lq) << 16);
         uint32_t db = 0, dph = 0;
@@ -432,12 +448,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
                 gc_tc_fence_after();
                 const uint32_t dre = lb + kColD + 128 * db, dim = dre + 64;
                 const bool first = s == 0;
-                if (half == 0) {
-                    column_residue<0>(dre, dim, lb + kColP + 0, first);
-                    column_residue<1>(dre, dim, lb + kColP + 32, first);
-                } else {
-                    column_residue<2>(dre, dim, lb + kColP + 64, first);
-                    column_residue<3>(dre, dim, lb + kColP + 96, first);
+                const uint32_t pc = lb + kColP + 32 * s2w;
+                switch (s2w) {
+                    case 0: column_residue<0>(dre, dim, pc, first); break;
+                    case 1: column_residue<1>(dre, dim, pc, first); break;
+                    case 2: column_residue<2>(dre, dim, pc, first); break;
+                    default: column_residue<3>(dre, dim, pc, first); break;
                 }
                 gc_tc_fence_before();
                 __syncwarp();
@@ -452,13 +468,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
             gc_tmem_wait_st();
             float *out = p.ppart + ((size_t)it.c * p.n_chunks + it.chunk) * kTM * kTM;
 #pragma unroll 1
-            for (int r = 0; r < 2; ++r) {
-                const int s2 = 2 * half + r;
-                uint32_t pv[32];
-                gc_tmem_ld32_nowait(lb + kColP + 32 * s2, pv);
-                gc_tmem_wait_ld_regs(pv);
+            for (int h = 0; h < 2; ++h) {
+                uint32_t pv[16];
+                gc_tmem_ld4_nowait(lb + kColP + 32 * s2w + 16 * h, pv);
+                gc_tmem_ld4_nowait(lb + kColP + 32 * s2w + 16 * h + 4, pv + 4);
+                gc_tmem_ld4_nowait(lb + kColP + 32 * s2w + 16 * h + 8, pv + 8);
+                gc_tmem_ld4_nowait(lb + kColP + 32 * s2w + 16 * h + 12, pv + 12);
+                gc_tmem_wait_ld16_regs(pv);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) out[(s2 + 4 * bitrev<32>(i)) * kTM + kx] = __uint_as_float(pv[i]);
+                for (int i = 0; i < 16; ++i)
+                    out[(s2w + 4 * bitrev<32>(16 * h + i)) * kTM + kx] = __uint_as_float(pv[i]);
             }
         }
         if (!ok) {
