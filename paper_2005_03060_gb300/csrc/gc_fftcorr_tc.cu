@@ -29,13 +29,14 @@
 // spectra [C][chunks][128][128] that fftcorr_finalize inverts.
 //
 // Warp roles (one CTA per SM, persistent over (channel, time chunk) items):
-//   warps 0-15  column stage: warp w takes tensor-memory lanes 32 (w % 4) ..
-//               +31 and the column residue s2 = w / 4;
-//   warps 16-19 converters: raw 4+4-bit samples -> w = v / g -> hi / lo
-//               binary16 B operands in shared memory (K-major, no swizzle);
-//   warp 20     bulk copies of raw samples (two per stage) into a ring;
-//   warp 21     MMA issue (one thread), completion committed to the rings;
-//   warps 22-23 idle (their warpgroup gives its registers to the others).
+//   warps 0-7   column stage: warp w takes tensor-memory lanes 32 (w % 4) ..
+//               +31 and the column residues w / 4 and w / 4 + 2 (one load of
+//               the D columns feeds both folds);
+//   warps 8-9   converters: raw 4+4-bit samples -> w = v / g -> hi / lo
+//               binary16 B operands in shared memory (K-major, no swizzle),
+//               two samples per stage;
+//   warp 10     bulk copies of raw samples (two per stage) into a ring;
+//   warp 11     MMA issue (one thread), completion committed to the rings.
 // Tensor memory (512 columns): D (two buffers of Re 64 + Im 64 columns),
 // A_hi, A_lo (64 columns each: two binary16 of K per column), the power
 // spectrum (128 columns: 4 residues x 32 bins).  Every wait is bounded; a
@@ -52,20 +53,20 @@ namespace {
 
 constexpr int kTM = 128;                 // FFT side
 constexpr int kTL = 64;                  // largest grid side (rows y and inputs x of the row stage)
-// 24 warps: column stage 0-15 (one residue s2 = warp / 4 each), converters
-// 16-19, bulk copies 20, MMA issue 21, 22-23 idle.  Launched at 80 registers
-// a thread (768 x 80 = 61 440); each warpgroup then resizes with setmaxnreg
-// at the top of its branch: column stage 96, converters 56, the last
-// warpgroup 40 (512 x 96 + 128 x 56 + 128 x 40 = 61 440, the launch total).
-constexpr int kThreadsTC = 768;
-constexpr int kEpiWarps = 16;
-constexpr int kWarpConv0 = 16, kConvWarps = 4, kWarpTma = 20, kWarpMma = 21;
+// 12 warps: column stage 0-7 (warp w: tensor-memory lanes 32 (w % 4) .. +31,
+// column residues s2 = (w / 4) and (w / 4) + 2, which share their fold
+// inputs), converters 8-9, bulk copies 10, MMA issue 11.
+constexpr int kThreadsTC = 384;
+constexpr int kEpiWarps = 8;
+constexpr int kWarpConv0 = 8, kConvWarps = 2, kWarpTma = 10, kWarpMma = 11;
 constexpr int kConvThreads = 32 * kConvWarps;
 constexpr int kTasks = kTL * 8 / kConvThreads;   // (row, group of 8 inputs) tasks per converter thread
-constexpr int kBStages = 3;
-constexpr int kBPlane = kTL * kTM * 2;   // one binary16 B operand: 64 rows y x 128 K = 16 KB
-constexpr int kBStage = 2 * kBPlane;     // hi, lo
-constexpr int kRawSamp = 2;              // samples per raw stage
+constexpr int kSamp = 2;                          // samples per raw stage and per B stage
+constexpr int kBStages = 2;
+constexpr int kBPlane = kSamp * kTL * kTM * 2;    // one binary16 B operand of kSamp samples: 32 KB
+constexpr int kBSample = kTL * kTM * 2;           // one sample's rows within a plane: 16 KB
+constexpr int kBStage = 2 * kBPlane;              // hi, lo
+constexpr int kRawSamp = kSamp;
 constexpr int kRawStages = 3;
 constexpr int kRawStride = kRawSamp * kTL * kTL + 128;   // + slack for the last row's 8-byte reads
 constexpr int kCoefBytes = kTasks * 8 * kConvThreads * 8;   // [task i][input e][converter thread] float2
@@ -101,49 +102,9 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
     lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
-// 4 columns (y .. y + 3 of Re and Im, and of Re and Im 32 rows further) of
-// this lane's D buffer into r[0..15], without the wait
-__device__ __forceinline__ void d_chunk_load(uint32_t dre, uint32_t dim, int y, uint32_t *r) {
-    gc_tmem_ld4_nowait(dre + y, r);
-    gc_tmem_ld4_nowait(dre + 32 + y, r + 4);
-    gc_tmem_ld4_nowait(dim + y, r + 8);
-    gc_tmem_ld4_nowait(dim + 32 + y, r + 12);
-}
-
-template <int S2V>
-__device__ __forceinline__ void fold_chunk(float2 (&b)[32], const uint32_t *r, int c) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int yp = 4 * c + j;
-        const float2 a0 = make_float2(__uint_as_float(r[j]), __uint_as_float(r[8 + j]));
-        const float2 a1 = make_float2(__uint_as_float(r[4 + j]), __uint_as_float(r[12 + j]));
-        float2 t;
-        if constexpr (S2V == 0) t = add2(a0, a1);
-        else if constexpr (S2V == 2) t = sub2(a0, a1);
-        else {
-            const float2 q = rot_mi_tc<S2V>(a1);
-            t = make_float2(a0.x + q.x, a0.y + q.y);
-        }
-        // omega_128^(s2 y) = omega_256^(2 s2 y)
-        b[yp] = S2V == 0 ? t : tw_apply(t, (2 * S2V * yp) & 255);
-    }
-}
-
-// One column residue S2V of the current sample: fold the 64 values of this
-// lane's D columns (four rows at a time; the other column-stage warps of the
-// SM hide the load latency), 32-point FFT, |X|^2 into the residue's power
-// columns (16 at a time).
-template <int S2V>
-__device__ __forceinline__ void column_residue(uint32_t dre, uint32_t dim, uint32_t pcol, bool first) {
-    float2 b[32];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        uint32_t r[16];
-        d_chunk_load(dre, dim, 4 * c, r);
-        gc_tmem_wait_ld16_regs(r);
-        fold_chunk<S2V>(b, r, c);
-    }
-    fft_reg<32>(b);
+// |X|^2 of one residue's 32 bins into its power columns (first sample of a
+// chunk: stored, later: added), 16 columns at a time
+__device__ __forceinline__ void power_update(const float2 (&b)[32], uint32_t pcol, bool first) {
     if (!first) gc_tmem_wait_st();
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -163,6 +124,45 @@ __device__ __forceinline__ void column_residue(uint32_t dre, uint32_t dim, uint3
         }
         gc_tmem_st16(pcol + 16 * h, pv);
     }
+}
+
+// The column stage of one sample for the residue pair PR: (0, 2) or (1, 3).
+// The 64 values X1[k_x][y] of this lane come in with one load of the Re and
+// one of the Im columns; each y and y + 32 give both residues' fold inputs
+//   s2 = PR:     (a0 + (-i)^PR a1) omega_128^(PR y)
+//   s2 = PR + 2: (a0 - (-i)^PR a1) omega_128^((PR + 2) y)
+// then a 32-point FFT and |X|^2 per residue.
+template <int PR>
+__device__ __forceinline__ void column_pair(uint32_t dre, uint32_t dim, uint32_t pcol_a, uint32_t pcol_b,
+                                            bool first) {
+    float2 ba[32], bb[32];
+    {
+        uint32_t re[64], im[64];
+        gc_tmem_ld64_nowait(dre, re);
+        gc_tmem_ld64_nowait(dim, im);
+        gc_tmem_wait_ld();
+        gc_reg_tie32(re);
+        gc_reg_tie32(re + 32);
+        gc_reg_tie32(im);
+        gc_reg_tie32(im + 32);
+#pragma unroll
+        for (int y = 0; y < 32; ++y) {
+            const float2 a0 = make_float2(__uint_as_float(re[y]), __uint_as_float(im[y]));
+            const float2 a1 = make_float2(__uint_as_float(re[y + 32]), __uint_as_float(im[y + 32]));
+            if constexpr (PR == 0) {
+                ba[y] = add2(a0, a1);
+                bb[y] = tw_apply(sub2(a0, a1), (4 * y) & 255);   // omega_128^(2 y)
+            } else {
+                const float2 r = rot_mi_tc<1>(a1);                // -i a1
+                ba[y] = tw_apply(add2(a0, r), (2 * y) & 255);     // omega_128^y
+                bb[y] = tw_apply(sub2(a0, r), (6 * y) & 255);     // omega_128^(3 y)
+            }
+        }
+    }
+    fft_reg<32>(ba);
+    power_update(ba, pcol_a, first);
+    fft_reg<32>(bb);
+    power_update(bb, pcol_b, first);
 }
 
 struct ItemTC {
@@ -243,11 +243,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
     __syncthreads();
     gc_tc_fence_after();
     bool ok = true;
-    const int wg = warp >> 2;
 
-    if (wg == kWarpTma / 4) {
-      asm volatile("setmaxnreg.dec.sync.aligned.u32 40;");
-      if (warp == kWarpTma) {
+    if (warp == kWarpTma) {
         // ---------------------------------------------------------------- bulk copies of raw samples
         if (lane == 0) {
             uint32_t rs = 0, rph = 0;
@@ -256,12 +253,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
             int round = 0;
             for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
                 const ItemTC it = decode_tc(p, item);
-                for (int s = 0; s < it.nt; s += kRawSamp) {
+                for (int s = 0; s < it.nt; s += kSamp) {
                     if (!gc_mbar_wait_abort(&empty_raw[rs], rph ^ 1u, &s_abort, GC_WAIT_LIMIT_NS)) {
                         ok = false;
                         break;
                     }
-                    const int ns = min(kRawSamp, it.nt - s);
+                    const int ns = min(kSamp, it.nt - s);
                     const uint32_t bytes = (uint32_t)(ns * N);
                     gc_mbar_expect_tx(&full_raw[rs], bytes);
                     gc_bulk_load(raw + (size_t)rs * kRawStride,
@@ -284,7 +281,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
                     gc_mbar_wait(&full_raw[i], (uint32_t)(last_round[i] & 1), GC_WAIT_LIMIT_NS / 10);
         }
         __syncwarp();
-      } else if (warp == kWarpMma) {
+    } else if (warp == kWarpMma) {
         // ---------------------------------------------------------------- MMA issue
         if (lane == 0) {
             const uint32_t idesc = gc_tc_idesc(128, kTL, false, false);
@@ -292,42 +289,48 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
             uint32_t bs = 0, bph = 0, db = 0, dph = 0;
             for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
                 const ItemTC it = decode_tc(p, item);
-                for (int s = 0; s < it.nt; ++s) {
-                    if (!gc_mbar_wait_abort(&full_b[bs], bph, &s_abort, GC_WAIT_LIMIT_NS) ||
-                        !gc_mbar_wait_abort(&empty_d[db], dph ^ 1u, &s_abort, GC_WAIT_LIMIT_NS)) {
+                for (int s = 0; s < it.nt && ok; s += kSamp) {
+                    if (!gc_mbar_wait_abort(&full_b[bs], bph, &s_abort, GC_WAIT_LIMIT_NS)) {
                         ok = false;
                         break;
                     }
-                    gc_tc_fence_after();
-                    const uint32_t dre = tmem + kColD + 128 * db, dim = dre + 64;
-                    const uint32_t b0 = bbase + (uint32_t)(bs * kBStage);
+                    const int ns = min(kSamp, it.nt - s);
+                    for (int j = 0; j < ns; ++j) {
+                        if (!gc_mbar_wait_abort(&empty_d[db], dph ^ 1u, &s_abort, GC_WAIT_LIMIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        gc_tc_fence_after();
+                        const uint32_t dre = tmem + kColD + 128 * db, dim = dre + 64;
+                        const uint32_t b0 = bbase + (uint32_t)(bs * kBStage + j * kBSample);
 #pragma unroll
-                    for (int term = 0; term < 3; ++term) {
-                        const uint32_t a = tmem + (term == 2 ? kColALo : kColAHi);
-                        const uint32_t b = b0 + (term == 1 ? (uint32_t)kBPlane : 0u);
+                        for (int term = 0; term < 3; ++term) {
+                            const uint32_t a = tmem + (term == 2 ? kColALo : kColAHi);
+                            const uint32_t b = b0 + (term == 1 ? (uint32_t)kBPlane : 0u);
 #pragma unroll
-                        for (int k = 0; k < 8; ++k)
-                            gc_tc_mma_f16_ts(dre, a + 8 * k, gc_tc_sdesc(b + 256 * k, kLBO, kSBO), idesc,
-                                             (term | k) != 0);
-                        // Im: C with Im w, then -S with Re w
+                            for (int k = 0; k < 8; ++k)
+                                gc_tc_mma_f16_ts(dre, a + 8 * k, gc_tc_sdesc(b + 256 * k, kLBO, kSBO), idesc,
+                                                 (term | k) != 0);
+                            // Im: C with Im w, then -S with Re w
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            gc_tc_mma_f16_ts(dim, a + 8 * k, gc_tc_sdesc(b + 256 * (k + 4), kLBO, kSBO), idesc,
-                                             (term | k) != 0);
+                            for (int k = 0; k < 4; ++k)
+                                gc_tc_mma_f16_ts(dim, a + 8 * k, gc_tc_sdesc(b + 256 * (k + 4), kLBO, kSBO), idesc,
+                                                 (term | k) != 0);
 #pragma unroll
-                        for (int k = 4; k < 8; ++k)
-                            gc_tc_mma_f16_ts(dim, a + 8 * k, gc_tc_sdesc(b + 256 * (k - 4), kLBO, kSBO),
-                                             idesc | GC_TC_NEGATE_A, 1u);
+                            for (int k = 4; k < 8; ++k)
+                                gc_tc_mma_f16_ts(dim, a + 8 * k, gc_tc_sdesc(b + 256 * (k - 4), kLBO, kSBO),
+                                                 idesc | GC_TC_NEGATE_A, 1u);
+                        }
+                        gc_tc_commit(&full_d[db]);
+                        if (++db == 2) {
+                            db = 0;
+                            dph ^= 1u;
+                        }
                     }
                     gc_tc_commit(&empty_b[bs]);
-                    gc_tc_commit(&full_d[db]);
                     if (++bs == kBStages) {
                         bs = 0;
                         bph ^= 1u;
-                    }
-                    if (++db == 2) {
-                        db = 0;
-                        dph ^= 1u;
                     }
                 }
             }
@@ -340,9 +343,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
             gc_mbar_wait(&mma_done, 0, GC_WAIT_LIMIT_NS / 10);
         }
         __syncwarp();
-      }
-    } else if (wg == kWarpConv0 / 4) {
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 56;");
+    } else if (warp >= kWarpConv0) {
         // ---------------------------------------------------------------- converters
         // task (row y, group of 8 inputs kg): y = (ct >> 3) + (kConvThreads / 8) i, kg = ct & 7
         const int ct = tid - 32 * kWarpConv0;
@@ -368,57 +369,59 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
                     coef[(i * 8 + e) * kConvThreads + ct] = cc;
                 }
             }
-            for (int s = 0; s < it.nt; ++s) {
-                const int j = s % kRawSamp;
-                if (j == 0 && !gc_mbar_wait_abort(&full_raw[rs], rph, &s_abort, GC_WAIT_LIMIT_NS)) ok = false;
+            for (int s = 0; s < it.nt; s += kSamp) {
+                if (!gc_mbar_wait_abort(&full_raw[rs], rph, &s_abort, GC_WAIT_LIMIT_NS)) ok = false;
                 if (ok && !gc_mbar_wait_abort(&empty_b[bs], bph ^ 1u, &s_abort, GC_WAIT_LIMIT_NS)) ok = false;
                 if (!__all_sync(0xffffffffu, ok)) {
                     ok = false;
                     break;
                 }
-                const unsigned char *rb = raw + (size_t)rs * kRawStride + (size_t)j * N;
-                unsigned char *bhi = bring + (size_t)bs * kBStage, *blo = bhi + kBPlane;
+                const int ns = min(kSamp, it.nt - s);
+                for (int j = 0; j < ns; ++j) {
+                    const unsigned char *rb = raw + (size_t)rs * kRawStride + (size_t)j * N;
+                    unsigned char *bhi = bring + (size_t)bs * kBStage + (size_t)j * kBSample, *blo = bhi + kBPlane;
 #pragma unroll 2
-                for (int i = 0; i < kTasks; ++i) {
-                    const int y = (ct >> 3) + (kConvThreads / 8) * i;
-                    if (y >= L) continue;
-                    const uint2 word = *reinterpret_cast<const uint2 *>(rb + y * L + 8 * kg);
-                    // n + 8 of the Re and Im nibbles, one byte each
-                    const uint32_t ure0 = ((word.x >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
-                    const uint32_t ure1 = ((word.y >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
-                    const uint32_t uim0 = (word.x & 0x0F0F0F0Fu) ^ 0x08080808u;
-                    const uint32_t uim1 = (word.y & 0x0F0F0F0Fu) ^ 0x08080808u;
-                    uint32_t rh[4], rl[4], ih[4], il[4];
+                    for (int i = 0; i < kTasks; ++i) {
+                        const int y = (ct >> 3) + (kConvThreads / 8) * i;
+                        if (y >= L) continue;
+                        const uint2 word = *reinterpret_cast<const uint2 *>(rb + y * L + 8 * kg);
+                        // n + 8 of the Re and Im nibbles, one byte each
+                        const uint32_t ure0 = ((word.x >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
+                        const uint32_t ure1 = ((word.y >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
+                        const uint32_t uim0 = (word.x & 0x0F0F0F0Fu) ^ 0x08080808u;
+                        const uint32_t uim1 = (word.y & 0x0F0F0F0Fu) ^ 0x08080808u;
+                        uint32_t rh[4], rl[4], ih[4], il[4];
 #pragma unroll
-                    for (int e = 0; e < 8; e += 2) {
-                        float2 w[2];
+                        for (int e = 0; e < 8; e += 2) {
+                            float2 w[2];
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int ee = e + h;
-                            const float2 v = i4c_bytes_to_f2(ee < 4 ? ure0 : ure1, ee < 4 ? uim0 : uim1, ee & 3);
-                            w[h] = cmul(v, coef[(i * 8 + ee) * kConvThreads + ct]);
+                            for (int h = 0; h < 2; ++h) {
+                                const int ee = e + h;
+                                const float2 v = i4c_bytes_to_f2(ee < 4 ? ure0 : ure1, ee < 4 ? uim0 : uim1, ee & 3);
+                                w[h] = cmul(v, coef[(i * 8 + ee) * kConvThreads + ct]);
+                            }
+                            split2(w[0].x, w[1].x, rh[e >> 1], rl[e >> 1]);
+                            split2(w[0].y, w[1].y, ih[e >> 1], il[e >> 1]);
                         }
-                        split2(w[0].x, w[1].x, rh[e >> 1], rl[e >> 1]);
-                        split2(w[0].y, w[1].y, ih[e >> 1], il[e >> 1]);
+                        // B[n = y][k]: Re at k = 8 kg .., Im at k = 64 + 8 kg ..
+                        const int off = (y >> 3) * (int)kSBO + (y & 7) * 16;
+                        *reinterpret_cast<uint4 *>(bhi + off + kg * (int)kLBO) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+                        *reinterpret_cast<uint4 *>(bhi + off + (8 + kg) * (int)kLBO) =
+                            make_uint4(ih[0], ih[1], ih[2], ih[3]);
+                        *reinterpret_cast<uint4 *>(blo + off + kg * (int)kLBO) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+                        *reinterpret_cast<uint4 *>(blo + off + (8 + kg) * (int)kLBO) =
+                            make_uint4(il[0], il[1], il[2], il[3]);
                     }
-                    // B[n = y][k]: Re at k = 8 kg .., Im at k = 64 + 8 kg ..
-                    const int off = (y >> 3) * (int)kSBO + (y & 7) * 16;
-                    *reinterpret_cast<uint4 *>(bhi + off + kg * (int)kLBO) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-                    *reinterpret_cast<uint4 *>(bhi + off + (8 + kg) * (int)kLBO) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
-                    *reinterpret_cast<uint4 *>(blo + off + kg * (int)kLBO) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
-                    *reinterpret_cast<uint4 *>(blo + off + (8 + kg) * (int)kLBO) = make_uint4(il[0], il[1], il[2], il[3]);
                 }
                 gc_fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) {
                     gc_mbar_arrive(&full_b[bs]);
-                    if (j == kRawSamp - 1 || s == it.nt - 1) gc_mbar_arrive(&empty_raw[rs]);
+                    gc_mbar_arrive(&empty_raw[rs]);
                 }
-                if (j == kRawSamp - 1 || s == it.nt - 1) {
-                    if (++rs == kRawStages) {
-                        rs = 0;
-                        rph ^= 1u;
-                    }
+                if (++rs == kRawStages) {
+                    rs = 0;
+                    rph ^= 1u;
                 }
                 if (++bs == kBStages) {
                     bs = 0;
@@ -431,11 +434,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
             if (lane == 0) atomicOr(p.status, GC_DEV_TIMEOUT_FFT);
         }
     } else {
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 96;");
-        // ---------------------------------------------------------------- column stage (warps 0-15)
-        const int lq = warp & 3, s2w = warp >> 2;
+        // ---------------------------------------------------------------- column stage (warps 0-7)
+        const int lq = warp & 3, pr = warp >> 2;
         const int kx = 32 * lq + lane;
         const uint32_t lb = tmem + ((uint32_t)(32 * lq) << 16);
+        const uint32_t pa = lb + kColP + 32 * pr, pb = lb + kColP + 32 * (pr + 2);
         uint32_t db = 0, dph = 0;
         for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
             const ItemTC it = decode_tc(p, item);
@@ -448,13 +451,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
                 gc_tc_fence_after();
                 const uint32_t dre = lb + kColD + 128 * db, dim = dre + 64;
                 const bool first = s == 0;
-                const uint32_t pc = lb + kColP + 32 * s2w;
-                switch (s2w) {
-                    case 0: column_residue<0>(dre, dim, pc, first); break;
-                    case 1: column_residue<1>(dre, dim, pc, first); break;
-                    case 2: column_residue<2>(dre, dim, pc, first); break;
-                    default: column_residue<3>(dre, dim, pc, first); break;
-                }
+                if (pr == 0) column_pair<0>(dre, dim, pa, pb, first);
+                else column_pair<1>(dre, dim, pa, pb, first);
                 gc_tc_fence_before();
                 __syncwarp();
                 if (lane == 0) gc_mbar_arrive(&empty_d[db]);
@@ -468,16 +466,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
             gc_tmem_wait_st();
             float *out = p.ppart + ((size_t)it.c * p.n_chunks + it.chunk) * kTM * kTM;
 #pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                uint32_t pv[16];
-                gc_tmem_ld4_nowait(lb + kColP + 32 * s2w + 16 * h, pv);
-                gc_tmem_ld4_nowait(lb + kColP + 32 * s2w + 16 * h + 4, pv + 4);
-                gc_tmem_ld4_nowait(lb + kColP + 32 * s2w + 16 * h + 8, pv + 8);
-                gc_tmem_ld4_nowait(lb + kColP + 32 * s2w + 16 * h + 12, pv + 12);
-                gc_tmem_wait_ld16_regs(pv);
+            for (int r = 0; r < 2; ++r) {
+                const int s2 = pr + 2 * r;
+                uint32_t pv[32];
+                gc_tmem_ld32_nowait(lb + kColP + 32 * s2, pv);
+                gc_tmem_wait_ld_regs(pv);
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    out[(s2w + 4 * bitrev<32>(16 * h + i)) * kTM + kx] = __uint_as_float(pv[i]);
+                for (int i = 0; i < 32; ++i) out[(s2 + 4 * bitrev<32>(i)) * kTM + kx] = __uint_as_float(pv[i]);
             }
         }
         if (!ok) {
