@@ -61,6 +61,7 @@ constexpr int kEpiWarps = 8;
 constexpr int kWarpConv0 = 8, kConvWarps = 2, kWarpTma = 10, kWarpMma = 11;
 constexpr int kConvThreads = 32 * kConvWarps;
 constexpr int kTasks = kTL * 8 / kConvThreads;   // (row, group of 8 inputs) tasks per converter thread
+static_assert(kConvWarps == 2 && kTasks == 8, "the converter task map covers 64 rows x 8 input groups with 64 threads");
 constexpr int kSamp = 2;                          // samples per raw stage and per B stage
 constexpr int kBStages = 2;
 constexpr int kBPlane = kSamp * kTL * kTM * 2;    // one binary16 B operand of kSamp samples: 32 KB
@@ -70,7 +71,8 @@ constexpr int kRawSamp = kSamp;
 constexpr int kRawStages = 3;
 constexpr int kRawStride = kRawSamp * kTL * kTL + 128;   // + slack for the last row's 8-byte reads
 constexpr int kCoefBytes = kTasks * 8 * kConvThreads * 8;   // [task i][input e][converter thread] float2
-constexpr size_t kSmemTC = (size_t)kBStages * kBStage + (size_t)kRawStages * kRawStride + kCoefBytes;
+constexpr int kTwBytes = 2 * 2 * 32 * 8;                   // [pr][residue][y] float2
+constexpr size_t kSmemTC = (size_t)kBStages * kBStage + (size_t)kRawStages * kRawStride + kCoefBytes + kTwBytes;
 constexpr uint32_t kColD = 0, kColAHi = 256, kColALo = 320, kColP = 384;
 constexpr uint32_t kLBO = 128, kSBO = 2048;   // K-adjacent / N-adjacent core-matrix strides
 
@@ -126,15 +128,16 @@ __device__ __forceinline__ void power_update(const float2 (&b)[32], uint32_t pco
     }
 }
 
-// The column stage of one sample for the residue pair PR: (0, 2) or (1, 3).
+// The column stage of one sample for the residue pair pr: (0, 2) or (1, 3).
 // The 64 values X1[k_x][y] of this lane come in with one load of the Re and
 // one of the Im columns; each y and y + 32 give both residues' fold inputs
-//   s2 = PR:     (a0 + (-i)^PR a1) omega_128^(PR y)
-//   s2 = PR + 2: (a0 - (-i)^PR a1) omega_128^((PR + 2) y)
-// then a 32-point FFT and |X|^2 per residue.
-template <int PR>
+//   s2 = pr:     (a0 + (-i)^pr a1) omega_128^(pr y)
+//   s2 = pr + 2: (a0 - (-i)^pr a1) omega_128^((pr + 2) y)
+// (twiddles from the table tw[r][y] = omega_128^((pr + 2 r) y)), then a
+// 32-point FFT and |X|^2 per residue -- one copy of the FFT code, run twice
+// (the instruction cache holds the whole column stage).
 __device__ __forceinline__ void column_pair(uint32_t dre, uint32_t dim, uint32_t pcol_a, uint32_t pcol_b,
-                                            bool first) {
+                                            bool first, int pr, const float2 *tw) {
     float2 ba[32], bb[32];
     {
         uint32_t re[64], im[64];
@@ -149,20 +152,20 @@ __device__ __forceinline__ void column_pair(uint32_t dre, uint32_t dim, uint32_t
         for (int y = 0; y < 32; ++y) {
             const float2 a0 = make_float2(__uint_as_float(re[y]), __uint_as_float(im[y]));
             const float2 a1 = make_float2(__uint_as_float(re[y + 32]), __uint_as_float(im[y + 32]));
-            if constexpr (PR == 0) {
-                ba[y] = add2(a0, a1);
-                bb[y] = tw_apply(sub2(a0, a1), (4 * y) & 255);   // omega_128^(2 y)
-            } else {
-                const float2 r = rot_mi_tc<1>(a1);                // -i a1
-                ba[y] = tw_apply(add2(a0, r), (2 * y) & 255);     // omega_128^y
-                bb[y] = tw_apply(sub2(a0, r), (6 * y) & 255);     // omega_128^(3 y)
-            }
+            const float2 r = pr ? make_float2(a1.y, -a1.x) : a1;   // (-i)^pr a1
+            ba[y] = cmul(add2(a0, r), tw[y]);
+            bb[y] = cmul(sub2(a0, r), tw[32 + y]);
         }
     }
-    fft_reg<32>(ba);
-    power_update(ba, pcol_a, first);
-    fft_reg<32>(bb);
-    power_update(bb, pcol_b, first);
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        fft_reg<32>(ba);
+        power_update(ba, h ? pcol_b : pcol_a, first);
+        if (h == 0) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) ba[i] = bb[i];
+        }
+    }
 }
 
 struct ItemTC {
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
     unsigned char *bring = smem;
     unsigned char *raw = smem + (size_t)kBStages * kBStage;
     float2 *coef = reinterpret_cast<float2 *>(raw + (size_t)kRawStages * kRawStride);
+    float2 *tws = coef + kCoefBytes / 8;   // column-fold twiddles omega_128^((pr + 2 r) y)
     __shared__ uint64_t full_raw[kRawStages], empty_raw[kRawStages], full_b[kBStages], empty_b[kBStages];
     __shared__ uint64_t full_d[2], empty_d[2], mma_done;
     __shared__ uint32_t tmem_slot;
@@ -208,6 +212,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
         }
         gc_mbar_init(&mma_done, 1);
         gc_fence_mbar_init();
+    }
+    for (int i = tid; i < 2 * 2 * 32; i += kThreadsTC) {
+        const int pr = i >> 6, r = (i >> 5) & 1, y = i & 31;
+        const cf w = c_tw.v[(2 * (pr + 2 * r) * y) & 255];
+        tws[i] = make_float2(w.x, w.y);
     }
     if (warp == 0) gc_tmem_alloc(&tmem_slot, 512);
     gc_tc_fence_before();
@@ -303,7 +312,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
                         gc_tc_fence_after();
                         const uint32_t dre = tmem + kColD + 128 * db, dim = dre + 64;
                         const uint32_t b0 = bbase + (uint32_t)(bs * kBStage + j * kBSample);
-#pragma unroll
+#pragma unroll 1
                         for (int term = 0; term < 3; ++term) {
                             const uint32_t a = tmem + (term == 2 ? kColALo : kColAHi);
                             const uint32_t b = b0 + (term == 1 ? (uint32_t)kBPlane : 0u);
@@ -345,9 +354,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
         __syncwarp();
     } else if (warp >= kWarpConv0) {
         // ---------------------------------------------------------------- converters
-        // task (row y, group of 8 inputs kg): y = (ct >> 3) + (kConvThreads / 8) i, kg = ct & 7
+        // task i of this thread: row y = 8 i + ((kg + g) & 7), inputs 8 kg ..
+        // 8 kg + 7, with kg = lane & 7 and g = lane / 8 + 4 (converter warp):
+        // the 8 lanes of a group write 8 different rows of a core-matrix
+        // column, so the 16-byte operand stores are free of bank conflicts
         const int ct = tid - 32 * kWarpConv0;
         const int kg = ct & 7;
+        const int ylo = (kg + ((ct & 31) >> 3) + 4 * (ct >> 5)) & 7;
         uint32_t rs = 0, rph = 0, bs = 0, bph = 0;
         for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
             const ItemTC it = decode_tc(p, item);
@@ -355,7 +368,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
             // antennas, in shared memory that only this thread reads
 #pragma unroll 1
             for (int i = 0; i < kTasks; ++i) {
-                const int y = (ct >> 3) + (kConvThreads / 8) * i;
+                const int y = 8 * i + ylo;
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int x = 8 * kg + e;
@@ -382,7 +395,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
                     unsigned char *bhi = bring + (size_t)bs * kBStage + (size_t)j * kBSample, *blo = bhi + kBPlane;
 #pragma unroll 2
                     for (int i = 0; i < kTasks; ++i) {
-                        const int y = (ct >> 3) + (kConvThreads / 8) * i;
+                        const int y = 8 * i + ylo;
                         if (y >= L) continue;
                         const uint2 word = *reinterpret_cast<const uint2 *>(rb + y * L + 8 * kg);
                         // n + 8 of the Re and Im nibbles, one byte each
@@ -451,8 +464,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) fftcorr_tc_accumulate(const TcF
                 gc_tc_fence_after();
                 const uint32_t dre = lb + kColD + 128 * db, dim = dre + 64;
                 const bool first = s == 0;
-                if (pr == 0) column_pair<0>(dre, dim, pa, pb, first);
-                else column_pair<1>(dre, dim, pa, pb, first);
+                column_pair(dre, dim, pa, pb, first, pr, tws + 64 * pr);
                 gc_tc_fence_before();
                 __syncwarp();
                 if (lane == 0) gc_mbar_arrive(&empty_d[db]);
