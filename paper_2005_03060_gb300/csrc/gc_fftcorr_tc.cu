@@ -129,42 +129,39 @@ __device__ __forceinline__ void power_update(const float2 (&b)[32], uint32_t pco
 }
 
 // The column stage of one sample for the residue pair pr: (0, 2) or (1, 3).
-// The 64 values X1[k_x][y] of this lane come in with one load of the Re and
-// one of the Im columns; each y and y + 32 give both residues' fold inputs
-//   s2 = pr:     (a0 + (-i)^pr a1) omega_128^(pr y)
-//   s2 = pr + 2: (a0 - (-i)^pr a1) omega_128^((pr + 2) y)
-// (twiddles from the table tw[r][y] = omega_128^((pr + 2 r) y)), then a
-// 32-point FFT and |X|^2 per residue -- one copy of the FFT code, run twice
-// (the instruction cache holds the whole column stage).
+// For each of the two residues the 64 values X1[k_x][y] of this lane come in
+// with one load of the Re and one of the Im columns (tensor memory is read
+// twice rather than holding both folds in registers); y and y + 32 give the
+// fold input
+//   s2 = pr + 2 h:  (a0 + (-1)^h (-i)^pr a1) omega_128^((pr + 2 h) y)
+// (twiddles from the table tw[h][y]), then a 32-point FFT and |X|^2 -- one
+// copy of the code for both residues and both pairs, so that the
+// instruction cache holds the whole column stage.
 __device__ __forceinline__ void column_pair(uint32_t dre, uint32_t dim, uint32_t pcol_a, uint32_t pcol_b,
                                             bool first, int pr, const float2 *tw) {
-    float2 ba[32], bb[32];
-    {
-        uint32_t re[64], im[64];
-        gc_tmem_ld64_nowait(dre, re);
-        gc_tmem_ld64_nowait(dim, im);
-        gc_tmem_wait_ld();
-        gc_reg_tie32(re);
-        gc_reg_tie32(re + 32);
-        gc_reg_tie32(im);
-        gc_reg_tie32(im + 32);
-#pragma unroll
-        for (int y = 0; y < 32; ++y) {
-            const float2 a0 = make_float2(__uint_as_float(re[y]), __uint_as_float(im[y]));
-            const float2 a1 = make_float2(__uint_as_float(re[y + 32]), __uint_as_float(im[y + 32]));
-            const float2 r = pr ? make_float2(a1.y, -a1.x) : a1;   // (-i)^pr a1
-            ba[y] = cmul(add2(a0, r), tw[y]);
-            bb[y] = cmul(sub2(a0, r), tw[32 + y]);
-        }
-    }
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
-        fft_reg<32>(ba);
-        power_update(ba, h ? pcol_b : pcol_a, first);
-        if (h == 0) {
+        const float sg = h ? -1.f : 1.f;
+        float2 b[32];
+        {
+            uint32_t re[64], im[64];
+            gc_tmem_ld64_nowait(dre, re);
+            gc_tmem_ld64_nowait(dim, im);
+            gc_tmem_wait_ld();
+            gc_reg_tie32(re);
+            gc_reg_tie32(re + 32);
+            gc_reg_tie32(im);
+            gc_reg_tie32(im + 32);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) ba[i] = bb[i];
+            for (int y = 0; y < 32; ++y) {
+                const float2 a0 = make_float2(__uint_as_float(re[y]), __uint_as_float(im[y]));
+                const float2 a1 = make_float2(__uint_as_float(re[y + 32]), __uint_as_float(im[y + 32]));
+                const float2 r = pr ? make_float2(a1.y, -a1.x) : a1;   // (-i)^pr a1
+                b[y] = cmul(make_float2(fmaf(sg, r.x, a0.x), fmaf(sg, r.y, a0.y)), tw[32 * h + y]);
+            }
         }
+        fft_reg<32>(b);
+        power_update(b, h ? pcol_b : pcol_a, first);
     }
 }
 
