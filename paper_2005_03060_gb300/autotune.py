@@ -36,15 +36,19 @@ def _sweep(ctx, knob: str, values, fn, reps: int) -> dict:
 
 
 def tune_correlator(ctx, volt, gains, L=None, reps: int = 3) -> dict:
-    """FFT-correlator: the launch shape ("fft.shape": sample grouping of the
-    CTA), then the time-chunk length of a work item ("fft.chunk_len")."""
+    """FFT-correlator: the path ("fft.path": row stage on the tensor cores
+    or all on the CUDA cores, where both exist), the launch shape of the
+    CUDA-core kernel ("fft.shape": sample grouping of the CTA; the
+    tensor-core kernel ignores it), then the time-chunk length of a work item
+    ("fft.chunk_len")."""
     L = L or int(round(volt.shape[2] ** 0.5))
     out = torch.empty(volt.shape[0], 2 * L - 1, 2 * L - 1, dtype=torch.complex64, device=volt.device)
     fn = lambda: ctx.correlate(volt, gains, L, out=out)   # noqa: E731
+    path = _sweep(ctx, "fft.path", [0, 1], fn, reps)
     shape = _sweep(ctx, "fft.shape", [0, 1], fn, reps)
-    chunk = _sweep(ctx, "fft.chunk_len", [0, 128, 256, 512, 1024], fn, reps)
-    return {"knob": "fft.shape, fft.chunk_len", "best": [shape["best"], chunk["best"]],
-            "ms": {"fft.shape": shape["ms"], "fft.chunk_len": chunk["ms"]}}
+    chunk = _sweep(ctx, "fft.chunk_len", [0, 256, 512, 1024, 2048], fn, reps)
+    return {"knob": "fft.path, fft.shape, fft.chunk_len", "best": [path["best"], shape["best"], chunk["best"]],
+            "ms": {"fft.path": path["ms"], "fft.shape": shape["ms"], "fft.chunk_len": chunk["ms"]}}
 
 
 def tune_xengine(ctx, volt, sel, reps: int = 3) -> dict:

@@ -103,11 +103,12 @@ def test_autotuner_sets_knobs(gc, ctx):
     L, C, T = 16, 4, 512
     volt, gains, _ = synth.make_voltages(4, L, C, T, n_src=10, device="cuda")
     r = autotune.tune_correlator(ctx, volt, gains, reps=1)
-    assert [ctx.get_tuning("fft.shape"), ctx.get_tuning("fft.chunk_len")] == r["best"]
+    assert [ctx.get_tuning("fft.path"), ctx.get_tuning("fft.shape"), ctx.get_tuning("fft.chunk_len")] == r["best"]
     sel = gc.Selection("subset", L, T)
     r = autotune.tune_xengine(ctx, volt, sel, reps=1)
     assert [ctx.get_tuning("xeng.tc_shape"), ctx.get_tuning("xeng.tsplit")] == r["best"]
-    for k in ("fft.chunk_len", "fft.shape", "xeng.tsplit", "xeng.tc_shape", "cal.order", "cal.ctas_per_sm"):
+    for k in ("fft.chunk_len", "fft.shape", "fft.path", "xeng.tsplit", "xeng.tc_shape", "cal.order",
+              "cal.ctas_per_sm"):
         ctx.set_tuning(k, 0)
     with pytest.raises(gc.GridcorrError):
         ctx.set_tuning("no.such.knob", 1)
