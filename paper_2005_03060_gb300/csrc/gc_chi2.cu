@@ -16,10 +16,11 @@
 // Selections of at most 16 types on a full grid take the stencil form: the
 // thread owning antenna m finds its pairs by grid arithmetic (pair index
 // from the type's row-major enumeration), so no pair lists are read; the
-// forward pass visits each pair once (m as first member), the adjoint visits
-// each pair from both members (the second visit finds the observation in L2)
-// and keeps each thread's model-visibility terms per type in shared memory
-// until one fixed-order reduction at the end of the CTA.
+// forward pass and the adjoint visit each pair once (m as first member); the
+// adjoint passes the second member's term through a shared slot, keeps each
+// thread's model-visibility terms per type in shared memory until one
+// fixed-order reduction at the end of the CTA, and hands the terms of
+// antennas below its range to a small second kernel.
 #include <algorithm>
 
 #include "gc_sel.h"
@@ -223,6 +224,8 @@ constexpr int kDvPitch = kKThreads + 8;   // conflict-free column reads of the d
 struct StSplit {
     int parts;         // antenna ranges per channel
     double *partial;   // fwd: [C][parts]; bwd: [C][parts][n_ubl][2]
+    int halo;          // bwd: largest pair offset dy L + dx over the types
+    float2 *hbuf;      // bwd: [C][parts][halo] second-member terms of the antennas below each range
 };
 
 // FL: bit 0 weights, bit 1 residuals stored (fwd) / read (bwd)
@@ -278,21 +281,31 @@ __global__ void __launch_bounds__(kKThreads) chi2_fwd_st(const Chi2Params p, con
     }
 }
 
+// The adjoint visits each pair once, from its first member m: the pair's
+// residual feeds dg_m (registers), dV_k (registers, then shared memory) and
+// the second member's term w conj(r) g_m V, which goes to a shared slot of
+// antenna m - d.  For one type the map m -> m - d is one-to-one, so a slot
+// takes at most one term per type and a barrier between types orders them;
+// slots below the range (antennas of the previous range, at most `halo`
+// of them) go to the workspace and chi2_st_halo adds them afterwards.
 template <int VF, int FL>
 __global__ void __launch_bounds__(kKThreads) chi2_bwd_st(const Chi2Params p, const StSplit sp) {
     __shared__ StTypes t;
     __shared__ float2 sV[kStTypes];
     __shared__ float sdv[2 * kStTypes * kDvPitch];   // per-thread dV terms of every type
+    extern __shared__ float2 sacc[];                  // [halo + range] second-member terms
     load_types(p, t);
-    const int L = p.L, nu = p.n_ubl;
+    const int L = p.L, nu = p.n_ubl, H = sp.halo;
+    constexpr int R = kStJ * kKThreads;
     const int c = blockIdx.x / sp.parts, part = blockIdx.x % sp.parts;
-    const int m0 = part * kStJ * kKThreads;
+    const int m0 = part * R;
     if (threadIdx.x < nu) sV[threadIdx.x] = p.V[(size_t)c * nu + threadIdx.x];
+    for (int i = threadIdx.x; i < H + R; i += kKThreads) sacc[i] = make_float2(0.f, 0.f);
     __syncthreads();
     const double go = p.gout ? p.gout[c] : 1.0;
     const float2 *g = p.g + (size_t)c * p.N;
     const size_t cP = (size_t)c * p.P;
-    float2 gm[kStJ], acc[kStJ];   // each antenna's gain and gradient (at most 2 x 16 terms)
+    float2 gm[kStJ], acc[kStJ];   // each antenna's gain and its first-member terms (at most 16)
     int xy[kStJ];
 #pragma unroll
     for (int j = 0; j < kStJ; ++j) {
@@ -303,7 +316,7 @@ __global__ void __launch_bounds__(kKThreads) chi2_bwd_st(const Chi2Params p, con
         acc[j] = make_float2(0.f, 0.f);
     }
     for (int k = 0; k < nu; ++k) {
-        const int dx = t.dx[k], dy = t.dy[k], off = t.off[k], rl = t.rowlen[k], a1 = t.a1[k], a2 = t.a2[k];
+        const int dx = t.dx[k], dy = t.dy[k], off = t.off[k], rl = t.rowlen[k], a1 = t.a1[k];
         const float inv = t.inv[k];
         const float2 V = sV[k];
         float vx = 0.f, vy = 0.f;   // this thread's part of dV_k (kStJ terms)
@@ -311,59 +324,72 @@ __global__ void __launch_bounds__(kKThreads) chi2_bwd_st(const Chi2Params p, con
         for (int j = 0; j < kStJ; ++j) {
             const int m = m0 + threadIdx.x + j * kKThreads;
             const int x = xy[j] & 0xffff, y = xy[j] >> 16;
-            const bool in = xy[j] >= 0;
-            // m = i_p of the pair (m, m - d): w r g_j conj(V) to dg_m, w r conj(g_m) g_j to dV_k
-            const bool v1 = in && (unsigned)(x - dx) < (unsigned)L && (unsigned)(y - dy) < (unsigned)L;
-            // m = j_p of the pair (m + d, m): w conj(r) g_i V to dg_m
-            const bool v2 = in && (unsigned)(x + dx) < (unsigned)L && (unsigned)(y + dy) < (unsigned)L;
-            const int yr = y * rl + x;
-            const int q1 = v1 ? a1 + yr : 0, q2 = v2 ? a2 + yr : 0;
+            const bool v1 = xy[j] >= 0 && (unsigned)(x - dx) < (unsigned)L && (unsigned)(y - dy) < (unsigned)L;
+            const int q1 = v1 ? a1 + y * rl + x : 0;
             const float2 gj = g[v1 ? m - off : 0];
-            const float2 gp = g[v2 ? m + off : 0];
-            float2 r1, r2;
-            if (FL & 2) {
-                r1 = p.resid_in[cP + q1];
-                r2 = p.resid_in[cP + q2];
-            } else {
-                r1 = st_resid<VF>(p.vred, cP + q1, inv, gm[j], gj, V);
-                r2 = st_resid<VF>(p.vred, cP + q2, inv, gp, gm[j], V);
-            }
-            float w1 = 1.f, w2 = 1.f;
-            if (FL & 1) {
-                w1 = p.w[cP + q1];
-                w2 = p.w[cP + q2];
-            }
+            float2 r1;
+            if (FL & 2) r1 = p.resid_in[cP + q1];
+            else r1 = st_resid<VF>(p.vred, cP + q1, inv, gm[j], gj, V);
+            float w1 = 1.f;
+            if (FL & 1) w1 = p.w[cP + q1];
             const float rx = v1 ? w1 * r1.x : 0.f, ry = v1 ? w1 * r1.y : 0.f;
-            const float tx = gj.x * V.x + gj.y * V.y, ty = gj.y * V.x - gj.x * V.y;   // g_j conj(V)
+            // first member m: w r g_j conj(V) to dg_m
+            const float tx = gj.x * V.x + gj.y * V.y, ty = gj.y * V.x - gj.x * V.y;
             acc[j].x = fmaf(rx, tx, fmaf(-ry, ty, acc[j].x));
             acc[j].y = fmaf(rx, ty, fmaf(ry, tx, acc[j].y));
-            const float ux = gm[j].x * gj.x + gm[j].y * gj.y, uy = gm[j].x * gj.y - gm[j].y * gj.x;   // conj(g_m) g_j
+            // w r conj(g_m) g_j to dV_k
+            const float ux = gm[j].x * gj.x + gm[j].y * gj.y, uy = gm[j].x * gj.y - gm[j].y * gj.x;
             vx = fmaf(rx, ux, fmaf(-ry, uy, vx));
             vy = fmaf(rx, uy, fmaf(ry, ux, vy));
-            const float sx = v2 ? w2 * r2.x : 0.f, sy = v2 ? w2 * r2.y : 0.f;
-            const float px = gp.x * V.x - gp.y * V.y, py = gp.x * V.y + gp.y * V.x;   // g_i V
-            acc[j].x = fmaf(sx, px, fmaf(sy, py, acc[j].x));
-            acc[j].y = fmaf(sx, py, fmaf(-sy, px, acc[j].y));
+            // second member m - d: w conj(r) g_m V
+            if (v1) {
+                const float px = gm[j].x * V.x - gm[j].y * V.y, py = gm[j].x * V.y + gm[j].y * V.x;
+                float2 &slot = sacc[m - off - m0 + H];
+                slot.x += fmaf(rx, px, ry * py);
+                slot.y += fmaf(rx, py, -ry * px);
+            }
         }
         sdv[(2 * k) * kDvPitch + threadIdx.x] = vx;
         sdv[(2 * k + 1) * kDvPitch + threadIdx.x] = vy;
+        __syncthreads();   // a slot takes one term per type
     }
 #pragma unroll
     for (int j = 0; j < kStJ; ++j) {
         const int m = m0 + threadIdx.x + j * kKThreads;
-        if (xy[j] >= 0) p.dg[(size_t)c * p.N + m] = make_float2((float)(-2.0 * go * acc[j].x), (float)(-2.0 * go * acc[j].y));
+        if (xy[j] >= 0) {
+            const float2 s2 = sacc[m - m0 + H];
+            p.dg[(size_t)c * p.N + m] = make_float2((float)(-2.0 * go * (acc[j].x + s2.x)),
+                                                    (float)(-2.0 * go * (acc[j].y + s2.y)));
+        }
     }
-    __syncthreads();
+    for (int i = threadIdx.x; i < H; i += kKThreads) sp.hbuf[(size_t)blockIdx.x * H + i] = sacc[i];
     // dV partials of the CTA: 8 threads per (type, component), each adding
     // 32 threads' terms in FP64, then the 8 in a fixed shuffle order
     const int combo = threadIdx.x >> 3, sub = threadIdx.x & 7;
-    double sacc = 0.0;
+    double dsum = 0.0;
     if (combo < 2 * nu)
-        for (int u = 0; u < kKThreads / 8; ++u) sacc += (double)sdv[combo * kDvPitch + u * 8 + sub];
-    sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
-    sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
-    sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
-    if (sub == 0 && combo < 2 * nu) sp.partial[((size_t)blockIdx.x * nu + (combo >> 1)) * 2 + (combo & 1)] = sacc;
+        for (int u = 0; u < kKThreads / 8; ++u) dsum += (double)sdv[combo * kDvPitch + u * 8 + sub];
+    dsum += __shfl_xor_sync(0xffffffffu, dsum, 1);
+    dsum += __shfl_xor_sync(0xffffffffu, dsum, 2);
+    dsum += __shfl_xor_sync(0xffffffffu, dsum, 4);
+    if (sub == 0 && combo < 2 * nu) sp.partial[((size_t)blockIdx.x * nu + (combo >> 1)) * 2 + (combo & 1)] = dsum;
+}
+
+// Second-member terms that range `part` computed for the last `halo`
+// antennas of range part - 1, added to their gradients (one thread each).
+__global__ void chi2_st_halo(const Chi2Params p, const StSplit sp) {
+    const int H = sp.halo;
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long per = (long)(sp.parts - 1) * H;
+    if (per <= 0 || idx >= (long)p.C * per) return;
+    const int c = (int)(idx / per), rem = (int)(idx % per);
+    const int part = 1 + rem / H, i = rem % H;
+    const int m = part * kStJ * kKThreads - H + i;
+    if (m < 0 || m >= p.N) return;
+    const double go = p.gout ? p.gout[c] : 1.0;
+    const float2 h = sp.hbuf[((size_t)c * sp.parts + part) * H + i];
+    float2 &d = p.dg[(size_t)c * p.N + m];
+    d = make_float2(d.x + (float)(-2.0 * go * h.x), d.y + (float)(-2.0 * go * h.y));
 }
 
 // chi^2 (fwd) or dV (bwd) from the ranges' partial sums, in range order
@@ -390,22 +416,36 @@ __global__ void chi2_st_reduce(const Chi2Params p, const StSplit sp, int bwd) {
 
 bool use_stencil(const gc_sel *sel) { return !sel->masked && sel->n_ubl <= kStTypes; }
 
+// largest pair offset dy L + dx of the selection's types (all positive: the
+// types are taken in the half-plane dy > 0 or dy = 0, dx > 0)
+int st_halo(const gc_sel *sel) {
+    int h = 0;
+    for (int k = 0; k < sel->n_ubl; ++k) h = std::max(h, sel->types[2 * k + 1] * sel->L + sel->types[2 * k]);
+    return h;
+}
+
 // kStJ x kKThreads antennas per CTA
-gc_status st_launch(gc_ctx *ctx, const Chi2Params &p, bool bwd, cudaStream_t s) {
+gc_status st_launch(gc_ctx *ctx, const Chi2Params &p, bool bwd, int halo, cudaStream_t s) {
     StSplit sp;
     sp.parts = (p.N + kStJ * kKThreads - 1) / (kStJ * kKThreads);
+    sp.halo = bwd ? halo : 0;
     const size_t n = (size_t)p.C * sp.parts * (bwd ? 2 * p.n_ubl : 1);
-    gc_status st = gc_scratch_reserve(ctx, n * sizeof(double));
+    const size_t part_bytes = (n * sizeof(double) + 255) / 256 * 256;
+    const size_t hb_bytes = (size_t)p.C * sp.parts * sp.halo * sizeof(float2);
+    gc_status st = gc_scratch_reserve(ctx, part_bytes + hb_bytes);
     if (st != GC_OK) return st;
     sp.partial = static_cast<double *>(ctx->scratch);
+    sp.hbuf = reinterpret_cast<float2 *>(static_cast<char *>(ctx->scratch) + part_bytes);
     const unsigned grid = (unsigned)(p.C * sp.parts);
+    const int dsm = bwd ? (sp.halo + kStJ * kKThreads) * (int)sizeof(float2) : 0;
     const int fl = (p.w ? 1 : 0) | ((bwd ? p.resid_in != nullptr : p.resid_out != nullptr) ? 2 : 0);
     const bool c64 = p.vfmt == GC_C64;
 #define GC_ST_CASE(F)                                                                    \
     case F:                                                                              \
         if (bwd) {                                                                       \
-            if (c64) chi2_bwd_st<GC_C64, F><<<grid, kKThreads, 0, s>>>(p, sp);           \
-            else chi2_bwd_st<GC_I4C, F><<<grid, kKThreads, 0, s>>>(p, sp);               \
+            auto kb = c64 ? chi2_bwd_st<GC_C64, F> : chi2_bwd_st<GC_I4C, F>;             \
+            cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm);   \
+            kb<<<grid, kKThreads, dsm, s>>>(p, sp);                                      \
         } else {                                                                         \
             if (c64) chi2_fwd_st<GC_C64, F><<<grid, kKThreads, 0, s>>>(p, sp);           \
             else chi2_fwd_st<GC_I4C, F><<<grid, kKThreads, 0, s>>>(p, sp);               \
@@ -420,6 +460,10 @@ gc_status st_launch(gc_ctx *ctx, const Chi2Params &p, bool bwd, cudaStream_t s) 
 #undef GC_ST_CASE
     const int nr = bwd ? p.C * p.n_ubl : p.C;
     chi2_st_reduce<<<(nr + 255) / 256, 256, 0, s>>>(p, sp, bwd ? 1 : 0);
+    if (bwd && sp.parts > 1 && sp.halo > 0) {
+        const long nh = (long)p.C * (sp.parts - 1) * sp.halo;
+        chi2_st_halo<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(p, sp);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return gc_cuda_fail(ctx, e, bwd ? "launch chi2_bwd" : "launch chi2_fwd");
     return GC_OK;
@@ -480,7 +524,7 @@ extern "C" gc_status gc_chi2(gc_ctx *ctx, const void *vreduced, int vfmt, const 
     const int grid = std::min(C, ctx->sm_count * 8);
     int rec = gc_prof_begin(ctx, s, "chi2_fwd");
     if (use_stencil(sel)) {
-        st = st_launch(ctx, p, false, s);
+        st = st_launch(ctx, p, false, 0, s);
         if (st != GC_OK) return st;
     } else {
         chi2_fwd<<<grid, kKThreads, 0, s>>>(p);
@@ -505,8 +549,8 @@ extern "C" gc_status gc_chi2_backward(gc_ctx *ctx, const void *vreduced, int vfm
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int grid = std::min(C, ctx->sm_count * 8);
     int rec = gc_prof_begin(ctx, s, "chi2_bwd");
-    if (use_stencil(sel)) {
-        st = st_launch(ctx, p, true, s);
+    if (use_stencil(sel) && st_halo(sel) <= kStJ * kKThreads) {
+        st = st_launch(ctx, p, true, st_halo(sel), s);
         if (st != GC_OK) return st;
     } else {
         chi2_bwd<<<grid, kKThreads, 0, s>>>(p);
@@ -531,7 +575,7 @@ extern "C" gc_status gc_chi2_ckpt(gc_ctx *ctx, const void *vreduced, int vfmt, c
     const int grid = std::min(C, ctx->sm_count * 8);
     int rec = gc_prof_begin(ctx, s, "chi2_fwd");
     if (use_stencil(sel)) {
-        st = st_launch(ctx, p, false, s);
+        st = st_launch(ctx, p, false, 0, s);
         if (st != GC_OK) return st;
     } else {
         chi2_fwd<<<grid, kKThreads, 0, s>>>(p);
@@ -559,8 +603,8 @@ extern "C" gc_status gc_chi2_backward_ckpt(gc_ctx *ctx, const float *residuals, 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int grid = std::min(C, ctx->sm_count * 8);
     int rec = gc_prof_begin(ctx, s, "chi2_bwd");
-    if (use_stencil(sel)) {
-        st = st_launch(ctx, p, true, s);
+    if (use_stencil(sel) && st_halo(sel) <= kStJ * kKThreads) {
+        st = st_launch(ctx, p, true, st_halo(sel), s);
         if (st != GC_OK) return st;
     } else {
         chi2_bwd<<<grid, kKThreads, 0, s>>>(p);
