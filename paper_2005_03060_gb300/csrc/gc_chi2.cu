@@ -353,13 +353,13 @@ __global__ void __launch_bounds__(kKThreads) chi2_bwd_st(const Chi2Params p, con
         sdv[(2 * k + 1) * kDvPitch + threadIdx.x] = vy;
         __syncthreads();   // a slot takes one term per type
     }
+    const float sc = (float)(-2.0 * go);
 #pragma unroll
     for (int j = 0; j < kStJ; ++j) {
         const int m = m0 + threadIdx.x + j * kKThreads;
         if (xy[j] >= 0) {
             const float2 s2 = sacc[m - m0 + H];
-            p.dg[(size_t)c * p.N + m] = make_float2((float)(-2.0 * go * (acc[j].x + s2.x)),
-                                                    (float)(-2.0 * go * (acc[j].y + s2.y)));
+            p.dg[(size_t)c * p.N + m] = make_float2(sc * (acc[j].x + s2.x), sc * (acc[j].y + s2.y));
         }
     }
     for (int i = threadIdx.x; i < H; i += kKThreads) sp.hbuf[(size_t)blockIdx.x * H + i] = sacc[i];
@@ -386,10 +386,10 @@ __global__ void chi2_st_halo(const Chi2Params p, const StSplit sp) {
     const int part = 1 + rem / H, i = rem % H;
     const int m = part * kStJ * kKThreads - H + i;
     if (m < 0 || m >= p.N) return;
-    const double go = p.gout ? p.gout[c] : 1.0;
+    const float sc = (float)(-2.0 * (p.gout ? p.gout[c] : 1.0));
     const float2 h = sp.hbuf[((size_t)c * sp.parts + part) * H + i];
     float2 &d = p.dg[(size_t)c * p.N + m];
-    d = make_float2(d.x + (float)(-2.0 * go * h.x), d.y + (float)(-2.0 * go * h.y));
+    d = make_float2(d.x + sc * h.x, d.y + sc * h.y);
 }
 
 // chi^2 (fwd) or dV (bwd) from the ranges' partial sums, in range order
