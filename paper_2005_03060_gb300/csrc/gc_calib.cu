@@ -66,6 +66,7 @@ struct CalParams {
     int bw;                      // band half-width (reals)
     char *work;
     size_t work_per_cta;
+    unsigned int *counter;   // next channel to take (matrix-free kernels; zeroed before the launch)
     unsigned int *status;
     unsigned long long deadline_ns;   // per-channel time budget
     int red32;                   // matrix-free solver: every reduction in FP32 (the plain-FP32 form)
@@ -695,9 +696,10 @@ __device__ void gn_project(const CalParams &p, GnWork<R> &w, R *red) {
 // Degeneracy convention of the output: mean ln|g| = 0, arg V_(1,0) =
 // arg V_(0,1) = 0, arg g_0 = 0.  Works on float2 gains in place.
 __device__ void output_convention(const CalParams &p, float2 *g, float2 *V, double *red) {
+    // per antenna in FP32 (the gains are FP32 values), summed in FP64
     double s[1] = {0.0};
     for (int i = threadIdx.x; i < p.N; i += blockDim.x)
-        if (!p.mask || p.mask[i]) s[0] += log(hypot((double)g[i].x, (double)g[i].y));
+        if (!p.mask || p.mask[i]) s[0] += (double)logf(hypotf(g[i].x, g[i].y));
     block_sum<double, 1>(s, red);
     const double sc = exp(s[0] / p.n_occ);
     const double kx = atan2((double)V[p.ax].y, (double)V[p.ax].x);
@@ -715,12 +717,15 @@ __device__ void output_convention(const CalParams &p, float2 *g, float2 *V, doub
     const int r0 = p.tree_ant ? p.tree_ant[0] : 0;
     const double psi = atan2((double)g[r0].y, (double)g[r0].x) + kx * (r0 % p.L) + ky * (r0 / p.L);
     __syncthreads();
+    // the ramp phase in FP64, reduced to [-pi, pi] there, then rotated in FP32
+    constexpr double kTwoPi = 6.283185307179586, kInvTwoPi = 0.15915494309189535;
+    const float isc = (float)(1.0 / sc);
     for (int i = threadIdx.x; i < p.N; i += blockDim.x) {
         const double ph = kx * (i % p.L) + ky * (i / p.L) - psi;
-        double sn, cs;
-        sincos(ph, &sn, &cs);
-        const double gx = g[i].x / sc, gy = g[i].y / sc;
-        g[i] = make_float2((float)(gx * cs - gy * sn), (float)(gx * sn + gy * cs));
+        float sn, cs;
+        sincosf((float)(ph - kTwoPi * rint(ph * kInvTwoPi)), &sn, &cs);
+        const float gx = g[i].x * isc, gy = g[i].y * isc;
+        g[i] = make_float2(gx * cs - gy * sn, gx * sn + gy * cs);
     }
     __syncthreads();
 }
@@ -734,21 +739,32 @@ __device__ void finish_channel(const CalParams &p, int c, const R *xg, const R *
     for (int k = threadIdx.x; k < p.n_ubl; k += blockDim.x) V[k] = make_float2((float)xv[2 * k], (float)xv[2 * k + 1]);
     __syncthreads();
     output_convention(p, g, V, red);
-    // chi^2 and chi^2_r (Eq. redchi, Eq. dof) at the output point
+    // chi^2 and chi^2_r (Eq. redchi, Eq. dof) at the output point: the
+    // model products in the solver's precision (FP32 for the FP32 solvers,
+    // FP64 for the FP64 one), the sums in FP64; the noise weight
+    // 1 / sigma_p^2 = t_p (t_a / a_i) (t_a / a_j) in FP32 (no FP64 division)
     double acc[2] = {0.0, 0.0};
-    const double ta = (double)p.t_autos;
+    const float ta = (float)p.t_autos;
     for (int q = threadIdx.x; q < p.P; q += blockDim.x) {
         const int i = p.pair_i[q], j = p.pair_j[q], k = p.pair_type[q];
         const float2 v = vobs(p, c, q);
-        const double gx = g[i].x, gy = g[i].y, hx = g[j].x, hy = -g[j].y;
-        const double ex = gx * hx - gy * hy, ey = gx * hy + gy * hx;
-        const double mx = ex * V[k].x - ey * V[k].y, my = ex * V[k].y + ey * V[k].x;
-        const double rx = v.x - mx, ry = v.y - my;
-        const double r2 = rx * rx + ry * ry;
+        double r2;
+        if constexpr (sizeof(R) == sizeof(float)) {
+            const float2 gi = g[i], gj = g[j], Vk = V[k];
+            const float ex = gi.x * gj.x + gi.y * gj.y, ey = gi.y * gj.x - gi.x * gj.y;   // g_i conj(g_j)
+            const float mx = ex * Vk.x - ey * Vk.y, my = ex * Vk.y + ey * Vk.x;
+            const float rx = v.x - mx, ry = v.y - my;
+            r2 = (double)rx * rx + (double)ry * ry;
+        } else {
+            const double gx = g[i].x, gy = g[i].y, hx = g[j].x, hy = -g[j].y;
+            const double ex = gx * hx - gy * hy, ey = gx * hy + gy * hx;
+            const double mx = ex * V[k].x - ey * V[k].y, my = ex * V[k].y + ey * V[k].x;
+            const double rx = v.x - mx, ry = v.y - my;
+            r2 = rx * rx + ry * ry;
+        }
         acc[0] += r2;
-        const double tp = (double)(p.win_t1[k] - p.win_t0[k]);
-        const double s2 = (auto_of(p, c, i) / ta) * (auto_of(p, c, j) / ta) / tp;
-        acc[1] += r2 / s2;
+        const float wp = (float)(p.win_t1[k] - p.win_t0[k]) * (ta / auto_of(p, c, i)) * (ta / auto_of(p, c, j));
+        acc[1] += r2 * (double)wp;
     }
     block_sum<double, 2>(acc, red);
     if (threadIdx.x == 0) {
@@ -839,7 +855,7 @@ __global__ void __launch_bounds__(kCThreads) lincal_kernel(const CalParams p) {
 // ----------------------------------------------------------------- lincal, matrix-free (mixed precision)
 // Gauss-Newton with the step from preconditioned conjugate gradients on
 // (J^T J + mu I) delta = J^T r, never forming J^T J.  Two operator forms: the
-// gather over the grid in relative coordinates (rel_op_pass and
+// gather over the grid in relative coordinates (rel_op_pass_to and
 // cg_solve_channel_rel, for selections of <= kStencilTypes types) and the
 // pair-list scatter below (cg_pass and cg_solve_channel, any selection).
 // The scatter form is one pass over the pairs: each pair evaluates its entry of J v,
@@ -1177,115 +1193,13 @@ __device__ double cg_pass(const CalParams &p, int c, const CgWork &w, bool resid
 // own row in registers: every pair is visited by both antennas and nothing
 // is scattered, so there are no atomics and the result does not depend on
 // the schedule.  The model-visibility rows are summed per type over the
-// first-member visits in registers and reduced across the CTA once per pass.
-template <int KT>
-__device__ __forceinline__ void rel_type_reduce(float (&tx)[KT], float (&ty)[KT], float (&td)[KT], bool with_d,
-                                                int nu, float *out_x /* stride 2 */, float *out_d, float *s_tsum) {
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < KT; ++k) {
-        if (k >= nu) break;
-        for (int o = 16; o > 0; o >>= 1) {
-            tx[k] += __shfl_xor_sync(0xffffffffu, tx[k], o);
-            ty[k] += __shfl_xor_sync(0xffffffffu, ty[k], o);
-            if (with_d) td[k] += __shfl_xor_sync(0xffffffffu, td[k], o);
-        }
-        if (lane == 0) {
-            s_tsum[(wp * 3 + 0) * KT + k] = tx[k];
-            s_tsum[(wp * 3 + 1) * KT + k] = ty[k];
-            s_tsum[(wp * 3 + 2) * KT + k] = td[k];
-        }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < 3 * nu; t += blockDim.x) {
-        const int comp = t / nu, k = t - comp * nu;
-        float a = 0.f;
-        for (int u = 0; u < nw; ++u) a += s_tsum[(u * 3 + comp) * KT + k];
-        if (comp < 2) out_x[2 * k + comp] = a;
-        else if (with_d) out_d[k] = a;
-    }
-}
-
-// Residual pass at the current (g, V): chi^2 (returned), the right-hand side
-// in relative coordinates (acc), G, the diagonal D of A and, for the coarse
-// operators, dv_k = D_k / |V_k|^2.  Also returns, in *dmax, the largest
-// (g, V)-form gain diagonal D_i / G_i that scales the Levenberg term.
-__device__ double rel_resid_pass(const CalParams &p, int c, const CgWork &w, double *red, float *dmax) {
-    constexpr int KT = kStencilTypes;
-    __shared__ float s_tsum[(kCgStThreads / 32) * 3 * KT];
-    const int L = p.L, nu = p.n_ubl, N = p.N;
-    // the gains are gathered from a copy in the q area (free between CG solves)
-    float2 *xg = reinterpret_cast<float2 *>(w.pp);
-    for (int m = threadIdx.x; m < N; m += blockDim.x) xg[m] = reinterpret_cast<const float2 *>(w.xg)[m];
-    __syncthreads();
-    const float2 *vobs2 = reinterpret_cast<const float2 *>(p.vred) + (size_t)c * p.P;
-    const int2 *vobsi = reinterpret_cast<const int2 *>(p.vred) + (size_t)c * p.P;
-    float tvx[KT], tvy[KT], tvd[KT];
-#pragma unroll
-    for (int k = 0; k < KT; ++k) tvx[k] = tvy[k] = tvd[k] = 0.f;
-    float chi = 0.f, dm = 0.f;
-    for (int m = threadIdx.x; m < N; m += blockDim.x) {
-        const int x = m % L, y = m / L;
-        const float2 gm = xg[m];
-        const float Gm = gm.x * gm.x + gm.y * gm.y;
-        float sx = 0.f, sy = 0.f, dsum = 0.f;
-#pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            if (k >= nu) break;
-            const int dx = __ldg(p.types + 2 * k), dy = __ldg(p.types + 2 * k + 1);
-            const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
-            const float inv = 1.0f / (float)(__ldg(p.win_t1 + k) - __ldg(p.win_t0 + k));
-            const int qb = __ldg(p.type_ptr + k);
-            const int W = L - abs(dx), xlo = max(0, -dx), ylo = max(0, -dy);
-            const int off = dy * L + dx;
-            auto vo = [&](int q) {
-                if (p.vfmt == GC_C64) {
-                    const float2 v = vobs2[q];
-                    return make_float2(v.x * inv, v.y * inv);
-                }
-                const int2 v = vobsi[q];
-                return make_float2((float)v.x * inv, (float)v.y * inv);
-            };
-            {   // m first: pair (m, j = m - d_k)
-                const int xj = x - dx, yj = y - dy;
-                if (xj >= 0 && xj < L && yj >= 0 && yj < L) {
-                    const float2 gj = xg[m - off];
-                    const float ex = gm.x * gj.x + gm.y * gj.y, ey = gm.y * gj.x - gm.x * gj.y;   // g_m conj(g_j)
-                    const float mx = ex * Vx - ey * Vy, my = ex * Vy + ey * Vx;                 // model m_p
-                    const float2 o = vo(qb + (yj - ylo) * W + (xj - xlo));
-                    const float rx = o.x - mx, ry = o.y - my;
-                    chi = fmaf(rx, rx, fmaf(ry, ry, chi));
-                    const float Wp = mx * mx + my * my;
-                    dsum += Wp;
-                    tvd[k] += Wp;
-                    const float hx = mx * rx + my * ry, hy = mx * ry - my * rx;   // conj(m) r
-                    sx += hx;
-                    sy += hy;
-                    tvx[k] += hx;
-                    tvy[k] += hy;
-                }
-            }
-            {   // m second: pair (i = m + d_k, m)
-                const int xi = x + dx, yi = y + dy;
-                if (xi >= 0 && xi < L && yi >= 0 && yi < L) {
-                    const float2 gi = xg[m + off];
-                    const float ex = gi.x * gm.x + gi.y * gm.y, ey = gi.y * gm.x - gi.x * gm.y;   // g_i conj(g_m)
-                    const float mx = ex * Vx - ey * Vy, my = ex * Vy + ey * Vx;
-                    const float2 o = vo(qb + (y - ylo) * W + (x - xlo));
-                    const float rx = o.x - mx, ry = o.y - my;
-                    dsum += mx * mx + my * my;
-                    sx += mx * rx + my * ry;      // m conj(r)
-                    sy += my * rx - mx * ry;
-                }
-            }
-        }
-        w.acc[2 * m] = sx;
-        w.acc[2 * m + 1] = sy;
-        w.G[m] = Gm;
-        w.D[m] = dsum;
-        dm = fmaxf(dm, Gm > 0.f ? dsum / Gm : 0.f);
-    }
-    rel_type_reduce<KT>(tvx, tvy, tvd, true, nu, w.acc + 2 * N, w.D + N, s_tsum);
+// first-member visits in registers and reduced across the warp, then in
+// shared memory across the CTA.
+// The end of a residual pass: |V_k|^2, dv_k, the chi^2 block sum and the
+// largest gain diagonal, from the thread's chi^2 part and running maximum
+// (acc, G and D of the antennas and the type sums are written by then).
+__device__ double rel_resid_finish(const CalParams &p, const CgWork &w, double *red, float *dmax, float chi, float dm) {
+    const int nu = p.n_ubl, N = p.N;
     for (int k = threadIdx.x; k < nu; k += blockDim.x) {
         const float Uk = w.xv[2 * k] * w.xv[2 * k] + w.xv[2 * k + 1] * w.xv[2 * k + 1];
         w.G[N + k] = Uk;
@@ -1309,6 +1223,133 @@ __device__ double rel_resid_pass(const CalParams &p, int c, const CgWork &w, dou
     *dmax = (float)mx;
     return s[0];
 }
+
+template <int VF>
+__device__ __forceinline__ float2 rel_obs(const CalParams &p, int c, int q, float inv) {
+    if (VF == GC_C64) {
+        const float2 v = reinterpret_cast<const float2 *>(p.vred)[(size_t)c * p.P + q];
+        return make_float2(v.x * inv, v.y * inv);
+    }
+    const int2 v = reinterpret_cast<const int2 *>(p.vred)[(size_t)c * p.P + q];
+    return make_float2((float)v.x * inv, (float)v.y * inv);
+}
+
+// Residual pass at the current (g, V): chi^2 (returned), the right-hand side
+// in relative coordinates (acc), G, the diagonal D of A and, for the coarse
+// operators, dv_k = D_k / |V_k|^2.  Also returns, in *dmax, the largest
+// (g, V)-form gain diagonal D_i / G_i that scales the Levenberg term.
+// The type loop is outermost, over the thread's antennas in blocks of 8 (each block's gains and sums in registers, the type constants
+// -- offset, pair-index base, 1 / window -- worked out once per type and
+// block); a pair off the grid reads element 0 and is selected away.
+template <int VF, int J>
+__device__ double rel_resid_pass_t(const CalParams &p, int c, const CgWork &w, double *red, float *dmax) {
+    constexpr int KT = kStencilTypes;
+    __shared__ float s_tsum[(kCgStThreads / 32) * 3 * KT];
+    const int L = p.L, nu = p.n_ubl, N = p.N, bd = blockDim.x;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = bd >> 5;
+    // the gains are gathered from a copy in the q area (free between CG solves)
+    float2 *xg = reinterpret_cast<float2 *>(w.pp);
+    for (int m = threadIdx.x; m < N; m += bd) xg[m] = reinterpret_cast<const float2 *>(w.xg)[m];
+    __syncthreads();
+    float chi = 0.f, dm = 0.f;
+    const int nblk = (N + J * bd - 1) / (J * bd);
+#pragma unroll 1
+    for (int h = 0; h < nblk; ++h) {
+        float2 gm[J];
+        float sx[J], sy[J], sd[J];
+        int xy[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int m = threadIdx.x + (J * h + j) * bd;
+            const bool in = m < N;
+            xy[j] = in ? (m % L) | ((m / L) << 16) : -1;
+            gm[j] = in ? xg[m] : make_float2(0.f, 0.f);
+            sx[j] = sy[j] = sd[j] = 0.f;
+        }
+#pragma unroll 1
+        for (int k = 0; k < nu; ++k) {
+            const int dx = __ldg(p.types + 2 * k), dy = __ldg(p.types + 2 * k + 1);
+            const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
+            const float inv = 1.0f / (float)(__ldg(p.win_t1 + k) - __ldg(p.win_t0 + k));
+            const int W = L - abs(dx), qb = __ldg(p.type_ptr + k) - max(0, -dy) * W - max(0, -dx);
+            const int off = dy * L + dx;
+            float tx = 0.f, ty = 0.f, td = 0.f;
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int m = threadIdx.x + (J * h + j) * bd;
+                const int x = xy[j] & 0xffff, y = xy[j] >> 16;
+                const bool in = xy[j] >= 0;
+                const bool v1 = in && (unsigned)(x - dx) < (unsigned)L && (unsigned)(y - dy) < (unsigned)L;
+                const bool v2 = in && (unsigned)(x + dx) < (unsigned)L && (unsigned)(y + dy) < (unsigned)L;
+                // m first: pair (m, j = m - d_k); m second: pair (i = m + d_k, m)
+                const float2 gj = xg[v1 ? m - off : 0], gi = xg[v2 ? m + off : 0];
+                const float2 o1 = rel_obs<VF>(p, c, v1 ? qb + (y - dy) * W + (x - dx) : 0, inv);
+                const float2 o2 = rel_obs<VF>(p, c, v2 ? qb + y * W + x : 0, inv);
+                {
+                    const float ex = gm[j].x * gj.x + gm[j].y * gj.y, ey = gm[j].y * gj.x - gm[j].x * gj.y;
+                    const float mx = ex * Vx - ey * Vy, my = ex * Vy + ey * Vx;   // model m_p
+                    const float rx = o1.x - mx, ry = o1.y - my;
+                    const float Wp = v1 ? mx * mx + my * my : 0.f;
+                    const float hx = v1 ? mx * rx + my * ry : 0.f, hy = v1 ? mx * ry - my * rx : 0.f;   // conj(m) r
+                    chi = v1 ? fmaf(rx, rx, fmaf(ry, ry, chi)) : chi;
+                    sd[j] += Wp;
+                    td += Wp;
+                    sx[j] += hx;
+                    sy[j] += hy;
+                    tx += hx;
+                    ty += hy;
+                }
+                {
+                    const float ex = gi.x * gm[j].x + gi.y * gm[j].y, ey = gi.y * gm[j].x - gi.x * gm[j].y;
+                    const float mx = ex * Vx - ey * Vy, my = ex * Vy + ey * Vx;
+                    const float rx = o2.x - mx, ry = o2.y - my;
+                    sd[j] += v2 ? mx * mx + my * my : 0.f;
+                    sx[j] += v2 ? mx * rx + my * ry : 0.f;   // m conj(r)
+                    sy[j] += v2 ? my * rx - mx * ry : 0.f;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                tx += __shfl_xor_sync(0xffffffffu, tx, o);
+                ty += __shfl_xor_sync(0xffffffffu, ty, o);
+                td += __shfl_xor_sync(0xffffffffu, td, o);
+            }
+            if (lane == 0) {
+                float *a0 = &s_tsum[(wp * 3 + 0) * KT + k], *a1 = &s_tsum[(wp * 3 + 1) * KT + k],
+                      *a2 = &s_tsum[(wp * 3 + 2) * KT + k];
+                *a0 = h ? *a0 + tx : tx;
+                *a1 = h ? *a1 + ty : ty;
+                *a2 = h ? *a2 + td : td;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int m = threadIdx.x + (J * h + j) * bd;
+            if (m >= N) continue;
+            const float Gm = gm[j].x * gm[j].x + gm[j].y * gm[j].y;
+            w.acc[2 * m] = sx[j];
+            w.acc[2 * m + 1] = sy[j];
+            w.G[m] = Gm;
+            w.D[m] = sd[j];
+            dm = fmaxf(dm, Gm > 0.f ? sd[j] / Gm : 0.f);
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * nu; t += bd) {
+        const int comp = t / nu, k = t - comp * nu;
+        float a = 0.f;
+        for (int u = 0; u < nw; ++u) a += s_tsum[(u * 3 + comp) * KT + k];
+        if (comp < 2) w.acc[2 * (N + k) + comp] = a;
+        else w.D[N + k] = a;
+    }
+    return rel_resid_finish(p, w, red, dmax, chi, dm);
+}
+
+constexpr int kResidBlock = 8;   // antennas per register block (no spills at 128 registers)
+__device__ double rel_resid_pass(const CalParams &p, int c, const CgWork &w, double *red, float *dmax) {
+    return p.vfmt == GC_C64 ? rel_resid_pass_t<GC_C64, kResidBlock>(p, c, w, red, dmax)
+                            : rel_resid_pass_t<GC_I4C, kResidBlock>(p, c, w, red, dmax);
+}
+
 
 // acc = A q (relative coordinates, no Levenberg term): the search direction
 // q is w.pp, G and q are gathered (shared memory when the arena holds them).
@@ -1537,7 +1578,7 @@ __device__ void coarse_assemble_scatter(const CalParams &p, const CgWork &w, flo
 
 // Gather assembly: one warp per patch a walks the patch's antennas and, for
 // every type, the antenna's pair as first and as second member (the same
-// grid arithmetic as rel_op_pass, weights from G), summing row a of both coarse
+// grid arithmetic as rel_op_pass_to, weights from G), summing row a of both coarse
 // operators in registers: the patch itself, its eight neighbour patches
 // (pairs never reach further when every type offset is within one patch
 // side) and the model-visibility columns.  A pair inside the patch is met
@@ -1949,7 +1990,7 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
 }
 
 // One channel of matrix-free Gauss-Newton in relative coordinates (the
-// stencil operator; see rel_op_pass).  Same outer iteration, forcing terms,
+// stencil operator; see rel_op_pass_to).  Same outer iteration, forcing terms,
 // preconditioner, projection, line search and stopping rule as
 // cg_solve_channel; the CG vectors hold (q, w) and the search direction q
 // lives in shared memory beside G, D and the coarse indices.  Convergence
@@ -2283,10 +2324,18 @@ lincal_cg_kernel(const CalParams p, double cg_tol, int cg_max, int smem_floats) 
     int hot_mode;
     bool coarse_smem;
     cg_modes(p, smem_floats, hot_mode, coarse_smem);
+    __shared__ int s_item;
     CgWork w = cg_layout(p, p.work + (size_t)blockIdx.x * p.work_per_cta, arena, smem_floats, hot_mode, coarse_smem);
     w.rc = s_rc;
     w.yc = s_yc;
-    for (int c = blockIdx.x; c < p.C; c += gridDim.x) {
+    // channels are taken from a device counter: their iteration counts
+    // differ, and a CTA that drew short solves takes more of them
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(p.counter, 1u);
+        __syncthreads();
+        const int c = s_item;
+        __syncthreads();
+        if (c >= p.C) break;
         if constexpr (kSten) {
             if (p.stencil) {
                 cg_solve_channel_rel(p, c, w, cg_tol, cg_max, red, redf);
@@ -2523,6 +2572,7 @@ static gc_status fill_params(gc_ctx *ctx, gc_sel *sel, int C, const void *vreduc
     p.mu_rel = fp64_ne ? 1e-12 : 1e-7;
     p.red32 = o.solver == GC_LINCAL_CG && o.fp32_reductions ? 1 : 0;
     p.work = nullptr;
+    p.counter = nullptr;
     p.work_per_cta = 0;
     return GC_OK;
 }
@@ -2585,11 +2635,16 @@ extern "C" gc_status gc_calibrate(gc_ctx *ctx, const void *vreduced, int vfmt, c
     if (e != cudaSuccess || occ < 1) return gc_cuda_fail(ctx, e, "occupancy(calibration)");
     if (ctx->tune[GC_TUNE_CAL_CTAS] > 0) occ = std::min(occ, ctx->tune[GC_TUNE_CAL_CTAS]);
     const int grid = std::min(C, occ * ctx->sm_count);
-    st = gc_scratch_reserve(ctx, per_cta * grid);
+    st = gc_scratch_reserve(ctx, 256 + per_cta * grid);
     if (st != GC_OK) return st;
-    p.work = static_cast<char *>(ctx->scratch);
+    p.counter = static_cast<unsigned int *>(ctx->scratch);
+    p.work = static_cast<char *>(ctx->scratch) + 256;
     p.work_per_cta = per_cta;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (o.solver == GC_LINCAL_CG) {
+        e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return gc_cuda_fail(ctx, e, "reset work counter");
+    }
     const char *name = o.solver == GC_LINCAL ? (fp64 ? "lincal_fp64" : "lincal_fp32")
                        : (o.solver == GC_LINCAL_CG ? "lincal_cg" : "omnical");
     int rec = gc_prof_begin(ctx, s, name);
