@@ -1198,10 +1198,11 @@ __device__ double cg_pass(const CalParams &p, int c, const CgWork &w, bool resid
 // The end of a residual pass: |V_k|^2, dv_k, the chi^2 block sum and the
 // largest gain diagonal, from the thread's chi^2 part and running maximum
 // (acc, G and D of the antennas and the type sums are written by then).
-__device__ double rel_resid_finish(const CalParams &p, const CgWork &w, double *red, float *dmax, float chi, float dm) {
+__device__ double rel_resid_finish(const CalParams &p, const CgWork &w, const float *xv, double *red, float *dmax,
+                                   float chi, float dm) {
     const int nu = p.n_ubl, N = p.N;
     for (int k = threadIdx.x; k < nu; k += blockDim.x) {
-        const float Uk = w.xv[2 * k] * w.xv[2 * k] + w.xv[2 * k + 1] * w.xv[2 * k + 1];
+        const float Uk = xv[2 * k] * xv[2 * k] + xv[2 * k + 1] * xv[2 * k + 1];
         w.G[N + k] = Uk;
     }
     __syncthreads();
@@ -1242,15 +1243,20 @@ __device__ __forceinline__ float2 rel_obs(const CalParams &p, int c, int q, floa
 // -- offset, pair-index base, 1 / window -- worked out once per type and
 // block); a pair off the grid reads element 0 and is selected away.
 template <int VF, int J>
-__device__ double rel_resid_pass_t(const CalParams &p, int c, const CgWork &w, double *red, float *dmax) {
+__device__ double rel_resid_pass_t(const CalParams &p, int c, const CgWork &w, bool staged, double *red, float *dmax) {
     constexpr int KT = kStencilTypes;
     __shared__ float s_tsum[(kCgStThreads / 32) * 3 * KT];
     const int L = p.L, nu = p.n_ubl, N = p.N, bd = blockDim.x;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = bd >> 5;
-    // the gains are gathered from a copy in the q area (free between CG solves)
+    // the gains are gathered from a copy in the q area (free between CG
+    // solves); a staged point (a line-search trial) is there already,
+    // followed by its model visibilities
     float2 *xg = reinterpret_cast<float2 *>(w.pp);
-    for (int m = threadIdx.x; m < N; m += bd) xg[m] = reinterpret_cast<const float2 *>(w.xg)[m];
-    __syncthreads();
+    const float *xv = staged ? w.pp + 2 * N : w.xv;
+    if (!staged) {
+        for (int m = threadIdx.x; m < N; m += bd) xg[m] = reinterpret_cast<const float2 *>(w.xg)[m];
+        __syncthreads();
+    }
     float chi = 0.f, dm = 0.f;
     const int nblk = (N + J * bd - 1) / (J * bd);
 #pragma unroll 1
@@ -1269,7 +1275,7 @@ __device__ double rel_resid_pass_t(const CalParams &p, int c, const CgWork &w, d
 #pragma unroll 1
         for (int k = 0; k < nu; ++k) {
             const int dx = __ldg(p.types + 2 * k), dy = __ldg(p.types + 2 * k + 1);
-            const float Vx = w.xv[2 * k], Vy = w.xv[2 * k + 1];
+            const float Vx = xv[2 * k], Vy = xv[2 * k + 1];
             const float inv = 1.0f / (float)(__ldg(p.win_t1 + k) - __ldg(p.win_t0 + k));
             const int W = L - abs(dx), qb = __ldg(p.type_ptr + k) - max(0, -dy) * W - max(0, -dx);
             const int off = dy * L + dx;
@@ -1341,13 +1347,13 @@ __device__ double rel_resid_pass_t(const CalParams &p, int c, const CgWork &w, d
         if (comp < 2) w.acc[2 * (N + k) + comp] = a;
         else w.D[N + k] = a;
     }
-    return rel_resid_finish(p, w, red, dmax, chi, dm);
+    return rel_resid_finish(p, w, xv, red, dmax, chi, dm);
 }
 
 constexpr int kResidBlock = 8;   // antennas per register block (no spills at 128 registers)
-__device__ double rel_resid_pass(const CalParams &p, int c, const CgWork &w, double *red, float *dmax) {
-    return p.vfmt == GC_C64 ? rel_resid_pass_t<GC_C64, kResidBlock>(p, c, w, red, dmax)
-                            : rel_resid_pass_t<GC_I4C, kResidBlock>(p, c, w, red, dmax);
+__device__ double rel_resid_pass(const CalParams &p, int c, const CgWork &w, bool staged, double *red, float *dmax) {
+    return p.vfmt == GC_C64 ? rel_resid_pass_t<GC_C64, kResidBlock>(p, c, w, staged, red, dmax)
+                            : rel_resid_pass_t<GC_I4C, kResidBlock>(p, c, w, staged, red, dmax);
 }
 
 
@@ -2130,12 +2136,56 @@ __device__ void cg_solve_channel_rel(const CalParams &p, int c, CgWork &w, doubl
         __syncthreads();
     };
     for (int t2 = threadIdx.x; t2 < 2 * kMaxCoarse; t2 += blockDim.x) w.rc[t2] = 0.f;
-    int st = GC_ENOCONV, it, inner = 0;
-    double grad0 = 0.0;
-    for (it = 1; it <= p.max_iter; ++it) {
-        // residual, right-hand side, G, D and the Levenberg scale
+    int st = GC_ENOCONV, it = 1, inner = 0;
+    double grad0 = 0.0, chi2 = 0.0;
+    double nr[2] = {0.0, 0.0};   // |x|^2 and |step|^2 of the last projected step
+    bool staged = false;         // the q area holds the last iteration's full step
+    float2 *stage = q;
+    for (;;) {
+        // residual, right-hand side, G, D and the Levenberg scale, at the
+        // current point or at the staged full step of the last iteration.
+        // A halving line search on chi^2 follows every step: the full step
+        // is tried with this (whole) pass, so that when it is taken (nearly
+        // always) the pass is also the next iteration's; shorter steps are
+        // tried with chi^2 alone.  (One call site keeps one copy of the
+        // pass in the instruction stream.)
         float dmax = 0.f;
-        const double chi2 = rel_resid_pass(p, c, w, red, &dmax);
+        const double c2 = rel_resid_pass(p, c, w, staged, red, &dmax);
+        if (staged) {
+            staged = false;
+            const bool full = c2 <= chi2 * (1.0 + 1e-6) + 1e-30;
+            float step = 1.f;
+            for (int ls = 1; ls < 8 && !full; ++ls) {
+                step *= 0.5f;
+                for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+                    const float2 sv = e < N ? reinterpret_cast<const float2 *>(w.xg)[e]
+                                            : reinterpret_cast<const float2 *>(w.xv)[e - N];
+                    const float2 dp = zs[e];
+                    stage[e] = make_float2(sv.x + step * dp.x, sv.y + step * dp.y);
+                }
+                __syncthreads();
+                const float ch = rel_chi2(p, c, reinterpret_cast<const float *>(stage),
+                                          reinterpret_cast<const float *>(stage + N), redf);
+                if ((double)ch <= chi2 * (1.0 + 1e-6) + 1e-30 || ls == 7) break;
+            }
+            for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+                if (e < N) reinterpret_cast<float2 *>(w.xg)[e] = stage[e];
+                else reinterpret_cast<float2 *>(w.xv)[e - N] = stage[e];
+            }
+            __syncthreads();
+            if ((double)step * sqrt(nr[1]) <= p.tol * sqrt(nr[0])) {
+                st = GC_OK;
+                break;
+            }
+            if (gc_globaltimer() - t_start > p.deadline_ns) {
+                st = GC_ETIMEOUT;
+                if (threadIdx.x == 0) atomicOr(p.status, GC_DEV_TIMEOUT_CAL);
+                break;
+            }
+            if (++it > p.max_iter) break;
+            if (!full) continue;   // the pass at the accepted point is still to come
+        }
+        chi2 = c2;
         const float mu = (float)(p.mu_rel * (double)dmax);
         if (coarse && it == 1) cg_coarse_setup(p, w, mu);   // later iterations reuse it
         // PCG from x = 0: r = b, q = M^-1 r
@@ -2248,7 +2298,7 @@ __device__ void cg_solve_channel_rel(const CalParams &p, int c, CgWork &w, doubl
         float cvec[4];
         solve_gram4<float>(pacc, cvec);
         // delta = s (x - sum_a c_a q_a) in the (g, V) form, into w.z
-        double nr[2] = {0.0, 0.0};
+        nr[0] = nr[1] = 0.0;
         for (int e = threadIdx.x; e < ne; e += blockDim.x) {
             float2 qa[4];
             degen(e, qa);
@@ -2262,6 +2312,9 @@ __device__ void cg_solve_channel_rel(const CalParams &p, int c, CgWork &w, doubl
                                     : reinterpret_cast<const float2 *>(w.xv)[e - N];
             const float2 dp = make_float2(sv.x * d.x - sv.y * d.y, sv.x * d.y + sv.y * d.x);
             zs[e] = dp;
+            // the full step, staged in the q area (free once the CG loop is
+            // done) for the pair gathers of the next pass
+            stage[e] = make_float2(sv.x + dp.x, sv.y + dp.y);
             if (p.red32) {
                 nr[0] = (double)((float)nr[0] + (sv.x * sv.x + sv.y * sv.y));
                 nr[1] = (double)((float)nr[1] + (dp.x * dp.x + dp.y * dp.y));
@@ -2278,37 +2331,8 @@ __device__ void cg_solve_channel_rel(const CalParams &p, int c, CgWork &w, doubl
         } else {
             block_sum<double, 2>(nr, red);
         }
-        // halving line search on chi^2; each trial point is staged in the
-        // q area (free once the CG loop is done) for the pair gathers
-        float step = 1.f;
-        float2 *stage = q;
-        for (int ls = 0; ls < 8; ++ls) {
-            for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-                const float2 sv = e < N ? reinterpret_cast<const float2 *>(w.xg)[e]
-                                        : reinterpret_cast<const float2 *>(w.xv)[e - N];
-                const float2 dp = zs[e];
-                stage[e] = make_float2(sv.x + step * dp.x, sv.y + step * dp.y);
-            }
-            __syncthreads();
-            const float c2 = rel_chi2(p, c, reinterpret_cast<const float *>(stage),
-                                      reinterpret_cast<const float *>(stage + N), redf);
-            if ((double)c2 <= chi2 * (1.0 + 1e-6) + 1e-30 || ls == 7) break;
-            step *= 0.5f;
-        }
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-            if (e < N) reinterpret_cast<float2 *>(w.xg)[e] = stage[e];
-            else reinterpret_cast<float2 *>(w.xv)[e - N] = stage[e];
-        }
         __syncthreads();
-        if ((double)step * sqrt(nr[1]) <= p.tol * sqrt(nr[0])) {
-            st = GC_OK;
-            break;
-        }
-        if (gc_globaltimer() - t_start > p.deadline_ns) {
-            st = GC_ETIMEOUT;
-            if (threadIdx.x == 0) atomicOr(p.status, GC_DEV_TIMEOUT_CAL);
-            break;
-        }
+        staged = true;
     }
     finish_channel<float>(p, c, w.xg, w.xv, min(it, p.max_iter), st, red, inner);
 }
