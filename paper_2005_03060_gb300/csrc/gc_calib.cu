@@ -53,6 +53,7 @@ struct CalParams {
     const int32_t *nbr;          // [2][n_ubl][N] neighbour table or null
     int ax, ay;                  // indices of types (1,0) and (0,1)
     int stencil;                 // matrix-free operator by per-antenna gather (<= kStencilTypes types)
+    int st_halo;                 // largest |dx| or |dy| of a type (stencil operator)
     // partly occupied lattice (null / L*L otherwise): occupancy [N], the
     // breadth-first start-point tree over the axis types, antennas
     const int32_t *mask, *tree_ant, *tree_pair, *tree_sign;
@@ -1364,42 +1365,87 @@ __device__ double rel_resid_pass(const CalParams &p, int c, const CgWork &w, boo
 __device__ float rel_op_pass(const CalParams &p, const CgWork &w, float mu) {
     constexpr int KT = kStencilTypes;
     __shared__ float s_tsum[(kCgStThreads / 32) * 2 * KT];
+    __shared__ float4 s_ty[KT];   // per type: offset d_k (as int bits), w_k, G_k
     const int L = p.L, nu = p.n_ubl, N = p.N;
     const float2 *q = reinterpret_cast<const float2 *>(w.pp);
     const float *G = w.G;
+    if (threadIdx.x < nu) {
+        const int k = threadIdx.x;
+        const float2 wk = q[N + k];
+        s_ty[k] = make_float4(__int_as_float(__ldg(p.types + 2 * k + 1) * L + __ldg(p.types + 2 * k)), wk.x, wk.y,
+                              G[N + k]);
+    }
+    __syncthreads();
     float tvx[KT], tvy[KT];
 #pragma unroll
     for (int k = 0; k < KT; ++k) tvx[k] = tvy[k] = 0.f;
     float curv = 0.f;
-    for (int m = threadIdx.x; m < N; m += blockDim.x) {
-        const int x = m % L, y = m / L;
+    // Antennas at least st_halo from every edge (index t < n_in, in row
+    // order) have both pairs of every type on the grid and take the path
+    // without tests; the rest of the grid (the border ring, t >= n_in)
+    // tests each pair.
+    const int h = p.st_halo, Wi = L > 2 * h ? L - 2 * h : 0, n_in = Wi * Wi;
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        int m = t;   // no interior (L <= 2 st_halo): every antenna in grid order
+        if (t < n_in) {
+            const int yy = t / Wi;
+            m = (yy + h) * L + (t - yy * Wi) + h;
+        } else if (n_in > 0) {   // the ring: h top rows, h bottom rows, then 2h columns of each middle row
+            const int u = t - n_in, hl = h * L;
+            if (u < 2 * hl) {
+                m = u < hl ? u : (L - h) * L + (u - hl);
+            } else {
+                const int v = u - 2 * hl, row = h + v / (2 * h), ci = v - (row - h) * 2 * h;
+                m = row * L + (ci < h ? ci : L - 2 * h + ci);
+            }
+        }
         const float2 qm = q[m];
         const float Gm = G[m];
         float sx = 0.f, sy = 0.f;
+        if (t < n_in) {
 #pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            if (k >= nu) break;
-            const int dx = __ldg(p.types + 2 * k), dy = __ldg(p.types + 2 * k + 1);
-            const float2 wk = q[N + k];
-            const float GU = Gm * G[N + k];
-            const int off = dy * L + dx;
-            // without branches: a pair off the grid reads antenna m itself
-            // and gets weight 0 (fmaf(0, a, s) = s, so the sums are those of
-            // the pairs that exist)
-            const bool v1 = (unsigned)(x - dx) < (unsigned)L && (unsigned)(y - dy) < (unsigned)L;
-            const bool v2 = (unsigned)(x + dx) < (unsigned)L && (unsigned)(y + dy) < (unsigned)L;
-            const int j = v1 ? m - off : m, i = v2 ? m + off : m;
-            const float2 qj = q[j], qi = q[i];
-            const float W1 = v1 ? GU * G[j] : 0.f, W2 = v2 ? GU * G[i] : 0.f;
-            // m first: s = q_m + conj(q_j) + w_k
-            const float ax = qm.x + wk.x + qj.x, ay = qm.y + wk.y - qj.y;
-            sx = fmaf(W1, ax, sx);
-            sy = fmaf(W1, ay, sy);
-            tvx[k] = fmaf(W1, ax, tvx[k]);
-            tvy[k] = fmaf(W1, ay, tvy[k]);
-            // m second: conj(s) = conj(q_i) + q_m + conj(w_k)
-            sx = fmaf(W2, qi.x + qm.x + wk.x, sx);
-            sy = fmaf(W2, qm.y - qi.y - wk.y, sy);
+            for (int k = 0; k < KT; ++k) {
+                if (k >= nu) break;
+                const float4 ty = s_ty[k];
+                const int off = __float_as_int(ty.x);
+                const float2 qj = q[m - off], qi = q[m + off];
+                const float GU = Gm * ty.w;
+                const float W1 = GU * G[m - off], W2 = GU * G[m + off];
+                // m first: s = q_m + conj(q_j) + w_k
+                const float ax = qm.x + ty.y + qj.x, ay = qm.y + ty.z - qj.y;
+                sx = fmaf(W1, ax, sx);
+                sy = fmaf(W1, ay, sy);
+                tvx[k] = fmaf(W1, ax, tvx[k]);
+                tvy[k] = fmaf(W1, ay, tvy[k]);
+                // m second: conj(s) = conj(q_i) + q_m + conj(w_k)
+                sx = fmaf(W2, qi.x + qm.x + ty.y, sx);
+                sy = fmaf(W2, qm.y - qi.y - ty.z, sy);
+            }
+        } else {
+            const int x = m % L, y = m / L;
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                if (k >= nu) break;
+                const int dx = __ldg(p.types + 2 * k), dy = __ldg(p.types + 2 * k + 1);
+                const float4 ty = s_ty[k];
+                const int off = __float_as_int(ty.x);
+                // without branches: a pair off the grid reads antenna m itself
+                // and gets weight 0 (fmaf(0, a, s) = s, so the sums are those
+                // of the pairs that exist)
+                const bool v1 = (unsigned)(x - dx) < (unsigned)L && (unsigned)(y - dy) < (unsigned)L;
+                const bool v2 = (unsigned)(x + dx) < (unsigned)L && (unsigned)(y + dy) < (unsigned)L;
+                const int j = v1 ? m - off : m, i = v2 ? m + off : m;
+                const float2 qj = q[j], qi = q[i];
+                const float GU = Gm * ty.w;
+                const float W1 = v1 ? GU * G[j] : 0.f, W2 = v2 ? GU * G[i] : 0.f;
+                const float ax = qm.x + ty.y + qj.x, ay = qm.y + ty.z - qj.y;
+                sx = fmaf(W1, ax, sx);
+                sy = fmaf(W1, ay, sy);
+                tvx[k] = fmaf(W1, ax, tvx[k]);
+                tvy[k] = fmaf(W1, ay, tvy[k]);
+                sx = fmaf(W2, qi.x + qm.x + ty.y, sx);
+                sy = fmaf(W2, qm.y - qi.y - ty.z, sy);
+            }
         }
         w.acc[2 * m] = sx;
         w.acc[2 * m + 1] = sy;
@@ -2575,6 +2621,9 @@ static gc_status fill_params(gc_ctx *ctx, gc_sel *sel, int C, const void *vreduc
     // both full-grid selection builders take baseline-types whole, in
     // pair_index order; a partly occupied lattice takes the pair-list form
     p.stencil = ctx->tune[GC_TUNE_CAL_OP] == 0 && sel->n_ubl <= kStencilTypes && !sel->masked ? 1 : 0;
+    p.st_halo = 0;
+    for (int k = 0; k < sel->n_ubl; ++k)
+        p.st_halo = std::max(p.st_halo, std::max(std::abs(sel->types[2 * k]), std::abs(sel->types[2 * k + 1])));
     p.mask = sel->masked ? sel->d_mask : nullptr;
     p.tree_ant = sel->masked ? sel->d_tree_ant : nullptr;
     p.tree_pair = sel->masked ? sel->d_tree_pair : nullptr;
