@@ -26,6 +26,7 @@
 // by gather over each antenna's pairs, model-visibility update one warp per
 // baseline-type.
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -1196,6 +1197,30 @@ __device__ double cg_pass(const CalParams &p, int c, const CgWork &w, bool resid
 // the schedule.  The model-visibility rows are summed per type over the
 // first-member visits in registers and reduced across the warp, then in
 // shared memory across the CTA.
+// Antenna order of the stencil passes: index t < n_in walks the interior
+// (antennas at least st_halo from every edge, whose pairs of every type are
+// all on the grid) in row order; t >= n_in walks the border ring: the h top
+// rows, the h bottom rows, then the 2h edge columns of each middle row.
+// Without an interior (L <= 2h) t is the grid index itself.
+struct RelOrder {
+    int L, h, Wi, n_in;
+    __device__ explicit RelOrder(const CalParams &p) : L(p.L), h(p.st_halo) {
+        Wi = L > 2 * h ? L - 2 * h : 0;
+        n_in = Wi * Wi;
+    }
+    __device__ __forceinline__ int antenna(int t) const {
+        if (t < n_in) {
+            const int yy = t / Wi;
+            return (yy + h) * L + (t - yy * Wi) + h;
+        }
+        if (n_in == 0) return t;
+        const int u = t - n_in, hl = h * L;
+        if (u < 2 * hl) return u < hl ? u : (L - h) * L + (u - hl);
+        const int v = u - 2 * hl, row = h + v / (2 * h), ci = v - (row - h) * 2 * h;
+        return row * L + (ci < h ? ci : L - 2 * h + ci);
+    }
+};
+
 // The end of a residual pass: |V_k|^2, dv_k, the chi^2 block sum and the
 // largest gain diagonal, from the thread's chi^2 part and running maximum
 // (acc, G and D of the antennas and the type sums are written by then).
@@ -1240,13 +1265,28 @@ __device__ __forceinline__ float2 rel_obs(const CalParams &p, int c, int q, floa
 // in relative coordinates (acc), G, the diagonal D of A and, for the coarse
 // operators, dv_k = D_k / |V_k|^2.  Also returns, in *dmax, the largest
 // (g, V)-form gain diagonal D_i / G_i that scales the Levenberg term.
-// The type loop is outermost, over the thread's antennas in blocks of 8 (each block's gains and sums in registers, the type constants
-// -- offset, pair-index base, 1 / window -- worked out once per type and
-// block); a pair off the grid reads element 0 and is selected away.
-template <int VF, int J>
+// Antenna m visits its pairs as first member (m, m - d_k), at pair index
+// b_k + y W_k + x - (d_y W_k + d_x), and as second member (m + d_k, m), at
+// b_k + y W_k + x (W_k = L - |d_x|, b_k the type's first pair less its
+// start offset), in the order of RelOrder; each type's constants come from
+// two shared-memory records.  Interior antennas skip the on-grid tests; on
+// the ring a pair off the grid reads element 0 and is selected away.
+template <int VF>
+__device__ __forceinline__ float2 rel_obs(const void *vc, int q, float inv) {
+    if (VF == GC_C64) {
+        const float2 v = reinterpret_cast<const float2 *>(vc)[q];
+        return make_float2(v.x * inv, v.y * inv);
+    }
+    const int2 v = reinterpret_cast<const int2 *>(vc)[q];
+    return make_float2((float)v.x * inv, (float)v.y * inv);
+}
+
+template <int VF>
 __device__ double rel_resid_pass_t(const CalParams &p, int c, const CgWork &w, bool staged, double *red, float *dmax) {
     constexpr int KT = kStencilTypes;
     __shared__ float s_tsum[(kCgStThreads / 32) * 3 * KT];
+    __shared__ int4 s_ra[KT];     // per type: offset d_k, d_y W_k + d_x, b_k, W_k
+    __shared__ float4 s_rb[KT];   // per type: 1 / window, V_k
     const int L = p.L, nu = p.n_ubl, N = p.N, bd = blockDim.x;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = bd >> 5;
     // the gains are gathered from a copy in the q area (free between CG
@@ -1254,90 +1294,89 @@ __device__ double rel_resid_pass_t(const CalParams &p, int c, const CgWork &w, b
     // followed by its model visibilities
     float2 *xg = reinterpret_cast<float2 *>(w.pp);
     const float *xv = staged ? w.pp + 2 * N : w.xv;
-    if (!staged) {
+    if (!staged)
         for (int m = threadIdx.x; m < N; m += bd) xg[m] = reinterpret_cast<const float2 *>(w.xg)[m];
-        __syncthreads();
+    if (threadIdx.x < nu) {
+        const int k = threadIdx.x;
+        const int dx = __ldg(p.types + 2 * k), dy = __ldg(p.types + 2 * k + 1), W = L - abs(dx);
+        s_ra[k] = make_int4(dy * L + dx, dy * W + dx, __ldg(p.type_ptr + k) - max(0, -dy) * W - max(0, -dx), W);
+        s_rb[k] = make_float4(1.0f / (float)(__ldg(p.win_t1 + k) - __ldg(p.win_t0 + k)), xv[2 * k], xv[2 * k + 1], 0.f);
     }
+    __syncthreads();
+    const void *vc = VF == GC_C64 ? (const void *)(reinterpret_cast<const float2 *>(p.vred) + (size_t)c * p.P)
+                                  : (const void *)(reinterpret_cast<const int2 *>(p.vred) + (size_t)c * p.P);
+    float tvx[KT], tvy[KT], tvd[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) tvx[k] = tvy[k] = tvd[k] = 0.f;
     float chi = 0.f, dm = 0.f;
-    const int nblk = (N + J * bd - 1) / (J * bd);
-#pragma unroll 1
-    for (int h = 0; h < nblk; ++h) {
-        float2 gm[J];
-        float sx[J], sy[J], sd[J];
-        int xy[J];
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            const int m = threadIdx.x + (J * h + j) * bd;
-            const bool in = m < N;
-            xy[j] = in ? (m % L) | ((m / L) << 16) : -1;
-            gm[j] = in ? xg[m] : make_float2(0.f, 0.f);
-            sx[j] = sy[j] = sd[j] = 0.f;
-        }
-#pragma unroll 1
-        for (int k = 0; k < nu; ++k) {
-            const int dx = __ldg(p.types + 2 * k), dy = __ldg(p.types + 2 * k + 1);
-            const float Vx = xv[2 * k], Vy = xv[2 * k + 1];
-            const float inv = 1.0f / (float)(__ldg(p.win_t1 + k) - __ldg(p.win_t0 + k));
-            const int W = L - abs(dx), qb = __ldg(p.type_ptr + k) - max(0, -dy) * W - max(0, -dx);
-            const int off = dy * L + dx;
-            float tx = 0.f, ty = 0.f, td = 0.f;
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                const int m = threadIdx.x + (J * h + j) * bd;
-                const int x = xy[j] & 0xffff, y = xy[j] >> 16;
-                const bool in = xy[j] >= 0;
-                const bool v1 = in && (unsigned)(x - dx) < (unsigned)L && (unsigned)(y - dy) < (unsigned)L;
-                const bool v2 = in && (unsigned)(x + dx) < (unsigned)L && (unsigned)(y + dy) < (unsigned)L;
-                // m first: pair (m, j = m - d_k); m second: pair (i = m + d_k, m)
-                const float2 gj = xg[v1 ? m - off : 0], gi = xg[v2 ? m + off : 0];
-                const float2 o1 = rel_obs<VF>(p, c, v1 ? qb + (y - dy) * W + (x - dx) : 0, inv);
-                const float2 o2 = rel_obs<VF>(p, c, v2 ? qb + y * W + x : 0, inv);
-                {
-                    const float ex = gm[j].x * gj.x + gm[j].y * gj.y, ey = gm[j].y * gj.x - gm[j].x * gj.y;
-                    const float mx = ex * Vx - ey * Vy, my = ex * Vy + ey * Vx;   // model m_p
+    const RelOrder ord(p);
+    for (int t = threadIdx.x; t < N; t += bd) {
+        const int m = ord.antenna(t), x = m % L, y = m / L;
+        const float2 gm = xg[m];
+        float sx = 0.f, sy = 0.f, sd = 0.f;
+        // one copy of the type loop per path (kIn: interior, no tests)
+        auto types_loop = [&](auto kIn) {
+    #pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                if (k >= nu) break;
+                const int4 ra = s_ra[k];
+                const float4 rb = s_rb[k];
+                bool v1 = true, v2 = true;
+                if (!decltype(kIn)::value) {
+                    const int dx = __ldg(p.types + 2 * k), dy = __ldg(p.types + 2 * k + 1);
+                    v1 = (unsigned)(x - dx) < (unsigned)L && (unsigned)(y - dy) < (unsigned)L;
+                    v2 = (unsigned)(x + dx) < (unsigned)L && (unsigned)(y + dy) < (unsigned)L;
+                }
+                const int i2 = ra.z + y * ra.w + x;
+                const float2 gj = xg[v1 ? m - ra.x : 0], gi = xg[v2 ? m + ra.x : 0];
+                const float2 o1 = rel_obs<VF>(vc, v1 ? i2 - ra.y : 0, rb.x);
+                const float2 o2 = rel_obs<VF>(vc, v2 ? i2 : 0, rb.x);
+                {   // m first: pair (m, j = m - d_k)
+                    const float ex = gm.x * gj.x + gm.y * gj.y, ey = gm.y * gj.x - gm.x * gj.y;   // g_m conj(g_j)
+                    const float mx = ex * rb.y - ey * rb.z, my = ex * rb.z + ey * rb.y;         // model m_p
                     const float rx = o1.x - mx, ry = o1.y - my;
                     const float Wp = v1 ? mx * mx + my * my : 0.f;
                     const float hx = v1 ? mx * rx + my * ry : 0.f, hy = v1 ? mx * ry - my * rx : 0.f;   // conj(m) r
                     chi = v1 ? fmaf(rx, rx, fmaf(ry, ry, chi)) : chi;
-                    sd[j] += Wp;
-                    td += Wp;
-                    sx[j] += hx;
-                    sy[j] += hy;
-                    tx += hx;
-                    ty += hy;
+                    sd += Wp;
+                    tvd[k] += Wp;
+                    sx += hx;
+                    sy += hy;
+                    tvx[k] += hx;
+                    tvy[k] += hy;
                 }
-                {
-                    const float ex = gi.x * gm[j].x + gi.y * gm[j].y, ey = gi.y * gm[j].x - gi.x * gm[j].y;
-                    const float mx = ex * Vx - ey * Vy, my = ex * Vy + ey * Vx;
+                {   // m second: pair (i = m + d_k, m)
+                    const float ex = gi.x * gm.x + gi.y * gm.y, ey = gi.y * gm.x - gi.x * gm.y;   // g_i conj(g_m)
+                    const float mx = ex * rb.y - ey * rb.z, my = ex * rb.z + ey * rb.y;
                     const float rx = o2.x - mx, ry = o2.y - my;
-                    sd[j] += v2 ? mx * mx + my * my : 0.f;
-                    sx[j] += v2 ? mx * rx + my * ry : 0.f;   // m conj(r)
-                    sy[j] += v2 ? my * rx - mx * ry : 0.f;
+                    sd += v2 ? mx * mx + my * my : 0.f;
+                    sx += v2 ? mx * rx + my * ry : 0.f;   // m conj(r)
+                    sy += v2 ? my * rx - mx * ry : 0.f;
                 }
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                tx += __shfl_xor_sync(0xffffffffu, tx, o);
-                ty += __shfl_xor_sync(0xffffffffu, ty, o);
-                td += __shfl_xor_sync(0xffffffffu, td, o);
-            }
-            if (lane == 0) {
-                float *a0 = &s_tsum[(wp * 3 + 0) * KT + k], *a1 = &s_tsum[(wp * 3 + 1) * KT + k],
-                      *a2 = &s_tsum[(wp * 3 + 2) * KT + k];
-                *a0 = h ? *a0 + tx : tx;
-                *a1 = h ? *a1 + ty : ty;
-                *a2 = h ? *a2 + td : td;
-            }
-        }
+        };
+        if (t < ord.n_in) types_loop(std::true_type());
+        else types_loop(std::false_type());
+        const float Gm = gm.x * gm.x + gm.y * gm.y;
+        w.acc[2 * m] = sx;
+        w.acc[2 * m + 1] = sy;
+        w.G[m] = Gm;
+        w.D[m] = sd;
+        dm = fmaxf(dm, Gm > 0.f ? sd / Gm : 0.f);
+    }
+    // per-type rows: warp trees, then one thread per type sums over the warps
 #pragma unroll
-        for (int j = 0; j < J; ++j) {
-            const int m = threadIdx.x + (J * h + j) * bd;
-            if (m >= N) continue;
-            const float Gm = gm[j].x * gm[j].x + gm[j].y * gm[j].y;
-            w.acc[2 * m] = sx[j];
-            w.acc[2 * m + 1] = sy[j];
-            w.G[m] = Gm;
-            w.D[m] = sd[j];
-            dm = fmaxf(dm, Gm > 0.f ? sd[j] / Gm : 0.f);
+    for (int k = 0; k < KT; ++k) {
+        if (k >= nu) break;
+        for (int o = 16; o > 0; o >>= 1) {
+            tvx[k] += __shfl_xor_sync(0xffffffffu, tvx[k], o);
+            tvy[k] += __shfl_xor_sync(0xffffffffu, tvy[k], o);
+            tvd[k] += __shfl_xor_sync(0xffffffffu, tvd[k], o);
+        }
+        if (lane == 0) {
+            s_tsum[(wp * 3 + 0) * KT + k] = tvx[k];
+            s_tsum[(wp * 3 + 1) * KT + k] = tvy[k];
+            s_tsum[(wp * 3 + 2) * KT + k] = tvd[k];
         }
     }
     __syncthreads();
@@ -1351,10 +1390,9 @@ __device__ double rel_resid_pass_t(const CalParams &p, int c, const CgWork &w, b
     return rel_resid_finish(p, w, xv, red, dmax, chi, dm);
 }
 
-constexpr int kResidBlock = 8;   // antennas per register block (no spills at 128 registers)
 __device__ double rel_resid_pass(const CalParams &p, int c, const CgWork &w, bool staged, double *red, float *dmax) {
-    return p.vfmt == GC_C64 ? rel_resid_pass_t<GC_C64, kResidBlock>(p, c, w, staged, red, dmax)
-                            : rel_resid_pass_t<GC_I4C, kResidBlock>(p, c, w, staged, red, dmax);
+    return p.vfmt == GC_C64 ? rel_resid_pass_t<GC_C64>(p, c, w, staged, red, dmax)
+                            : rel_resid_pass_t<GC_I4C>(p, c, w, staged, red, dmax);
 }
 
 
@@ -1384,25 +1422,13 @@ __device__ float rel_op_pass(const CalParams &p, const CgWork &w, float mu) {
     // order) have both pairs of every type on the grid and take the path
     // without tests; the rest of the grid (the border ring, t >= n_in)
     // tests each pair.
-    const int h = p.st_halo, Wi = L > 2 * h ? L - 2 * h : 0, n_in = Wi * Wi;
+    const RelOrder ord(p);
     for (int t = threadIdx.x; t < N; t += blockDim.x) {
-        int m = t;   // no interior (L <= 2 st_halo): every antenna in grid order
-        if (t < n_in) {
-            const int yy = t / Wi;
-            m = (yy + h) * L + (t - yy * Wi) + h;
-        } else if (n_in > 0) {   // the ring: h top rows, h bottom rows, then 2h columns of each middle row
-            const int u = t - n_in, hl = h * L;
-            if (u < 2 * hl) {
-                m = u < hl ? u : (L - h) * L + (u - hl);
-            } else {
-                const int v = u - 2 * hl, row = h + v / (2 * h), ci = v - (row - h) * 2 * h;
-                m = row * L + (ci < h ? ci : L - 2 * h + ci);
-            }
-        }
+        const int m = ord.antenna(t);
         const float2 qm = q[m];
         const float Gm = G[m];
         float sx = 0.f, sy = 0.f;
-        if (t < n_in) {
+        if (t < ord.n_in) {
 #pragma unroll
             for (int k = 0; k < KT; ++k) {
                 if (k >= nu) break;
@@ -2089,31 +2115,51 @@ __device__ void cg_solve_channel_rel(const CalParams &p, int c, CgWork &w, doubl
     // another pass; the prolongation z = z_j + R y rides on the q update.
     // (called by every lane of a warp, e >= ne with r = 0: the restriction
     // sums each run of equal coarse index across the warp -- consecutive
-    // antennas share a patch -- and the run's first lane adds it once)
+    // antennas share a patch -- and the run's first lane adds it once; when
+    // B divides both L and 32 every patch row is an aligned run of B lanes)
+    const bool aligned_runs = coarse && w.B > 0 && L % w.B == 0 && 32 % w.B == 0;
     auto jacobi = [&](int e, float2 r, float mu, float &rzj, float &rr) {
         int ci = -1;
         if (e < ne) {
-            const float iv = 1.f / (w.D[e] + mu * w.G[e]);
+            // the preconditioner's diagonal and the norm's weights by the
+            // fast reciprocal (within 2 ulp; a preconditioner only has to be
+            // the same operator at every step, which this is)
+            const float iv = __fdividef(1.f, w.D[e] + mu * w.G[e]);
             const float2 z = make_float2(r.x * iv, r.y * iv);
             zs[e] = z;
             rzj = fmaf(r.x, z.x, fmaf(r.y, z.y, rzj));
-            rr += (r.x * r.x + r.y * r.y) / w.G[e];
+            rr += __fdividef(r.x * r.x + r.y * r.y, w.G[e]);
             const unsigned cu = w.cid[e];
             ci = cu == 0xffffu ? -1 : (int)cu;
         }
         if (!coarse) return;
         const int lane = threadIdx.x & 31;
+        float qx = r.x, qy = r.y;
+        if (aligned_runs && e - lane + 32 <= N) {
+            // a warp of antennas whose patch rows are aligned runs of B
+            // lanes: a butterfly within each run, its first lane adds it
+            for (int o = 1; o < w.B; o <<= 1) {
+                qx += __shfl_xor_sync(0xffffffffu, qx, o);
+                qy += __shfl_xor_sync(0xffffffffu, qy, o);
+            }
+            if ((lane & (w.B - 1)) == 0 && ci >= 0) {
+                atomicAdd(&w.rc[ci], qx);
+                atomicAdd(&w.rc[nc + ci], qy);
+            }
+            return;
+        }
         const int kprev = __shfl_up_sync(0xffffffffu, ci, 1);
         const bool head = lane == 0 || kprev != ci;
-        const int run = __popc(__ballot_sync(0xffffffffu, head) & (0xffffffffu >> (31 - lane)));
-        float qx = r.x, qy = r.y;
-        for (int o = 1; o < 32; o <<= 1) {
-            const float tx = __shfl_down_sync(0xffffffffu, qx, o);
-            const float ty = __shfl_down_sync(0xffffffffu, qy, o);
-            const int tr = __shfl_down_sync(0xffffffffu, run, o);
-            if (lane + o < 32 && tr == run) {
-                qx += tx;
-                qy += ty;
+        {
+            const int run = __popc(__ballot_sync(0xffffffffu, head) & (0xffffffffu >> (31 - lane)));
+            for (int o = 1; o < 32; o <<= 1) {
+                const float tx = __shfl_down_sync(0xffffffffu, qx, o);
+                const float ty = __shfl_down_sync(0xffffffffu, qy, o);
+                const int tr = __shfl_down_sync(0xffffffffu, run, o);
+                if (lane + o < 32 && tr == run) {
+                    qx += tx;
+                    qy += ty;
+                }
             }
         }
         if (head && ci >= 0) {
