@@ -1316,7 +1316,7 @@ __device__ double rel_resid_pass_t(const CalParams &p, int c, const CgWork &w, b
         float sx = 0.f, sy = 0.f, sd = 0.f;
         // one copy of the type loop per path (kIn: interior, no tests)
         auto types_loop = [&](auto kIn) {
-    #pragma unroll
+#pragma unroll
             for (int k = 0; k < KT; ++k) {
                 if (k >= nu) break;
                 const int4 ra = s_ra[k];
