@@ -1992,9 +1992,9 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
         // eta = min(0.05, (|grad| / |grad_0|)^(1/4)) (floor cg_tol).  Gauss-
         // Newton on a problem with noise in the data converges linearly, so
         // tighter solves buy little: on the 4096-antenna workload this
-        // forcing takes 73 CG steps a channel over 10 Gauss-Newton
+        // forcing takes 76 CG steps a channel over 9.0 Gauss-Newton
         // iterations where (|grad| / |grad_0|)^(1/2) capped at 0.1 took 159
-        // over 9, for the same solution to within FP32 rounding.
+        // over 9.3, for the same solution to within FP32 rounding.
         if (it == 1) grad0 = bnorm2;
         const float eta =
             (float)fmin(0.05, fmax(cg_tol, sqrt(sqrt(sqrt((double)bnorm2 / fmax(grad0, 1e-300))))));
@@ -2311,9 +2311,9 @@ __device__ void cg_solve_channel_rel(const CalParams &p, int c, CgWork &w, doubl
         // eta = min(0.05, (|grad| / |grad_0|)^(1/4)) (floor cg_tol).  Gauss-
         // Newton on a problem with noise in the data converges linearly, so
         // tighter solves buy little: on the 4096-antenna workload this
-        // forcing takes 73 CG steps a channel over 10 Gauss-Newton
+        // forcing takes 76 CG steps a channel over 9.0 Gauss-Newton
         // iterations where (|grad| / |grad_0|)^(1/2) capped at 0.1 took 159
-        // over 9, for the same solution to within FP32 rounding.
+        // over 9.3, for the same solution to within FP32 rounding.
         if (it == 1) grad0 = bnorm2;
         const float eta =
             (float)fmin(0.05, fmax(cg_tol, sqrt(sqrt(sqrt((double)bnorm2 / fmax(grad0, 1e-300))))));
