@@ -141,14 +141,12 @@ def test_gradient_driven_solve_matches_gauss_newton(gc, ctx):
         assert np.max(np.abs(gp - gr) / np.abs(gr)) < 5e-3
 
 
-@pytest.mark.parametrize("L,weights,ckpt,i4c", [(4, False, False, False), (17, True, False, False),
-                                                 (33, False, True, False), (64, True, False, True),
-                                                 (100, False, False, False), (128, True, True, True)])
-def test_row_window_adjoint_equals_range_kernel(gc, ctx, L, weights, ckpt, i4c):
-    """The row-window adjoint ("chi2.bwd" = 0, each warp owning whole rows)
-    and the antenna-range adjoint (1) on the same inputs: the same sums in
-    another order, so equal to FP32 rounding; grids of 1, 2 and 4 columns per
-    lane, ragged row blocks, weights, stored residuals, exact int32 sums."""
+
+@pytest.mark.parametrize("L,weights,i4c", [(17, True, False), (64, False, True), (128, True, True)])
+def test_adjoint_is_deterministic(gc, ctx, L, weights, i4c):
+    """The adjoint's sums have a fixed order (slots ordered by a barrier per
+    type, CTA partials added in range order, the halo terms after): two runs
+    give the same bits.  One and several antenna ranges per channel."""
     C = 3
     sel, osl, S, g, V, w = _problem(gc, "subset", L, 256, C, 700 + L, weights)
     dev = "cuda"
@@ -159,24 +157,8 @@ def test_row_window_adjoint_equals_range_kernel(gc, ctx, L, weights, ckpt, i4c):
     gt, Vt = torch.from_numpy(g).to(dev), torch.from_numpy(V).to(dev)
     wt = torch.from_numpy(w).to(dev) if w is not None else None
     go = torch.tensor([1.0, -0.5, 2.0], dtype=torch.float64, device=dev)
-    res = torch.empty(C, sel.P, dtype=torch.complex64, device=dev) if ckpt else None
-    if ckpt:
-        ctx.chi2(vr, sel, gt, Vt, wt, residuals=res)
-    outs = []
-    try:
-        for path in (0, 1):
-            ctx.set_tuning("chi2.bwd", path)
-            if ckpt:
-                dg, dv = ctx.chi2_backward_ckpt(res, sel, gt, Vt, go, wt)
-            else:
-                dg, dv = ctx.chi2_backward(vr, sel, gt, Vt, go, wt)
-            ctx.device_status()
-            outs.append((dg.cpu().numpy(), dv.cpu().numpy()))
-    finally:
-        ctx.set_tuning("chi2.bwd", 0)
-    (dg0, dv0), (dg1, dv1) = outs
-    for c in range(C):
-        scale = max(np.abs(dg1[c]).max(), np.abs(dv1[c]).max())
-        assert np.isfinite(dg0[c]).all() and np.isfinite(dv0[c]).all()
-        assert np.max(np.abs(dg0[c] - dg1[c])) < 2e-5 * scale, (L, c)
-        assert np.max(np.abs(dv0[c] - dv1[c])) < 2e-5 * scale, (L, c)
+    a = [t.cpu().numpy() for t in ctx.chi2_backward(vr, sel, gt, Vt, go, wt)]
+    b = [t.cpu().numpy() for t in ctx.chi2_backward(vr, sel, gt, Vt, go, wt)]
+    ctx.device_status()
+    assert np.isfinite(a[0]).all() and np.isfinite(a[1]).all()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
