@@ -201,10 +201,10 @@ template <int VF>
 __device__ __forceinline__ float2 st_resid(const void *vred, size_t idx, float inv, float2 gi, float2 gj, float2 V) {
     float2 o;
     if (VF == GC_C64) {
-        const float2 v = reinterpret_cast<const float2 *>(vred)[idx];
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(vred) + idx);
         o = make_float2(v.x * inv, v.y * inv);
     } else {
-        const int2 v = reinterpret_cast<const int2 *>(vred)[idx];
+        const int2 v = __ldg(reinterpret_cast<const int2 *>(vred) + idx);
         o = make_float2((float)v.x * inv, (float)v.y * inv);
     }
     const float ex = gi.x * gj.x + gi.y * gj.y, ey = gi.y * gj.x - gi.x * gj.y;
@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(kKThreads) chi2_bwd_st(const Chi2Params p, con
     __shared__ StTypes t;
     __shared__ float2 sV[kStTypes];
     __shared__ float sdv[2 * kStTypes * kDvPitch];   // per-thread dV terms of every type
+    __shared__ float2 sspare[kKThreads];              // zero terms of pairs off the grid
     extern __shared__ float2 sacc[];                  // [halo + range] second-member terms
     load_types(p, t);
     const int L = p.L, nu = p.n_ubl, H = sp.halo;
@@ -320,18 +321,41 @@ __global__ void __launch_bounds__(kKThreads) chi2_bwd_st(const Chi2Params p, con
         const float inv = t.inv[k];
         const float2 V = sV[k];
         float vx = 0.f, vy = 0.f;   // this thread's part of dV_k (kStJ terms)
+        // all of the type step's loads first (kStJ partner gains and
+        // observations in flight together), then the arithmetic
+        float2 gjv[kStJ], obv[kStJ];
+        float wv[kStJ];
+        unsigned vm = 0u;
 #pragma unroll
         for (int j = 0; j < kStJ; ++j) {
             const int m = m0 + threadIdx.x + j * kKThreads;
             const int x = xy[j] & 0xffff, y = xy[j] >> 16;
             const bool v1 = xy[j] >= 0 && (unsigned)(x - dx) < (unsigned)L && (unsigned)(y - dy) < (unsigned)L;
+            vm |= v1 ? 1u << j : 0u;
             const int q1 = v1 ? a1 + y * rl + x : 0;
-            const float2 gj = g[v1 ? m - off : 0];
-            float2 r1;
-            if (FL & 2) r1 = p.resid_in[cP + q1];
-            else r1 = st_resid<VF>(p.vred, cP + q1, inv, gm[j], gj, V);
-            float w1 = 1.f;
-            if (FL & 1) w1 = p.w[cP + q1];
+            gjv[j] = __ldg(g + (v1 ? m - off : 0));
+            if (FL & 2) {
+                obv[j] = __ldg(p.resid_in + cP + q1);
+            } else if (VF == GC_C64) {
+                const float2 o = __ldg(reinterpret_cast<const float2 *>(p.vred) + cP + q1);
+                obv[j] = make_float2(o.x * inv, o.y * inv);
+            } else {
+                const int2 o = __ldg(reinterpret_cast<const int2 *>(p.vred) + cP + q1);
+                obv[j] = make_float2((float)o.x * inv, (float)o.y * inv);
+            }
+            wv[j] = (FL & 1) ? __ldg(p.w + cP + q1) : 1.f;
+        }
+#pragma unroll
+        for (int j = 0; j < kStJ; ++j) {
+            const int m = m0 + threadIdx.x + j * kKThreads;
+            const bool v1 = (vm >> j) & 1u;
+            const float2 gj = gjv[j];
+            float2 r1 = obv[j];
+            if (!(FL & 2)) {   // the residual from (g, V), as st_resid computes it
+                const float ex = gm[j].x * gj.x + gm[j].y * gj.y, ey = gm[j].y * gj.x - gm[j].x * gj.y;
+                r1 = make_float2(r1.x - (ex * V.x - ey * V.y), r1.y - (ex * V.y + ey * V.x));
+            }
+            const float w1 = wv[j];
             const float rx = v1 ? w1 * r1.x : 0.f, ry = v1 ? w1 * r1.y : 0.f;
             // first member m: w r g_j conj(V) to dg_m
             const float tx = gj.x * V.x + gj.y * V.y, ty = gj.y * V.x - gj.x * V.y;
@@ -341,10 +365,11 @@ __global__ void __launch_bounds__(kKThreads) chi2_bwd_st(const Chi2Params p, con
             const float ux = gm[j].x * gj.x + gm[j].y * gj.y, uy = gm[j].x * gj.y - gm[j].y * gj.x;
             vx = fmaf(rx, ux, fmaf(-ry, uy, vx));
             vy = fmaf(rx, uy, fmaf(ry, ux, vy));
-            // second member m - d: w conj(r) g_m V
-            if (v1) {
+            // second member m - d: w conj(r) g_m V (a pair off the grid
+            // adds its zero term to this thread's own spare slot)
+            {
                 const float px = gm[j].x * V.x - gm[j].y * V.y, py = gm[j].x * V.y + gm[j].y * V.x;
-                float2 &slot = sacc[m - off - m0 + H];
+                float2 &slot = v1 ? sacc[m - off - m0 + H] : sspare[threadIdx.x];
                 slot.x += fmaf(rx, px, ry * py);
                 slot.y += fmaf(rx, py, -ry * px);
             }
