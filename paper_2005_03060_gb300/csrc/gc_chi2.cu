@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kKThreads) chi2_fwd_st(const Chi2Params p, con
 // slots below the range (antennas of the previous range, at most `halo`
 // of them) go to the workspace and chi2_st_halo adds them afterwards.
 template <int VF, int FL>
-__global__ void __launch_bounds__(kKThreads) chi2_bwd_st(const Chi2Params p, const StSplit sp) {
+__global__ void __launch_bounds__(kKThreads, (FL & 2) ? 3 : 2) chi2_bwd_st(const Chi2Params p, const StSplit sp) {
     __shared__ StTypes t;
     __shared__ float2 sV[kStTypes];
     __shared__ float sdv[2 * kStTypes * kDvPitch];   // per-thread dV terms of every type
