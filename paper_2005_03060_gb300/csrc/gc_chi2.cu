@@ -389,11 +389,13 @@ __global__ void __launch_bounds__(kKThreads, (FL & 2) ? 3 : 2) chi2_bwd_st(const
     }
     for (int i = threadIdx.x; i < H; i += kKThreads) sp.hbuf[(size_t)blockIdx.x * H + i] = sacc[i];
     // dV partials of the CTA: 8 threads per (type, component), each adding
-    // 32 threads' terms in FP64, then the 8 in a fixed shuffle order
+    // 32 threads' terms, then the 8 in FP64 in a fixed shuffle order
     const int combo = threadIdx.x >> 3, sub = threadIdx.x & 7;
-    double dsum = 0.0;
+    float fsum = 0.f;   // 32 threads' terms in FP32, the 8 partial sums in FP64
     if (combo < 2 * nu)
-        for (int u = 0; u < kKThreads / 8; ++u) dsum += (double)sdv[combo * kDvPitch + u * 8 + sub];
+#pragma unroll 8
+        for (int u = 0; u < kKThreads / 8; ++u) fsum += sdv[combo * kDvPitch + u * 8 + sub];
+    double dsum = (double)fsum;
     dsum += __shfl_xor_sync(0xffffffffu, dsum, 1);
     dsum += __shfl_xor_sync(0xffffffffu, dsum, 2);
     dsum += __shfl_xor_sync(0xffffffffu, dsum, 4);
