@@ -519,8 +519,9 @@ def rooflines(w: Workload, kern: dict, st_last, peaks: dict, probes: dict):
                            "unit": "TFLOP/s", "frac": flops / dur / 1e12 / probes["fp32"], "traffic": None,
                            "algorithmic_flops": flops, "cg_iterations": cg_it, "gn_iterations": gn_it,
                            "chans_per_s": C / dur,
-                           "note": ("one 256-thread CTA per channel, two per SM; each pair is evaluated by "
-                                    "both of its antennas (no atomics); bound by block barriers and latency"),
+                           "note": ("one 256-thread CTA per channel, two per SM, channels taken from a device "
+                                    "counter; each pair is evaluated by both of its antennas (no atomics); "
+                                    "bound by latency (L2-resident CG vectors) and block barriers"),
                            "peak_source": "measured: gc_peak_probe FP32 FMA on this GPU"}
     return rl
 
