@@ -857,7 +857,7 @@ __global__ void __launch_bounds__(kCThreads) lincal_kernel(const CalParams p) {
 // ----------------------------------------------------------------- lincal, matrix-free (mixed precision)
 // Gauss-Newton with the step from preconditioned conjugate gradients on
 // (J^T J + mu I) delta = J^T r, never forming J^T J.  Two operator forms: the
-// gather over the grid in relative coordinates (rel_op_pass_to and
+// gather over the grid in relative coordinates (rel_op_pass and
 // cg_solve_channel_rel, for selections of <= kStencilTypes types) and the
 // pair-list scatter below (cg_pass and cg_solve_channel, any selection).
 // The scatter form is one pass over the pairs: each pair evaluates its entry of J v,
@@ -1556,8 +1556,10 @@ __device__ float rel_chi2(const CalParams &p, int c, const float *tg, const floa
 // so the coarse normal matrix splits into a real "amplitude" system
 // (Re c: c_Pi + c_Pj + c_k) and a real "phase" system (Im c: c_Pi - c_Pj + c_k),
 // each with entries sum |m_p|^2 -- the patch-level form of Eq. logcal.  The
-// coarse operators are inverted in FP64 once per Gauss-Newton iteration and
-// applied in FP32: M^-1 = D^-1 + R A_c^-1 R^T.
+// coarse operators are inverted (Gauss-Jordan in FP32, with a diagonal shift
+// of 1e-5 of the largest diagonal entry) at the first Gauss-Newton iteration
+// -- the first two for the pair-list form -- and reused after it; applied in
+// FP32: M^-1 = D^-1 + R A_c^-1 R^T.
 __device__ __forceinline__ int patch_of(const CgWork &w, int i, int L) {
     return ((i / L) / w.B) * w.npx + (i % L) / w.B;
 }
@@ -1656,7 +1658,7 @@ __device__ void coarse_assemble_scatter(const CalParams &p, const CgWork &w, flo
 
 // Gather assembly: one warp per patch a walks the patch's antennas and, for
 // every type, the antenna's pair as first and as second member (the same
-// grid arithmetic as rel_op_pass_to, weights from G), summing row a of both coarse
+// grid arithmetic as rel_op_pass, weights from G), summing row a of both coarse
 // operators in registers: the patch itself, its eight neighbour patches
 // (pairs never reach further when every type offset is within one patch
 // side) and the model-visibility columns.  A pair inside the patch is met
@@ -1848,7 +1850,8 @@ __device__ void coarse_invert(float *A, int nc, int ncp, bool amp, bool cv, floa
     __syncthreads();
 }
 
-// Build and invert the coarse operators (Gauss-Newton iterations 1 and 2).
+// Build and invert the coarse operators (the first Gauss-Newton iteration of the
+// relative-coordinate solver, the first two of the pair-list solver).
 __device__ void cg_coarse_setup(const CalParams &p, const CgWork &w, float mu) {
     __shared__ float s_buf[32];
     if (p.stencil && w.coarse_gather) coarse_assemble_gather(p, w, mu);
@@ -2075,7 +2078,7 @@ __device__ void cg_solve_channel(const CalParams &p, int c, CgWork &w, double cg
 }
 
 // One channel of matrix-free Gauss-Newton in relative coordinates (the
-// stencil operator; see rel_op_pass_to).  Same outer iteration, forcing terms,
+// stencil operator; see rel_op_pass).  Same outer iteration, forcing terms,
 // preconditioner, projection, line search and stopping rule as
 // cg_solve_channel; the CG vectors hold (q, w) and the search direction q
 // lives in shared memory beside G, D and the coarse indices.  Convergence
