@@ -284,10 +284,12 @@ GC_API gc_status gc_quantize(gc_ctx *ctx, const float *volt, int C, int T, int N
  *              J^T J, preconditioned by Jacobi plus a patch-level coarse
  *              space, matrix-free (per-antenna gather over the grid, or a
  *              scatter over the pair list: "cal.operator"), FP32 products
- *              with FP64 reductions; inexact-Newton CG tolerance from 0.1 down
- *              to 1e-4 relative residual as the gradient falls, at most 500
- *              CG iterations per step; any selection, and the only solver
- *              for partly occupied lattices.
+ *              with FP64 reductions; inexact-Newton CG tolerance
+ *              min(0.05, (|grad| / |grad_0|)^(1/4)) relative residual (at
+ *              least 1e-4), at most 500 CG iterations per step; channels are
+ *              taken from a device counter (the call enqueues a memset before
+ *              the kernel); any selection, and the only solver for partly
+ *              occupied lattices.
  * Start point (unless warm_start): spanning-tree phases over the (1,0) and
  * (0,1) types, unit amplitudes, group-mean model visibilities.  Warm start
  * reads gains and vmodel as given.
